@@ -1,0 +1,204 @@
+/*
+ * kpsvd.h - C ABI of the GB300 (sm_103a) library for Kronecker-product SVD
+ * preconditioned Tikhonov deblurring.
+ *
+ * Problem (arXiv 2311.15393, Section 1 eqs. invp, lsp:Tik, tik:normal1):
+ * given blurred, noisy data b = A x_true + eps of an n_r x n_c image, the PSF
+ * that defines A, and a regularisation parameter lambda, solve the Tikhonov
+ * normal equations (A^T A + lambda^2 I) x = A^T b by preconditioned CG or
+ * flexible PCG (Section 2.3; Section 3 last paragraph), with the
+ * preconditioner M = V (Sigma^T Sigma + lambda^2 I) V^T of the Kronecker
+ * product SVD of the blur (eqs. AKronSVD, PreconSystem, PreconSolve), and
+ * choose lambda in closed form over the KP spectrum (Section 2.2).
+ *
+ * Conventions shared by every entry point
+ *  - Images are column-major n_r x n_c arrays (vec = column stacking,
+ *    Section 3): element (i, j) at offset i + n_r * j.
+ *  - Pointers documented "device" are device memory of the context's GPU,
+ *    at least 16-byte aligned, owned by the caller, and must stay valid until
+ *    the call's work on the context's stream has finished.  Pointers
+ *    documented "host" are ordinary host memory.
+ *  - The element type of image arguments is the context's vector precision
+ *    (KP_F64 -> double, KP_F32 -> float) set by kp_setup.
+ *  - All work is issued on the stream given to kp_create.  Calls that return
+ *    scalars to the host (choose_lambda, tik_pcg info, kp_forward noise norm,
+ *    getters) synchronise that stream before returning; kp_apply_* are
+ *    asynchronous.
+ *  - No call aborts or throws.  Each returns a kp_status; on failure a
+ *    message is kept per thread and read with kp_last_error().  A CUDA error
+ *    leaves the context usable only if the error is not sticky.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef KPSVD_H
+#define KPSVD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kp_ctx kp_ctx; /* opaque; owns all factor and workspace device memory */
+
+typedef enum {
+  KP_OK = 0,
+  KP_EINVAL = 1,      /* bad argument (shape, pointer, enum, combination) */
+  KP_ENOMEM = 2,      /* device or host allocation failed */
+  KP_ECUDA = 3,       /* CUDA runtime / driver error */
+  KP_ENOTSUP = 4,     /* valid but unsupported combination or device */
+  KP_ENOCONV = 5,     /* maxit reached before tol; x holds the last iterate */
+  KP_EBREAKDOWN = 6,  /* p^T K p <= 0 or z^T r <= 0 in (F)PCG */
+  KP_ENUMERIC = 7,    /* NaN / Inf met in a reduction */
+  KP_ENOROOT = 8,     /* discrepancy equation has no root */
+  KP_ETIMEOUT = 9,    /* a bounded device-side wait gave up */
+  KP_ESTATE = 10      /* call out of order (e.g. solve before kp_setup) */
+} kp_status;
+
+typedef enum { KP_BC_ZERO = 0, KP_BC_REFLEXIVE = 1 } kp_bc;
+
+/* Arithmetic of a part of the path.
+ *   KP_F64   FP64 SIMT kernels
+ *   KP_F32   FP32 SIMT kernels
+ *   KP_BF16  tcgen05 BF16 x BF16 -> FP32 (operator: one product per GEMM,
+ *            with reliable residual updates through an FP32-accurate
+ *            six-product split; preconditioner: plain BF16)
+ *   KP_BF16X3 tcgen05, operands split into bf16 hi + lo, three products
+ *   KP_F16   tcgen05 FP16 x FP16 -> FP32 (preconditioner)
+ *   KP_E4M3  tcgen05 FP8 E4M3 x E4M3 -> FP32 with power-of-two per-tensor
+ *            scales (preconditioner) */
+typedef enum { KP_F64 = 0, KP_F32 = 1, KP_BF16 = 2, KP_BF16X3 = 3, KP_F16 = 4, KP_E4M3 = 5 } kp_prec;
+
+/* KP spectrum used by the preconditioner and by choose_lambda:
+ *   PRODUCT    Sigma = Sigma_r (x) Sigma_c (eq. AKronSVD)
+ *   PROJECTED  Sigma = diag((U_r (x) U_c)^T A (V_r (x) V_c)), the diagonal of
+ *              the full Kronecker-sum operator in the KP basis (equal to
+ *              PRODUCT when A has one term). */
+typedef enum { KP_SIGMA_PRODUCT = 0, KP_SIGMA_PROJECTED = 1 } kp_sigma;
+
+typedef enum {
+  KP_LAMBDA_GCV = 0,          /* eq. GCVTikSVD */
+  KP_LAMBDA_WGCV = 1,         /* eq. wGCVTikSVD, param = omega */
+  KP_LAMBDA_DISCREPANCY = 2,  /* eq. DSCTikSVD, param = eps = eta ||e||_2 (absolute) */
+  KP_LAMBDA_OPT = 3           /* eq. OptTikSVD, needs x_true */
+} kp_lambda_method;
+
+typedef struct {
+  int iters;             /* (F)PCG iterations done (one K application each) */
+  int replacements;      /* reliable residual updates done */
+  double rel_res;        /* ||r|| / ||A^T b|| of the residual the solver ended with */
+  kp_status status;      /* same as the return value of tik_pcg */
+  double ms_solve;       /* device time of the solve (CUDA events) */
+  double* res_hist;      /* optional caller-owned host buffer of res_hist_len doubles: */
+  int res_hist_len;      /*   ||r_k|| / ||A^T b|| for k = 0 .. min(iters, len - 1) */
+} kp_solve_info;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream). */
+kp_status kp_create(kp_ctx** out, int device, void* cuda_stream);
+
+/* Release every device allocation of the context.  NULL is allowed. */
+void kp_destroy(kp_ctx* ctx);
+
+/* Build the operator and the preconditioner from the PSF (Sections 3 and 5).
+ *   psf      device, double, column-major n_r x n_c, PSF with 0-based
+ *            centre (center_r, center_c) (the entry weighting the pixel itself)
+ *   bc       boundary condition of the blur
+ *   op_rank  number of Kronecker terms of A (eq. KronSumDecomp), from the
+ *            SVD of the weighted PSF D_c P D_r (Frobenius-optimal first term);
+ *            0 = full rank min(n_r, n_c)
+ *   op_prec  KP_F64 | KP_F32 | KP_BF16 | KP_BF16X3
+ *   pc_prec  KP_F64 | KP_F32 | KP_BF16 | KP_F16 | KP_E4M3 (rank-1 KP-SVD preconditioner)
+ *   vec_prec KP_F64 | KP_F32: element type of images and of the PCG vectors
+ *   sigma    KP spectrum definition
+ * Supported combinations: (F64, F64, F64); (F32, F32|BF16|F16|E4M3, F32);
+ * (BF16|BF16X3, F32|BF16|F16|E4M3, F32).  Tensor-core precisions need
+ * n_r and n_c multiples of 16.  Factor SVDs (one-sided Jacobi), Sigma and the
+ * spectral quantities are computed in FP64 on the device.  May be called
+ * again on the same context to replace the problem.  Synchronises. */
+kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, int center_r, int center_c,
+                   kp_bc bc, int op_rank, kp_prec op_prec, kp_prec pc_prec, kp_prec vec_prec,
+                   kp_sigma sigma);
+
+/* Observed data (eq. invp, Section 5 noise level): b = A x + e with
+ * e = noise_level * ||A x||_2 * g / ||g||_2, A applied in FP64-accurate
+ * arithmetic of the context's vector type.
+ *   x, g    device, vec type, n_r x n_c (g: caller's noise direction)
+ *   b       device, vec type, n_r x n_c, written
+ *   noise_norm  host, nullable: ||e||_2 */
+kp_status kp_forward(kp_ctx* ctx, const void* x, const void* g, double noise_level, void* b,
+                     double* noise_norm);
+
+/* Solve (A^T A + lambda^2 I) x = A^T b by PCG (flexible = 0, Fletcher-Reeves
+ * beta) or flexible PCG (flexible = 1, Polak-Ribiere beta), preconditioned by
+ * the KP-SVD with the same lambda.  Stops when ||r|| <= tol ||A^T b|| or after
+ * maxit iterations (returns KP_ENOCONV, x = last iterate).
+ *   b        device, vec type, n_r x n_c
+ *   x        device, vec type, n_r x n_c; input when warm_start != 0, output
+ *   info     host, nullable
+ * With a reduced-precision operator the residual is replaced by the true
+ * residual A^T (b - A x) - lambda^2 x, computed with an FP32-accurate
+ * operator, whenever ||r|| has fallen by the reliable-update factor since the
+ * last replacement, and always before convergence is declared. */
+kp_status tik_pcg(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible,
+                  void* x, int warm_start, kp_solve_info* info);
+
+/* Choose lambda in closed form over the KP spectrum (Section 2.2):
+ * b_hat = vec(U_c^T B U_r), x_hat = vec(V_c^T X_true V_r) in FP64.
+ * GCV / wGCV / OPT: minimum on lambda in [max(min|Sigma|>0, 1e-10 max|Sigma|),
+ * max|Sigma|] by a 400-point grid in log lambda and a golden-section /
+ * parabolic refinement in the best cell (ties -> larger lambda; for wGCV with
+ * omega > 1 the range starts at the root of trace(I - omega A A^+)).
+ * DISCREPANCY: root of D(lambda) (increasing) by bracketing in log lambda and
+ * safeguarded bisection / secant; KP_ENOROOT when no root exists.
+ *   b        device, vec type
+ *   x_true   device, vec type, only for KP_LAMBDA_OPT (else NULL)
+ *   lambda_out host */
+kp_status choose_lambda(kp_ctx* ctx, const void* b, kp_lambda_method method, double param,
+                        const void* x_true, double* lambda_out);
+
+/* Operator hooks (asynchronous).  y = A x (transpose = 0) or y = A^T x
+ * (transpose = 1) with the context's operator precision; kp_apply_K gives
+ * y = (A^T A + lambda^2 I) x.  x, y: device, vec type, n_r x n_c, distinct. */
+kp_status kp_apply_A(kp_ctx* ctx, const void* x, void* y, int transpose);
+kp_status kp_apply_K(kp_ctx* ctx, const void* x, void* y, double lambda);
+
+/* Preconditioner solve z = M^-1 r = V_c (S .* (V_c^T R V_r)) V_r^T with
+ * S = 1 / (Sigma^2 + lambda^2) (eq. PreconSolve), in the context's
+ * preconditioner precision.  r, z: device, vec type, distinct. */
+kp_status kp_apply_Minv(kp_ctx* ctx, const void* r, void* z, double lambda);
+
+/* Getters (synchronise; host buffers).
+ *   kp_get_spectrum  sigma: n_r * n_c doubles, column-major KP spectrum
+ *   kp_get_terms     s: op_rank doubles (weighted PSF singular values),
+ *                    u: n_r * op_rank, v: n_c * op_rank (column m = term m;
+ *                    u_m's largest-magnitude entry is positive); any may be NULL
+ *   kp_get_kpsvd     sr (n_c), Vr (n_c x n_c col-major), sc (n_r), Vc (n_r x n_r),
+ *                    Ur, Uc likewise; any may be NULL; singular values descending
+ *   kp_get_rank      op_rank in use */
+kp_status kp_get_spectrum(kp_ctx* ctx, double* sigma);
+kp_status kp_get_terms(kp_ctx* ctx, double* s, double* u, double* v);
+kp_status kp_get_kpsvd(kp_ctx* ctx, double* sr, double* Ur, double* Vr, double* sc, double* Uc,
+                       double* Vc);
+kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
+
+/* Tuning knobs (name = value); unknown names return KP_EINVAL.
+ *   "reliable_delta"  factor by which ||r|| must fall before a reliable
+ *                     residual update (default 0.1 for BF16 operators, 0 = off
+ *                     for F64 / F32 operators)
+ *   "check_every"     iterations between host convergence checks (default 4)
+ *   "jacobi_tol"      one-sided Jacobi rotation threshold (default 1e-15)
+ *   "jacobi_max_sweeps" (default 40) */
+kp_status kp_set_option(kp_ctx* ctx, const char* name, double value);
+
+/* Number of this library's kernel launches issued on the context since the
+ * last reset (reset = 1 clears it after reading). */
+long long kp_launch_count(kp_ctx* ctx, int reset);
+
+const char* kp_status_str(kp_status s);
+const char* kp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KPSVD_H */

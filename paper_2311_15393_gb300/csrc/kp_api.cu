@@ -1,0 +1,260 @@
+// C ABI entry points: context lifetime, errors, options, getters.
+// The operations themselves are in kp_setup.cu, kp_solver.cu, kp_lambda.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "kp_internal.h"
+
+static thread_local std::string g_last_error;
+
+void kp_set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+extern "C" const char* kp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* kp_status_str(kp_status s) {
+  switch (s) {
+    case KP_OK: return "KP_OK";
+    case KP_EINVAL: return "KP_EINVAL: invalid argument";
+    case KP_ENOMEM: return "KP_ENOMEM: out of memory";
+    case KP_ECUDA: return "KP_ECUDA: CUDA error";
+    case KP_ENOTSUP: return "KP_ENOTSUP: unsupported";
+    case KP_ENOCONV: return "KP_ENOCONV: not converged";
+    case KP_EBREAKDOWN: return "KP_EBREAKDOWN: PCG breakdown";
+    case KP_ENUMERIC: return "KP_ENUMERIC: NaN or Inf";
+    case KP_ENOROOT: return "KP_ENOROOT: no root";
+    case KP_ETIMEOUT: return "KP_ETIMEOUT: device wait timed out";
+    case KP_ESTATE: return "KP_ESTATE: call out of order";
+  }
+  return "unknown status";
+}
+
+kp_status kp_alloc(kp_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    kp_set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return KP_ENOMEM;
+  }
+  ctx->allocs.push_back(*p);
+  return KP_OK;
+}
+
+void tc_plans_free(kp_ctx* ctx);
+
+void ops_state_free(kp_ctx* ctx);
+
+kp_status kp_enter(kp_ctx* ctx) {
+  KP_CUDA(cudaSetDevice(ctx->device));
+  KP_CUDA(cudaEventRecord(ctx->ev_in, ctx->user_stream));
+  KP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+  return KP_OK;
+}
+
+kp_status kp_leave(kp_ctx* ctx) {
+  KP_CUDA(cudaEventRecord(ctx->ev_out, ctx->stream));
+  KP_CUDA(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
+  return KP_OK;
+}
+
+void kp_free_all(kp_ctx* ctx) {
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ops_state_free(ctx);
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  tc_plans_free(ctx);
+  ctx->ready = false;
+}
+
+kp_status read_status(kp_ctx* ctx) {
+  int h = 0;
+  KP_CUDA(cudaMemcpyAsync(&h, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (h & DEV_ERR_TIMEOUT) {
+    kp_set_error("a bounded device-side wait gave up (status word 0x%x)", h);
+    return KP_ETIMEOUT;
+  }
+  if (h & DEV_ERR_BOUNDS) {
+    kp_set_error("device-side bounds check failed (status word 0x%x)", h);
+    return KP_EINVAL;
+  }
+  return KP_OK;
+}
+
+extern "C" kp_status kp_create(kp_ctx** out, int device, void* cuda_stream) {
+  if (!out) {
+    kp_set_error("kp_create: out is NULL");
+    return KP_EINVAL;
+  }
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    kp_set_error("kp_create: no CUDA device (%s)", cudaGetErrorString(e));
+    return KP_ECUDA;
+  }
+  if (device < 0 || device >= ndev) {
+    kp_set_error("kp_create: device %d out of range [0, %d)", device, ndev);
+    return KP_EINVAL;
+  }
+  KP_CUDA(cudaSetDevice(device));
+  kp_ctx* ctx = new kp_ctx();
+  ctx->device = device;
+  ctx->user_stream = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    kp_set_error("kp_create: stream / event creation failed");
+    return KP_ECUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  // context-level buffers (not released by a new kp_setup)
+  void* p = nullptr;
+  const size_t bytes = 4096 + 64 * 1024 * sizeof(double) + 256;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    kp_set_error("kp_create: cudaMalloc failed");
+    return KP_ENOMEM;
+  }
+  cudaMemset(p, 0, bytes);
+  ctx->dev_status = (int*)p;                                   // [0..63] bytes: status word
+  ctx->dflags = (int*)((char*)p + 64);                         // [64..255] bytes: solver flags
+  ctx->red_count = (unsigned int*)((char*)p + 256);            // reduction counter
+  ctx->dscal = (double*)((char*)p + 1024);                     // 384 doubles of scalars
+  ctx->red_part = (double*)((char*)p + 4096);                  // reduction partials
+  ctx->ctx_block = p;
+  *out = ctx;
+  return KP_OK;
+}
+
+extern "C" void kp_destroy(kp_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  kp_free_all(ctx);
+  if (ctx->ctx_block) cudaFree(ctx->ctx_block);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) {
+  if (!ctx || !name) {
+    kp_set_error("kp_set_option: NULL argument");
+    return KP_EINVAL;
+  }
+  if (!strcmp(name, "reliable_delta")) {
+    if (value < 0 || value >= 1) {
+      kp_set_error("reliable_delta must be in [0, 1)");
+      return KP_EINVAL;
+    }
+    ctx->reliable_delta = value;
+  } else if (!strcmp(name, "check_every")) {
+    if (value < 1 || value > 64) {
+      kp_set_error("check_every must be in [1, 64]");
+      return KP_EINVAL;
+    }
+    ctx->check_every = (int)value;
+  } else if (!strcmp(name, "jacobi_tol")) {
+    if (!(value > 0 && value < 1e-3)) {
+      kp_set_error("jacobi_tol must be in (0, 1e-3)");
+      return KP_EINVAL;
+    }
+    ctx->jacobi_tol = value;
+  } else if (!strcmp(name, "jacobi_max_sweeps")) {
+    if (value < 1 || value > 1000) {
+      kp_set_error("jacobi_max_sweeps must be in [1, 1000]");
+      return KP_EINVAL;
+    }
+    ctx->jacobi_max_sweeps = (int)value;
+  } else if (!strcmp(name, "splitk")) {
+    ctx->splitk_override = (int)value;
+  } else {
+    kp_set_error("kp_set_option: unknown option '%s'", name);
+    return KP_EINVAL;
+  }
+  return KP_OK;
+}
+
+extern "C" long long kp_launch_count(kp_ctx* ctx, int reset) {
+  if (!ctx) return -1;
+  long long n = ctx->launches;
+  if (reset) ctx->launches = 0;
+  return n;
+}
+
+static kp_status need_ready(kp_ctx* ctx) {
+  if (!ctx) {
+    kp_set_error("NULL context");
+    return KP_EINVAL;
+  }
+  if (!ctx->ready) {
+    kp_set_error("kp_setup has not completed on this context");
+    return KP_ESTATE;
+  }
+  cudaSetDevice(ctx->device);
+  return KP_OK;
+}
+
+extern "C" kp_status kp_get_rank(kp_ctx* ctx, int* op_rank) {
+  KP_TRY(need_ready(ctx));
+  if (!op_rank) {
+    kp_set_error("kp_get_rank: NULL output");
+    return KP_EINVAL;
+  }
+  *op_rank = ctx->rank;
+  return KP_OK;
+}
+
+extern "C" kp_status kp_get_spectrum(kp_ctx* ctx, double* sigma) {
+  KP_TRY(need_ready(ctx));
+  if (!sigma) {
+    kp_set_error("kp_get_spectrum: NULL output");
+    return KP_EINVAL;
+  }
+  KP_CUDA(cudaMemcpyAsync(sigma, ctx->Sigma64, sizeof(double) * ctx->n_r * ctx->n_c, cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return KP_OK;
+}
+
+extern "C" kp_status kp_get_terms(kp_ctx* ctx, double* s, double* u, double* v) {
+  KP_TRY(need_ready(ctx));
+  const int r = ctx->rank;
+  if (s) KP_CUDA(cudaMemcpyAsync(s, ctx->s_terms, sizeof(double) * r, cudaMemcpyDeviceToHost, ctx->stream));
+  if (u) KP_CUDA(cudaMemcpyAsync(u, ctx->u_terms, sizeof(double) * r * ctx->n_r, cudaMemcpyDeviceToHost, ctx->stream));
+  if (v) KP_CUDA(cudaMemcpyAsync(v, ctx->v_terms, sizeof(double) * r * ctx->n_c, cudaMemcpyDeviceToHost, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return KP_OK;
+}
+
+extern "C" kp_status kp_get_kpsvd(kp_ctx* ctx, double* sr, double* Ur, double* Vr, double* sc, double* Uc,
+                                  double* Vc) {
+  KP_TRY(need_ready(ctx));
+  const size_t nr = ctx->n_r, nc = ctx->n_c;
+  cudaStream_t st = ctx->stream;
+  if (sr) KP_CUDA(cudaMemcpyAsync(sr, ctx->sr, sizeof(double) * nc, cudaMemcpyDeviceToHost, st));
+  if (Ur) KP_CUDA(cudaMemcpyAsync(Ur, ctx->Ur, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost, st));
+  if (Vr) KP_CUDA(cudaMemcpyAsync(Vr, ctx->Vr, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost, st));
+  if (sc) KP_CUDA(cudaMemcpyAsync(sc, ctx->sc, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+  if (Uc) KP_CUDA(cudaMemcpyAsync(Uc, ctx->Uc, sizeof(double) * nr * nr, cudaMemcpyDeviceToHost, st));
+  if (Vc) KP_CUDA(cudaMemcpyAsync(Vc, ctx->Vc, sizeof(double) * nr * nr, cudaMemcpyDeviceToHost, st));
+  KP_CUDA(cudaStreamSynchronize(st));
+  return KP_OK;
+}
+
+kp_status kp_check_ready(kp_ctx* ctx) { return need_ready(ctx); }

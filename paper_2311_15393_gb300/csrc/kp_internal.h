@@ -1,0 +1,204 @@
+// Internal declarations of the KP-SVD deblurring library (sm_103a).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/kpsvd.h"
+
+// ---------------------------------------------------------------- errors
+void kp_set_error(const char* fmt, ...);
+
+#define KP_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      kp_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return KP_ECUDA;                                                                \
+    }                                                                                 \
+  } while (0)
+
+#define KP_TRY(call)              \
+  do {                            \
+    kp_status s_ = (call);        \
+    if (s_ != KP_OK) return s_;   \
+  } while (0)
+
+#define KP_LAUNCHED(ctx) \
+  do { (ctx)->launches++; } while (0)
+
+// device status word bits (written by kernels, read by the host at sync points)
+enum : int { DEV_ERR_TIMEOUT = 1, DEV_ERR_NUMERIC = 2, DEV_ERR_BREAKDOWN = 4, DEV_ERR_BOUNDS = 8 };
+
+// bounded spin limit for device-side waits (each try_wait already suspends
+// for a hardware-defined interval, so this is a few seconds at most)
+constexpr long long KP_SPIN_LIMIT = 1LL << 24;
+
+// ---------------------------------------------------------------- GEMM descriptors
+// D[m][n] = sum_{pair p} sum_{term k} sum_kk A[ta][m][kk] * B[tb][n][kk],
+// ta = sa[p] * a_terms + k, tb = sb[p] * b_terms + k; A and B are K-major
+// (row-major rows x K with leading dimension ld, one block per term index).
+enum EpiMode : int {
+  EPI_F32 = 0,     // out_f32 = alpha * acc + beta * aux           (aux optional)
+  EPI_SLICES = 1,  // v = alpha * acc + beta * aux; out = ns bf16 slices of v
+  EPI_NARROW = 2,  // v = alpha * acc [* lam2 / (sigma^2 + lam2)]; out = narrow type
+  EPI_T = 3,       // SIMT: out_T = alpha * acc + beta * aux [* sigma factor]
+  EPI_PARTIAL = 4  // split-K partial: ws[split][m][n] = acc (fp32)
+};
+enum NarrowType : int { NT_BF16 = 0, NT_F16 = 1, NT_E4M3 = 2 };
+
+constexpr int KP_MAX_PAIRS = 6;
+
+struct GemmOp {
+  const void* ptr = nullptr;
+  int rows = 0;           // M (A) or N (B)
+  int K = 0;
+  long long ld = 0;       // elements between rows
+  long long tstride = 0;  // elements between term blocks
+  int nterm_idx = 0;      // number of term blocks present (for the TMA map)
+};
+
+struct EpiParams {
+  int mode = EPI_F32;
+  void* out = nullptr;
+  long long ldd = 0;
+  int slices = 1;
+  long long slice_stride = 0;
+  double alpha = 1.0, beta = 0.0;
+  const void* aux = nullptr;  // same index as out (T or float)
+  long long ld_aux = 0;
+  const float* sigma32 = nullptr;
+  const double* sigma64 = nullptr;
+  double lam2 = 0.0;
+  int narrow = NT_BF16;
+};
+
+struct GemmDesc {
+  int M = 0, N = 0, K = 0;
+  int nkron = 1;        // k runs over [0, nkron)
+  int npairs = 1;
+  int sa[KP_MAX_PAIRS] = {0}, sb[KP_MAX_PAIRS] = {0};
+  int a_terms = 1, b_terms = 1;  // term blocks per slice
+  GemmOp A, B;
+  EpiParams epi;
+  const int* flags = nullptr;  // when non-null and *flags != 0 the launch does nothing
+};
+
+// ---------------------------------------------------------------- context
+struct TcGemmPlan;  // prepared tensor-core GEMM (tensor maps + params)
+
+struct kp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;       // private work stream (capturable)
+  cudaStream_t user_stream = nullptr;  // caller's stream, ordered with `stream` by events
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  void* ops_state = nullptr;
+  int* dflags = nullptr;               // device solver flags
+  int sm_count = 0;
+  long long launches = 0;
+
+  // problem
+  bool ready = false;
+  int n_r = 0, n_c = 0, c_r = 0, c_c = 0, rank = 0;
+  kp_bc bc = KP_BC_ZERO;
+  kp_prec op_prec = KP_F64, pc_prec = KP_F64, vec_prec = KP_F64;
+  kp_sigma sigma_mode = KP_SIGMA_PROJECTED;
+
+  // options
+  double reliable_delta = -1.0;  // < 0: default for the operator precision
+  int check_every = 4;
+  double jacobi_tol = 1e-15;
+  int jacobi_max_sweeps = 40;
+  int splitk_override = 0;  // > 0: fixed split-K factor for the square GEMMs
+
+  // device allocations: ctx_block lives with the context, allocs with the problem
+  void* ctx_block = nullptr;
+  std::vector<void*> allocs;
+  int* dev_status = nullptr;     // device status word
+  double* dscal = nullptr;       // device scalars (see kp_solver.cu)
+  double* red_part = nullptr;    // reduction partials
+  unsigned int* red_count = nullptr;
+
+  // FP64 masters
+  double* s_terms = nullptr;  // rank
+  double* u_terms = nullptr;  // n_r x rank (col-major)
+  double* v_terms = nullptr;  // n_c x rank
+  double* Ac64 = nullptr;     // [rank][n_r][n_r] row-major A_c^(k)
+  double* Ar64 = nullptr;     // [rank][n_c][n_c] row-major A_r^(k)
+  double *Ur = nullptr, *Vr = nullptr, *sr = nullptr;  // col-major n_c x n_c
+  double *Uc = nullptr, *Vc = nullptr, *sc = nullptr;  // col-major n_r x n_r
+  double* Sigma64 = nullptr;  // n_r x n_c col-major
+  float* Sigma32 = nullptr;
+
+  // operator factors in the four GEMM layouts (T = op type, or bf16 slices)
+  void* opAc = nullptr;   // G1: [slice][k][i'][i] = A_c^(k)[i', i]
+  void* opAr = nullptr;   // G2: [slice][k][l][j]  = A_r^(k)[l, j]
+  void* opAcT = nullptr;  // G3: [slice][k][i'][i] = A_c^(k)[i, i']
+  void* opArT = nullptr;  // G4: [slice][k][l][j]  = A_r^(k)[j, l]
+  int op_slices = 1;
+  // preconditioner factors (pc type), row-major
+  void* pcVcT = nullptr;  // P1 A: V_c^T
+  void* pcVrT = nullptr;  // P2 A: V_r^T
+  void* pcVc = nullptr;   // P3 A: V_c
+  void* pcVr = nullptr;   // P4 A: V_r
+  float pc_vscale_c = 1.f, pc_vscale_r = 1.f;  // power-of-two factor scales (E4M3)
+
+  // workspaces (sized by kp_setup)
+  void* w_stack = nullptr;   // G1/G3 outputs: [slices][rank * n_r][n_c]
+  void* w_img = nullptr;     // G2 outputs / inputs of G3: [slices][n_r * n_c]
+  void* w_img2 = nullptr;    // p slices (inner operator input)
+  void* w_img3 = nullptr;    // x slices (accurate operator input)
+  double* hist = nullptr;    // residual history (device)
+  int hist_cap = 0;
+  float* w_split = nullptr;  // split-K partials
+  long long w_split_elems = 0;
+  void* pc_in = nullptr;     // quantised residual R
+  void* pc_t1 = nullptr;     // P1 out
+  void* pc_t2 = nullptr;     // P2 out
+  void* pc_t3 = nullptr;     // P3 out
+  float* pc_f32 = nullptr;   // FP32 staging for E4M3 dynamic scaling
+  void* vbuf[10] = {nullptr};  // solver vectors (vec type)
+  void* tmp_img = nullptr;   // vec-type scratch image
+  void* tmp_img2 = nullptr;
+
+  // prepared tensor-core GEMM plans
+  std::vector<TcGemmPlan*> tc_plans;
+};
+
+// allocation helper: registers the pointer with the context
+kp_status kp_alloc(kp_ctx* ctx, void** p, size_t bytes);
+void kp_free_all(kp_ctx* ctx);
+
+// ---------------------------------------------------------------- kernels (host launchers)
+// SIMT GEMM (double or float)
+template <typename T>
+kp_status simt_gemm(kp_ctx* ctx, const GemmDesc& g);
+
+// tensor-core GEMM: prepare a plan (tensor maps) once, run it many times
+enum TcKind : int { TC_BF16 = 0, TC_F16 = 1, TC_E4M3 = 2 };
+kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, TcGemmPlan** out);
+kp_status tc_plan_run(kp_ctx* ctx, TcGemmPlan* plan, const EpiParams* epi_override);
+void tc_plan_set_epi(TcGemmPlan* plan, const EpiParams& e);
+bool tc_device_supported(kp_ctx* ctx);
+
+// one-sided Jacobi SVD (FP64): A (m x n col-major, m >= n) -> U (m x n), s (n), V (n x n)
+kp_status jacobi_svd(kp_ctx* ctx, const double* A, int m, int n, double* U, double* s, double* V,
+                     int* sweeps_out);
+
+// vector / reduction helpers (kp_vec.cu)
+kp_status dot_dev(kp_ctx* ctx, const void* x, const void* y, long long n, bool f64, double* out_dev);
+kp_status norm2_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out_dev);
+kp_status split_bf16(kp_ctx* ctx, const void* x, bool f64, long long n, void* out, int slices,
+                     long long slice_stride);
+kp_status copy_vec(kp_ctx* ctx, const void* x, void* y, long long n, bool f64);
+kp_status read_status(kp_ctx* ctx);
+kp_status kp_check_ready(kp_ctx* ctx);
+kp_status kp_enter(kp_ctx* ctx);   // order the work stream after the caller's stream
+kp_status kp_leave(kp_ctx* ctx);   // order the caller's stream after the work stream
+void tc_plan_set_runtime(TcGemmPlan* plan, const float* alpha_dev, const int* flags);

@@ -1,0 +1,562 @@
+// choose_lambda: regularisation parameter in closed form over the KP spectrum
+// (Section 2.2; the paper evaluates these with the Kronecker product
+// approximate SVD, Section 5.1).
+//
+// b_hat = vec(U_c^T B U_r), x_hat = vec(V_c^T X_true V_r) (FP64 GEMMs), and
+// with phi_i = lam^2 / (sigma_i^2 + lam^2) in (0, 1]:
+//   GCV  (eq. GCVTikSVD)    G(lam)   = N sum (phi b_hat)^2 / (sum phi)^2
+//   wGCV (eq. wGCVTikSVD)   G_w(lam) = N sum (phi b_hat)^2 / (sum ((1-w) sigma^2 + lam^2) / d)^2
+//   disc (eq. DSCTikSVD)    D(lam)   = sum (phi b_hat)^2 - eps^2
+//   opt  (eq. OptTikSVD)    O(lam)   = sum (sigma b_hat / d - x_hat)^2
+// (the lam^4 factors of GCV cancel, so the phi form equals eq. GCVTikSVD and
+// keeps every term bounded).  Minimisation: the 400 log-spaced grid values
+// are evaluated in one launch (FP32 terms, FP64 block sums), the best grid
+// point is re-checked in FP64 with its neighbours, then golden-section search
+// in log lam over the two adjacent cells, FP64 throughout.  The discrepancy
+// root is bracketed by decades in log lam and refined by Illinois regula
+// falsi with bisection safeguards.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "kp_internal.h"
+#include "kp_vec.cuh"
+
+namespace {
+
+constexpr int NGRID = 400;
+constexpr int GPB = 8;  // grid values per block
+constexpr int LT = 256;
+
+enum LMethod { LM_GCV = 0, LM_WGCV = 1, LM_DISC = 2, LM_OPT = 3, LM_TRACE = 4 };
+
+struct LamData {
+  const double* s2;   // sigma^2
+  const double* sg;   // sigma
+  const double* bh;   // b_hat
+  const double* xh;   // x_hat (opt)
+  const float* s2f;
+  const float* sgf;
+  const float* bhf;
+  const float* xhf;
+  long long n;
+  double omega;
+  int method;
+};
+
+// per-element contributions (s1, s2) of the sums for one lambda
+template <typename T>
+__device__ __forceinline__ void terms(int method, T s2, T sg, T bh, T xh, T lam2, T omega, T& a, T& b) {
+  const T d = s2 + lam2;
+  const T phi = lam2 / d;
+  switch (method) {
+    case LM_OPT: {
+      const T e = sg * bh / d - xh;
+      a = e * e;
+      b = T(0);
+      break;
+    }
+    case LM_TRACE:
+      a = T(0);
+      b = ((T(1) - omega) * s2 + lam2) / d;
+      break;
+    default: {  // GCV / wGCV / discrepancy share the residual sum
+      const T pb = phi * bh;
+      a = pb * pb;
+      b = ((T(1) - omega) * s2 + lam2) / d;
+      break;
+    }
+  }
+}
+
+__device__ __forceinline__ double lwarp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// grid scan: blockIdx.y = group of GPB lambdas, blockIdx.x = element chunk
+__global__ void __launch_bounds__(LT) k_lam_grid(LamData d, const double* __restrict__ lam2s, int ng,
+                                                 double* __restrict__ part) {
+  const int g0 = blockIdx.y * GPB;
+  float l2[GPB];
+  float acc_a[GPB], acc_b[GPB];
+#pragma unroll
+  for (int q = 0; q < GPB; ++q) {
+    l2[q] = (g0 + q < ng) ? (float)lam2s[g0 + q] : 1.f;
+    acc_a[q] = 0.f;
+    acc_b[q] = 0.f;
+  }
+  const float om = (float)d.omega;
+  for (long long i = blockIdx.x * (long long)LT + threadIdx.x; i < d.n; i += (long long)gridDim.x * LT) {
+    const float s2 = d.s2f[i], sg = d.sgf[i], bh = d.bhf[i], xh = d.xhf ? d.xhf[i] : 0.f;
+#pragma unroll
+    for (int q = 0; q < GPB; ++q) {
+      float a, b;
+      terms<float>(d.method, s2, sg, bh, xh, l2[q], om, a, b);
+      acc_a[q] += a;
+      acc_b[q] += b;
+    }
+  }
+  __shared__ double sh[LT / 32][GPB][2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < GPB; ++q) {
+    double a = lwarp_sum((double)acc_a[q]), b = lwarp_sum((double)acc_b[q]);
+    if (lane == 0) {
+      sh[wid][q][0] = a;
+      sh[wid][q][1] = b;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < GPB * 2) {
+    const int q = threadIdx.x >> 1, w = threadIdx.x & 1;
+    double t = 0.0;
+    for (int k = 0; k < LT / 32; ++k) t += sh[k][q][w];
+    if (g0 + q < ng) part[((long long)(g0 + q) * gridDim.x + blockIdx.x) * 2 + w] = t;
+  }
+}
+
+__global__ void k_lam_grid_finish(const double* __restrict__ part, int nchunks, int ng, double* __restrict__ out) {
+  const int g = blockIdx.x;
+  if (g >= ng) return;
+  double a = 0, b = 0;
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
+    a += part[((long long)g * nchunks + c) * 2];
+    b += part[((long long)g * nchunks + c) * 2 + 1];
+  }
+  __shared__ double sa[256], sb[256];
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sb[threadIdx.x] += sb[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * g] = sa[0];
+    out[2 * g + 1] = sb[0];
+  }
+}
+
+// FP64 evaluation of (s1, s2) for a few lambdas (one per blockIdx.y)
+__global__ void __launch_bounds__(LT) k_lam_eval64(LamData d, const double* __restrict__ lam2s,
+                                                   double* __restrict__ part) {
+  const double l2 = lam2s[blockIdx.y];
+  double a = 0, b = 0;
+  for (long long i = blockIdx.x * (long long)LT + threadIdx.x; i < d.n; i += (long long)gridDim.x * LT) {
+    double ta, tb;
+    terms<double>(d.method, d.s2[i], d.sg[i], d.bh[i], d.xh ? d.xh[i] : 0.0, l2, d.omega, ta, tb);
+    a += ta;
+    b += tb;
+  }
+  __shared__ double sh[LT / 32][2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  a = lwarp_sum(a);
+  b = lwarp_sum(b);
+  if (lane == 0) {
+    sh[wid][0] = a;
+    sh[wid][1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0;
+    for (int k = 0; k < LT / 32; ++k) t += sh[k][threadIdx.x];
+    part[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 2 + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_prep(const double* __restrict__ Sigma, const double* __restrict__ bh, const double* __restrict__ xh,
+                       long long n, double* __restrict__ s2, float* __restrict__ s2f, float* __restrict__ sgf,
+                       float* __restrict__ bhf, float* __restrict__ xhf) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double s = Sigma[i];
+    s2[i] = s * s;
+    s2f[i] = (float)(s * s);
+    sgf[i] = (float)s;
+    bhf[i] = (float)bh[i];
+    if (xh) xhf[i] = (float)xh[i];
+  }
+}
+
+template <typename T>
+__global__ void k_to_f64(const T* __restrict__ x, long long n, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+__global__ void k_absmax_min(const double* __restrict__ S, long long n, double* out) {
+  // out[0] = max |S|, out[1] = min |S| over |S| > 0 (single block)
+  double mx = 0.0, mn = INFINITY;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    double a = fabs(S[i]);
+    mx = fmax(mx, a);
+    if (a > 0) mn = fmin(mn, a);
+  }
+  __shared__ double smx[1024], smn[1024];
+  smx[threadIdx.x] = mx;
+  smn[threadIdx.x] = mn;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + o]);
+      smn[threadIdx.x] = fmin(smn[threadIdx.x], smn[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = smx[0];
+    out[1] = smn[0];
+  }
+}
+
+}  // namespace
+
+struct LamCtx {
+  kp_ctx* ctx;
+  LamData d;
+  double* lam2_dev;
+  double* part;
+  double* sums;
+  int chunks;
+};
+
+// FP64 sums (s1, s2) at the given lambdas (host), up to 16 at once
+static kp_status eval64(LamCtx& L, const double* lams, int k, double* s1, double* s2) {
+  kp_ctx* ctx = L.ctx;
+  double l2[16];
+  for (int i = 0; i < k; ++i) l2[i] = lams[i] * lams[i];
+  KP_CUDA(cudaMemcpyAsync(L.lam2_dev, l2, sizeof(double) * k, cudaMemcpyHostToDevice, ctx->stream));
+  dim3 grid(L.chunks, k);
+  k_lam_eval64<<<grid, LT, 0, ctx->stream>>>(L.d, L.lam2_dev, L.part);
+  KP_LAUNCHED(ctx);
+  k_lam_grid_finish<<<k, 256, 0, ctx->stream>>>(L.part, L.chunks, k, L.sums);
+  KP_LAUNCHED(ctx);
+  double h[32];
+  KP_CUDA(cudaMemcpyAsync(h, L.sums, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < k; ++i) {
+    s1[i] = h[2 * i];
+    s2[i] = h[2 * i + 1];
+  }
+  return KP_OK;
+}
+
+static double objective(int method, double s1, double s2, double N, double eps) {
+  switch (method) {
+    case LM_GCV:
+    case LM_WGCV: return N * s1 / (s2 * s2);
+    case LM_DISC: return s1 - eps * eps;
+    case LM_OPT: return s1;
+    default: return s2;
+  }
+}
+
+static kp_status f64_at(LamCtx& L, int method, double lam, double N, double eps, double* f) {
+  double s1, s2;
+  KP_TRY(eval64(L, &lam, 1, &s1, &s2));
+  *f = objective(method, s1, s2, N, eps);
+  return KP_OK;
+}
+
+static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method method, double param,
+                                    const void* x_true, double* lambda_out) {
+  const int n_r = ctx->n_r, n_c = ctx->n_c;
+  const long long N = (long long)n_r * n_c;
+  cudaStream_t st = ctx->stream;
+  const bool f64 = ctx->vec_prec == KP_F64;
+  const int gr = std::max(1, std::min((int)((N + 255) / 256), ctx->sm_count * 8));
+  // scratch (problem-lifetime allocations, made once)
+  double *B64, *T, *bh, *xh = nullptr, *s2, *lam2_dev, *part, *sums, *ext;
+  float *s2f, *sgf, *bhf, *xhf = nullptr;
+  KP_TRY(kp_alloc(ctx, (void**)&B64, sizeof(double) * N));
+  KP_TRY(kp_alloc(ctx, (void**)&T, sizeof(double) * N));
+  KP_TRY(kp_alloc(ctx, (void**)&bh, sizeof(double) * N));
+  KP_TRY(kp_alloc(ctx, (void**)&s2, sizeof(double) * N));
+  KP_TRY(kp_alloc(ctx, (void**)&s2f, sizeof(float) * N));
+  KP_TRY(kp_alloc(ctx, (void**)&sgf, sizeof(float) * N));
+  KP_TRY(kp_alloc(ctx, (void**)&bhf, sizeof(float) * N));
+  KP_TRY(kp_alloc(ctx, (void**)&lam2_dev, sizeof(double) * NGRID));
+  const int chunks = std::max(1, std::min((int)((N + LT - 1) / LT), ctx->sm_count * 2));
+  KP_TRY(kp_alloc(ctx, (void**)&part, sizeof(double) * 2 * (size_t)chunks * NGRID));
+  KP_TRY(kp_alloc(ctx, (void**)&sums, sizeof(double) * 2 * NGRID));
+  KP_TRY(kp_alloc(ctx, (void**)&ext, sizeof(double) * 2));
+
+  // coefficients in the KP basis: Y^ = U_c^T Y U_r (or V for x_true)
+  auto kp_coeffs = [&](const void* img, const double* Lc, const double* Rr, double* out) -> kp_status {
+    const double* src;
+    if (f64) {
+      src = (const double*)img;
+    } else {
+      k_to_f64<float><<<gr, 256, 0, st>>>((const float*)img, N, B64);
+      KP_LAUNCHED(ctx);
+      src = B64;
+    }
+    GemmDesc g1;  // T[i'][j] = sum_i Lc[i, i'] Y[i, j]
+    g1.M = n_r;
+    g1.N = n_c;
+    g1.K = n_r;
+    g1.A.ptr = Lc;
+    g1.A.ld = n_r;
+    g1.B.ptr = src;
+    g1.B.ld = n_r;
+    g1.epi.mode = EPI_T;
+    g1.epi.out = T;
+    g1.epi.ldd = n_c;
+    KP_TRY(simt_gemm<double>(ctx, g1));
+    GemmDesc g2;  // out[l][i'] = sum_j Rr[j, l] T[i'][j]  (column-major result)
+    g2.M = n_c;
+    g2.N = n_r;
+    g2.K = n_c;
+    g2.A.ptr = Rr;
+    g2.A.ld = n_c;
+    g2.B.ptr = T;
+    g2.B.ld = n_c;
+    g2.epi.mode = EPI_T;
+    g2.epi.out = out;
+    g2.epi.ldd = n_r;
+    return simt_gemm<double>(ctx, g2);
+  };
+  KP_TRY(kp_coeffs(b, ctx->Uc, ctx->Ur, bh));
+  if (method == KP_LAMBDA_OPT) {
+    KP_TRY(kp_alloc(ctx, (void**)&xh, sizeof(double) * N));
+    KP_TRY(kp_alloc(ctx, (void**)&xhf, sizeof(float) * N));
+    KP_TRY(kp_coeffs(x_true, ctx->Vc, ctx->Vr, xh));
+  }
+  k_prep<<<gr, 256, 0, st>>>(ctx->Sigma64, bh, xh, N, s2, s2f, sgf, bhf, xhf);
+  KP_LAUNCHED(ctx);
+  k_absmax_min<<<1, 1024, 0, st>>>(ctx->Sigma64, N, ext);
+  KP_LAUNCHED(ctx);
+  double he[2];
+  KP_CUDA(cudaMemcpyAsync(he, ext, sizeof(he), cudaMemcpyDeviceToHost, st));
+  KP_CUDA(cudaStreamSynchronize(st));
+  const double smax = he[0];
+  const double smin = std::isfinite(he[1]) ? he[1] : smax;
+  if (!(smax > 0)) {
+    kp_set_error("choose_lambda: KP spectrum is zero");
+    return KP_ENUMERIC;
+  }
+  double lo = std::max(smin, 1e-10 * smax), hi = smax;
+
+  LamCtx L;
+  L.ctx = ctx;
+  L.d.s2 = s2;
+  L.d.sg = ctx->Sigma64;
+  L.d.bh = bh;
+  L.d.xh = xh;
+  L.d.s2f = s2f;
+  L.d.sgf = sgf;
+  L.d.bhf = bhf;
+  L.d.xhf = xhf;
+  L.d.n = N;
+  L.d.omega = 1.0;
+  L.lam2_dev = lam2_dev;
+  L.part = part;
+  L.sums = sums;
+  L.chunks = chunks;
+  const double Nd = (double)N;
+
+  int lm = LM_GCV;
+  double eps = 0.0;
+  switch (method) {
+    case KP_LAMBDA_GCV: lm = LM_GCV; break;
+    case KP_LAMBDA_WGCV: lm = LM_WGCV; L.d.omega = param; break;
+    case KP_LAMBDA_DISCREPANCY: lm = LM_DISC; eps = param; break;
+    case KP_LAMBDA_OPT: lm = LM_OPT; break;
+  }
+  L.d.method = lm == LM_WGCV ? LM_GCV : lm;  // wGCV shares the GCV sums with omega != 1
+
+  if (lm == LM_DISC) {
+    // D increases with lambda; D(inf) = ||b_hat||^2 - eps^2
+    double bb;
+    {
+      double s1, s2v, big = 1e30 * smax;
+      KP_TRY(eval64(L, &big, 1, &s1, &s2v));
+      bb = s1;
+    }
+    if (!(bb > eps * eps)) {
+      kp_set_error("choose_lambda: discrepancy has no root (eps >= ||b_hat||)");
+      return KP_ENOROOT;
+    }
+    double tl = std::log(lo), th = std::log(hi), fl, fh;
+    const double tfloor = std::log(1e-16 * hi);
+    KP_TRY(f64_at(L, lm, lo, Nd, eps, &fl));
+    while (fl > 0) {
+      tl -= std::log(10.0);
+      if (tl < tfloor) {
+        kp_set_error("choose_lambda: discrepancy has no root above 1e-16 sigma_max");
+        return KP_ENOROOT;
+      }
+      KP_TRY(f64_at(L, lm, std::exp(tl), Nd, eps, &fl));
+    }
+    KP_TRY(f64_at(L, lm, hi, Nd, eps, &fh));
+    int guard = 0;
+    while (fh < 0 && guard++ < 64) {
+      th += std::log(10.0);
+      KP_TRY(f64_at(L, lm, std::exp(th), Nd, eps, &fh));
+    }
+    if (fh < 0) {
+      kp_set_error("choose_lambda: discrepancy bracket failed");
+      return KP_ENOROOT;
+    }
+    // Illinois regula falsi with bisection safeguard in t = log lambda
+    int side = 0;
+    double t = 0.5 * (tl + th);
+    for (int it = 0; it < 200; ++it) {
+      double tn = th - fh * (th - tl) / (fh - fl);
+      if (!(tn > tl && tn < th)) tn = 0.5 * (tl + th);
+      if (it % 8 == 7) tn = 0.5 * (tl + th);  // guarantees progress
+      double fn;
+      KP_TRY(f64_at(L, lm, std::exp(tn), Nd, eps, &fn));
+      t = tn;
+      if (fn == 0.0) break;
+      if (fn < 0) {
+        tl = tn;
+        fl = fn;
+        if (side == -1) fh *= 0.5;
+        side = -1;
+      } else {
+        th = tn;
+        fh = fn;
+        if (side == 1) fl *= 0.5;
+        side = 1;
+      }
+      if (th - tl <= 1e-15 * std::max(1.0, std::fabs(t))) break;
+    }
+    *lambda_out = std::exp(t);
+    return KP_OK;
+  }
+
+  if (lm == LM_WGCV && param > 1.0) {
+    // start the search where trace(I - omega A A^+) > 0 (bisection in log lam)
+    L.d.method = LM_TRACE;
+    double tr;
+    KP_TRY(f64_at(L, LM_TRACE, lo, Nd, 0.0, &tr));
+    if (!(tr > 0)) {
+      double trh;
+      KP_TRY(f64_at(L, LM_TRACE, hi, Nd, 0.0, &trh));
+      if (!(trh > 0)) {
+        lo = hi;
+      } else {
+        double a = std::log(lo), bnd = std::log(hi);
+        for (int it = 0; it < 200 && bnd - a > 1e-15 * std::max(1.0, std::fabs(a)); ++it) {
+          double m = 0.5 * (a + bnd), tm;
+          KP_TRY(f64_at(L, LM_TRACE, std::exp(m), Nd, 0.0, &tm));
+          if (tm > 0)
+            bnd = m;
+          else
+            a = m;
+        }
+        lo = std::exp(bnd);
+      }
+    }
+    L.d.method = LM_GCV;
+  }
+
+  // ---- grid scan (all grid values in one launch)
+  std::vector<double> tg(NGRID), l2(NGRID);
+  const double tlo = std::log(lo), thi = std::log(hi);
+  for (int g = 0; g < NGRID; ++g) {
+    tg[g] = NGRID > 1 ? tlo + (thi - tlo) * g / (NGRID - 1) : tlo;
+    double l = std::exp(tg[g]);
+    l2[g] = l * l;
+  }
+  KP_CUDA(cudaMemcpyAsync(lam2_dev, l2.data(), sizeof(double) * NGRID, cudaMemcpyHostToDevice, st));
+  {
+    dim3 grid(chunks, (NGRID + GPB - 1) / GPB);
+    k_lam_grid<<<grid, LT, 0, st>>>(L.d, lam2_dev, NGRID, part);
+    KP_LAUNCHED(ctx);
+    k_lam_grid_finish<<<NGRID, 256, 0, st>>>(part, chunks, NGRID, sums);
+    KP_LAUNCHED(ctx);
+  }
+  std::vector<double> hsum(2 * NGRID);
+  KP_CUDA(cudaMemcpyAsync(hsum.data(), sums, sizeof(double) * 2 * NGRID, cudaMemcpyDeviceToHost, st));
+  KP_CUDA(cudaStreamSynchronize(st));
+  int best = 0;
+  double bv = INFINITY;
+  for (int g = 0; g < NGRID; ++g) {
+    double f = objective(lm, hsum[2 * g], hsum[2 * g + 1], Nd, eps);
+    if (f <= bv) {  // ties -> larger lambda
+      bv = f;
+      best = g;
+    }
+  }
+  // FP64 re-check of the best grid point and its neighbours
+  {
+    int g0 = std::max(0, best - 2), g1 = std::min(NGRID - 1, best + 2);
+    double lams[5], s1v[5], s2v[5];
+    int k = g1 - g0 + 1;
+    for (int i = 0; i < k; ++i) lams[i] = std::exp(tg[g0 + i]);
+    KP_TRY(eval64(L, lams, k, s1v, s2v));
+    bv = INFINITY;
+    for (int i = 0; i < k; ++i) {
+      double f = objective(lm, s1v[i], s2v[i], Nd, eps);
+      if (f <= bv) {
+        bv = f;
+        best = g0 + i;
+      }
+    }
+  }
+  // golden-section search in log lambda over [t_{best-1}, t_{best+1}]
+  double a = tg[std::max(best - 1, 0)], c = tg[std::min(best + 1, NGRID - 1)];
+  const double gr_ = 0.5 * (std::sqrt(5.0) - 1.0);
+  double x1 = c - gr_ * (c - a), x2 = a + gr_ * (c - a), f1, f2;
+  KP_TRY(f64_at(L, lm, std::exp(x1), Nd, eps, &f1));
+  KP_TRY(f64_at(L, lm, std::exp(x2), Nd, eps, &f2));
+  for (int it = 0; it < 200 && (c - a) > 1e-12; ++it) {
+    if (f1 < f2) {
+      c = x2;
+      x2 = x1;
+      f2 = f1;
+      x1 = c - gr_ * (c - a);
+      KP_TRY(f64_at(L, lm, std::exp(x1), Nd, eps, &f1));
+    } else {
+      a = x1;
+      x1 = x2;
+      f1 = f2;
+      x2 = a + gr_ * (c - a);
+      KP_TRY(f64_at(L, lm, std::exp(x2), Nd, eps, &f2));
+    }
+  }
+  double tbest = f1 < f2 ? x1 : x2, fbest = std::min(f1, f2);
+  if (!(fbest <= bv)) tbest = tg[best];
+  *lambda_out = std::exp(tbest);
+  return KP_OK;
+}
+
+extern "C" kp_status choose_lambda(kp_ctx* ctx, const void* b, kp_lambda_method method, double param,
+                                   const void* x_true, double* lambda_out) {
+  KP_TRY(kp_check_ready(ctx));
+  if (!b || !lambda_out) {
+    kp_set_error("choose_lambda: NULL argument");
+    return KP_EINVAL;
+  }
+  if (method < KP_LAMBDA_GCV || method > KP_LAMBDA_OPT) {
+    kp_set_error("choose_lambda: unknown method %d", (int)method);
+    return KP_EINVAL;
+  }
+  if (method == KP_LAMBDA_OPT && !x_true) {
+    kp_set_error("choose_lambda: KP_LAMBDA_OPT needs x_true");
+    return KP_EINVAL;
+  }
+  if (method == KP_LAMBDA_DISCREPANCY && !(param > 0.0)) {
+    kp_set_error("choose_lambda: discrepancy needs eps > 0");
+    return KP_EINVAL;
+  }
+  if (method == KP_LAMBDA_WGCV && !(param > 0.0)) {
+    kp_set_error("choose_lambda: wGCV needs omega > 0");
+    return KP_EINVAL;
+  }
+  KP_TRY(kp_enter(ctx));
+  size_t nalloc = ctx->allocs.size();
+  kp_status s = choose_lambda_impl(ctx, b, method, param, x_true, lambda_out);
+  // release this call's scratch
+  cudaStreamSynchronize(ctx->stream);
+  for (size_t i = nalloc; i < ctx->allocs.size(); ++i) cudaFree(ctx->allocs[i]);
+  ctx->allocs.resize(nalloc);
+  kp_status l = kp_leave(ctx);
+  return s != KP_OK ? s : l;
+}

@@ -1,0 +1,405 @@
+// Operator and preconditioner applications.
+//
+// Layout: images are column-major n_r x n_c (vec order, Section 3).  The
+// Kronecker sum A vec(X) = vec(sum_k A_c^(k) X A_r^(k)^T) (eq. KronSumDecomp)
+// runs as two GEMMs whose operands are all K-major:
+//   G1  W = [A_c^(1); ...; A_c^(r)] X           M = r n_r, N = n_c, K = n_r
+//       (output row-major W_k[i', j], stacked over k)
+//   G2  Z^T = sum_k A_r^(k) W_k^T                M = n_c, N = n_r, K = n_c per term
+//       (output row-major [l][i'] = column-major Z)
+// and A^T vec(Y) = vec(sum_k A_c^(k)^T Y A_r^(k)) is G3 / G4 with the
+// transposed factors.  The preconditioner solve Z = V_c (S .* (V_c^T R V_r)) V_r^T
+// (eq. PreconSolve) is P1..P4 with the same alternation, S applied in the
+// P2 epilogue as lam^2 / (Sigma^2 + lam^2) and 1 / lam^2 folded into P4.
+//
+// Tensor-core operators split activations and factors into bf16 slices.
+// The inner (per-iteration) operator uses the slice pairs {(0,0)} (KP_BF16)
+// or {(0,0),(0,1),(1,0)} (KP_BF16X3); the accurate operator used for true
+// residuals uses {(0,0),(0,1),(1,0),(0,2),(1,1),(2,0)}, whose dropped terms are
+// below 2^-24 relative (FP32 level).
+#include <algorithm>
+
+#include "kp_ops.h"
+#include "kp_vec.cuh"
+
+namespace {
+struct OpsState {
+  TcGemmPlan* G[2][4] = {{nullptr}};  // [mode][gemm]
+  TcGemmPlan* P[4] = {nullptr};
+  float* inv_slot = nullptr;          // device scale for P4
+  double* stat = nullptr;             // device [rr, amax] scratch
+};
+}  // namespace
+
+static OpsState* ops(kp_ctx* ctx) { return reinterpret_cast<OpsState*>(ctx->ops_state); }
+
+void ops_state_free(kp_ctx* ctx) {
+  delete ops(ctx);
+  ctx->ops_state = nullptr;
+}
+
+static bool op_is_tc(kp_ctx* ctx) { return ctx->op_prec == KP_BF16 || ctx->op_prec == KP_BF16X3; }
+static bool pc_is_tc(kp_ctx* ctx) {
+  return ctx->pc_prec == KP_BF16 || ctx->pc_prec == KP_F16 || ctx->pc_prec == KP_E4M3;
+}
+static bool vec64(kp_ctx* ctx) { return ctx->vec_prec == KP_F64; }
+
+int op_inner_slices(kp_ctx* ctx) {
+  if (!op_is_tc(ctx)) return 0;
+  return ctx->op_prec == KP_BF16X3 ? 2 : 1;
+}
+
+static void pairs_for(kp_ctx* ctx, int mode, GemmDesc& g) {
+  static const int acc_a[6] = {0, 0, 1, 0, 1, 2}, acc_b[6] = {0, 1, 0, 2, 1, 0};
+  static const int x3_a[3] = {0, 0, 1}, x3_b[3] = {0, 1, 0};
+  if (mode == OP_ACCURATE) {
+    g.npairs = 6;
+    for (int i = 0; i < 6; ++i) {
+      g.sa[i] = acc_a[i];
+      g.sb[i] = acc_b[i];
+    }
+  } else if (ctx->op_prec == KP_BF16X3) {
+    g.npairs = 3;
+    for (int i = 0; i < 3; ++i) {
+      g.sa[i] = x3_a[i];
+      g.sb[i] = x3_b[i];
+    }
+  } else {
+    g.npairs = 1;
+    g.sa[0] = g.sb[0] = 0;
+  }
+}
+
+static int choose_splits(kp_ctx* ctx, int M, int N, int steps) {
+  if (ctx->splitk_override > 0) return std::min(ctx->splitk_override, steps);
+  const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
+  int s = (ctx->sm_count + tiles - 1) / tiles;
+  s = std::max(1, std::min(s, 4));
+  return std::min(s, steps);
+}
+
+// GEMM descriptors of the operator: which = 0..3 (G1..G4)
+static GemmDesc op_desc(kp_ctx* ctx, int which, int mode, const void* bptr) {
+  const int n_r = ctx->n_r, n_c = ctx->n_c, r = ctx->rank;
+  const long long N = (long long)n_r * n_c;
+  GemmDesc g;
+  pairs_for(ctx, mode, g);
+  const int slices = op_is_tc(ctx) ? 3 : 1;
+  if (which == 0 || which == 2) {  // G1 / G3: stacked factors x image
+    g.M = r * n_r;
+    g.N = n_c;
+    g.K = n_r;
+    g.nkron = 1;
+    g.A.ptr = which == 0 ? ctx->opAc : ctx->opAcT;
+    g.A.rows = r * n_r;
+    g.A.K = n_r;
+    g.A.ld = n_r;
+    g.A.tstride = (long long)r * n_r * n_r;
+    g.A.nterm_idx = slices;
+    g.a_terms = 1;
+    g.B.ptr = bptr;
+    g.B.rows = n_c;
+    g.B.K = n_r;
+    g.B.ld = n_r;
+    g.B.tstride = N;
+    g.B.nterm_idx = slices;
+    g.b_terms = 1;
+  } else {  // G2 / G4: sum over terms of factor x stacked intermediate
+    g.M = n_c;
+    g.N = n_r;
+    g.K = n_c;
+    g.nkron = r;
+    g.A.ptr = which == 1 ? ctx->opAr : ctx->opArT;
+    g.A.rows = n_c;
+    g.A.K = n_c;
+    g.A.ld = n_c;
+    g.A.tstride = (long long)n_c * n_c;
+    g.A.nterm_idx = slices * r;
+    g.a_terms = r;
+    g.B.ptr = ctx->w_stack;
+    g.B.rows = n_r;
+    g.B.K = n_c;
+    g.B.ld = n_c;
+    g.B.tstride = N;
+    g.B.nterm_idx = slices * r;
+    g.b_terms = r;
+  }
+  return g;
+}
+
+static GemmDesc pc_desc(kp_ctx* ctx, int which) {
+  const int n_r = ctx->n_r, n_c = ctx->n_c;
+  GemmDesc g;
+  g.npairs = 1;
+  g.nkron = 1;
+  if (which == 0 || which == 2) {  // P1: V_c^T R ; P3: V_c W
+    g.M = n_r;
+    g.N = n_c;
+    g.K = n_r;
+    g.A.ptr = which == 0 ? ctx->pcVcT : ctx->pcVc;
+    g.A.rows = n_r;
+    g.A.ld = n_r;
+    g.B.ptr = which == 0 ? ctx->pc_in : ctx->pc_t2;
+    g.B.rows = n_c;
+    g.B.ld = n_r;
+  } else {  // P2: V_r^T T1^T ; P4: V_r T3^T
+    g.M = n_c;
+    g.N = n_r;
+    g.K = n_c;
+    g.A.ptr = which == 1 ? ctx->pcVrT : ctx->pcVr;
+    g.A.rows = n_c;
+    g.A.ld = n_c;
+    g.B.ptr = which == 1 ? ctx->pc_t1 : ctx->pc_t3;
+    g.B.rows = n_r;
+    g.B.ld = n_c;
+  }
+  g.A.K = g.K;
+  g.B.K = g.K;
+  g.A.tstride = (long long)g.A.rows * g.A.ld;
+  g.B.tstride = (long long)g.B.rows * g.B.ld;
+  g.A.nterm_idx = 1;
+  g.B.nterm_idx = 1;
+  return g;
+}
+
+kp_status ops_prepare(kp_ctx* ctx) {
+  const int n_r = ctx->n_r, n_c = ctx->n_c, r = ctx->rank;
+  const long long N = (long long)n_r * n_c;
+  const size_t vs = vec64(ctx) ? 8 : 4;
+  ops_state_free(ctx);
+  OpsState* os = new OpsState();
+  ctx->ops_state = os;
+  KP_TRY(kp_alloc(ctx, (void**)&os->inv_slot, 16));
+  KP_TRY(kp_alloc(ctx, (void**)&os->stat, 4 * sizeof(double)));
+  // solver vectors and scratch images
+  for (int i = 0; i < 8; ++i) KP_TRY(kp_alloc(ctx, &ctx->vbuf[i], vs * N));
+  KP_TRY(kp_alloc(ctx, &ctx->tmp_img, vs * N));
+  KP_TRY(kp_alloc(ctx, &ctx->tmp_img2, vs * N));
+  ctx->hist_cap = 1 << 16;
+  KP_TRY(kp_alloc(ctx, (void**)&ctx->hist, sizeof(double) * ctx->hist_cap));
+  // operator workspaces
+  if (op_is_tc(ctx)) {
+    const size_t b = sizeof(__nv_bfloat16);
+    KP_TRY(kp_alloc(ctx, &ctx->w_stack, b * 3 * r * N));
+    KP_TRY(kp_alloc(ctx, &ctx->w_img, b * 3 * N));
+    KP_TRY(kp_alloc(ctx, &ctx->w_img2, b * 3 * N));
+    KP_TRY(kp_alloc(ctx, &ctx->w_img3, b * 3 * N));
+  } else {
+    KP_TRY(kp_alloc(ctx, &ctx->w_stack, vs * r * N));
+    KP_TRY(kp_alloc(ctx, &ctx->w_img, vs * N));
+  }
+  // preconditioner workspaces
+  {
+    const size_t es = pc_is_tc(ctx) ? (ctx->pc_prec == KP_E4M3 ? 1 : 2) : vs;
+    KP_TRY(kp_alloc(ctx, &ctx->pc_in, es * N));
+    KP_TRY(kp_alloc(ctx, &ctx->pc_t1, es * N));
+    KP_TRY(kp_alloc(ctx, &ctx->pc_t2, es * N));
+    KP_TRY(kp_alloc(ctx, &ctx->pc_t3, es * N));
+    KP_TRY(kp_alloc(ctx, (void**)&ctx->pc_f32, sizeof(float) * N));
+  }
+  // split-K workspace: up to 8 partial images
+  const long long nmax = std::max(n_r, n_c);
+  ctx->w_split_elems = 8 * nmax * nmax;
+  KP_TRY(kp_alloc(ctx, (void**)&ctx->w_split, sizeof(float) * ctx->w_split_elems));
+
+  if (op_is_tc(ctx)) {
+    for (int mode = 0; mode < 2; ++mode) {
+      for (int w = 0; w < 4; ++w) {
+        const void* bptr = w == 0 ? (mode == OP_INNER ? ctx->w_img2 : ctx->w_img3) : (w == 2 ? ctx->w_img : nullptr);
+        GemmDesc g = op_desc(ctx, w, mode, bptr);
+        const int bk = 64;
+        const int steps = g.npairs * g.nkron * ((g.K + bk - 1) / bk);
+        const int splits = (w == 1 || w == 3) ? choose_splits(ctx, g.M, g.N, steps) : 1;
+        KP_TRY(tc_plan_create(ctx, g, TC_BF16, splits, &os->G[mode][w]));
+      }
+    }
+  }
+  if (pc_is_tc(ctx)) {
+    const int kind = ctx->pc_prec == KP_BF16 ? TC_BF16 : (ctx->pc_prec == KP_F16 ? TC_F16 : TC_E4M3);
+    for (int w = 0; w < 4; ++w) {
+      GemmDesc g = pc_desc(ctx, w);
+      const int bk = kind == TC_E4M3 ? 128 : 64;
+      const int steps = (g.K + bk - 1) / bk;
+      KP_TRY(tc_plan_create(ctx, g, kind, choose_splits(ctx, g.M, g.N, steps), &os->P[w]));
+    }
+  }
+  return KP_OK;
+}
+
+// ------------------------------------------------------------- operator
+template <typename T>
+static kp_status simt_op(kp_ctx* ctx, int which, const void* bptr, EpiParams e, const int* flags) {
+  GemmDesc g = op_desc(ctx, which, OP_INNER, bptr);
+  g.npairs = 1;
+  g.sa[0] = g.sb[0] = 0;
+  e.mode = EPI_T;
+  g.epi = e;
+  g.flags = flags;
+  return simt_gemm<T>(ctx, g);
+}
+
+static kp_status run_op(kp_ctx* ctx, int which, int mode, const void* bptr, const EpiParams& e, const int* flags) {
+  if (op_is_tc(ctx)) {
+    TcGemmPlan* pl = ops(ctx)->G[mode][which];
+    tc_plan_set_runtime(pl, nullptr, flags);
+    return tc_plan_run(ctx, pl, &e);
+  }
+  if (vec64(ctx)) return simt_op<double>(ctx, which, bptr, e, flags);
+  return simt_op<float>(ctx, which, bptr, e, flags);
+}
+
+// epilogue writing the stacked intermediate (G1 / G3 output)
+static EpiParams epi_stack(kp_ctx* ctx, int mode) {
+  EpiParams e;
+  e.out = ctx->w_stack;
+  e.ldd = ctx->n_c;
+  if (op_is_tc(ctx)) {
+    e.mode = EPI_SLICES;
+    e.slices = mode == OP_ACCURATE ? 3 : op_inner_slices(ctx);
+    e.slice_stride = (long long)ctx->rank * ctx->n_r * ctx->n_c;
+  } else {
+    e.mode = EPI_T;
+  }
+  return e;
+}
+// epilogue writing an image-shaped output (G2 / G4): out = alpha acc + beta aux
+static EpiParams epi_img(kp_ctx* ctx, int mode, void* out, bool as_slices, double alpha, double beta,
+                         const void* aux) {
+  EpiParams e;
+  e.out = out;
+  e.ldd = ctx->n_r;
+  e.alpha = alpha;
+  e.beta = beta;
+  e.aux = aux;
+  e.ld_aux = ctx->n_r;
+  if (op_is_tc(ctx)) {
+    if (as_slices) {
+      e.mode = EPI_SLICES;
+      e.slices = mode == OP_ACCURATE ? 3 : op_inner_slices(ctx);
+      e.slice_stride = (long long)ctx->n_r * ctx->n_c;
+    } else {
+      e.mode = EPI_F32;
+    }
+  } else {
+    e.mode = EPI_T;
+  }
+  return e;
+}
+
+// B operand of G1 for image x: tensor cores need bf16 slices in w_img2 / w_img3
+static kp_status stage_input(kp_ctx* ctx, const void* x, int mode, const void** bptr) {
+  if (!op_is_tc(ctx)) {
+    *bptr = x;
+    return KP_OK;
+  }
+  void* dst = mode == OP_INNER ? ctx->w_img2 : ctx->w_img3;
+  const int slices = mode == OP_ACCURATE ? 3 : op_inner_slices(ctx);
+  KP_TRY(split_bf16(ctx, x, false, (long long)ctx->n_r * ctx->n_c, dst, slices, (long long)ctx->n_r * ctx->n_c));
+  *bptr = dst;
+  return KP_OK;
+}
+
+kp_status op_apply(kp_ctx* ctx, const void* x, void* y, int transpose, int mode) {
+  const void* bx;
+  KP_TRY(stage_input(ctx, x, mode, &bx));
+  const int g_first = transpose ? 2 : 0;
+  if (transpose && op_is_tc(ctx)) {
+    // G3 reads its image operand from w_img (slices)
+    const int slices = mode == OP_ACCURATE ? 3 : op_inner_slices(ctx);
+    KP_TRY(split_bf16(ctx, x, false, (long long)ctx->n_r * ctx->n_c, ctx->w_img, slices,
+                      (long long)ctx->n_r * ctx->n_c));
+    bx = ctx->w_img;
+  }
+  KP_TRY(run_op(ctx, g_first, mode, bx, epi_stack(ctx, mode), nullptr));
+  KP_TRY(run_op(ctx, g_first + 1, mode, nullptr, epi_img(ctx, mode, y, false, 1.0, 0.0, nullptr), nullptr));
+  return KP_OK;
+}
+
+kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_slices_ready, const int* flags) {
+  const void* bx = p;
+  if (op_is_tc(ctx)) {
+    if (!p_slices_ready) KP_TRY(stage_input(ctx, p, OP_INNER, &bx));
+    bx = ctx->w_img2;
+  }
+  const bool tc = op_is_tc(ctx);
+  KP_TRY(run_op(ctx, 0, OP_INNER, bx, epi_stack(ctx, OP_INNER), flags));
+  KP_TRY(run_op(ctx, 1, OP_INNER, nullptr, epi_img(ctx, OP_INNER, ctx->w_img, tc, 1.0, 0.0, nullptr), flags));
+  KP_TRY(run_op(ctx, 2, OP_INNER, ctx->w_img, epi_stack(ctx, OP_INNER), flags));
+  KP_TRY(run_op(ctx, 3, OP_INNER, nullptr, epi_img(ctx, OP_INNER, q, false, 1.0, lam2, p), flags));
+  return KP_OK;
+}
+
+kp_status op_true_residual(kp_ctx* ctx, const void* b, const void* x, void* r, double lam2, const int* flags) {
+  const void* bx;
+  const int mode = OP_ACCURATE;
+  if (op_is_tc(ctx)) {
+    KP_TRY(stage_input(ctx, x, mode, &bx));
+  } else {
+    bx = x;
+  }
+  const bool tc = op_is_tc(ctx);
+  KP_TRY(run_op(ctx, 0, mode, bx, epi_stack(ctx, mode), flags));
+  // data-space residual b - A x
+  KP_TRY(run_op(ctx, 1, mode, nullptr, epi_img(ctx, mode, ctx->w_img, tc, -1.0, 1.0, b), flags));
+  KP_TRY(run_op(ctx, 2, mode, ctx->w_img, epi_stack(ctx, mode), flags));
+  KP_TRY(run_op(ctx, 3, mode, nullptr, epi_img(ctx, mode, r, false, 1.0, -lam2, x), flags));
+  return KP_OK;
+}
+
+// ------------------------------------------------------------- preconditioner
+template <typename T>
+static kp_status simt_pc(kp_ctx* ctx, const void* r, void* z, double lam2, const int* flags) {
+  for (int w = 0; w < 4; ++w) {
+    GemmDesc g = pc_desc(ctx, w);
+    if (w == 0) g.B.ptr = r;
+    if (w == 2) g.B.ptr = ctx->pc_t2;
+    g.flags = flags;
+    g.epi.mode = EPI_T;
+    g.epi.ldd = g.N;
+    g.epi.out = w == 0 ? ctx->pc_t1 : (w == 1 ? ctx->pc_t2 : (w == 2 ? ctx->pc_t3 : z));
+    if (w == 1) {
+      g.epi.sigma64 = ctx->Sigma64;
+      g.epi.lam2 = lam2;
+    }
+    if (w == 3) g.epi.alpha = 1.0 / lam2;
+    KP_TRY(simt_gemm<T>(ctx, g));
+  }
+  return KP_OK;
+}
+
+kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat, const int* flags) {
+  if (!pc_is_tc(ctx)) {
+    if (vec64(ctx)) return simt_pc<double>(ctx, r, z, lam2, flags);
+    return simt_pc<float>(ctx, r, z, lam2, flags);
+  }
+  OpsState* os = ops(ctx);
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  if (!stat) {
+    KP_TRY(norm_amax_dev(ctx, r, N, false, os->stat));
+    stat = os->stat;
+  }
+  const int nt = ctx->pc_prec == KP_BF16 ? NT_BF16 : (ctx->pc_prec == KP_F16 ? NT_F16 : NT_E4M3);
+  // E4M3 factors carry power-of-two scales; undo them in the last GEMM
+  const double fscale = (double)ctx->pc_vscale_c * ctx->pc_vscale_r;
+  KP_TRY(quantize_dev(ctx, r, N, false, stat, nt, lam2 * fscale * fscale, ctx->pc_in, os->inv_slot, flags));
+  for (int w = 0; w < 4; ++w) {
+    EpiParams e;
+    e.ldd = w == 0 || w == 2 ? ctx->n_c : ctx->n_r;
+    e.narrow = nt;
+    if (w < 3) {
+      e.mode = EPI_NARROW;
+      e.out = w == 0 ? ctx->pc_t1 : (w == 1 ? ctx->pc_t2 : ctx->pc_t3);
+      if (w == 1) {
+        e.sigma32 = ctx->Sigma32;
+        e.lam2 = lam2;
+      }
+      tc_plan_set_runtime(os->P[w], nullptr, flags);
+    } else {
+      e.mode = EPI_F32;
+      e.out = z;
+      tc_plan_set_runtime(os->P[w], os->inv_slot, flags);
+    }
+    KP_TRY(tc_plan_run(ctx, os->P[w], &e));
+  }
+  return KP_OK;
+}

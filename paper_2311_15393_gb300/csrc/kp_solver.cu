@@ -1,0 +1,394 @@
+// tik_pcg: preconditioned CG / flexible PCG on (A^T A + lam^2 I) x = A^T b
+// (eq. tik:normal2), KP-SVD preconditioner with the same lambda
+// (eq. PreconSystem), Fletcher-Reeves beta (PCG) or Polak-Ribiere beta
+// (flexible PCG; Section 3, last paragraph).
+//
+// All scalars (alpha, beta, inner products, norms) are FP64 values in device
+// memory; the host never waits inside an iteration.  Iterations run in
+// blocks of `check_every`, captured once per solve as a CUDA graph.  Each
+// kernel returns at once while the device pause flag is set; the flag is
+// raised on convergence of the recurred residual, when a reliable residual
+// update is due, at maxit, or on breakdown / NaN.  The host reads the flags
+// after each block and acts (replace the residual, stop).
+//
+// Reliable updates: with a reduced-precision operator the recurred residual
+// drifts from the true one, by about the operator's rounding error times
+// cond(A^T A + lam^2 I).  Whenever ||r|| has fallen by `reliable_delta`
+// since the last replacement, and before convergence is declared, r is
+// replaced by A^T (b - A x) - lam^2 x computed with the FP32-accurate
+// operator; the search direction is kept.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "kp_internal.h"
+#include "kp_ops.h"
+#include "kp_vec.cuh"
+
+namespace {
+
+// device scalar slots (ctx->dscal)
+enum {
+  S_RR = 0, S_AMAX = 1, S_PQ = 2, S_ALPHA = 3, S_ZR = 4, S_ZRNEW = 5, S_ZROLD = 6, S_BETA = 7,
+  S_RR0 = 8, S_RMAX = 9, S_TOL2 = 10, S_DELTA2 = 11
+};
+// device flag slots (ctx->dflags)
+enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4 };
+enum { R_CONV = 1, R_REPLACE = 2, R_MAXIT = 4, R_BREAKDOWN = 8, R_NUMERIC = 16 };
+
+__device__ __forceinline__ bool is_paused(const int* f) { return *(volatile const int*)f != 0; }
+
+__global__ void k_alpha(double* s, int* f) {
+  if (is_paused(f)) return;
+  const double pq = s[S_PQ], zr = s[S_ZR];
+  if (!isfinite(pq) || !isfinite(zr)) {
+    f[F_REASON] |= R_NUMERIC;
+    f[F_PAUSE] = 1;
+    return;
+  }
+  if (!(pq > 0.0) || !(zr > 0.0)) {
+    f[F_REASON] |= R_BREAKDOWN;
+    f[F_PAUSE] = 1;
+    return;
+  }
+  s[S_ALPHA] = zr / pq;
+}
+
+__global__ void k_check(double* s, int* f, double* hist, int hist_cap) {
+  if (is_paused(f)) return;
+  const int it = ++f[F_ITER];
+  const double rr = s[S_RR];
+  if (it < hist_cap) hist[it] = sqrt(rr / s[S_RR0]);
+  int reason = 0;
+  if (!isfinite(rr)) reason |= R_NUMERIC;
+  else if (rr <= s[S_TOL2]) reason |= R_CONV;
+  else if (s[S_DELTA2] > 0.0 && rr < s[S_DELTA2] * s[S_RMAX]) reason |= R_REPLACE;
+  if (it >= f[F_MAXIT]) reason |= R_MAXIT;
+  if (reason) {
+    f[F_REASON] |= reason;
+    f[F_PAUSE] = 1;
+  }
+}
+
+__global__ void k_beta(double* s, int* f) {
+  if (is_paused(f)) return;
+  const double zn = s[S_ZRNEW], zo = s[S_ZROLD], zr = s[S_ZR];
+  if (!isfinite(zn) || !isfinite(zo)) {
+    f[F_REASON] |= R_NUMERIC;
+    f[F_PAUSE] = 1;
+    return;
+  }
+  if (!(zn > 0.0)) {
+    f[F_REASON] |= R_BREAKDOWN;
+    f[F_PAUSE] = 1;
+    return;
+  }
+  s[S_BETA] = f[F_FLEX] ? (zn - zo) / zr : zn / zr;
+  s[S_ZR] = zn;
+}
+
+}  // namespace
+
+struct SolveBufs {
+  void *r, *r_old, *p, *q, *z, *rhs;
+};
+
+static SolveBufs bufs(kp_ctx* ctx) {
+  SolveBufs b;
+  b.r = ctx->vbuf[0];
+  b.r_old = ctx->vbuf[1];
+  b.p = ctx->vbuf[2];
+  b.q = ctx->vbuf[3];
+  b.z = ctx->vbuf[4];
+  b.rhs = ctx->vbuf[5];
+  return b;
+}
+
+// first half of an iteration: q = K p, alpha, x/r update, convergence flags
+static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  const bool f64 = ctx->vec_prec == KP_F64;
+  const int* fl = ctx->dflags;
+  double* s = ctx->dscal;
+  KP_TRY(op_apply_K(ctx, B.p, B.q, lam2, op_inner_slices(ctx) > 0, fl));
+  KP_TRY(dot2_dev(ctx, B.p, B.q, nullptr, N, f64, s + S_PQ, fl));
+  k_alpha<<<1, 1, 0, ctx->stream>>>(s, ctx->dflags);
+  KP_LAUNCHED(ctx);
+  KP_TRY(update_xr_dev(ctx, x, B.r, B.r_old, B.p, B.q, N, f64, s + S_ALPHA, s + S_RR, fl));
+  k_check<<<1, 1, 0, ctx->stream>>>(s, ctx->dflags, ctx->hist, ctx->hist_cap);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+// second half: z = M^-1 r, beta, p = z + beta p (+ bf16 slices of p)
+static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2) {
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  const bool f64 = ctx->vec_prec == KP_F64;
+  const int* fl = ctx->dflags;
+  double* s = ctx->dscal;
+  KP_TRY(pc_apply(ctx, B.r, B.z, lam2, s + S_RR, fl));
+  KP_TRY(dot2_dev(ctx, B.z, B.r, B.r_old, N, f64, s + S_ZRNEW, fl));
+  k_beta<<<1, 1, 0, ctx->stream>>>(s, ctx->dflags);
+  KP_LAUNCHED(ctx);
+  const int sl = op_inner_slices(ctx);
+  KP_TRY(p_update_dev(ctx, B.p, B.z, N, f64, s + S_BETA, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N, fl));
+  return KP_OK;
+}
+
+struct HostFlags {
+  int pause, reason, iter, maxit, flex;
+};
+
+static kp_status read_flags(kp_ctx* ctx, HostFlags* h, double* hs) {
+  KP_CUDA(cudaMemcpyAsync(h, ctx->dflags, sizeof(HostFlags), cudaMemcpyDeviceToHost, ctx->stream));
+  if (hs) KP_CUDA(cudaMemcpyAsync(hs, ctx->dscal, 12 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return KP_OK;
+}
+
+static kp_status set_scalar(kp_ctx* ctx, int slot, double v) {
+  KP_CUDA(cudaMemcpyAsync(ctx->dscal + slot, &v, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));  // v is a host stack value
+  return KP_OK;
+}
+
+// replace r by the true residual; returns its ||r||^2 via the RR / RMAX slots
+static kp_status replace_residual(kp_ctx* ctx, const SolveBufs& B, const void* b, const void* x, double lam2) {
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  KP_TRY(op_true_residual(ctx, b, x, B.r, lam2, nullptr));
+  KP_TRY(norm_amax_dev(ctx, B.r, N, ctx->vec_prec == KP_F64, ctx->dscal + S_RR));
+  KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RMAX, ctx->dscal + S_RR, sizeof(double), cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+  return KP_OK;
+}
+
+static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible, void* x,
+                              int warm_start, kp_solve_info* info) {
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  const bool f64 = ctx->vec_prec == KP_F64;
+  const double lam2 = lambda * lambda;
+  const SolveBufs B = bufs(ctx);
+  cudaStream_t st = ctx->stream;
+  const bool reduced_op = ctx->op_prec == KP_BF16 || ctx->op_prec == KP_BF16X3;
+  double delta = ctx->reliable_delta >= 0 ? ctx->reliable_delta : (reduced_op ? 0.1 : 0.0);
+  const bool reliable = delta > 0.0;
+
+  cudaEvent_t e0, e1;
+  KP_CUDA(cudaEventCreate(&e0));
+  KP_CUDA(cudaEventCreate(&e1));
+  KP_CUDA(cudaEventRecord(e0, st));
+  KP_CUDA(cudaMemsetAsync(ctx->dflags, 0, 64, st));
+  KP_CUDA(cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), st));
+  {
+    int hf[5] = {0, 0, 0, maxit, flexible ? 1 : 0};
+    KP_CUDA(cudaMemcpyAsync(ctx->dflags, hf, sizeof(hf), cudaMemcpyHostToDevice, st));
+    KP_CUDA(cudaStreamSynchronize(st));
+  }
+  // rhs = A^T b (accurate operator) and its norm
+  KP_TRY(op_apply(ctx, b, B.rhs, 1, OP_ACCURATE));
+  KP_TRY(dot2_dev(ctx, B.rhs, B.rhs, nullptr, N, f64, ctx->dscal + S_RR0, nullptr));
+  HostFlags hf;
+  double hs[12];
+  KP_TRY(read_flags(ctx, &hf, hs));
+  const double rr0 = hs[S_RR0];
+  kp_status result = KP_OK;
+  int iters = 0, repl = 0;
+  double final_rr = 0.0;
+  if (!(rr0 > 0.0) || !std::isfinite(rr0)) {
+    if (!std::isfinite(rr0)) {
+      kp_set_error("tik_pcg: A^T b is not finite");
+      result = KP_ENUMERIC;
+    } else {
+      KP_CUDA(cudaMemsetAsync(x, 0, N * (f64 ? 8 : 4), st));
+    }
+  } else {
+    KP_TRY(set_scalar(ctx, S_TOL2, tol * tol * rr0));
+    KP_TRY(set_scalar(ctx, S_DELTA2, reliable ? delta * delta : 0.0));
+    if (warm_start) {
+      KP_TRY(replace_residual(ctx, B, b, x, lam2));
+    } else {
+      KP_CUDA(cudaMemsetAsync(x, 0, N * (f64 ? 8 : 4), st));
+      KP_TRY(copy_vec(ctx, B.rhs, B.r, N, f64));
+      KP_TRY(norm_amax_dev(ctx, B.r, N, f64, ctx->dscal + S_RR));
+      KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RMAX, ctx->dscal + S_RR, 8, cudaMemcpyDeviceToDevice, st));
+    }
+    KP_TRY(read_flags(ctx, &hf, hs));
+    double h0 = std::sqrt(hs[S_RR] / rr0);
+    KP_CUDA(cudaMemcpyAsync(ctx->hist, &h0, sizeof(double), cudaMemcpyHostToDevice, st));
+    final_rr = hs[S_RR];
+    if (hs[S_RR] <= tol * tol * rr0) {
+      result = KP_OK;
+    } else {
+      // z0 = M^-1 r0, zr, p0 = z0
+      KP_TRY(pc_apply(ctx, B.r, B.z, lam2, ctx->dscal + S_RR, nullptr));
+      KP_TRY(dot2_dev(ctx, B.z, B.r, nullptr, N, f64, ctx->dscal + S_ZR, nullptr));
+      const int sl = op_inner_slices(ctx);
+      KP_TRY(p_update_dev(ctx, B.p, B.z, N, f64, nullptr, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N,
+                          nullptr));
+      // capture one block of iterations
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      const int blk = std::max(1, ctx->check_every);
+      long long l0 = ctx->launches;
+      KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      kp_status cs = KP_OK;
+      for (int i = 0; i < blk && cs == KP_OK; ++i) {
+        cs = half_a(ctx, B, x, lam2);
+        if (cs == KP_OK) cs = half_b(ctx, B, lam2);
+      }
+      cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      const long long per_block = ctx->launches - l0;
+      ctx->launches = l0;
+      if (cs != KP_OK) return cs;
+      if (ce != cudaSuccess) {
+        kp_set_error("tik_pcg: graph capture failed: %s", cudaGetErrorString(ce));
+        return KP_ECUDA;
+      }
+      KP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      bool done = false;
+      while (!done) {
+        KP_CUDA(cudaGraphLaunch(exec, st));
+        ctx->launches += per_block;
+        KP_TRY(read_flags(ctx, &hf, hs));
+        if (!hf.pause) continue;
+        iters = hf.iter;
+        final_rr = hs[S_RR];
+        if (hf.reason & R_NUMERIC) {
+          kp_set_error("tik_pcg: NaN / Inf at iteration %d", iters);
+          result = KP_ENUMERIC;
+          break;
+        }
+        if (hf.reason & R_BREAKDOWN) {
+          kp_set_error("tik_pcg: breakdown (p^T K p <= 0 or z^T r <= 0) at iteration %d", iters);
+          result = KP_EBREAKDOWN;
+          break;
+        }
+        bool need_replace = reliable && (hf.reason & (R_CONV | R_REPLACE | R_MAXIT));
+        if (need_replace) {
+          KP_TRY(replace_residual(ctx, B, b, x, lam2));
+          ++repl;
+          KP_TRY(read_flags(ctx, &hf, hs));
+          final_rr = hs[S_RR];
+          double hv = std::sqrt(final_rr / rr0);
+          if (iters < ctx->hist_cap)
+            KP_CUDA(cudaMemcpyAsync(ctx->hist + iters, &hv, sizeof(double), cudaMemcpyHostToDevice, st));
+          KP_CUDA(cudaStreamSynchronize(st));
+          if (final_rr <= tol * tol * rr0) {
+            result = KP_OK;
+            break;
+          }
+        } else if (hf.reason & R_CONV) {
+          result = KP_OK;
+          break;
+        }
+        if (hf.reason & R_MAXIT) {
+          result = KP_ENOCONV;
+          kp_set_error("tik_pcg: maxit %d reached, ||r||/||A^T b|| = %.3e", maxit, std::sqrt(final_rr / rr0));
+          break;
+        }
+        // resume: clear the pause, finish the interrupted iteration, continue
+        int zero2[2] = {0, 0};
+        KP_CUDA(cudaMemcpyAsync(ctx->dflags, zero2, sizeof(zero2), cudaMemcpyHostToDevice, st));
+        KP_TRY(half_b(ctx, B, lam2));
+        KP_CUDA(cudaStreamSynchronize(st));
+      }
+      cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
+    }
+  }
+  KP_CUDA(cudaEventRecord(e1, st));
+  KP_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  kp_status dst = read_status(ctx);
+  if (dst != KP_OK) result = dst;
+  if (info) {
+    info->iters = iters;
+    info->replacements = repl;
+    info->rel_res = rr0 > 0 ? std::sqrt(final_rr / rr0) : 0.0;
+    info->status = result;
+    info->ms_solve = ms;
+    if (info->res_hist && info->res_hist_len > 0) {
+      int n = std::min(info->res_hist_len, std::min(iters + 1, ctx->hist_cap));
+      KP_CUDA(cudaMemcpy(info->res_hist, ctx->hist, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    }
+  }
+  return result;
+}
+
+extern "C" kp_status tik_pcg(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible, void* x,
+                             int warm_start, kp_solve_info* info) {
+  KP_TRY(kp_check_ready(ctx));
+  if (!b || !x || ((uintptr_t)b & 15) || ((uintptr_t)x & 15)) {
+    kp_set_error("tik_pcg: b and x must be non-NULL, 16-byte aligned device pointers");
+    return KP_EINVAL;
+  }
+  if (!(lambda > 0.0) || !std::isfinite(lambda) || !(tol >= 0.0) || maxit < 1) {
+    kp_set_error("tik_pcg: need lambda > 0, tol >= 0, maxit >= 1");
+    return KP_EINVAL;
+  }
+  KP_TRY(kp_enter(ctx));
+  kp_status s = tik_pcg_impl(ctx, b, lambda, tol, maxit, flexible, x, warm_start, info);
+  kp_status l = kp_leave(ctx);
+  return s != KP_OK ? s : l;
+}
+
+// ---------------------------------------------------------------- operator hooks
+extern "C" kp_status kp_apply_A(kp_ctx* ctx, const void* x, void* y, int transpose) {
+  KP_TRY(kp_check_ready(ctx));
+  if (!x || !y || x == y) {
+    kp_set_error("kp_apply_A: x and y must be distinct device pointers");
+    return KP_EINVAL;
+  }
+  KP_TRY(kp_enter(ctx));
+  KP_TRY(op_apply(ctx, x, y, transpose ? 1 : 0, OP_INNER));
+  return kp_leave(ctx);
+}
+
+extern "C" kp_status kp_apply_K(kp_ctx* ctx, const void* x, void* y, double lambda) {
+  KP_TRY(kp_check_ready(ctx));
+  if (!x || !y || x == y) {
+    kp_set_error("kp_apply_K: x and y must be distinct device pointers");
+    return KP_EINVAL;
+  }
+  KP_TRY(kp_enter(ctx));
+  KP_TRY(op_apply_K(ctx, x, y, lambda * lambda, false, nullptr));
+  return kp_leave(ctx);
+}
+
+extern "C" kp_status kp_apply_Minv(kp_ctx* ctx, const void* r, void* z, double lambda) {
+  KP_TRY(kp_check_ready(ctx));
+  if (!r || !z || r == z || !(lambda > 0.0)) {
+    kp_set_error("kp_apply_Minv: need distinct device pointers and lambda > 0");
+    return KP_EINVAL;
+  }
+  KP_TRY(kp_enter(ctx));
+  KP_TRY(pc_apply(ctx, r, z, lambda * lambda, nullptr, nullptr));
+  return kp_leave(ctx);
+}
+
+// observed data b = A x + nl ||A x|| g / ||g|| (accurate operator)
+extern "C" kp_status kp_forward(kp_ctx* ctx, const void* x, const void* g, double noise_level, void* b,
+                                double* noise_norm) {
+  KP_TRY(kp_check_ready(ctx));
+  if (!x || !g || !b || !(noise_level >= 0.0)) {
+    kp_set_error("kp_forward: bad arguments");
+    return KP_EINVAL;
+  }
+  KP_TRY(kp_enter(ctx));
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  const bool f64 = ctx->vec_prec == KP_F64;
+  KP_TRY(op_apply(ctx, x, b, 0, OP_ACCURATE));
+  KP_TRY(dot2_dev(ctx, b, b, nullptr, N, f64, ctx->dscal + 20, nullptr));
+  KP_TRY(dot2_dev(ctx, g, g, nullptr, N, f64, ctx->dscal + 21, nullptr));
+  double h[2];
+  KP_CUDA(cudaMemcpyAsync(h, ctx->dscal + 20, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  const double scale = h[1] > 0 ? noise_level * std::sqrt(h[0]) / std::sqrt(h[1]) : 0.0;
+  KP_TRY(axpby_dev(ctx, g, b, N, f64, scale, 1.0));
+  if (noise_norm) *noise_norm = scale * std::sqrt(h[1]);
+  return kp_leave(ctx);
+}

@@ -1,0 +1,349 @@
+// Vector kernels of the (F)PCG loop and helper reductions.
+//
+// Every inner product and norm is accumulated in FP64 as a tree: per-thread
+// partial sums, warp shuffles, a block reduction, per-block partials, and a
+// final ordered reduction by the last block to finish.  The result does not
+// depend on block scheduling.  This is the GPU form of the pairwise
+// summation the paper uses to limit rounding-error growth in inner products
+// (Section 4).
+#include "kp_vec.cuh"
+
+namespace kpv {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-level reduction of NV sums (+ optional max in slot NV-1 when
+// last_is_max) and the cross-block ordered finish.  blockDim.x == VEC_THREADS.
+template <int NV>
+__device__ void reduce_finish(double (&v)[NV], bool last_is_max, double* partials, unsigned int* counter,
+                              double* out, int nout) {
+  __shared__ double sh[VEC_THREADS / 32][NV];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const bool mx = last_is_max && i == NV - 1;
+    v[i] = mx ? warp_max(v[i]) : warp_sum(v[i]);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[wid][i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NV; ++i) {
+      const bool mx = last_is_max && i == NV - 1;
+      double t = sh[0][i];
+      for (int w = 1; w < VEC_THREADS / 32; ++w) t = mx ? fmax(t, sh[w][i]) : t + sh[w][i];
+      partials[blockIdx.x * NV + i] = t;
+    }
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += VEC_THREADS) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const bool mx = last_is_max && i == NV - 1;
+      double pv = ((volatile double*)partials)[b * NV + i];
+      acc[i] = mx ? fmax(acc[i], pv) : acc[i] + pv;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const bool mx = last_is_max && i == NV - 1;
+    acc[i] = mx ? warp_max(acc[i]) : warp_sum(acc[i]);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[wid][i] = acc[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nout; ++i) {
+      const bool mx = last_is_max && i == NV - 1;
+      double t = sh[0][i];
+      for (int w = 1; w < VEC_THREADS / 32; ++w) t = mx ? fmax(t, sh[w][i]) : t + sh[w][i];
+      out[i] = t;
+    }
+    *counter = 0u;
+  }
+}
+
+__device__ __forceinline__ bool paused(const int* flags) { return flags != nullptr && *(volatile const int*)flags != 0; }
+
+// ------------------------------------------------------------- dot products
+// out[0] = a.b ; if c != null, out[1] = a.c
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS) k_dot2(const T* __restrict__ a, const T* __restrict__ b,
+                                                      const T* __restrict__ c, long long n, double* partials,
+                                                      unsigned int* counter, double* out, const int* flags) {
+  if (paused(flags)) return;
+  double v[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)VEC_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * VEC_THREADS) {
+    double ai = (double)a[i];
+    v[0] = fma(ai, (double)b[i], v[0]);
+    if (c) v[1] = fma(ai, (double)c[i], v[1]);
+  }
+  reduce_finish<2>(v, false, partials, counter, out, c ? 2 : 1);
+}
+
+// y = alpha*x + beta*y (scalars from host); used by setup / hooks
+template <typename T>
+__global__ void k_axpby(const T* __restrict__ x, T* __restrict__ y, long long n, double alpha, double beta) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (T)(alpha * (double)x[i] + beta * (double)y[i]);
+}
+
+// ------------------------------------------------------------- PCG updates
+// x += alpha p ; r_old = r ; r -= alpha q ; out: rr = ||r||^2, amax(r)
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T* __restrict__ r,
+                                                           T* __restrict__ r_old, const T* __restrict__ p,
+                                                           const T* __restrict__ q, long long n,
+                                                           const double* __restrict__ alpha_dev, double* partials,
+                                                           unsigned int* counter, double* out, const int* flags) {
+  if (paused(flags)) return;
+  const double alpha = *alpha_dev;
+  double v[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)VEC_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * VEC_THREADS) {
+    T ri = r[i];
+    x[i] = (T)((double)x[i] + alpha * (double)p[i]);
+    r_old[i] = ri;
+    T rn = (T)((double)ri - alpha * (double)q[i]);
+    r[i] = rn;
+    double d = (double)rn;
+    v[0] = fma(d, d, v[0]);
+    v[1] = fmax(v[1], fabs(d));
+  }
+  reduce_finish<2>(v, true, partials, counter, out, 2);
+}
+
+// p = z + beta p ; optional bf16 split copy of p (slices written at stride)
+template <typename T>
+__global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long n, const double* __restrict__ beta_dev,
+                           __nv_bfloat16* __restrict__ ps, int slices, long long sstride, const int* flags) {
+  if (paused(flags)) return;
+  const double beta = beta_dev ? *beta_dev : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    T pn = (T)((double)z[i] + beta * (double)p[i]);
+    p[i] = pn;
+    if (ps) {
+      float v = (float)pn;
+      for (int s = 0; s < slices; ++s) {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        ps[s * sstride + i] = h;
+        v -= __bfloat162float(h);
+      }
+    }
+  }
+}
+
+// bf16 slices of a vector (x -> hi, mid, lo)
+template <typename T>
+__global__ void k_split(const T* __restrict__ x, long long n, __nv_bfloat16* __restrict__ out, int slices,
+                        long long sstride) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float v = (float)x[i];
+    for (int s = 0; s < slices; ++s) {
+      __nv_bfloat16 h = __float2bfloat16_rn(v);
+      out[s * sstride + i] = h;
+      v -= __bfloat162float(h);
+    }
+  }
+}
+
+// Quantise r for the reduced-precision preconditioner: out = narrow(r * 2^e)
+// with 2^e chosen from amax(r) (stat[1]) so that amax * 2^e lies in
+// [target/2, target); writes inv_out = 1 / (lam2 * 2^e) for the last GEMM.
+__device__ __forceinline__ float pow2_scale(double amax, double target) {
+  if (!(amax > 0.0) || !isfinite(amax)) return 1.f;
+  int e;
+  frexp(target / amax, &e);  // target/amax = m 2^e, m in [0.5, 1)
+  return (float)ldexp(1.0, e - 1);
+}
+template <typename T, typename N>
+__global__ void k_quantize(const T* __restrict__ r, long long n, const double* __restrict__ stat, double target,
+                           double lam2, N* __restrict__ out, float* __restrict__ inv_out, const int* flags) {
+  if (paused(flags)) return;
+  const float s = pow2_scale(stat[1], target);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *inv_out = (float)(1.0 / (lam2 * (double)s));
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = to_narrow<N>((float)r[i] * s);
+}
+
+// amax only (for one-off applies outside the loop)
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS) k_norm_amax(const T* __restrict__ x, long long n, double* partials,
+                                                           unsigned int* counter, double* out) {
+  double v[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)VEC_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * VEC_THREADS) {
+    double d = (double)x[i];
+    v[0] = fma(d, d, v[0]);
+    v[1] = fmax(v[1], fabs(d));
+  }
+  reduce_finish<2>(v, true, partials, counter, out, 2);
+}
+
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (B)x[i];
+}
+
+}  // namespace kpv
+
+// ------------------------------------------------------------- host wrappers
+using namespace kpv;
+
+int vec_grid(kp_ctx* ctx, long long n) {
+  long long b = (n + VEC_THREADS * 4 - 1) / (VEC_THREADS * 4);
+  long long cap = (long long)ctx->sm_count * 4;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+kp_status dot2_dev(kp_ctx* ctx, const void* a, const void* b, const void* c, long long n, bool f64, double* out,
+                   const int* flags) {
+  int g = vec_grid(ctx, n);
+  if (f64)
+    k_dot2<double><<<g, VEC_THREADS, 0, ctx->stream>>>((const double*)a, (const double*)b, (const double*)c, n,
+                                                       ctx->red_part, ctx->red_count, out, flags);
+  else
+    k_dot2<float><<<g, VEC_THREADS, 0, ctx->stream>>>((const float*)a, (const float*)b, (const float*)c, n,
+                                                      ctx->red_part, ctx->red_count, out, flags);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+kp_status dot_dev(kp_ctx* ctx, const void* x, const void* y, long long n, bool f64, double* out_dev) {
+  return dot2_dev(ctx, x, y, nullptr, n, f64, out_dev, nullptr);
+}
+
+kp_status norm_amax_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out2) {
+  int g = vec_grid(ctx, n);
+  if (f64)
+    k_norm_amax<double><<<g, VEC_THREADS, 0, ctx->stream>>>((const double*)x, n, ctx->red_part, ctx->red_count, out2);
+  else
+    k_norm_amax<float><<<g, VEC_THREADS, 0, ctx->stream>>>((const float*)x, n, ctx->red_part, ctx->red_count, out2);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+kp_status norm2_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out_dev) {
+  return dot2_dev(ctx, x, x, nullptr, n, f64, out_dev, nullptr);
+}
+
+kp_status update_xr_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* p, const void* q, long long n,
+                        bool f64, const double* alpha_dev, double* out2, const int* flags) {
+  int g = vec_grid(ctx, n);
+  if (f64)
+    k_update_xr<double><<<g, VEC_THREADS, 0, ctx->stream>>>((double*)x, (double*)r, (double*)r_old, (const double*)p,
+                                                            (const double*)q, n, alpha_dev, ctx->red_part,
+                                                            ctx->red_count, out2, flags);
+  else
+    k_update_xr<float><<<g, VEC_THREADS, 0, ctx->stream>>>((float*)x, (float*)r, (float*)r_old, (const float*)p,
+                                                           (const float*)q, n, alpha_dev, ctx->red_part,
+                                                           ctx->red_count, out2, flags);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+kp_status p_update_dev(kp_ctx* ctx, void* p, const void* z, long long n, bool f64, const double* beta_dev,
+                       __nv_bfloat16* ps, int slices, long long sstride, const int* flags) {
+  int g = vec_grid(ctx, n);
+  if (f64)
+    k_p_update<double><<<g, VEC_THREADS, 0, ctx->stream>>>((double*)p, (const double*)z, n, beta_dev, ps, slices,
+                                                           sstride, flags);
+  else
+    k_p_update<float><<<g, VEC_THREADS, 0, ctx->stream>>>((float*)p, (const float*)z, n, beta_dev, ps, slices,
+                                                          sstride, flags);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+kp_status split_bf16(kp_ctx* ctx, const void* x, bool f64, long long n, void* out, int slices, long long sstride) {
+  int g = vec_grid(ctx, n);
+  if (f64)
+    k_split<double><<<g, VEC_THREADS, 0, ctx->stream>>>((const double*)x, n, (__nv_bfloat16*)out, slices, sstride);
+  else
+    k_split<float><<<g, VEC_THREADS, 0, ctx->stream>>>((const float*)x, n, (__nv_bfloat16*)out, slices, sstride);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+kp_status quantize_dev(kp_ctx* ctx, const void* r, long long n, bool f64, const double* stat, int narrow,
+                       double lam2, void* out, float* inv_out, const int* flags) {
+  int g = vec_grid(ctx, n);
+  double target = narrow == NT_E4M3 ? 448.0 : 1.0;
+  if (f64) {
+    kp_set_error("reduced-precision preconditioner needs FP32 vectors");
+    return KP_ENOTSUP;
+  }
+  const float* rf = (const float*)r;
+  if (narrow == NT_BF16)
+    k_quantize<float, __nv_bfloat16><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, stat, target, lam2,
+                                                                          (__nv_bfloat16*)out, inv_out, flags);
+  else if (narrow == NT_F16)
+    k_quantize<float, __half><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, stat, target, lam2, (__half*)out, inv_out,
+                                                                   flags);
+  else
+    k_quantize<float, __nv_fp8_e4m3><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, stat, target, lam2,
+                                                                          (__nv_fp8_e4m3*)out, inv_out, flags);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+kp_status copy_vec(kp_ctx* ctx, const void* x, void* y, long long n, bool f64) {
+  KP_CUDA(cudaMemcpyAsync(y, x, n * (f64 ? 8 : 4), cudaMemcpyDeviceToDevice, ctx->stream));
+  return KP_OK;
+}
+
+kp_status axpby_dev(kp_ctx* ctx, const void* x, void* y, long long n, bool f64, double alpha, double beta) {
+  int g = vec_grid(ctx, n);
+  if (f64)
+    k_axpby<double><<<g, VEC_THREADS, 0, ctx->stream>>>((const double*)x, (double*)y, n, alpha, beta);
+  else
+    k_axpby<float><<<g, VEC_THREADS, 0, ctx->stream>>>((const float*)x, (float*)y, n, alpha, beta);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+kp_status convert_f64_to_f32(kp_ctx* ctx, const double* x, float* y, long long n) {
+  int g = vec_grid(ctx, n);
+  k_convert<double, float><<<g, VEC_THREADS, 0, ctx->stream>>>(x, y, n);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+kp_status convert_f32_to_f64(kp_ctx* ctx, const float* x, double* y, long long n) {
+  int g = vec_grid(ctx, n);
+  k_convert<float, double><<<g, VEC_THREADS, 0, ctx->stream>>>(x, y, n);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}

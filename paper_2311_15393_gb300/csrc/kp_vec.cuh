@@ -1,0 +1,28 @@
+// Shared declarations of the vector kernels (kp_vec.cu).
+#pragma once
+#include "kp_internal.h"
+
+constexpr int VEC_THREADS = 256;
+
+template <typename N>
+__device__ __forceinline__ N to_narrow(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_narrow<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_narrow<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_fp8_e4m3 to_narrow<__nv_fp8_e4m3>(float v) { return __nv_fp8_e4m3(v); }
+
+int vec_grid(kp_ctx* ctx, long long n);
+kp_status dot2_dev(kp_ctx* ctx, const void* a, const void* b, const void* c, long long n, bool f64, double* out,
+                   const int* flags);
+kp_status norm_amax_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out2);
+kp_status update_xr_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* p, const void* q, long long n,
+                        bool f64, const double* alpha_dev, double* out2, const int* flags);
+kp_status p_update_dev(kp_ctx* ctx, void* p, const void* z, long long n, bool f64, const double* beta_dev,
+                       __nv_bfloat16* ps, int slices, long long sstride, const int* flags);
+kp_status quantize_dev(kp_ctx* ctx, const void* r, long long n, bool f64, const double* stat, int narrow,
+                       double lam2, void* out, float* inv_out, const int* flags);
+kp_status axpby_dev(kp_ctx* ctx, const void* x, void* y, long long n, bool f64, double alpha, double beta);
+kp_status convert_f64_to_f32(kp_ctx* ctx, const double* x, float* y, long long n);
+kp_status convert_f32_to_f64(kp_ctx* ctx, const float* x, double* y, long long n);

@@ -1,0 +1,221 @@
+"""ctypes binding of libkpsvd.so (include/kpsvd.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device images are torch CUDA tensors holding vec(X), i.e. the
+column-major n_r x n_c image (``to_device`` / ``from_device`` convert numpy
+arrays).  The library must have been built (``paper_2311_15393_gb300.build``);
+importing this module raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libkpsvd.so")
+
+KP_OK, KP_EINVAL, KP_ENOMEM, KP_ECUDA, KP_ENOTSUP, KP_ENOCONV, KP_EBREAKDOWN, KP_ENUMERIC, KP_ENOROOT, \
+    KP_ETIMEOUT, KP_ESTATE = range(11)
+BC = {"zero": 0, "reflexive": 1}
+PREC = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "f16": 4, "e4m3": 5}
+SIGMA = {"product": 0, "projected": 1}
+LAMBDA = {"gcv": 0, "wgcv": 1, "discrepancy": 2, "opt": 3}
+
+# every function declared in include/kpsvd.h
+EXPORTS = ["kp_create", "kp_destroy", "kp_setup", "kp_forward", "tik_pcg", "choose_lambda", "kp_apply_A",
+           "kp_apply_K", "kp_apply_Minv", "kp_get_spectrum", "kp_get_terms", "kp_get_kpsvd", "kp_get_rank",
+           "kp_set_option", "kp_launch_count", "kp_status_str", "kp_last_error"]
+
+
+class KpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("replacements", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("status", ctypes.c_int), ("ms_solve", ctypes.c_double),
+                ("res_hist", ctypes.POINTER(ctypes.c_double)), ("res_hist_len", ctypes.c_int)]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libkpsvd.so not built ({path}); run python -m paper_2311_15393_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "kp_create": ([ctypes.POINTER(vp), i, vp], i),
+        "kp_destroy": ([vp], None),
+        "kp_setup": ([vp, vp, i, i, i, i, i, i, i, i, i, i], i),
+        "kp_forward": ([vp, vp, vp, d, vp, dp], i),
+        "tik_pcg": ([vp, vp, d, d, i, i, vp, i, ctypes.POINTER(SolveInfo)], i),
+        "choose_lambda": ([vp, vp, i, d, vp, dp], i),
+        "kp_apply_A": ([vp, vp, vp, i], i),
+        "kp_apply_K": ([vp, vp, vp, d], i),
+        "kp_apply_Minv": ([vp, vp, vp, d], i),
+        "kp_get_spectrum": ([vp, dp], i),
+        "kp_get_terms": ([vp, dp, dp, dp], i),
+        "kp_get_kpsvd": ([vp, dp, dp, dp, dp, dp, dp], i),
+        "kp_get_rank": ([vp, ctypes.POINTER(i)], i),
+        "kp_set_option": ([vp, ctypes.c_char_p, d], i),
+        "kp_launch_count": ([vp, i], ctypes.c_longlong),
+        "kp_status_str": ([i], ctypes.c_char_p),
+        "kp_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = load_library()
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _check(status: int):
+    if status != KP_OK:
+        msg = _lib.kp_last_error().decode()
+        raise KpError(status, f"{_lib.kp_status_str(status).decode()}: {msg}")
+
+
+def _dptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def to_device(X: np.ndarray, dtype=None, device: str = "cuda:0"):
+    """numpy n_r x n_c image -> torch CUDA vector vec(X) (column stacking)."""
+    import torch
+    dtype = dtype or torch.float64
+    v = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, order="F"))
+    return torch.from_numpy(v).to(device=device, dtype=dtype)
+
+
+def from_device(t, n_r: int, n_c: int) -> np.ndarray:
+    return t.detach().to("cpu").double().numpy().reshape((n_r, n_c), order="F")
+
+
+@dataclass
+class Info:
+    iters: int
+    replacements: int
+    rel_res: float
+    status: int
+    ms_solve: float
+    res_hist: np.ndarray
+
+
+class KpContext:
+    """Owns one kp_ctx.  All methods mirror the C ABI."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = ctypes.c_void_p()
+        _check(_lib.kp_create(ctypes.byref(h), device, stream))
+        self._h = h
+        self.n_r = self.n_c = 0
+        self.vec = "f64"
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.kp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- setup / solve -------------------------------------------------------------
+    def kp_setup(self, psf_dev, n_r: int, n_c: int, center, bc: str = "reflexive", op_rank: int = 0,
+                 op_prec: str = "f64", pc_prec: str = "f64", vec_prec: str = "f64", sigma: str = "projected"):
+        _check(_lib.kp_setup(self._h, _ptr(psf_dev), n_r, n_c, int(center[0]), int(center[1]), BC[bc], op_rank,
+                             PREC[op_prec], PREC[pc_prec], PREC[vec_prec], SIGMA[sigma]))
+        self.n_r, self.n_c, self.vec = n_r, n_c, vec_prec
+
+    def kp_forward(self, x, g, noise_level: float, b) -> float:
+        nn = ctypes.c_double(0.0)
+        _check(_lib.kp_forward(self._h, _ptr(x), _ptr(g), noise_level, _ptr(b), ctypes.byref(nn)))
+        return nn.value
+
+    def tik_pcg(self, b, lam: float, tol: float, maxit: int, flexible: bool, x, warm_start: bool = False,
+                hist_len: int = 0, check: bool = True) -> Info:
+        info = SolveInfo()
+        hist = np.zeros(max(hist_len, 0), dtype=np.float64)
+        if hist_len > 0:
+            info.res_hist = _dptr(hist)
+            info.res_hist_len = hist_len
+        st = _lib.tik_pcg(self._h, _ptr(b), lam, tol, maxit, 1 if flexible else 0, _ptr(x), 1 if warm_start else 0,
+                          ctypes.byref(info))
+        if check and st not in (KP_OK,):
+            _check(st)
+        n = min(hist_len, info.iters + 1) if hist_len > 0 else 0
+        return Info(info.iters, info.replacements, info.rel_res, st, info.ms_solve, hist[:n])
+
+    def choose_lambda(self, b, method: str, param: float = 0.0, x_true=None) -> float:
+        lam = ctypes.c_double(0.0)
+        _check(_lib.choose_lambda(self._h, _ptr(b), LAMBDA[method], param, _ptr(x_true), ctypes.byref(lam)))
+        return lam.value
+
+    # -- hooks ---------------------------------------------------------------------
+    def kp_apply_A(self, x, y, transpose: bool = False):
+        _check(_lib.kp_apply_A(self._h, _ptr(x), _ptr(y), 1 if transpose else 0))
+
+    def kp_apply_K(self, x, y, lam: float):
+        _check(_lib.kp_apply_K(self._h, _ptr(x), _ptr(y), lam))
+
+    def kp_apply_Minv(self, r, z, lam: float):
+        _check(_lib.kp_apply_Minv(self._h, _ptr(r), _ptr(z), lam))
+
+    def kp_get_rank(self) -> int:
+        r = ctypes.c_int(0)
+        _check(_lib.kp_get_rank(self._h, ctypes.byref(r)))
+        return r.value
+
+    def kp_get_spectrum(self) -> np.ndarray:
+        s = np.zeros(self.n_r * self.n_c)
+        _check(_lib.kp_get_spectrum(self._h, _dptr(s)))
+        return s.reshape((self.n_r, self.n_c), order="F")
+
+    def kp_get_terms(self):
+        r = self.kp_get_rank()
+        s, u, v = np.zeros(r), np.zeros(self.n_r * r), np.zeros(self.n_c * r)
+        _check(_lib.kp_get_terms(self._h, _dptr(s), _dptr(u), _dptr(v)))
+        return s, u.reshape((self.n_r, r), order="F"), v.reshape((self.n_c, r), order="F")
+
+    def kp_get_kpsvd(self):
+        nr, nc = self.n_r, self.n_c
+        sr, Ur, Vr = np.zeros(nc), np.zeros(nc * nc), np.zeros(nc * nc)
+        sc, Uc, Vc = np.zeros(nr), np.zeros(nr * nr), np.zeros(nr * nr)
+        _check(_lib.kp_get_kpsvd(self._h, _dptr(sr), _dptr(Ur), _dptr(Vr), _dptr(sc), _dptr(Uc), _dptr(Vc)))
+        f = lambda a, n: a.reshape((n, n), order="F")  # noqa: E731
+        return dict(sr=sr, Ur=f(Ur, nc), Vr=f(Vr, nc), sc=sc, Uc=f(Uc, nr), Vc=f(Vc, nr))
+
+    def kp_set_option(self, name: str, value: float):
+        _check(_lib.kp_set_option(self._h, name.encode(), float(value)))
+
+    def kp_launch_count(self, reset: bool = False) -> int:
+        return int(_lib.kp_launch_count(self._h, 1 if reset else 0))

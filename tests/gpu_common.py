@@ -1,0 +1,101 @@
+"""Shared helpers of the GPU parity tests (test infrastructure: builds oracle
+problems and the reduced-precision emulation of the tensor-core path)."""
+import numpy as np
+import pytest
+
+from oracle import forward, kpsvd as okp, kron, lowprec as lp
+from paper_2311_15393_gb300 import synth
+
+torch = pytest.importorskip("torch")
+
+
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def lib():
+    need_gpu()
+    from paper_2311_15393_gb300 import build
+    build.build()
+    from paper_2311_15393_gb300 import kpsvd
+    return kpsvd
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+class OracleProblem:
+    """Oracle-side view of a synthetic problem."""
+
+    def __init__(self, name, n=None, psf=None, center=None, bc=None, rank=None, noise_idx=0, shape=None, seed=None):
+        P = synth.make_problem(name, n=n, seed=seed)
+        if shape is not None:   # rectangular variant: crop image / re-sample PSF
+            n_r, n_c = shape
+            c = center or (n_r // 2, n_c // 2)
+            P.x_true = P.x_true[:n_r, :n_c]
+            P.psf = synth.gaussian_psf(n_r, n_c, c[0], c[1], P.extra["sigma_x"], P.extra["sigma_y"], P.extra["rho"])
+            P.noise_dirs = [g[:n_r, :n_c] for g in P.noise_dirs]
+            P.n_r, P.n_c, P.center = n_r, n_c, c
+        if psf is not None:
+            P.psf = psf
+        if center is not None:
+            P.center = center
+        if bc is not None:
+            P.bc = bc
+        if rank is not None:
+            P.op_rank = rank
+        self.P = P
+        self.op = kron.kron_operator(P.psf, P.center, P.bc, P.op_rank)
+        self.kp = okp.kp_svd(self.op, "projected")
+        self.B, self.enorm = forward.observe(self.op, P.x_true, P.noise_dirs[noise_idx], P.noise_levels[noise_idx])
+
+
+def setup_ctx(kpsvd, prob: OracleProblem, op_prec, pc_prec, vec_prec, sigma="projected"):
+    P = prob.P
+    ctx = kpsvd.KpContext(0)
+    psf = kpsvd.to_device(P.psf)
+    ctx.kp_setup(psf, P.n_r, P.n_c, P.center, P.bc, P.op_rank, op_prec, pc_prec, vec_prec, sigma)
+    torch.cuda.synchronize()
+    return ctx
+
+
+def vt(vec_prec):
+    return torch.float64 if vec_prec == "f64" else torch.float32
+
+
+# ---------------------------------------------------------------- emulation
+def bf(x):
+    return lp.to_bf16(x)
+
+
+def emulate_apply_A_bf16(op, X):
+    """Tensor-core inner operator with one bf16 slice: factors and activations
+    rounded to bf16, products summed exactly, outputs of each GEMM rounded to
+    fp32 and (intermediate) to bf16."""
+    Xb = bf(lp.to_fp32(X))
+    W = [bf(lp.to_fp32(bf(Ac) @ Xb)) for Ac in op.Ac]
+    return lp.to_fp32(sum(Wk @ bf(Ar).T for Wk, Ar in zip(W, op.Ar)))
+
+
+def emulate_minv(kp, Sigma, R, lam, fmt):
+    """Reduced-precision preconditioner solve with the GPU's rounding points:
+    R scaled by 2^e (amax(R) 2^e in [1/2, 1)) and rounded; each GEMM output
+    rounded to fp32 then to the narrow format; S applied as
+    lam^2 / (Sigma^2 + lam^2) in the P2 output; 1 / (lam^2 2^e) at the end."""
+    rd = lp.ROUND[fmt]
+    am = np.max(np.abs(lp.to_fp32(R)))
+    m, e = np.frexp(1.0 / am)
+    s = np.ldexp(1.0, e - 1)
+    Rq = rd(lp.to_fp32(R) * s)
+    Vc, Vr = rd(kp.Vc), rd(kp.Vr)
+    T1 = rd(lp.to_fp32(Vc.T @ Rq))
+    S32 = lp.to_fp32(Sigma)
+    fac = lp.to_fp32(lam * lam / (S32.astype(np.float64) ** 2 + lam * lam))
+    W = rd(lp.to_fp32(lp.to_fp32(T1 @ Vr) * fac))
+    T3 = rd(lp.to_fp32(Vc @ W))
+    inv = lp.to_fp32(1.0 / (lam * lam * s))
+    return lp.to_fp32(lp.to_fp32(T3 @ Vr.T) * inv)

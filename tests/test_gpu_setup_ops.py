@@ -1,0 +1,136 @@
+"""GPU parity of kp_setup, the operator hooks and the preconditioner solve
+against the FP64 oracle (all calls through the C ABI)."""
+import numpy as np
+import pytest
+
+from gpu_common import OracleProblem, emulate_apply_A_bf16, emulate_minv, lib, rel, setup_ctx, torch, vt
+from oracle import kpsvd as okp, kron
+from paper_2311_15393_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (workload, n, shape, bc, rank)
+    ("deblur64_fp64", None, None, "zero", 0),          # full 64 x 64 workload, full rank
+    ("deblur256_fp32", 64, None, "reflexive", 3),
+    ("deblur256_fp32", 64, (48, 40), "reflexive", 4),  # rectangular, off-centre sizes
+    ("deblur64_fp64", 64, (40, 56), "zero", 5),
+]
+
+
+@pytest.fixture(scope="module")
+def kpsvd():
+    return lib()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}-{c[2]}-{c[3]}-r{c[4]}")
+def test_setup_fp64_matches_oracle(kpsvd, case):
+    name, n, shape, bc, rank = case
+    pr = OracleProblem(name, n=n, shape=shape, bc=bc, rank=rank)
+    with setup_ctx(kpsvd, pr, "f64", "f64", "f64") as ctx:
+        s, U, V = ctx.kp_get_terms()
+        r = pr.op.rank
+        assert ctx.kp_get_rank() == r
+        keep = pr.op.s > 1e-9 * pr.op.s[0]
+        np.testing.assert_allclose(s[keep], pr.op.s[keep], rtol=1e-10)
+        for m in range(min(3, r)):
+            np.testing.assert_allclose(np.outer(U[:, m], V[:, m]), np.outer(pr.op.u[:, m], pr.op.v[:, m]),
+                                       rtol=0, atol=1e-11 * np.abs(pr.P.psf).max())
+        svd = ctx.kp_get_kpsvd()
+        np.testing.assert_allclose(svd["sr"], pr.kp.sr, rtol=0, atol=1e-12 * pr.kp.sr[0])
+        np.testing.assert_allclose(svd["sc"], pr.kp.sc, rtol=0, atol=1e-12 * pr.kp.sc[0])
+        Sg = ctx.kp_get_spectrum()
+        np.testing.assert_allclose(Sg, pr.kp.Sigma, rtol=0, atol=1e-11 * np.abs(pr.kp.Sigma).max())
+        # factor SVDs reconstruct the factors
+        A1 = pr.op.Ar[0]
+        np.testing.assert_allclose(svd["Ur"] @ np.diag(svd["sr"]) @ svd["Vr"].T, A1, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("vec", ["f64", "f32"])
+@pytest.mark.parametrize("case", CASES[1:3], ids=lambda c: f"{c[2]}-{c[3]}")
+def test_apply_A_and_K(kpsvd, case, vec):
+    name, n, shape, bc, rank = case
+    pr = OracleProblem(name, n=n, shape=shape, bc=bc, rank=rank)
+    tol = 1e-12 if vec == "f64" else 2e-6
+    with setup_ctx(kpsvd, pr, vec, vec, vec) as ctx:
+        X = synth.random_matrix(pr.P.n_r, pr.P.n_c, 7)
+        x = kpsvd.to_device(X, vt(vec))
+        y = torch.empty_like(x)
+        ctx.kp_apply_A(x, y, False)
+        assert rel(kpsvd.from_device(y, pr.P.n_r, pr.P.n_c), kron.apply_A(pr.op, X)) < tol
+        ctx.kp_apply_A(x, y, True)
+        assert rel(kpsvd.from_device(y, pr.P.n_r, pr.P.n_c), kron.apply_AT(pr.op, X)) < tol
+        ctx.kp_apply_K(x, y, 0.03)
+        assert rel(kpsvd.from_device(y, pr.P.n_r, pr.P.n_c), kron.apply_K(pr.op, X, 0.03)) < tol
+
+
+@pytest.mark.parametrize("vec", ["f64", "f32"])
+def test_apply_Minv_simt(kpsvd, vec):
+    pr = OracleProblem("deblur256_fp32", n=64, rank=3)
+    lam = 0.02
+    with setup_ctx(kpsvd, pr, vec, vec, vec) as ctx:
+        R = synth.random_matrix(64, 64, 3)
+        r = kpsvd.to_device(R, vt(vec))
+        z = torch.empty_like(r)
+        ctx.kp_apply_Minv(r, z, lam)
+        Zref = okp.precond_apply(pr.kp, okp.precond_scale(pr.kp.Sigma, lam), R)
+        assert rel(kpsvd.from_device(z, 64, 64), Zref) < (1e-11 if vec == "f64" else 1e-5)
+
+
+def test_forward_matches_oracle(kpsvd):
+    pr = OracleProblem("deblur256_fp32", n=64, rank=3)
+    with setup_ctx(kpsvd, pr, "f64", "f64", "f64") as ctx:
+        x = kpsvd.to_device(pr.P.x_true)
+        g = kpsvd.to_device(pr.P.noise_dirs[0])
+        b = torch.empty_like(x)
+        en = ctx.kp_forward(x, g, pr.P.noise_levels[0], b)
+        assert rel(kpsvd.from_device(b, 64, 64), pr.B) < 1e-12
+        assert abs(en - pr.enorm) < 1e-12 * pr.enorm
+
+
+# ------------------------------------------------------------ tensor-core paths
+@pytest.mark.parametrize("n", [64, 256])
+def test_tensor_core_operator_bf16(kpsvd, n):
+    """Inner BF16 operator (one bf16 slice): equals the bf16 emulation to FP32
+    accumulation-order error, and FP64 to bf16 rounding error."""
+    pr = OracleProblem("deblur256_fp32", n=n, rank=3)
+    with setup_ctx(kpsvd, pr, "bf16", "f16", "f32") as ctx:
+        X = synth.random_matrix(n, n, 11)
+        x = kpsvd.to_device(X, torch.float32)
+        y = torch.empty_like(x)
+        ctx.kp_apply_A(x, y, False)
+        Y = kpsvd.from_device(y, n, n)
+        assert rel(Y, emulate_apply_A_bf16(pr.op, X)) < 1e-5
+        assert rel(Y, kron.apply_A(pr.op, X)) < 2e-2
+
+
+@pytest.mark.parametrize("n", [64, 256])
+def test_tensor_core_accurate_operator(kpsvd, n):
+    """The six-product bf16 split (used for A^T b, true residuals and
+    kp_forward) is FP32-accurate."""
+    pr = OracleProblem("deblur256_fp32", n=n, rank=3)
+    with setup_ctx(kpsvd, pr, "bf16", "f16", "f32") as ctx:
+        x = kpsvd.to_device(pr.P.x_true, torch.float32)
+        g = kpsvd.to_device(pr.P.noise_dirs[0], torch.float32)
+        b = torch.empty_like(x)
+        ctx.kp_forward(x, g, pr.P.noise_levels[0], b)
+        assert rel(kpsvd.from_device(b, n, n), pr.B) < 2e-6
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+@pytest.mark.parametrize("n", [64, 256])
+def test_tensor_core_preconditioner(kpsvd, fmt, n):
+    """Reduced-precision KP-SVD solve: equals its emulation (same rounding
+    points), and for a broadband residual is within 5e-3 of FP64."""
+    pr = OracleProblem("deblur256_fp32", n=n, rank=3)
+    lam = 0.02
+    with setup_ctx(kpsvd, pr, "f32", fmt, "f32") as ctx:
+        R = synth.random_matrix(n, n, 5)
+        r = kpsvd.to_device(R, torch.float32)
+        z = torch.empty_like(r)
+        ctx.kp_apply_Minv(r, z, lam)
+        Z = kpsvd.from_device(z, n, n)
+        Zemu = emulate_minv(pr.kp, pr.kp.Sigma, R, lam, fmt)
+        assert rel(Z, Zemu) < 2e-3
+        Z64 = okp.precond_apply(pr.kp, okp.precond_scale(pr.kp.Sigma, lam), R)
+        assert rel(Z, Z64) < 5e-3

@@ -1,0 +1,139 @@
+"""GPU parity of tik_pcg (PCG / flexible PCG) and choose_lambda against the
+FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from gpu_common import OracleProblem, lib, rel, setup_ctx, torch, vt
+from oracle import forward, kpsvd as okp, kron, lam as olam, pcg as opcg
+from paper_2311_15393_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kpsvd():
+    return lib()
+
+
+def run(kpsvd, ctx, pr, lam, tol, maxit, flexible, vec, x0=None, hist=0):
+    b = kpsvd.to_device(pr.B, vt(vec))
+    x = torch.zeros_like(b) if x0 is None else kpsvd.to_device(x0, vt(vec))
+    info = ctx.tik_pcg(b, lam, tol, maxit, flexible, x, warm_start=x0 is not None, hist_len=hist, check=False)
+    return kpsvd.from_device(x, pr.P.n_r, pr.P.n_c), info
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+def test_fp64_iterates_match_oracle(kpsvd, flexible):
+    """64 x 64 FP64 workload (full-rank zero-BC operator, lambda = 0.01): the
+    iterates after k steps equal the oracle's."""
+    pr = OracleProblem("deblur64_fp64")
+    lam = pr.P.lam
+    with setup_ctx(kpsvd, pr, "f64", "f64", "f64") as ctx:
+        for k in [1, 5, 20, 50]:
+            x, info = run(kpsvd, ctx, pr, lam, 0.0, k, flexible, "f64", hist=k + 1)
+            xo, io = opcg.tik_pcg(pr.op, pr.kp, pr.B, lam, 0.0, k, flexible)
+            assert info.iters == k
+            assert rel(x, xo) < 1e-9, k
+            np.testing.assert_allclose(info.res_hist, io.res_hist, rtol=1e-7)
+
+
+def test_fp64_workload_stops_by_rule(kpsvd):
+    """50 iterations or relative residual 1e-8, whichever comes first."""
+    pr = OracleProblem("deblur64_fp64")
+    with setup_ctx(kpsvd, pr, "f64", "f64", "f64") as ctx:
+        x, info = run(kpsvd, ctx, pr, pr.P.lam, 1e-8, 50, False, "f64")
+        xo, io = opcg.tik_pcg(pr.op, pr.kp, pr.B, pr.P.lam, 1e-8, 50, False)
+        assert info.iters == io.iters
+        assert (info.status == kpsvd.KP_OK) == io.converged
+        assert rel(x, xo) < 1e-9
+
+
+def test_separable_zero_bc_converges_in_one_iteration(kpsvd):
+    n = 32
+    psf = synth.separable_psf(n, n, 16, 16, 2.5, 1.5)
+    pr = OracleProblem("deblur64_fp64", n=n, psf=psf, center=(16, 16), bc="zero", rank=1)
+    lam = 0.02
+    x_star = opcg.tik_exact_dense(pr.op, pr.B, lam)
+    with setup_ctx(kpsvd, pr, "f64", "f64", "f64") as ctx:
+        x, info = run(kpsvd, ctx, pr, lam, 1e-10, 10, False, "f64")
+        assert info.iters == 1
+        assert rel(x, x_star) < 1e-10
+
+
+@pytest.mark.parametrize("pc", ["f32", "f16", "bf16"])
+def test_fp32_operator_fixed_iterations(kpsvd, pc):
+    """256 x 256 workload, rank-3 FP32 operator: x after 10 iterations is within
+    1e-5 of the oracle's (FP32 preconditioner), and the reduced-precision
+    preconditioners stay close."""
+    pr = OracleProblem("deblur256_fp32")
+    lam = 0.03
+    with setup_ctx(kpsvd, pr, "f32", pc, "f32") as ctx:
+        x, info = run(kpsvd, ctx, pr, lam, 0.0, 10, True, "f32")
+        xo, _ = opcg.tik_pcg(pr.op, pr.kp, pr.B, lam, 0.0, 10, True)
+        assert rel(x, xo) < (1e-5 if pc == "f32" else 5e-3)
+
+
+@pytest.mark.parametrize("op", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("pc", ["f16", "bf16"])
+def test_reduced_precision_fpcg_reaches_oracle_solution(kpsvd, op, pc):
+    """256 x 256: BF16 tensor-core operator with reliable residual updates and a
+    half-precision preconditioner reaches the oracle's x_lambda to 1e-4 with
+    an iteration count within +3 of the oracle's FP64 FPCG (Section 5.2:
+    same final error, about the same iterations)."""
+    pr = OracleProblem("deblur256_fp32")
+    lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
+    tol = 1e-7
+    x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam)
+    _, io = opcg.tik_pcg(pr.op, pr.kp, pr.B, lam, tol, 500, True)
+    with setup_ctx(kpsvd, pr, op, pc, "f32") as ctx:
+        x, info = run(kpsvd, ctx, pr, lam, tol, 500, True, "f32")
+        assert info.status == kpsvd.KP_OK
+        assert rel(x, x_star) < 1e-4
+        assert info.iters <= io.iters + 3
+
+
+def test_edge_cases(kpsvd):
+    pr = OracleProblem("deblur256_fp32", n=64, rank=2)
+    with setup_ctx(kpsvd, pr, "f64", "f64", "f64") as ctx:
+        b = torch.zeros(64 * 64, dtype=torch.float64, device="cuda")
+        x = torch.ones_like(b)
+        info = ctx.tik_pcg(b, 0.1, 1e-8, 10, False, x)
+        assert info.iters == 0 and float(x.abs().max()) == 0.0
+        x, info = run(kpsvd, ctx, pr, 0.01, 1e-14, 3, False, "f64")
+        assert info.status == kpsvd.KP_ENOCONV and info.iters == 3
+        # warm start from the converged solution stops at once
+        x_star = opcg.tik_exact_dense(pr.op, pr.B, 0.05)
+        x, info = run(kpsvd, ctx, pr, 0.05, 1e-9, 10, False, "f64", x0=x_star)
+        assert info.iters <= 1 and rel(x, x_star) < 1e-9
+        with pytest.raises(kpsvd.KpError):
+            ctx.tik_pcg(b, -1.0, 1e-6, 10, False, x)
+        with pytest.raises(kpsvd.KpError):
+            ctx.kp_setup(kpsvd.to_device(pr.P.psf), 64, 64, (64, 0), "zero", 1)
+    ctx = kpsvd.KpContext(0)
+    with pytest.raises(kpsvd.KpError) as e:
+        ctx.tik_pcg(b, 0.1, 1e-6, 10, False, x)
+    assert e.value.status == kpsvd.KP_ESTATE
+    ctx.close()
+
+
+@pytest.mark.parametrize("vec", ["f64", "f32"])
+@pytest.mark.parametrize("method", ["gcv", "wgcv", "discrepancy", "opt"])
+def test_choose_lambda_matches_oracle(kpsvd, method, vec):
+    pr = OracleProblem("deblur256_fp32", n=128, rank=3)
+    param = {"gcv": 0.0, "wgcv": 3.0, "discrepancy": 1.01 * pr.enorm, "opt": 0.0}[method]
+    lo = olam.choose_lambda(pr.kp, pr.B, method, param, X_true=pr.P.x_true)
+    with setup_ctx(kpsvd, pr, vec, vec, vec) as ctx:
+        b = kpsvd.to_device(pr.B, vt(vec))
+        xt = kpsvd.to_device(pr.P.x_true, vt(vec)) if method == "opt" else None
+        lg = ctx.choose_lambda(b, method, param, xt)
+    tol = 1e-9 if (method == "discrepancy" and vec == "f64") else (1e-6 if vec == "f64" else 1e-4)
+    assert abs(np.log(lg) - np.log(lo)) < tol, (lg, lo)
+
+
+def test_discrepancy_without_root(kpsvd):
+    pr = OracleProblem("deblur256_fp32", n=64, rank=2)
+    with setup_ctx(kpsvd, pr, "f64", "f64", "f64") as ctx:
+        b = kpsvd.to_device(pr.B)
+        with pytest.raises(kpsvd.KpError) as e:
+            ctx.choose_lambda(b, "discrepancy", 2.0 * np.linalg.norm(pr.B))
+        assert e.value.status == kpsvd.KP_ENOROOT
