@@ -61,7 +61,8 @@ typedef enum { KP_BC_ZERO = 0, KP_BC_REFLEXIVE = 1 } kp_bc;
  *   KP_F32   FP32 SIMT kernels
  *   KP_BF16  tcgen05 BF16 x BF16 -> FP32 (operator: one product per GEMM,
  *            with reliable residual updates through an FP32-accurate
- *            six-product split; preconditioner: plain BF16)
+ *            six-product split; preconditioner: bf16 activations, factors
+ *            V_c, V_r carried as bf16 hi + lo pairs)
  *   KP_BF16X3 tcgen05, operands split into bf16 hi + lo, three products
  *   KP_F16   tcgen05 FP16 x FP16 -> FP32 (preconditioner)
  *   KP_E4M3  tcgen05 FP8 E4M3 x E4M3 -> FP32 with power-of-two per-tensor
@@ -135,10 +136,10 @@ kp_status kp_forward(kp_ctx* ctx, const void* x, const void* g, double noise_lev
  *   b        device, vec type, n_r x n_c
  *   x        device, vec type, n_r x n_c; input when warm_start != 0, output
  *   info     host, nullable
- * With a reduced-precision operator the residual is replaced by the true
- * residual A^T (b - A x) - lambda^2 x, computed with an FP32-accurate
- * operator, whenever ||r|| has fallen by the reliable-update factor since the
- * last replacement, and always before convergence is declared. */
+ * With an operator below FP64 the residual is replaced by the true residual
+ * A^T (b - A x) - lambda^2 x, computed with an FP32-accurate operator,
+ * whenever ||r|| has fallen by the reliable-update factor since the last
+ * replacement, and always before convergence is declared. */
 kp_status tik_pcg(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible,
                   void* x, int warm_start, kp_solve_info* info);
 
@@ -183,8 +184,8 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
 
 /* Tuning knobs (name = value); unknown names return KP_EINVAL.
  *   "reliable_delta"  factor by which ||r|| must fall before a reliable
- *                     residual update (default 0.1 for BF16 operators, 0 = off
- *                     for F64 / F32 operators)
+ *                     residual update (default 0.1 for F32 / BF16 / BF16X3
+ *                     operators, 0 = off for the F64 operator)
  *   "check_every"     iterations between host convergence checks (default 4)
  *   "jacobi_tol"      one-sided Jacobi rotation threshold (default 1e-15)
  *   "jacobi_max_sweeps" (default 40) */

@@ -113,7 +113,7 @@ struct kp_ctx {
   // options
   double reliable_delta = -1.0;  // < 0: default for the operator precision
   int check_every = 4;
-  double jacobi_tol = 1e-15;
+  double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD
   int jacobi_max_sweeps = 40;
   int splitk_override = 0;  // > 0: fixed split-K factor for the square GEMMs
 
@@ -190,6 +190,13 @@ bool tc_device_supported(kp_ctx* ctx);
 // one-sided Jacobi SVD (FP64): A (m x n col-major, m >= n) -> U (m x n), s (n), V (n x n)
 kp_status jacobi_svd(kp_ctx* ctx, const double* A, int m, int n, double* U, double* s, double* V,
                      int* sweeps_out);
+// SVD F = U diag(s) V^T of a square blur factor given row-major; transform 0 =
+// DCT-II (reflexive BC), 1 = DST-I (zero BC) preconditioning
+kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, double* U, double* s, double* V,
+                     int* sweeps_out);
+// leading r singular triplets of W (m x n col-major, m >= n) by subspace iteration
+kp_status topr_svd(kp_ctx* ctx, const double* W, int m, int n, int r, double* U, double* s, double* V,
+                   int* iters_out);
 
 // vector / reduction helpers (kp_vec.cu)
 kp_status dot_dev(kp_ctx* ctx, const void* x, const void* y, long long n, bool f64, double* out_dev);

@@ -10,9 +10,16 @@
 // Pairs are visited in the round-robin (circle) order: each of the n - 1
 // rounds holds n / 2 disjoint pairs, one per thread block, and a sweep is the
 // n - 1 rounds, captured once as a CUDA graph.  Sweeps repeat until no pair
-// needs a rotation (|gamma| <= tol sqrt(alpha beta)).  Then
+// needs a rotation: |gamma| <= tol sqrt(alpha beta) (tol >= m eps), or
+// |gamma| <= m eps ||A||_F max(|a_i|, |a_j|), i.e. what would be removed is
+// below the rounding noise every column carries (without this absolute
+// floor, columns of singular values below eps ||A|| never settle).  Then
 // sigma_i = |a_i|, u_i = a_i / sigma_i, and the triplets are sorted by
 // decreasing sigma.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "kp_internal.h"
 
 namespace {
@@ -31,7 +38,7 @@ __device__ __forceinline__ int rr_player(int t, int round, int npad) {
 }
 
 __global__ void __launch_bounds__(JT) k_jacobi_round(double* __restrict__ W, double* __restrict__ V, int m, int n,
-                                                     int npad, int round, double tol,
+                                                     int npad, int round, double tol, double floor,
                                                      unsigned int* __restrict__ rot_count) {
   const int pidx = blockIdx.x;
   int i = rr_player(pidx, round, npad);
@@ -71,7 +78,10 @@ __global__ void __launch_bounds__(JT) k_jacobi_round(double* __restrict__ W, dou
       ga += sh[2][w];
     }
     double c = 1.0, s = 0.0;
-    if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+    // rotate only if the pair is not orthogonal to relative precision tol and
+    // the projection of the smaller column on the larger, |gamma| / |a_max|,
+    // is above the noise floor m eps ||A||_F that rounding leaves in any column
+    if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be) && fabs(ga) > floor * sqrt(fmax(al, be))) {
       double zeta = (be - al) / (2.0 * ga);
       double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
       c = 1.0 / sqrt(1.0 + t * t);
@@ -171,35 +181,154 @@ __global__ void k_gather(const double* __restrict__ W, const double* __restrict_
   if (threadIdx.x == 0) so[c] = sg;
 }
 
+// orthogonal transform that nearly diagonalises the blur factors:
+// DCT-II (reflexive BC) or DST-I (zero BC), column-major n x n
+__global__ void k_transform(int n, int kind, double* __restrict__ C) {
+  long long tot = (long long)n * n;
+  const double pi = 3.141592653589793238462643;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t % n), k = (int)(t / n);
+    double v;
+    if (kind == 0) {
+      v = sqrt(2.0 / n) * cos(pi * (2.0 * j + 1.0) * k / (2.0 * n));
+      if (k == 0) v *= 0.70710678118654752440;
+    } else {
+      v = sqrt(2.0 / (n + 1.0)) * sin(pi * (j + 1.0) * (k + 1.0) / (n + 1.0));
+    }
+    C[t] = v;
+  }
+}
+
+// B (n x m col-major) = A^T for A m x n col-major
+__global__ void k_transpose_cm(const double* __restrict__ A, int m, int n, double* __restrict__ B) {
+  long long tot = (long long)m * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % m), j = (int)(t / m);
+    B[j + (long long)n * i] = A[t];
+  }
+}
+
+// flip column c of U when it points against column c of R (one block per column)
+__global__ void k_align_signs(double* __restrict__ U, const double* __restrict__ R, int m) {
+  const int c = blockIdx.x;
+  double v = 0.0;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) v = fma(U[(long long)c * m + r], R[(long long)c * m + r], v);
+  __shared__ double sh[JT / 32];
+  v = jwarp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  __shared__ double tot;
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < JT / 32; ++w) t += sh[w];
+    tot = t;
+  }
+  __syncthreads();
+  if (tot < 0)
+    for (int r = threadIdx.x; r < m; r += blockDim.x) U[(long long)c * m + r] = -U[(long long)c * m + r];
+}
+
+__global__ void k_sumsq(const double* __restrict__ A, long long n, double* out) {
+  double v = 0.0;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) v = fma(A[t], A[t], v);
+  __shared__ double sh[1024 / 32];
+  v = jwarp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += sh[w];
+    *out = t;
+  }
+}
+
+// Orthonormalise the p columns of Q (m x p col-major) in place: modified
+// Gram-Schmidt, each projection done twice; a column that vanishes (rank
+// deficiency) is replaced by a unit vector e_t and orthogonalised again.
+// One block.
+__global__ void k_mgs2(double* __restrict__ Q, int m, int p) {
+  __shared__ double sh[JT / 32];
+  __shared__ double tot;
+  auto bsum = [&](double v) -> double {
+    v = jwarp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int w = 0; w < JT / 32; ++w) t += sh[w];
+      tot = t;
+    }
+    __syncthreads();
+    return tot;
+  };
+  for (int k = 0; k < p; ++k) {
+    double* qk = Q + (long long)k * m;
+    double n0 = 0;
+    for (int r = threadIdx.x; r < m; r += JT) n0 = fma(qk[r], qk[r], n0);
+    n0 = sqrt(bsum(n0));
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int j = 0; j < k; ++j) {
+          const double* qj = Q + (long long)j * m;
+          double d = 0;
+          for (int r = threadIdx.x; r < m; r += JT) d = fma(qj[r], qk[r], d);
+          d = bsum(d);
+          for (int r = threadIdx.x; r < m; r += JT) qk[r] -= d * qj[r];
+          __syncthreads();
+        }
+      }
+      double nk = 0;
+      for (int r = threadIdx.x; r < m; r += JT) nk = fma(qk[r], qk[r], nk);
+      nk = sqrt(bsum(nk));
+      if (nk > 1e-10 * n0 && nk > 0) {
+        for (int r = threadIdx.x; r < m; r += JT) qk[r] /= nk;
+        __syncthreads();
+        break;
+      }
+      // rank deficient: restart from a unit vector
+      const int t = (int)(((long long)(k + 1) * 7919 + attempt * 104729) % m);
+      for (int r = threadIdx.x; r < m; r += JT) qk[r] = (r == t) ? 1.0 : 0.0;
+      n0 = 1.0;
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace
 
-kp_status jacobi_svd(kp_ctx* ctx, const double* A, int m, int n, double* U, double* s, double* V, int* sweeps_out) {
-  if (m < n || n < 1) {
-    kp_set_error("jacobi_svd: need m >= n >= 1 (m=%d n=%d)", m, n);
-    return KP_EINVAL;
-  }
+// Sweeps on W (m x n col-major, in place) accumulating into V (n x n,
+// holding its initial value); then sigma, sorting, U = W / sigma.
+static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, double* U, double* s, double* V,
+                            int* sweeps_out) {
   cudaStream_t st = ctx->stream;
-  double *W = nullptr, *Vw = nullptr, *sw = nullptr;
+  double *sw = nullptr, *nrm = nullptr;
   int* perm = nullptr;
   unsigned int* cnt = nullptr;
-  KP_TRY(kp_alloc(ctx, (void**)&W, sizeof(double) * (size_t)m * n));
-  KP_TRY(kp_alloc(ctx, (void**)&Vw, sizeof(double) * (size_t)n * n));
   KP_TRY(kp_alloc(ctx, (void**)&sw, sizeof(double) * n));
   KP_TRY(kp_alloc(ctx, (void**)&perm, sizeof(int) * n));
   KP_TRY(kp_alloc(ctx, (void**)&cnt, sizeof(unsigned int)));
-  KP_CUDA(cudaMemcpyAsync(W, A, sizeof(double) * (size_t)m * n, cudaMemcpyDeviceToDevice, st));
-  k_set_identity<<<ctx->sm_count * 2, 256, 0, st>>>(Vw, n);
+  KP_TRY(kp_alloc(ctx, (void**)&nrm, sizeof(double)));
+  // noise floor m eps ||A||_F
+  k_sumsq<<<1, 1024, 0, st>>>(W, (long long)m * n, nrm);
   KP_LAUNCHED(ctx);
+  double fro2 = 0.0;
+  KP_CUDA(cudaMemcpyAsync(&fro2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  KP_CUDA(cudaStreamSynchronize(st));
+  const double eps = 2.220446049250313e-16;
+  const double floor = (double)m * eps * sqrt(fro2);
   const int npad = n + (n & 1);
   int sweeps = 0;
   if (npad >= 2) {
-    // capture one sweep
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     k_zero_u32<<<1, 1, 0, st>>>(cnt);
+    // pairs count as orthogonal at |gamma| <= tol sqrt(alpha beta); below m eps
+    // the inner products are rounding noise and rotations would never stop
+    const double tol = std::max(ctx->jacobi_tol, (double)m * eps);
     for (int round = 0; round < npad - 1; ++round)
-      k_jacobi_round<<<npad / 2, JT, 0, st>>>(W, Vw, m, n, npad, round, ctx->jacobi_tol, cnt);
+      k_jacobi_round<<<npad / 2, JT, 0, st>>>(W, Vw, m, n, npad, round, tol, floor, cnt);
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (ce != cudaSuccess) {
       kp_set_error("jacobi_svd: capture failed: %s", cudaGetErrorString(ce));
@@ -236,5 +365,175 @@ kp_status jacobi_svd(kp_ctx* ctx, const double* A, int m, int n, double* U, doub
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   if (sweeps_out) *sweeps_out = sweeps;
+  return KP_OK;
+}
+
+kp_status jacobi_svd(kp_ctx* ctx, const double* A, int m, int n, double* U, double* s, double* V, int* sweeps_out) {
+  if (m < n || n < 1) {
+    kp_set_error("jacobi_svd: need m >= n >= 1 (m=%d n=%d)", m, n);
+    return KP_EINVAL;
+  }
+  double *W = nullptr, *Vw = nullptr;
+  KP_TRY(kp_alloc(ctx, (void**)&W, sizeof(double) * (size_t)m * n));
+  KP_TRY(kp_alloc(ctx, (void**)&Vw, sizeof(double) * (size_t)n * n));
+  KP_CUDA(cudaMemcpyAsync(W, A, sizeof(double) * (size_t)m * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  k_set_identity<<<ctx->sm_count * 2, 256, 0, ctx->stream>>>(Vw, n);
+  KP_LAUNCHED(ctx);
+  return jacobi_run(ctx, W, m, n, Vw, U, s, V, sweeps_out);
+}
+
+// SVD of a square blur factor F (n x n, given row-major) with an orthogonal
+// transform C that nearly diagonalises it: one-sided Jacobi on F C with V
+// starting at C (so V ends as C Q, exact for any orthogonal C); the
+// transform only shortens the sweeps (DCT-II for reflexive BC, DST-I for
+// zero BC).  A second run on F^T gives U as accumulated rotations, hence
+// orthonormal also where sigma is below the noise floor; its columns are
+// sign-aligned with F v_i / sigma_i of the first run.
+kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, double* U, double* s, double* V,
+                     int* sweeps_out) {
+  cudaStream_t st = ctx->stream;
+  const long long nn = (long long)n * n;
+  double *C, *W, *Vw, *FT_rm, *U1, *s2;
+  KP_TRY(kp_alloc(ctx, (void**)&C, sizeof(double) * nn));
+  KP_TRY(kp_alloc(ctx, (void**)&W, sizeof(double) * nn));
+  KP_TRY(kp_alloc(ctx, (void**)&Vw, sizeof(double) * nn));
+  KP_TRY(kp_alloc(ctx, (void**)&FT_rm, sizeof(double) * nn));
+  KP_TRY(kp_alloc(ctx, (void**)&U1, sizeof(double) * nn));
+  KP_TRY(kp_alloc(ctx, (void**)&s2, sizeof(double) * n));
+  const int g = std::max(1, std::min((int)((nn + 255) / 256), ctx->sm_count * 16));
+  k_transform<<<g, 256, 0, st>>>(n, transform, C);
+  KP_LAUNCHED(ctx);
+  // W (col-major) = F C, computed as the row-major product D[k][i] = sum_j C[j,k] F[i,j]
+  auto mul = [&](const double* X_rm, double* out) -> kp_status {
+    GemmDesc gd;
+    gd.M = n;
+    gd.N = n;
+    gd.K = n;
+    gd.A.ptr = C;
+    gd.A.ld = n;
+    gd.B.ptr = X_rm;
+    gd.B.ld = n;
+    gd.epi.mode = EPI_T;
+    gd.epi.out = out;
+    gd.epi.ldd = n;
+    return simt_gemm<double>(ctx, gd);
+  };
+  int sw1 = 0, sw2 = 0;
+  // run 1: F = U1 S V^T
+  KP_TRY(mul(F_rm, W));
+  KP_CUDA(cudaMemcpyAsync(Vw, C, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+  KP_TRY(jacobi_run(ctx, W, n, n, Vw, U1, s, V, &sw1));
+  // run 2: F^T = V' S U^T  (F^T row-major = F column-major = transpose of F_rm)
+  k_transpose_cm<<<g, 256, 0, st>>>(F_rm, n, n, FT_rm);
+  KP_LAUNCHED(ctx);
+  KP_TRY(mul(FT_rm, W));
+  KP_CUDA(cudaMemcpyAsync(Vw, C, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+  KP_TRY(jacobi_run(ctx, W, n, n, Vw, FT_rm /* scratch */, s2, U, &sw2));
+  k_align_signs<<<n, JT, 0, st>>>(U, U1, n);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  if (sweeps_out) *sweeps_out = sw1 + sw2;
+  return KP_OK;
+}
+
+// Leading r singular triplets of W (m x n col-major, m >= n) by subspace
+// iteration: Q <- orth(W (W^T Q)) with p = min(n, r + 8) columns, started
+// from the lowest-frequency DCT-II columns, until the Ritz values
+// sigma_1..sigma_r of Q^T W change by less than 4 eps relative (at most 200
+// iterations); then the SVD of the p x n matrix Q^T W by one-sided Jacobi.
+// Outputs: U (m x r), s (r), V (n x r) col-major, s descending.
+kp_status topr_svd(kp_ctx* ctx, const double* W, int m, int n, int r, double* U, double* s, double* V,
+                   int* iters_out) {
+  cudaStream_t st = ctx->stream;
+  const int p = std::min(n, r + 8);
+  double *Q, *Z, *Uz, *sz, *Vz, *C;
+  KP_TRY(kp_alloc(ctx, (void**)&Q, sizeof(double) * (size_t)m * p));
+  KP_TRY(kp_alloc(ctx, (void**)&Z, sizeof(double) * (size_t)n * p));
+  KP_TRY(kp_alloc(ctx, (void**)&Uz, sizeof(double) * (size_t)n * p));
+  KP_TRY(kp_alloc(ctx, (void**)&sz, sizeof(double) * p));
+  KP_TRY(kp_alloc(ctx, (void**)&Vz, sizeof(double) * (size_t)p * p));
+  KP_TRY(kp_alloc(ctx, (void**)&C, sizeof(double) * (size_t)m * m));
+  double* WT;  // W^T (n x m col-major) = W row-major
+  KP_TRY(kp_alloc(ctx, (void**)&WT, sizeof(double) * (size_t)m * n));
+  const int g = std::max(1, std::min((int)(((long long)m * n + 255) / 256), ctx->sm_count * 16));
+  k_transpose_cm<<<g, 256, 0, st>>>(W, m, n, WT);
+  k_transform<<<g, 256, 0, st>>>(m, 0, C);  // first p columns: smooth start vectors
+  ctx->launches += 2;
+  KP_CUDA(cudaMemcpyAsync(Q, C, sizeof(double) * (size_t)m * p, cudaMemcpyDeviceToDevice, st));
+  // Z (n x p col-major) = W^T Q : row-major D[k][j] = sum_i Q[i,k] W[i,j]
+  auto mulZ = [&]() -> kp_status {
+    GemmDesc gd;
+    gd.M = p;
+    gd.N = n;
+    gd.K = m;
+    gd.A.ptr = Q;
+    gd.A.ld = m;
+    gd.B.ptr = W;
+    gd.B.ld = m;
+    gd.epi.mode = EPI_T;
+    gd.epi.out = Z;
+    gd.epi.ldd = n;
+    return simt_gemm<double>(ctx, gd);
+  };
+  // Q (m x p col-major) = W Z : row-major D[k][i] = sum_j Z[j,k] W[i,j]
+  auto mulY = [&]() -> kp_status {
+    GemmDesc gd;
+    gd.M = p;
+    gd.N = m;
+    gd.K = n;
+    gd.A.ptr = Z;
+    gd.A.ld = n;
+    gd.B.ptr = WT;
+    gd.B.ld = n;
+    gd.epi.mode = EPI_T;
+    gd.epi.out = Q;
+    gd.epi.ldd = m;
+    return simt_gemm<double>(ctx, gd);
+  };
+  std::vector<double> prev(r, 0.0), cur(r, 0.0);
+  int it = 0;
+  const int maxit = 200;
+  for (it = 0; it < maxit; ++it) {
+    k_mgs2<<<1, JT, 0, st>>>(Q, m, p);
+    KP_LAUNCHED(ctx);
+    KP_TRY(mulZ());  // Z = W^T Q = (Q^T W)^T
+    // Ritz values: singular values of Z (n x p)
+    KP_TRY(jacobi_svd(ctx, Z, n, p, Uz, sz, Vz, nullptr));
+    KP_CUDA(cudaMemcpyAsync(cur.data(), sz, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
+    KP_CUDA(cudaStreamSynchronize(st));
+    double d = 0.0;
+    for (int k = 0; k < r; ++k) d = std::max(d, std::fabs(cur[k] - prev[k]) / std::max(cur[0], 1e-300));
+    if (it > 0 && d <= 4 * 2.220446049250313e-16) break;
+    prev = cur;
+    KP_TRY(mulY());  // Q = W Z
+  }
+  if (it == maxit) {
+    kp_set_error("topr_svd: subspace iteration did not settle in %d iterations", maxit);
+    return KP_ENOCONV;
+  }
+  // Z = W^T Q = V_W S (Q^T U_W)^T: Jacobi on Z gave Uz (normalised Z V_z ->
+  // right singular vectors of W), sz, Vz (p x p); left vectors U = Q Vz.
+  KP_CUDA(cudaMemcpyAsync(V, Uz, sizeof(double) * (size_t)n * r, cudaMemcpyDeviceToDevice, st));
+  KP_CUDA(cudaMemcpyAsync(s, sz, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
+  {
+    // U (m x r col-major) = Q Vz[:, :r] : row-major D[k][i] = sum_j Vz[j,k] Q[i,j]
+    double* QT;
+    KP_TRY(kp_alloc(ctx, (void**)&QT, sizeof(double) * (size_t)m * p));
+    k_transpose_cm<<<g, 256, 0, st>>>(Q, m, p, QT);
+    KP_LAUNCHED(ctx);
+    GemmDesc gd;
+    gd.M = r;
+    gd.N = m;
+    gd.K = p;
+    gd.A.ptr = Vz;
+    gd.A.ld = p;
+    gd.B.ptr = QT;
+    gd.B.ld = p;
+    gd.epi.mode = EPI_T;
+    gd.epi.out = U;
+    gd.epi.ldd = m;
+    KP_TRY(simt_gemm<double>(ctx, gd));
+  }
+  if (iters_out) *iters_out = it + 1;
   return KP_OK;
 }

@@ -11,6 +11,8 @@
 // transposed factors.  The preconditioner solve Z = V_c (S .* (V_c^T R V_r)) V_r^T
 // (eq. PreconSolve) is P1..P4 with the same alternation, S applied in the
 // P2 epilogue as lam^2 / (Sigma^2 + lam^2) and 1 / lam^2 folded into P4.
+// A BF16 preconditioner keeps V_c, V_r as bf16 hi + lo slices (two products
+// per GEMM); FP16 keeps them as single fp16 values.
 //
 // Tensor-core operators split activations and factors into bf16 slices.
 // The inner (per-iteration) operator uses the slice pairs {(0,0)} (KP_BF16)
@@ -159,6 +161,13 @@ static GemmDesc pc_desc(kp_ctx* ctx, int which) {
   g.B.tstride = (long long)g.B.rows * g.B.ld;
   g.A.nterm_idx = 1;
   g.B.nterm_idx = 1;
+  if (ctx->pc_prec == KP_BF16) {  // factor slices hi, lo times the single activation slice
+    g.npairs = 2;
+    g.sa[0] = 0;
+    g.sa[1] = 1;
+    g.sb[0] = g.sb[1] = 0;
+    g.A.nterm_idx = 2;
+  }
   return g;
 }
 
@@ -219,7 +228,7 @@ kp_status ops_prepare(kp_ctx* ctx) {
     for (int w = 0; w < 4; ++w) {
       GemmDesc g = pc_desc(ctx, w);
       const int bk = kind == TC_E4M3 ? 128 : 64;
-      const int steps = (g.K + bk - 1) / bk;
+      const int steps = g.npairs * ((g.K + bk - 1) / bk);
       KP_TRY(tc_plan_create(ctx, g, kind, choose_splits(ctx, g.M, g.N, steps), &os->P[w]));
     }
   }

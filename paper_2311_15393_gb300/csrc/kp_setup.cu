@@ -4,13 +4,15 @@
 //     number of times PSF row / column k occurs in a Toeplitz factor, so that
 //     the leading SVD term is the Frobenius-optimal Kronecker product
 //     (Section 5, the argmin below eq. KronSumDecomp);
-//  2. SVD of W by one-sided Jacobi (FP64); terms
+//  2. SVD of W in FP64: subspace iteration for the leading `rank` terms when
+//     rank <= min(n_r, n_c) / 4, else the full one-sided Jacobi SVD; terms
 //     u_m = sqrt(s_m) D_c^-1 u~_m, v_m = sqrt(s_m) D_r^-1 v~_m, m < rank, with the
 //     largest-magnitude entry of u_m made positive;
 //  3. factors A_c^(m) = F(u_m), A_r^(m) = F(v_m) with F(u) = T(u) (zero BC) or
 //     T(u) + H(u) (reflexive BC), T(u)[i,j] = u[c+i-j],
 //     H(u)[i,j] = u[c+i+j+1] + u[c+i+j+1-2n] (eq. KronSumDecomp);
-//  4. SVDs of A_r^(1), A_c^(1) (eq. AKronSVD) by one-sided Jacobi (FP64);
+//  4. SVDs of A_r^(1), A_c^(1) (eq. AKronSVD) by one-sided Jacobi (FP64),
+//     preconditioned by the DCT-II / DST-I (see kp_jacobi.cu);
 //  5. KP spectrum Sigma = sigma_c sigma_r^T (PRODUCT) or
 //     sum_k diag(U_c^T A_c^(k) V_c) diag(U_r^T A_r^(k) V_r)^T (PROJECTED);
 //  6. copies of the factors in the operator precision (FP64, FP32 or bf16
@@ -310,18 +312,27 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
   k_weight_psf<<<grid_for(ctx, N), 256, 0, st>>>(psf, n_r, n_c, center_r, center_c, W);
   KP_LAUNCHED(ctx);
   double *Uc_w, *Vc_w;  // left (n_r) and right (n_c) singular vectors of W
-  if (n_r >= n_c) {
-    KP_TRY(jacobi_svd(ctx, W, n_r, n_c, Uw, sw, Vw, nullptr));
-    Uc_w = Uw;
-    Vc_w = Vw;
-  } else {
+  const double* Wsrc = W;
+  if (n_r < n_c) {  // work on W^T (m >= n)
     double* WT;
     KP_TRY(kp_alloc(ctx, (void**)&WT, sizeof(double) * N));
     k_transpose64<<<grid_for(ctx, N), 256, 0, st>>>(W, n_r, n_c, WT);
     KP_LAUNCHED(ctx);
-    KP_TRY(jacobi_svd(ctx, WT, n_c, n_r, Uw, sw, Vw, nullptr));  // W^T = Uw S Vw^T
-    Uc_w = Vw;                                                     // n_r x n_r
-    Vc_w = Uw;                                                     // n_c x n_r
+    Wsrc = WT;
+  }
+  // few terms: subspace iteration for the leading ones; otherwise the full
+  // one-sided Jacobi SVD
+  if (4 * rank <= nn) {
+    KP_TRY(topr_svd(ctx, Wsrc, mm, nn, rank, Uw, sw, Vw, nullptr));
+  } else {
+    KP_TRY(jacobi_svd(ctx, Wsrc, mm, nn, Uw, sw, Vw, nullptr));
+  }
+  if (n_r >= n_c) {
+    Uc_w = Uw;
+    Vc_w = Vw;
+  } else {  // W^T = Uw S Vw^T
+    Uc_w = Vw;
+    Vc_w = Uw;
   }
   KP_TRY(kp_alloc(ctx, (void**)&ctx->s_terms, sizeof(double) * rank));
   KP_TRY(kp_alloc(ctx, (void**)&ctx->u_terms, sizeof(double) * (size_t)n_r * rank));
@@ -339,16 +350,16 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
                                                                              reflexive, ctx->Ar64);
   ctx->launches += 2;
 
-  // ---- 4: factor SVDs.  The row-major buffer of F is the column-major F^T:
-  // Jacobi on F^T = Uj S Vj^T gives F = Vj S Uj^T.
+  // ---- 4: factor SVDs (eq. AKronSVD): A_r^(1) = U_r S_r V_r^T, A_c^(1) = U_c S_c V_c^T
   KP_TRY(kp_alloc(ctx, (void**)&ctx->Ur, sizeof(double) * (size_t)n_c * n_c));
   KP_TRY(kp_alloc(ctx, (void**)&ctx->Vr, sizeof(double) * (size_t)n_c * n_c));
   KP_TRY(kp_alloc(ctx, (void**)&ctx->sr, sizeof(double) * n_c));
   KP_TRY(kp_alloc(ctx, (void**)&ctx->Uc, sizeof(double) * (size_t)n_r * n_r));
   KP_TRY(kp_alloc(ctx, (void**)&ctx->Vc, sizeof(double) * (size_t)n_r * n_r));
   KP_TRY(kp_alloc(ctx, (void**)&ctx->sc, sizeof(double) * n_r));
-  KP_TRY(jacobi_svd(ctx, ctx->Ar64, n_c, n_c, ctx->Vr, ctx->sr, ctx->Ur, nullptr));
-  KP_TRY(jacobi_svd(ctx, ctx->Ac64, n_r, n_r, ctx->Vc, ctx->sc, ctx->Uc, nullptr));
+  const int transform = reflexive ? 0 : 1;
+  KP_TRY(factor_svd(ctx, ctx->Ar64, n_c, transform, ctx->Ur, ctx->sr, ctx->Vr, nullptr));
+  KP_TRY(factor_svd(ctx, ctx->Ac64, n_r, transform, ctx->Uc, ctx->sc, ctx->Vc, nullptr));
 
   // ---- 5: KP spectrum
   KP_TRY(kp_alloc(ctx, (void**)&ctx->Sigma64, sizeof(double) * N));
@@ -429,7 +440,7 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
     k_transpose_blocks<float><<<grid_for(ctx, nr2), 256, 0, st>>>(ctx->Vr, n_c, 1, (float*)ctx->pcVr);
     ctx->launches += 4;
   } else {
-    const size_t es = pc_prec == KP_E4M3 ? 1 : 2;
+    const size_t es = pc_prec == KP_E4M3 ? 1 : (pc_prec == KP_BF16 ? 4 : 2);  // BF16: two slices
     KP_TRY(kp_alloc(ctx, &ctx->pcVcT, es * nc2));
     KP_TRY(kp_alloc(ctx, &ctx->pcVrT, es * nr2));
     KP_TRY(kp_alloc(ctx, &ctx->pcVc, es * nc2));
@@ -454,10 +465,12 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
     ctx->pc_vscale_c = (float)sc_c;
     ctx->pc_vscale_r = (float)sc_r;
     if (pc_prec == KP_BF16) {
-      k_narrow64<__nv_bfloat16><<<grid_for(ctx, nc2), 256, 0, st>>>(ctx->Vc, n_r, 0, 1.0, (__nv_bfloat16*)ctx->pcVcT);
-      k_narrow64<__nv_bfloat16><<<grid_for(ctx, nr2), 256, 0, st>>>(ctx->Vr, n_c, 0, 1.0, (__nv_bfloat16*)ctx->pcVrT);
-      k_narrow64<__nv_bfloat16><<<grid_for(ctx, nc2), 256, 0, st>>>(ctx->Vc, n_r, 1, 1.0, (__nv_bfloat16*)ctx->pcVc);
-      k_narrow64<__nv_bfloat16><<<grid_for(ctx, nr2), 256, 0, st>>>(ctx->Vr, n_c, 1, 1.0, (__nv_bfloat16*)ctx->pcVr);
+      // bf16 factors as a hi + lo pair (slices at stride n^2): their 8-bit
+      // mantissa alone would cost ~4e-3 relative per apply
+      k_split64<<<grid_for(ctx, nc2), 256, 0, st>>>(ctx->Vc, n_r, 1, 0, 2, nc2, (__nv_bfloat16*)ctx->pcVcT);
+      k_split64<<<grid_for(ctx, nr2), 256, 0, st>>>(ctx->Vr, n_c, 1, 0, 2, nr2, (__nv_bfloat16*)ctx->pcVrT);
+      k_split64<<<grid_for(ctx, nc2), 256, 0, st>>>(ctx->Vc, n_r, 1, 1, 2, nc2, (__nv_bfloat16*)ctx->pcVc);
+      k_split64<<<grid_for(ctx, nr2), 256, 0, st>>>(ctx->Vr, n_c, 1, 1, 2, nr2, (__nv_bfloat16*)ctx->pcVr);
     } else if (pc_prec == KP_F16) {
       k_narrow64<__half><<<grid_for(ctx, nc2), 256, 0, st>>>(ctx->Vc, n_r, 0, 1.0, (__half*)ctx->pcVcT);
       k_narrow64<__half><<<grid_for(ctx, nr2), 256, 0, st>>>(ctx->Vr, n_c, 0, 1.0, (__half*)ctx->pcVrT);

@@ -170,8 +170,8 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
   const double lam2 = lambda * lambda;
   const SolveBufs B = bufs(ctx);
   cudaStream_t st = ctx->stream;
-  const bool reduced_op = ctx->op_prec == KP_BF16 || ctx->op_prec == KP_BF16X3;
-  double delta = ctx->reliable_delta >= 0 ? ctx->reliable_delta : (reduced_op ? 0.1 : 0.0);
+  // default: reliable updates for every operator below FP64
+  double delta = ctx->reliable_delta >= 0 ? ctx->reliable_delta : (ctx->op_prec == KP_F64 ? 0.0 : 0.1);
   const bool reliable = delta > 0.0;
 
   cudaEvent_t e0, e1;

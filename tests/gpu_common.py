@@ -83,7 +83,8 @@ def emulate_apply_A_bf16(op, X):
 
 def emulate_minv(kp, Sigma, R, lam, fmt):
     """Reduced-precision preconditioner solve with the GPU's rounding points:
-    R scaled by 2^e (amax(R) 2^e in [1/2, 1)) and rounded; each GEMM output
+    R scaled by 2^e (amax(R) 2^e in [1/2, 1)) and rounded (bf16 factors as
+    hi + lo pairs); each GEMM output
     rounded to fp32 then to the narrow format; S applied as
     lam^2 / (Sigma^2 + lam^2) in the P2 output; 1 / (lam^2 2^e) at the end."""
     rd = lp.ROUND[fmt]
@@ -91,7 +92,11 @@ def emulate_minv(kp, Sigma, R, lam, fmt):
     m, e = np.frexp(1.0 / am)
     s = np.ldexp(1.0, e - 1)
     Rq = rd(lp.to_fp32(R) * s)
-    Vc, Vr = rd(kp.Vc), rd(kp.Vr)
+    if fmt == "bf16":   # factors carried as bf16 hi + lo pairs
+        Vc = lp.to_bf16(kp.Vc) + lp.to_bf16(kp.Vc - lp.to_bf16(kp.Vc))
+        Vr = lp.to_bf16(kp.Vr) + lp.to_bf16(kp.Vr - lp.to_bf16(kp.Vr))
+    else:
+        Vc, Vr = rd(kp.Vc), rd(kp.Vr)
     T1 = rd(lp.to_fp32(Vc.T @ Rq))
     S32 = lp.to_fp32(Sigma)
     fac = lp.to_fp32(lam * lam / (S32.astype(np.float64) ** 2 + lam * lam))

@@ -119,9 +119,34 @@ def test_tensor_core_accurate_operator(kpsvd, n):
 
 @pytest.mark.parametrize("fmt", ["f16", "bf16"])
 @pytest.mark.parametrize("n", [64, 256])
-def test_tensor_core_preconditioner(kpsvd, fmt, n):
-    """Reduced-precision KP-SVD solve: equals its emulation (same rounding
-    points), and for a broadband residual is within 5e-3 of FP64."""
+def test_tensor_core_preconditioner_vs_emulation(kpsvd, fmt, n):
+    """Reduced-precision KP-SVD solve equals its emulation (same rounded
+    factors, same rounding points).  A narrow PSF keeps every factor singular
+    value well above rounding level, so V is unique up to column signs on
+    both sides and both round the same numbers."""
+    c = (n // 2, n // 2)
+    psf = synth.gaussian_psf(n, n, c[0], c[1], 0.8, 0.6, 0.3)
+    pr = OracleProblem("deblur256_fp32", n=n, psf=psf, rank=3)
+    assert min(pr.kp.sc.min(), pr.kp.sr.min()) > 1e-3 * pr.kp.sc[0]
+    lam = 0.02
+    with setup_ctx(kpsvd, pr, "f32", fmt, "f32") as ctx:
+        R = synth.random_matrix(n, n, 5)
+        r = kpsvd.to_device(R, torch.float32)
+        z = torch.empty_like(r)
+        ctx.kp_apply_Minv(r, z, lam)
+        Z = kpsvd.from_device(z, n, n)
+        # the only differences are FP32 accumulation order flipping a rounding
+        # at the same points: bounded by half a unit of the narrow format
+        u = 2.0 ** -11 if fmt == "f16" else 2.0 ** -8
+        assert rel(Z, emulate_minv(pr.kp, pr.kp.Sigma, R, lam, fmt)) < 0.5 * u
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+@pytest.mark.parametrize("n", [64, 256])
+def test_tensor_core_preconditioner_vs_fp64(kpsvd, fmt, n):
+    """Single preconditioner apply against FP64: within 5e-3 for a broadband
+    residual (for smooth residuals the 1 / lam^2 amplification of the input
+    rounding dominates; the solver tests cover that regime)."""
     pr = OracleProblem("deblur256_fp32", n=n, rank=3)
     lam = 0.02
     with setup_ctx(kpsvd, pr, "f32", fmt, "f32") as ctx:
@@ -130,7 +155,5 @@ def test_tensor_core_preconditioner(kpsvd, fmt, n):
         z = torch.empty_like(r)
         ctx.kp_apply_Minv(r, z, lam)
         Z = kpsvd.from_device(z, n, n)
-        Zemu = emulate_minv(pr.kp, pr.kp.Sigma, R, lam, fmt)
-        assert rel(Z, Zemu) < 2e-3
         Z64 = okp.precond_apply(pr.kp, okp.precond_scale(pr.kp.Sigma, lam), R)
         assert rel(Z, Z64) < 5e-3
