@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark: KP-SVD preconditioned flexible PCG deblurring of a 1024 x 1024
+image (rank-4 Kronecker-sum blur, reflexive BC) on GB300.
+
+One step = the whole path for one synthetic problem: kp_setup (PSF ->
+Kronecker sum -> KP-SVD), then for each of the two noise levels (0.5 %, 5 %)
+choose_lambda (GCV over the KP spectrum) and tik_pcg (FPCG to the relative
+residual that reaches <= 1e-4 relative error against the FP64 oracle).
+value = solves per second over all ranks (2 solves per step per rank).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same step and prints its JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution at ≤1e-4 rel. err vs FP64 oracle (1024² deblur); solves/s"
+WORKLOAD = "deblur1024_mixed"
+TOL = 1e-7          # relative residual that gives <= 1e-4 error vs the oracle's x_lambda
+MAXIT = 500
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--op", default="bf16", choices=["bf16", "bf16x3", "f32"])
+    ap.add_argument("--pc", default="f16", choices=["f16", "bf16", "f32", "e4m3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-form", action="store_true", help="also time the all-FP64 GPU form (per iteration)")
+    ap.add_argument("--n", type=int, default=None, help="override the image size (smaller test runs)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps only (no phase breakdown, e2e, kernel timing or CPU baseline): for launch lists")
+    ap.add_argument("--kernel-only", choices=["kapply", "minv"], default=None,
+                    help="set up once, then run only the operator application (or preconditioner solve) "
+                         "--steps times: for kernel profiles")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ problem
+def make_inputs(n, seed_offset):
+    from paper_2311_15393_gb300 import synth
+    P = synth.make_problem(WORKLOAD, n=n, seed=synth.SEED_BASE + synth.WORKLOAD_INDEX[WORKLOAD] + seed_offset)
+    return P
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(P, iters_per_solve):
+    """Bounded sample of the step on the host cores with the FP64 oracle:
+    setup, GCV lambda for one noise level, 3 FPCG iterations; extrapolated to
+    one step (setup + 2 x (lambda + iters_per_solve iterations))."""
+    import numpy as np
+    from oracle import forward, kpsvd as okp, kron, lam as olam, pcg as opcg
+    t0 = time.perf_counter()
+    op = kron.kron_operator(P.psf, P.center, P.bc, P.op_rank)
+    kp = okp.kp_svd(op, "projected")
+    t1 = time.perf_counter()
+    B, _ = forward.observe(op, P.x_true, P.noise_dirs[0], P.noise_levels[0])
+    t2 = time.perf_counter()
+    lam = olam.choose_lambda(kp, B, "gcv")
+    t3 = time.perf_counter()
+    k = 3
+    opcg.tik_pcg(op, kp, B, lam, 0.0, k, True)
+    t4 = time.perf_counter()
+    t_setup, t_lam, t_it = t1 - t0, t3 - t2, (t4 - t3) / (k + 1)  # + A^T b and z0 ~ one iteration
+    step = t_setup + 2 * (t_lam + iters_per_solve * t_it)
+    return {"step_s": step, "sample_s": t4 - t0, "t_setup": t_setup, "t_lambda": t_lam, "t_iter": t_it}
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, ws, rank, dist):
+    if rank != 0:
+        return 0
+    n = args.n
+    P = make_inputs(n, 0)
+    iters = 111  # FP64 FPCG iterations per solve at the workload's GCV lambda (0.5 % noise)
+    for _ in range(args.warmup):
+        oracle_sample(P, iters)
+    times = [oracle_sample(P, iters) for _ in range(args.steps)]
+    step = sum(t["step_s"] for t in times) / len(times)
+    value = 2.0 / step
+    cores = blas_threads()
+    sample = ("per step: FP64 oracle setup (Kronecker sum + KP-SVD), GCV lambda at one noise level, "
+              "3 FPCG iterations; extrapolated to setup + 2 x (lambda + %d iterations)" % iters)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": P.n_r, "op_rank": P.op_rank, "bc": P.bc,
+                       "noise_levels": P.noise_levels, "solves_per_step": 2},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, ws, rank, local, dist):
+    import numpy as np
+    import torch
+    from paper_2311_15393_gb300 import build as _build
+    _build.build()
+    from paper_2311_15393_gb300 import kpsvd
+
+    dev = local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    P = make_inputs(args.n, 1000 * rank)
+    n_r, n_c = P.n_r, P.n_c
+    N = n_r * n_c
+    f32 = torch.float32
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=f32, device=dev)
+    with torch.cuda.stream(stream):
+        psf = kpsvd.to_device(P.psf, torch.float64, f"cuda:{dev}")
+        xt = kpsvd.to_device(P.x_true, f32, f"cuda:{dev}")
+        gs = [kpsvd.to_device(g, f32, f"cuda:{dev}") for g in P.noise_dirs]
+        bs = [torch.empty(N, dtype=f32, device=dev) for _ in gs]
+        xs = [torch.zeros(N, dtype=f32, device=dev) for _ in gs]
+        ctx = kpsvd.KpContext(dev, stream=stream.cuda_stream)
+        # observed data with this context's own operator (untimed input preparation)
+        ctx.kp_setup(psf, n_r, n_c, P.center, P.bc, P.op_rank, args.op, args.pc, "f32", "projected")
+        for g, b, nl in zip(gs, bs, P.noise_levels):
+            ctx.kp_forward(xt, g, nl, b)
+    torch.cuda.synchronize()
+
+    if args.kernel_only:
+        with torch.cuda.stream(stream):
+            pk = torch.randn(N, dtype=f32, device=dev)
+            qk = torch.empty_like(pk)
+            fn = ctx.kp_apply_K if args.kernel_only == "kapply" else ctx.kp_apply_Minv
+            for _ in range(args.warmup):
+                fn(pk, qk, 0.02)
+            k0 = torch.cuda.Event(enable_timing=True)
+            k1 = torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            for _ in range(args.steps):
+                fn(pk, qk, 0.02)
+            k1.record(stream)
+            torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"kernel_only": args.kernel_only, "n": n_r, "ms_per_call": k0.elapsed_time(k1) / args.steps,
+                              "launches": ctx.kp_launch_count()}), flush=True)
+        ctx.close()
+        return 0
+
+    phase = {"setup": [], "lambda": [], "solve": []}
+    infos = []
+
+    def step(record=False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        flush.fill_(1.0)
+        ev[0].record(stream)
+        ctx.kp_setup(psf, n_r, n_c, P.center, P.bc, P.op_rank, args.op, args.pc, "f32", "projected")
+        ev[1].record(stream)
+        out = []
+        for k, b in enumerate(bs):
+            lam = ctx.choose_lambda(b, "gcv")
+            ev[2 + 2 * k].record(stream)
+            info = ctx.tik_pcg(b, lam, TOL, MAXIT, True, xs[k])
+            ev[3 + 2 * k].record(stream)
+            out.append((lam, info))
+        if record:
+            torch.cuda.synchronize()
+            phase["setup"].append(ev[0].elapsed_time(ev[1]))
+            phase["lambda"].append(ev[1].elapsed_time(ev[2]) + ev[3].elapsed_time(ev[4]))
+            phase["solve"].append(ev[2].elapsed_time(ev[3]) + ev[4].elapsed_time(ev[5]))
+            infos.append(out)
+        return out
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ctx.kp_launch_count(reset=True)
+        clocks = ClockSampler(dev)
+        clocks.start()
+        barrier(dist)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(record=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(dist)
+        clk = clocks.stop()
+        launches = ctx.kp_launch_count(reset=True)
+        ms = e0.elapsed_time(e1) / args.steps
+        ms_max = max_over_ranks(dist, ms)
+        solves = 2 * args.steps
+        value = sum_over_ranks(dist, solves) / (ms_max * args.steps / 1e3)
+
+        if args.quick:
+            if rank == 0:
+                print(json.dumps({"quick": True, "value": value, "ms_per_step": ms_max, "gpu_launches": launches}),
+                      flush=True)
+            ctx.close()
+            return 0
+        # per-phase breakdown (separate, recorded steps)
+        for _ in range(2):
+            step(record=True)
+
+        # end to end through the public API with host buffers
+        pin_psf = torch.from_numpy(np.ascontiguousarray(P.psf.reshape(-1, order="F"))).pin_memory()
+        pin_b = [b.to("cpu").pin_memory() for b in bs]
+        pin_x = [torch.empty(N, dtype=f32).pin_memory() for _ in bs]
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            psf.copy_(pin_psf, non_blocking=True)
+            for b, hb in zip(bs, pin_b):
+                b.copy_(hb, non_blocking=True)
+            ctx.kp_setup(psf, n_r, n_c, P.center, P.bc, P.op_rank, args.op, args.pc, "f32", "projected")
+            for k, b in enumerate(bs):
+                lam = ctx.choose_lambda(b, "gcv")
+                ctx.tik_pcg(b, lam, TOL, MAXIT, True, xs[k])
+                pin_x[k].copy_(xs[k], non_blocking=True)
+            stream.synchronize()
+        t1 = time.perf_counter()
+        barrier(dist)
+        e2e_s = max_over_ranks(dist, (t1 - t0) / args.steps)
+        e2e_value = sum_over_ranks(dist, 2.0) / e2e_s
+        h2d = P.psf.size * 8 + sum(b.numel() * 4 for b in bs)
+        d2h = sum(x.numel() * 4 for x in xs)
+
+        # dominant-kernel timing: the operator application K p (four
+        # tensor-core GEMMs) launched repeatedly on the same stream
+        pk = torch.randn(N, dtype=f32, device=dev)
+        qk = torch.empty_like(pk)
+        for _ in range(3):
+            ctx.kp_apply_K(pk, qk, 0.02)
+        reps = 20
+        flush.fill_(1.0)
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(reps):
+            ctx.kp_apply_K(pk, qk, 0.02)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        kapply_ms = k0.elapsed_time(k1) / reps
+
+        fp64_form = None
+        if args.fp64_form:
+            ctx64 = kpsvd.KpContext(dev, stream=stream.cuda_stream)
+            psf64 = psf
+            ctx64.kp_setup(psf64, n_r, n_c, P.center, P.bc, P.op_rank, "f64", "f64", "f64", "projected")
+            b64 = bs[0].double()
+            x64 = torch.zeros(N, dtype=torch.float64, device=dev)
+            lam = infos[-1][0][0]
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            ctx64.tik_pcg(b64, lam, 0.0, 2, True, x64, check=False)
+            f0.record(stream)
+            it64 = 5
+            ctx64.tik_pcg(b64, lam, 0.0, it64, True, x64, check=False)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            ms_iter = f0.elapsed_time(f1) / (it64 + 1)
+            fp64_form = {"ms_per_iter": ms_iter,
+                         "est_ms_per_solve": ms_iter * (infos[-1][0][1].iters + 1),
+                         "note": "all-FP64 GPU form (FP64 SIMT operator, preconditioner, vectors), timed over "
+                                 f"{it64} iterations and scaled to the iteration count of the mixed solve"}
+            ctx64.close()
+
+    # roofline of the operator GEMMs (dominant in the solve): 2 M N K flops each
+    r = P.op_rank
+    flops_kapply = 4 * 2.0 * r * n_r * n_r * n_c   # G1..G4: 2 (r n_r) n_c n_r each (square: 8 r n^3)
+    pk_, how = peaks()
+    peak_tf = pk_.get("bf16_tflops")   # burst figure: the GEMMs are timed alone
+    achieved = flops_kapply / (kapply_ms * 1e-3) / 1e12
+    last = infos[-1]
+    result = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n_r, "op_rank": r, "bc": P.bc, "op_prec": args.op,
+                   "pc_prec": args.pc, "vec_prec": "f32", "lambda": "gcv", "noise_levels": P.noise_levels,
+                   "tol": TOL, "solves_per_step": 2, "parallelism": f"replicas x{ws}",
+                   "l2": "256 MiB buffer written before every step",
+                   "step": "kp_setup + 2 x (choose_lambda GCV + tik_pcg FPCG)"},
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "operator GEMMs (tcgen05 bf16, 4 per K application)", "bound": "tensor",
+                     "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
+                     "traffic": None, "peak_source": how + " bf16_tflops (burst)",
+                     "flops_per_launch": flops_kapply / 4, "ms_per_launch": kapply_ms / 4},
+        "clocks": clk,
+        "phases_ms": {k: (statistics.mean(v) if v else None) for k, v in phase.items()},
+        "solves": [{"lambda": lam, "iters": inf.iters, "replacements": inf.replacements,
+                    "rel_res": inf.rel_res, "status": inf.status} for lam, inf in last],
+    }
+    if fp64_form:
+        result["fp64_form"] = fp64_form
+    ctx.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        iters = max(inf.iters for _, inf in last)
+        smp = oracle_sample(P, iters)
+        result["cpu_baseline"] = {"value": 2.0 / smp["step_s"], "unit": "solves/s", "cores": blas_threads(),
+                                  "kind": "oracle",
+                                  "sample": "FP64 oracle setup + GCV lambda (one noise level) + 3 FPCG iterations "
+                                            f"({smp['sample_s']:.1f} s), extrapolated to setup + 2 x (lambda + "
+                                            f"{iters} iterations)"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local, dist = dist_init(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, ws, rank, dist)
+        return run_ours(args, ws, rank, local, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -94,7 +94,9 @@ typedef struct {
 } kp_solve_info;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
- * (a cudaStream_t, or NULL for the legacy default stream). */
+ * (a cudaStream_t).  NULL means the legacy default stream: the work then
+ * runs on a private stream of the context that is ordered after the
+ * default stream's earlier work at each call and before its later work. */
 kp_status kp_create(kp_ctx** out, int device, void* cuda_stream);
 
 /* Release every device allocation of the context.  NULL is allowed. */

@@ -56,12 +56,14 @@ void ops_state_free(kp_ctx* ctx);
 
 kp_status kp_enter(kp_ctx* ctx) {
   KP_CUDA(cudaSetDevice(ctx->device));
+  if (!ctx->own_stream) return KP_OK;
   KP_CUDA(cudaEventRecord(ctx->ev_in, ctx->user_stream));
   KP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
   return KP_OK;
 }
 
 kp_status kp_leave(kp_ctx* ctx) {
+  if (!ctx->own_stream) return KP_OK;
   KP_CUDA(cudaEventRecord(ctx->ev_out, ctx->stream));
   KP_CUDA(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
   return KP_OK;
@@ -112,7 +114,12 @@ extern "C" kp_status kp_create(kp_ctx** out, int device, void* cuda_stream) {
   kp_ctx* ctx = new kp_ctx();
   ctx->device = device;
   ctx->user_stream = (cudaStream_t)cuda_stream;
-  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+  // a caller's stream is used directly; the legacy default stream (NULL) can
+  // not be captured into graphs, so then work runs on a private stream
+  // ordered with it through events
+  ctx->own_stream = cuda_stream == nullptr;
+  if (!ctx->own_stream) ctx->stream = ctx->user_stream;
+  if ((ctx->own_stream && cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) ||
       cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -148,7 +155,7 @@ extern "C" void kp_destroy(kp_ctx* ctx) {
   if (ctx->ctx_block) cudaFree(ctx->ctx_block);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
-  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->stream && ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
 

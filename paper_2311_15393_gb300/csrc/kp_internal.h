@@ -97,6 +97,7 @@ struct kp_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;       // private work stream (capturable)
   cudaStream_t user_stream = nullptr;  // caller's stream, ordered with `stream` by events
+  bool own_stream = false;             // `stream` is private (caller passed the legacy stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   void* ops_state = nullptr;
   int* dflags = nullptr;               // device solver flags
