@@ -170,6 +170,28 @@ kp_status kp_apply_K(kp_ctx* ctx, const void* x, void* y, double lambda);
  * preconditioner precision.  r, z: device, vec type, distinct. */
 kp_status kp_apply_Minv(kp_ctx* ctx, const void* r, void* z, double lambda);
 
+/* Preconditioner solve that allocates nothing, for callers that cannot call
+ * cudaMalloc: code running where the allocator is off limits (a memory
+ * pool or arena owned by someone else, an embedding runtime that forbids
+ * device allocation, a real-time loop that must not allocate).  It needs no
+ * context: the caller passes every input and output, and the intermediates
+ * go to a fixed 5 MiB scratch array inside the library (held by every GPU
+ * that loads the library until the process exits).  The paper has no
+ * counterpart; the arithmetic is that of kp_apply_Minv with FP32
+ * preconditioner factors:
+ *   z = V_c (S .* (V_c^T R V_r)) V_r^T,  S = 1 / (Sigma^2 + lambda^2).
+ *   Vc       device, float, column-major n_r x n_r (right singular vectors of A_c^(1))
+ *   Vr       device, float, column-major n_c x n_c (right singular vectors of A_r^(1))
+ *   sigma    device, double, column-major n_r x n_c KP spectrum
+ *   r, z     device, float, column-major n_r x n_c, distinct
+ *   cuda_stream  cudaStream_t the work is issued on (asynchronous)
+ * Limits: n_r, n_c <= 512 (KP_EINVAL beyond).  The first call on a device
+ * looks up the scratch address on that device (make it before any stream
+ * capture).  All calls share the scratch array and it keeps the last call's
+ * contents: calls that overlap on the GPU (two streams at once) race. */
+kp_status kp_apply_Minv_noalloc(const float* Vc, const float* Vr, const double* sigma, int n_r, int n_c,
+                                double lambda, const float* r, float* z, void* cuda_stream);
+
 /* Getters (synchronise; host buffers).
  *   kp_get_spectrum  sigma: n_r * n_c doubles, column-major KP spectrum
  *   kp_get_terms     s: op_rank doubles (weighted PSF singular values),

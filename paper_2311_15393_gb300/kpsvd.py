@@ -27,7 +27,7 @@ LAMBDA = {"gcv": 0, "wgcv": 1, "discrepancy": 2, "opt": 3}
 # every function declared in include/kpsvd.h
 EXPORTS = ["kp_create", "kp_destroy", "kp_setup", "kp_forward", "tik_pcg", "choose_lambda", "kp_apply_A",
            "kp_apply_K", "kp_apply_Minv", "kp_get_spectrum", "kp_get_terms", "kp_get_kpsvd", "kp_get_rank",
-           "kp_set_option", "kp_launch_count", "kp_status_str", "kp_last_error"]
+           "kp_set_option", "kp_launch_count", "kp_status_str", "kp_last_error", "kp_apply_Minv_noalloc"]
 
 
 class KpError(RuntimeError):
@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "kp_launch_count": ([vp, i], ctypes.c_longlong),
         "kp_status_str": ([i], ctypes.c_char_p),
         "kp_last_error": ([], ctypes.c_char_p),
+        "kp_apply_Minv_noalloc": ([vp, vp, vp, i, i, d, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -107,6 +108,15 @@ def to_device(X: np.ndarray, dtype=None, device: str = "cuda:0"):
 
 def from_device(t, n_r: int, n_c: int) -> np.ndarray:
     return t.detach().to("cpu").double().numpy().reshape((n_r, n_c), order="F")
+
+
+def kp_apply_Minv_noalloc(Vc, Vr, sigma, n_r: int, n_c: int, lam: float, r, z, stream: int | None = None):
+    """Preconditioner solve without any device allocation (see include/kpsvd.h):
+    Vc, Vr float32 column-major factors, sigma float64 spectrum, r, z float32."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(_lib.kp_apply_Minv_noalloc(_ptr(Vc), _ptr(Vr), _ptr(sigma), n_r, n_c, lam, _ptr(r), _ptr(z), stream))
 
 
 @dataclass
