@@ -75,6 +75,7 @@ void kp_free_all(kp_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   tc_plans_free(ctx);
+  ctx->lam_ws = nullptr;
   ctx->ready = false;
 }
 

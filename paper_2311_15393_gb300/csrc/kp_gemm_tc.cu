@@ -11,27 +11,40 @@
 // bf16 slices (hi + lo + ...) and sum slice products to recover FP32-level
 // accuracy where needed.
 //
-// One CTA computes one 128 x 128 output tile (optionally one K-range of it
-// when split-K is used):
-//   warp 0      TMA producer (one elected thread)
-//   warp 1      TMEM allocation + MMA issuer (one elected thread)
+// Persistent kernel, one CTA per SM.  Work units are (128 x BN output tile,
+// K split) pairs handed out round-robin over the grid:
+//   warp 0      TMA producer (one thread): STAGES-deep shared-memory ring
+//   warp 1      TMEM allocation + MMA issuer (one thread)
 //   warps 2..5  epilogue: tcgen05.ld TMEM -> registers -> fused output
-// STAGES-deep shared-memory ring with full / empty mbarriers.  Every wait is
-// bounded; a wait that gives up sets DEV_ERR_TIMEOUT in the device status
-// word and the CTA drains and returns.
+// The accumulator is double-buffered in TMEM (2 x BN columns), so the
+// epilogue of one unit overlaps the main loop of the next.  With split-K each
+// split writes an FP32 partial tile; the split that arrives last (per-tile
+// counter) sums the partials in split order, so results do not depend on
+// scheduling, and runs the fused epilogue.  Every wait is bounded; a wait
+// that gives up sets DEV_ERR_TIMEOUT in the device status word, and the CTA
+// drains and returns.
 #include <cudaTypedefs.h>
+
+#include <algorithm>
 
 #include "kp_internal.h"
 #include "kp_vec.cuh"
 
 namespace {
 
-constexpr int TBM = 128, TBN = 128;
-constexpr int STAGES = 4;
-constexpr int TILE_BYTES = 128 * 128;           // 128 rows x 128 bytes
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;     // A + B
+constexpr int TBM = 128;
 constexpr int TC_THREADS = 192;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+template <int BN>
+struct TcCfg {
+  static constexpr int A_BYTES = TBM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int STAGES = BN == 256 ? 4 : 3;
+  static constexpr int CTAS_PER_SM = BN == 256 ? 1 : 2;  // 2 x (96 KiB ring, 256 TMEM columns) per SM
+  static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 512 /*barriers*/;
+  static constexpr int TMEM_COLS = 2 * BN;
+};
 
 struct TcParams {
   int M, N, K;
@@ -40,10 +53,12 @@ struct TcParams {
   int kblocks;      // ceil(K / BK)
   int splits;       // split-K factor over the (pair, term, kblock) steps
   int steps_total;  // npairs * nkron * kblocks
+  int tiles_m, tiles_n, units;
   uint32_t idesc;
   EpiParams epi;
-  float* ws;        // split-K partials [split][M][N]
-  const float* alpha_dev;  // optional device scale multiplied into the output
+  float* ws;                // split-K partials [split][M][N]
+  unsigned int* counters;   // split-K arrival counters, one per tile (self-resetting)
+  const float* alpha_dev;   // optional device scale multiplied into the output
   const int* flags;
   int* status;
 };
@@ -57,6 +72,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -84,6 +102,7 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
 // 1024 bytes (stride byte offset), descriptor version 1 (sm_100 family)
@@ -134,144 +153,227 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // ------------------------------------------------------------- epilogue
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d) {
+  __nv_fp8_e4m3 q[4] = {__nv_fp8_e4m3(a), __nv_fp8_e4m3(b), __nv_fp8_e4m3(c), __nv_fp8_e4m3(d)};
+  return (uint32_t)q[0].__x | ((uint32_t)q[1].__x << 8) | ((uint32_t)q[2].__x << 16) | ((uint32_t)q[3].__x << 24);
+}
+
 // Fused output of one row segment of 32 columns (row gm, columns gn0..gn0+31).
-// Full, 16-byte aligned segments use vector loads and stores.
+// All indexing is at compile time (the values stay in registers); full
+// segments use 16-byte vector accesses, ragged ones predicated scalars.
 __device__ __forceinline__ void epi_store32(const EpiParams& e, float scale_dev, int gm, int gn0, int N,
-                                            const float (&acc)[32]) {
-  const long long base = (long long)gm * e.ldd + gn0;
+                                            float (&v)[32]) {
   const int cnt = min(32, N - gn0);
   if (cnt <= 0) return;
+  const long long base = (long long)gm * e.ldd + gn0;
   const float* aux = (const float*)e.aux;
   const long long abase = (long long)gm * e.ld_aux + gn0;
   const bool vec = (cnt == 32) && ((base & 7) == 0) && (aux == nullptr || (abase & 3) == 0);
-  float v[32];
   const float a = (float)e.alpha * scale_dev;
 #pragma unroll
-  for (int c = 0; c < 32; ++c) v[c] = a * acc[c];
+  for (int c = 0; c < 32; ++c) v[c] *= a;
   if (aux) {
+    const float bt = (float)e.beta;
     if (vec) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        float4 t = *reinterpret_cast<const float4*>(aux + abase + 4 * q);
-        v[4 * q + 0] = fmaf((float)e.beta, t.x, v[4 * q + 0]);
-        v[4 * q + 1] = fmaf((float)e.beta, t.y, v[4 * q + 1]);
-        v[4 * q + 2] = fmaf((float)e.beta, t.z, v[4 * q + 2]);
-        v[4 * q + 3] = fmaf((float)e.beta, t.w, v[4 * q + 3]);
+        const float4 t = *reinterpret_cast<const float4*>(aux + abase + 4 * q);
+        v[4 * q + 0] = fmaf(bt, t.x, v[4 * q + 0]);
+        v[4 * q + 1] = fmaf(bt, t.y, v[4 * q + 1]);
+        v[4 * q + 2] = fmaf(bt, t.z, v[4 * q + 2]);
+        v[4 * q + 3] = fmaf(bt, t.w, v[4 * q + 3]);
       }
     } else {
-      for (int c = 0; c < cnt; ++c) v[c] = fmaf((float)e.beta, aux[abase + c], v[c]);
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < cnt) v[c] = fmaf(bt, aux[abase + c], v[c]);
     }
   }
   if (e.mode == EPI_NARROW && e.sigma32) {
-    for (int c = 0; c < cnt; ++c) {
-      const double sg = (double)e.sigma32[base + c];
-      v[c] = v[c] * (float)(e.lam2 / (sg * sg + e.lam2));
+    // S' = lam^2 / (sigma^2 + lam^2) in FP32 (it scales a value about to be
+    // rounded to 16 or 8 bits; FP64 arithmetic is slow on this part)
+    const float l2 = (float)e.lam2;
+    if (vec) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 sg = *reinterpret_cast<const float4*>(e.sigma32 + base + 4 * q);
+        v[4 * q + 0] *= __fdividef(l2, fmaf(sg.x, sg.x, l2));
+        v[4 * q + 1] *= __fdividef(l2, fmaf(sg.y, sg.y, l2));
+        v[4 * q + 2] *= __fdividef(l2, fmaf(sg.z, sg.z, l2));
+        v[4 * q + 3] *= __fdividef(l2, fmaf(sg.w, sg.w, l2));
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < cnt) {
+          const float sg = e.sigma32[base + c];
+          v[c] *= __fdividef(l2, fmaf(sg, sg, l2));
+        }
+      }
     }
   }
-  switch (e.mode) {
-    case EPI_F32: {
-      float* out = (float*)e.out + base;
+  if (e.mode == EPI_F32) {
+    float* out = (float*)e.out + base;
+    if (vec) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4*>(out + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < cnt) out[c] = v[c];
+    }
+  } else if (e.mode == EPI_SLICES) {
+    __nv_bfloat16* out = (__nv_bfloat16*)e.out + base;
+    for (int s = 0; s < e.slices; ++s) {
+      __nv_bfloat16* o = out + s * e.slice_stride;
       if (vec) {
+        uint32_t w[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          *reinterpret_cast<float4*>(out + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < 16; ++q) {
+          w[q] = pack_bf16(v[2 * q], v[2 * q + 1]);
+          const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[q]);
+          v[2 * q] -= __bfloat162float(h.x);
+          v[2 * q + 1] -= __bfloat162float(h.y);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(o + 8 * q) = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
       } else {
-        for (int c = 0; c < cnt; ++c) out[c] = v[c];
-      }
-      break;
-    }
-    case EPI_SLICES: {
-      __nv_bfloat16* out = (__nv_bfloat16*)e.out + base;
-      for (int s = 0; s < e.slices; ++s) {
-        __align__(16) __nv_bfloat16 h[32];
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
-          h[c] = __float2bfloat16_rn(v[c]);
-          v[c] -= __bfloat162float(h[c]);
-        }
-        __nv_bfloat16* o = out + s * e.slice_stride;
-        if (vec) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(o + 8 * q) = *reinterpret_cast<const uint4*>(h + 8 * q);
-        } else {
-          for (int c = 0; c < cnt; ++c) o[c] = h[c];
+          const __nv_bfloat16 h = __float2bfloat16_rn(v[c]);
+          if (c < cnt) o[c] = h;
+          v[c] -= __bfloat162float(h);
         }
       }
-      break;
     }
-    case EPI_NARROW: {
-      if (e.narrow == NT_E4M3) {
-        __align__(16) __nv_fp8_e4m3 h[32];
+  } else if (e.mode == EPI_NARROW) {
+    if (e.narrow == NT_E4M3) {
+      uint8_t* o = (uint8_t*)e.out + base;
+      if (vec && (base & 15) == 0) {
+        uint32_t w[8];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) h[c] = __nv_fp8_e4m3(v[c]);
-        __nv_fp8_e4m3* o = (__nv_fp8_e4m3*)e.out + base;
-        if (vec && (base & 15) == 0) {
-          *reinterpret_cast<uint4*>(o) = *reinterpret_cast<const uint4*>(h);
-          *reinterpret_cast<uint4*>(o + 16) = *reinterpret_cast<const uint4*>(h + 16);
-        } else {
-          for (int c = 0; c < cnt; ++c) o[c] = h[c];
-        }
+        for (int q = 0; q < 8; ++q) w[q] = pack_e4m3(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        *reinterpret_cast<uint4*>(o) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(o + 16) = make_uint4(w[4], w[5], w[6], w[7]);
       } else {
-        __align__(16) uint16_t h[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < cnt) o[c] = __nv_fp8_e4m3(v[c]).__x;
+      }
+    } else {
+      const bool bf = e.narrow == NT_BF16;
+      uint16_t* o = (uint16_t*)e.out + base;
+      if (vec) {
+        uint32_t w[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) w[q] = bf ? pack_bf16(v[2 * q], v[2 * q + 1]) : pack_f16(v[2 * q], v[2 * q + 1]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(o + 8 * q) = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+      } else {
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
-          if (e.narrow == NT_BF16) {
-            __nv_bfloat16 b = __float2bfloat16_rn(v[c]);
-            h[c] = *reinterpret_cast<uint16_t*>(&b);
-          } else {
-            __half b = __float2half_rn(v[c]);
-            h[c] = *reinterpret_cast<uint16_t*>(&b);
+          if (c < cnt) {
+            const uint32_t w = bf ? pack_bf16(v[c], 0.f) : pack_f16(v[c], 0.f);
+            o[c] = (uint16_t)(w & 0xFFFFu);
           }
         }
-        uint16_t* o = (uint16_t*)e.out + base;
-        if (vec) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(o + 8 * q) = *reinterpret_cast<const uint4*>(h + 8 * q);
-        } else {
-          for (int c = 0; c < cnt; ++c) o[c] = h[c];
-        }
       }
-      break;
     }
-    default:
-      break;
   }
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// FP32 partial of one 32-column row segment (split-K)
+__device__ __forceinline__ void partial_store32(float* w, int cnt, const float (&v)[32]) {
+  if (cnt == 32) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<float4*>(w + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < cnt) w[c] = v[c];
+  }
+}
+__device__ __forceinline__ void partial_add32(const float* w, int cnt, float (&v)[32]) {
+  if (cnt == 32) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 t = __ldcg(reinterpret_cast<const float4*>(w + 4 * q));
+      v[4 * q + 0] += t.x;
+      v[4 * q + 1] += t.y;
+      v[4 * q + 2] += t.z;
+      v[4 * q + 3] += t.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < cnt) v[c] += __ldcg(w + c);
+  }
+}
+
+struct Unit {
+  int m0, n0, tile, split, step0, nsteps;
+};
+__device__ __forceinline__ Unit decode_unit(const TcParams& p, int u, int bn) {
+  Unit r;
+  r.split = u % p.splits;
+  r.tile = u / p.splits;
+  r.m0 = (r.tile / p.tiles_n) * TBM;
+  r.n0 = (r.tile % p.tiles_n) * bn;
+  const int per = (p.steps_total + p.splits - 1) / p.splits;
+  r.step0 = r.split * per;
+  r.nsteps = max(0, min(p.steps_total, r.step0 + per) - r.step0);
+  return r;
+}
+
+template <int KIND, int BN>
+__global__ void __launch_bounds__(TC_THREADS, TcCfg<BN>::CTAS_PER_SM)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+  using C = TcCfg<BN>;
   if (p.flags && *(volatile const int*)p.flags) return;
+  if (threadIdx.x == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
   extern __shared__ unsigned char smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE);
   uint64_t* full = bars;
-  uint64_t* empty = bars + STAGES;
-  uint64_t* tfull = bars + 2 * STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  uint64_t* empty = bars + C::STAGES;
+  uint64_t* tfull = bars + 2 * C::STAGES;   // [2]
+  uint64_t* tempty = tfull + 2;             // [2]
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   __shared__ int s_abort;
+  __shared__ int s_last;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
-  const int split = blockIdx.z;
-  const int per = (p.steps_total + p.splits - 1) / p.splits;
-  const int step0 = split * per;
-  const int step1 = min(p.steps_total, step0 + per);
-  const int nsteps = max(0, step1 - step0);
-
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    mbar_init(smem_u32(tfull), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TBN)
+                 "r"(C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -279,81 +381,141 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const int ksh = KIND == TC_E4M3 ? 0 : 1;  // K elements per 128-byte row: 128 >> ksh
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      for (int it = 0; it < nsteps; ++it) {
-        const int stp = step0 + it;
-        const int kb = stp % p.kblocks;
-        const int rest = stp / p.kblocks;
-        const int k = rest % p.nkron;
-        const int pr = rest / p.nkron;
-        const int ta = p.sa[pr] * p.a_terms + k;
-        const int tb = p.sb[pr] * p.b_terms + k;
-        const int s = it % STAGES;
-        const uint32_t ph = (it / STAGES) & 1;
-        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, p.status)) {
-          s_abort = 1;
-          break;
+      int it = 0;
+      for (int u = blockIdx.x; u < p.units && !*(volatile int*)&s_abort; u += gridDim.x) {
+        const Unit w = decode_unit(p, u, BN);
+        for (int j = 0; j < w.nsteps; ++j, ++it) {
+          const int stp = w.step0 + j;
+          const int kb = stp % p.kblocks;
+          const int rest = stp / p.kblocks;
+          const int k = rest % p.nkron;
+          const int pr = rest / p.nkron;
+          const int s = it % C::STAGES;
+          const uint32_t ph = (it / C::STAGES) & 1;
+          if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, p.status)) {
+            s_abort = 1;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full[s]);
+          mbar_expect_tx(fb, C::STAGE);
+          const int kc = (kb * 128) >> ksh;
+          const uint32_t sa = smem_u32(smem + s * C::STAGE);
+          tma_load_3d(sa, &tmA, kc, w.m0, p.sa[pr] * p.a_terms + k, fb);
+          tma_load_3d(sa + C::A_BYTES, &tmB, kc, w.n0, p.sb[pr] * p.b_terms + k, fb);
         }
-        const uint32_t fb = smem_u32(&full[s]);
-        mbar_expect_tx(fb, STAGE_BYTES);
-        const int kc = kb * 128 / (KIND == TC_E4M3 ? 1 : 2);
-        tma_load_3d(smem_u32(smem + s * STAGE_BYTES), &tmA, kc, m0, ta, fb);
-        tma_load_3d(smem_u32(smem + s * STAGE_BYTES + TILE_BYTES), &tmB, kc, n0, tb, fb);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      for (int it = 0; it < nsteps; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (it / STAGES) & 1;
-        if (*(volatile int*)&s_abort || !mbar_wait(smem_u32(&full[s]), ph, p.status)) {
+      int it = 0, i = 0;
+      for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++i) {
+        const Unit w = decode_unit(p, u, BN);
+        const int buf = i & 1;
+        if (*(volatile int*)&s_abort || !mbar_wait(smem_u32(&tempty[buf]), ((i >> 1) & 1) ^ 1, p.status)) {
           s_abort = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t b0 = a0 + TILE_BYTES;
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        bool ok = true;
+        for (int j = 0; j < w.nsteps; ++j, ++it) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (it / C::STAGES) & 1;
+          if (*(volatile int*)&s_abort || !mbar_wait(smem_u32(&full[s]), ph, p.status)) {
+            s_abort = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + s * C::STAGE);
+          const uint32_t b0 = a0 + C::A_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {  // 4 x 32 bytes of K per 128-byte row
-          mma_issue<KIND>(tmem, make_sdesc(a0 + kk * 32), make_sdesc(b0 + kk * 32), p.idesc,
-                          (it > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < 4; ++kk)  // 4 x 32 bytes of K per 128-byte row
+            mma_issue<KIND>(d, make_sdesc(a0 + kk * 32), make_sdesc(b0 + kk * 32), p.idesc,
+                            (j > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&empty[s]));
         }
-        mma_commit(smem_u32(&empty[s]));
+        mma_commit(smem_u32(&tfull[buf]));
+        if (!ok) break;
       }
-      mma_commit(smem_u32(tfull));
     }
   } else {
     // ---------------- epilogue warps 2..5 -> TMEM lanes 32 * (warp % 4)
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
-    const int gm = m0 + row;
-    bool ok = mbar_wait(smem_u32(tfull), 0, p.status);
-    tc_fence_after();
-    if (ok) {
-      const float sdev = p.alpha_dev ? *p.alpha_dev : 1.f;
+    const int etid = threadIdx.x - 64;
+    const float sdev = p.alpha_dev ? *p.alpha_dev : 1.f;
+    int i = 0;
+    for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++i) {
+      const Unit w = decode_unit(p, u, BN);
+      const int buf = i & 1;
+      if (!mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1, p.status)) break;
+      tc_fence_after();
+      const int gm = w.m0 + row;
+      const bool row_ok = gm < p.M;
+      if (p.splits == 1) {
 #pragma unroll 1
-      for (int chunk = 0; chunk < TBN / 32; ++chunk) {
-        float acc[32];
-        if (nsteps > 0) {
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + chunk * 32, acc);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-        }
-        const int gn0 = n0 + chunk * 32;
-        if (gm < p.M && gn0 < p.N) {
-          if (p.epi.mode == EPI_PARTIAL) {
-            float* w = p.ws + ((long long)split * p.M + gm) * p.N + gn0;
-            const int cnt = min(32, p.N - gn0);
-            for (int c = 0; c < cnt; ++c) w[c] = acc[c];
+        for (int chunk = 0; chunk < BN / 32; ++chunk) {
+          float acc[32];
+          if (w.nsteps > 0) {
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + chunk * 32), acc);
           } else {
-            epi_store32(p.epi, sdev, gm, gn0, p.N, acc);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+          }
+          const int gn0 = w.n0 + chunk * 32;
+          if (row_ok && gn0 < p.N) epi_store32(p.epi, sdev, gm, gn0, p.N, acc);
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&tempty[buf]));
+      } else {
+        // split-K: FP32 partial, then the last split to arrive finishes the tile
+#pragma unroll 1
+        for (int chunk = 0; chunk < BN / 32; ++chunk) {
+          float acc[32];
+          if (w.nsteps > 0) {
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + chunk * 32), acc);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+          }
+          const int gn0 = w.n0 + chunk * 32;
+          if (row_ok && gn0 < p.N)
+            partial_store32(p.ws + ((long long)w.split * p.M + gm) * p.N + gn0, min(32, p.N - gn0), acc);
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&tempty[buf]));
+        __threadfence();
+        epi_bar();
+        if (etid == 0) {
+          const unsigned int prev = atomicAdd(&p.counters[w.tile], 1u);
+          s_last = (prev == (unsigned int)(p.splits - 1)) ? 1 : 0;
+          if (s_last) p.counters[w.tile] = 0u;
+        }
+        epi_bar();
+        if (s_last) {
+          __threadfence();
+          if (row_ok) {
+#pragma unroll 1
+            for (int chunk = 0; chunk < BN / 32; ++chunk) {
+              const int gn0 = w.n0 + chunk * 32;
+              if (gn0 >= p.N) break;
+              const int cnt = min(32, p.N - gn0);
+              float acc[32];
+#pragma unroll
+              for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+              for (int s = 0; s < p.splits; ++s) partial_add32(p.ws + ((long long)s * p.M + gm) * p.N + gn0, cnt, acc);
+              epi_store32(p.epi, sdev, gm, gn0, p.N, acc);
+            }
           }
         }
+        epi_bar();  // s_last is reused by the next unit
       }
     }
   }
@@ -361,28 +523,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN) : "memory");
-  }
-}
-
-// split-K finish: sum partials in split order, then the fused epilogue
-__global__ void k_splitk_finish(const float* __restrict__ ws, int splits, int M, int N, EpiParams e,
-                                const float* alpha_dev, const int* flags) {
-  if (flags && *(volatile const int*)flags) return;
-  const float sdev = alpha_dev ? *alpha_dev : 1.f;
-  const long long tot = (long long)M * ((N + 31) / 32);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const int gm = (int)(t / ((N + 31) / 32));
-    const int gn0 = (int)(t % ((N + 31) / 32)) * 32;
-    float acc[32];
-    const int cnt = min(32, N - gn0);
-#pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-    for (int s = 0; s < splits; ++s) {
-      const float* w = ws + ((long long)s * M + gm) * N + gn0;
-      for (int c = 0; c < cnt; ++c) acc[c] += w[c];
-    }
-    epi_store32(e, sdev, gm, gn0, N, acc);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
   }
 }
 
@@ -393,6 +534,7 @@ struct TcGemmPlan {
   CUtensorMap mapA, mapB;
   TcParams params;
   int kind;
+  int bn;
   dim3 grid;
 };
 
@@ -417,12 +559,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-static kp_status make_map(CUtensorMap* map, const GemmOp& op, int kind) {
+static kp_status make_map(CUtensorMap* map, const GemmOp& op, int kind, int box_rows) {
   const int esize = kind == TC_E4M3 ? 1 : 2;
   const int bk = 128 / esize;
   cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows, (cuuint64_t)(op.nterm_idx > 0 ? op.nterm_idx : 1)};
   cuuint64_t strides[2] = {(cuuint64_t)(op.ld * esize), (cuuint64_t)(op.tstride * esize)};
-  cuuint32_t box[3] = {(cuuint32_t)bk, 128u, 1u};
+  cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1u};
   cuuint32_t estr[3] = {1, 1, 1};
   if (((uintptr_t)op.ptr & 15) || (strides[0] & 15) || (strides[1] & 15)) {
     kp_set_error("tensor map: base or strides not 16-byte aligned (ld=%lld ts=%lld)", op.ld, op.tstride);
@@ -444,7 +586,7 @@ static kp_status make_map(CUtensorMap* map, const GemmOp& op, int kind) {
   return KP_OK;
 }
 
-static uint32_t make_idesc(int kind) {
+static uint32_t make_idesc(int kind, int bn) {
   uint32_t d = 0;
   d |= 1u << 4;  // D format F32
   if (kind == TC_BF16) {
@@ -452,7 +594,7 @@ static uint32_t make_idesc(int kind) {
     d |= 1u << 10;  // B BF16
   }                 // F16 / E4M3: format code 0
   // K-major A and B (bits 15, 16 = 0)
-  d |= (uint32_t)(TBN >> 3) << 17;
+  d |= (uint32_t)(bn >> 3) << 17;
   d |= (uint32_t)(TBM >> 4) << 24;
   return d;
 }
@@ -474,9 +616,12 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
     kp_set_error("tc_plan_create: K * element size must be a multiple of 16 bytes (K=%d)", g.K);
     return KP_ENOTSUP;
   }
+  // 128 x 128 tiles, two CTAs per SM so that one's prologue / epilogue
+  // overlaps the other's main loop (128 x 256 kept for very wide outputs)
+  const int bn = (g.N >= 256 && (long long)((g.M + TBM - 1) / TBM) * ((g.N + 255) / 256) >= 4LL * ctx->sm_count) ? 256 : 128;
   TcGemmPlan* pl = new TcGemmPlan();
-  kp_status st = make_map(&pl->mapA, g.A, kind);
-  if (st == KP_OK) st = make_map(&pl->mapB, g.B, kind);
+  kp_status st = make_map(&pl->mapA, g.A, kind, TBM);
+  if (st == KP_OK) st = make_map(&pl->mapB, g.B, kind, bn);
   if (st != KP_OK) {
     delete pl;
     return st;
@@ -496,23 +641,42 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
   const int bk = 128 / esize;
   p.kblocks = (g.K + bk - 1) / bk;
   p.steps_total = g.npairs * g.nkron * p.kblocks;
-  if (splits < 1) splits = 1;
-  if (splits > p.steps_total) splits = p.steps_total;
+  p.tiles_m = (g.M + TBM - 1) / TBM;
+  p.tiles_n = (g.N + bn - 1) / bn;
+  const int tiles = p.tiles_m * p.tiles_n;
+  if (splits < 1) {  // split K only for few tiles and long K (>= 32 steps per split)
+    splits = 1;
+    const int slots = 2 * ctx->sm_count;
+    if (2 * tiles < slots && p.steps_total >= 64)
+      splits = std::max(1, std::min({4, p.steps_total / 32, (slots + tiles - 1) / tiles}));
+  }
+  splits = std::min(splits, p.steps_total);
   p.splits = splits;
-  p.idesc = make_idesc(kind);
+  p.units = tiles * splits;
+  p.idesc = make_idesc(kind, bn);
   p.epi = g.epi;
   if (p.epi.ld_aux == 0) p.epi.ld_aux = p.epi.ldd;
   p.ws = ctx->w_split;
+  p.counters = nullptr;
   p.alpha_dev = nullptr;
   p.flags = g.flags;
   p.status = ctx->dev_status;
-  if (splits > 1 && (long long)splits * g.M * g.N > ctx->w_split_elems) {
-    delete pl;
-    kp_set_error("tc_plan_create: split-K workspace too small");
-    return KP_EINVAL;
+  if (splits > 1) {
+    if ((long long)splits * g.M * g.N > ctx->w_split_elems) {
+      delete pl;
+      kp_set_error("tc_plan_create: split-K workspace too small");
+      return KP_EINVAL;
+    }
+    kp_status as = kp_alloc(ctx, (void**)&p.counters, sizeof(unsigned int) * tiles);
+    if (as != KP_OK) {
+      delete pl;
+      return as;
+    }
+    cudaMemsetAsync(p.counters, 0, sizeof(unsigned int) * tiles, ctx->stream);
   }
   pl->kind = kind;
-  pl->grid = dim3((g.N + TBN - 1) / TBN, (g.M + TBM - 1) / TBM, splits);
+  pl->bn = bn;
+  pl->grid = dim3(std::min(p.units, ctx->sm_count * (bn == 256 ? 1 : 2)), 1, 1);
   ctx->tc_plans.push_back(pl);
   *out = pl;
   return KP_OK;
@@ -528,14 +692,15 @@ void tc_plan_set_runtime(TcGemmPlan* plan, const float* alpha_dev, const int* fl
   plan->params.flags = flags;
 }
 
-template <int KIND>
+template <int KIND, int BN>
 static kp_status launch_kind(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
   static bool attr_set = false;
   if (!attr_set) {
-    KP_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    KP_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TcCfg<BN>::SMEM));
     attr_set = true;
   }
-  tc_gemm_kernel<KIND><<<pl->grid, TC_THREADS, SMEM_BYTES, ctx->stream>>>(pl->mapA, pl->mapB, p);
+  tc_gemm_kernel<KIND, BN><<<pl->grid, TC_THREADS, TcCfg<BN>::SMEM, ctx->stream>>>(pl->mapA, pl->mapB, p);
   KP_LAUNCHED(ctx);
   return KP_OK;
 }
@@ -546,22 +711,16 @@ kp_status tc_plan_run(kp_ctx* ctx, TcGemmPlan* pl, const EpiParams* epi_override
     p.epi = *epi_override;
     if (p.epi.ld_aux == 0) p.epi.ld_aux = p.epi.ldd;
   }
-  const EpiParams final_epi = p.epi;
-  if (p.splits > 1) p.epi.mode = EPI_PARTIAL;
+  const bool wide = pl->bn == 256;
+  kp_status st;
   if (pl->kind == TC_BF16)
-    KP_TRY(launch_kind<TC_BF16>(ctx, pl, p));
+    st = wide ? launch_kind<TC_BF16, 256>(ctx, pl, p) : launch_kind<TC_BF16, 128>(ctx, pl, p);
   else if (pl->kind == TC_F16)
-    KP_TRY(launch_kind<TC_F16>(ctx, pl, p));
+    st = wide ? launch_kind<TC_F16, 256>(ctx, pl, p) : launch_kind<TC_F16, 128>(ctx, pl, p);
   else
-    KP_TRY(launch_kind<TC_E4M3>(ctx, pl, p));
+    st = wide ? launch_kind<TC_E4M3, 256>(ctx, pl, p) : launch_kind<TC_E4M3, 128>(ctx, pl, p);
+  KP_TRY(st);
   KP_CUDA(cudaGetLastError());
-  if (p.splits > 1) {
-    long long tot = (long long)p.M * ((p.N + 31) / 32);
-    int blocks = (int)std::min<long long>((tot + 255) / 256, (long long)ctx->sm_count * 8);
-    k_splitk_finish<<<blocks, 256, 0, ctx->stream>>>(p.ws, p.splits, p.M, p.N, final_epi, p.alpha_dev, p.flags);
-    KP_LAUNCHED(ctx);
-    KP_CUDA(cudaGetLastError());
-  }
   return KP_OK;
 }
 

@@ -156,6 +156,7 @@ struct kp_ctx {
   void* w_img2 = nullptr;    // p slices (inner operator input)
   void* w_img3 = nullptr;    // x slices (accurate operator input)
   double* hist = nullptr;    // residual history (device)
+  void* lam_ws = nullptr;    // choose_lambda scratch (allocated at its first call)
   int hist_cap = 0;
   float* w_split = nullptr;  // split-K partials
   long long w_split_elems = 0;

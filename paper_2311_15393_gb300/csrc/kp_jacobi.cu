@@ -9,7 +9,10 @@
 // makes the two columns orthogonal; it is applied to A and accumulated in V.
 // Pairs are visited in the round-robin (circle) order: each of the n - 1
 // rounds holds n / 2 disjoint pairs, one per thread block, and a sweep is the
-// n - 1 rounds, captured once as a CUDA graph.  Sweeps repeat until no pair
+// n - 1 rounds, captured once as a CUDA graph (a sweep that would rotate no
+// pair is replaced by the same test on the Gram matrix W^T W, one FP64
+// GEMM, before the first sweep and after sweeps with few rotations).  Sweeps
+// repeat until no pair
 // needs a rotation: |gamma| <= tol sqrt(alpha beta) (tol >= m eps), or
 // |gamma| <= m eps ||A||_F max(|a_i|, |a_j|), i.e. what would be removed is
 // below the rounding noise every column carries (without this absolute
@@ -295,6 +298,21 @@ __global__ void k_mgs2(double* __restrict__ Q, int m, int p) {
   }
 }
 
+// count pairs (i < j) of the Gram matrix G = W^T W that still need a rotation
+// (same test as k_jacobi_round: relative and absolute floors)
+__global__ void k_gram_violations(const double* __restrict__ G, int n, double tol, double floor,
+                                  unsigned int* __restrict__ count) {
+  const long long tot = (long long)n * n;
+  unsigned int local = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    if (i >= j) continue;
+    const double ga = G[t], al = G[(long long)i * n + i], be = G[(long long)j * n + j];
+    if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be) && fabs(ga) > floor * sqrt(fmax(al, be))) ++local;
+  }
+  if (local) atomicAdd(count, local);
+}
+
 }  // namespace
 
 // Sweeps on W (m x n col-major, in place) accumulating into V (n x n,
@@ -335,8 +353,39 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
       return KP_ECUDA;
     }
     KP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    // Before the first sweep, and instead of a sweep that would only confirm
+    // convergence, count the pairs that need a rotation on G = W^T W (one
+    // FP64 GEMM): a sweep over a matrix with no such pair rotates nothing.
+    double* G = nullptr;
+    KP_TRY(kp_alloc(ctx, (void**)&G, sizeof(double) * (size_t)n * n));
+    auto gram_clean = [&](bool* clean) -> kp_status {
+      GemmDesc gd;  // G[i][j] = sum_r W[r, i] W[r, j]
+      gd.M = n;
+      gd.N = n;
+      gd.K = m;
+      gd.A.ptr = W;
+      gd.A.ld = m;
+      gd.B.ptr = W;
+      gd.B.ld = m;
+      gd.epi.mode = EPI_T;
+      gd.epi.out = G;
+      gd.epi.ldd = n;
+      KP_TRY(simt_gemm<double>(ctx, gd));
+      KP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st));
+      const int gb = std::max(1, std::min((int)(((long long)n * n + 255) / 256), ctx->sm_count * 8));
+      k_gram_violations<<<gb, 256, 0, st>>>(G, n, tol, floor, cnt);
+      KP_LAUNCHED(ctx);
+      unsigned int h = 0;
+      KP_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+      KP_CUDA(cudaStreamSynchronize(st));
+      *clean = h == 0;
+      return KP_OK;
+    };
     unsigned int h_cnt = 1;
-    for (sweeps = 0; sweeps < ctx->jacobi_max_sweeps; ++sweeps) {
+    bool clean = false;
+    KP_TRY(gram_clean(&clean));
+    if (clean) h_cnt = 0;
+    for (sweeps = 0; !clean && sweeps < ctx->jacobi_max_sweeps; ++sweeps) {
       KP_CUDA(cudaGraphLaunch(exec, st));
       ctx->launches += npad;
       KP_CUDA(cudaMemcpyAsync(&h_cnt, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
@@ -344,6 +393,15 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
       if (h_cnt == 0) {
         ++sweeps;
         break;
+      }
+      // few rotations: the next sweep is likely only a confirmation
+      if ((long long)h_cnt * 8 < (long long)npad) {
+        KP_TRY(gram_clean(&clean));
+        if (clean) {
+          h_cnt = 0;
+          ++sweeps;
+          break;
+        }
       }
     }
     cudaGraphExecDestroy(exec);

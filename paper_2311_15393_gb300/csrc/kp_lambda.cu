@@ -269,21 +269,37 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
   cudaStream_t st = ctx->stream;
   const bool f64 = ctx->vec_prec == KP_F64;
   const int gr = std::max(1, std::min((int)((N + 255) / 256), ctx->sm_count * 8));
-  // scratch (problem-lifetime allocations, made once)
-  double *B64, *T, *bh, *xh = nullptr, *s2, *lam2_dev, *part, *sums, *ext;
-  float *s2f, *sgf, *bhf, *xhf = nullptr;
-  KP_TRY(kp_alloc(ctx, (void**)&B64, sizeof(double) * N));
-  KP_TRY(kp_alloc(ctx, (void**)&T, sizeof(double) * N));
-  KP_TRY(kp_alloc(ctx, (void**)&bh, sizeof(double) * N));
-  KP_TRY(kp_alloc(ctx, (void**)&s2, sizeof(double) * N));
-  KP_TRY(kp_alloc(ctx, (void**)&s2f, sizeof(float) * N));
-  KP_TRY(kp_alloc(ctx, (void**)&sgf, sizeof(float) * N));
-  KP_TRY(kp_alloc(ctx, (void**)&bhf, sizeof(float) * N));
-  KP_TRY(kp_alloc(ctx, (void**)&lam2_dev, sizeof(double) * NGRID));
+  // scratch: allocated at the first call after a kp_setup, kept with the problem
+  if (!ctx->lam_ws) {
+    const int chunks_max = std::max(1, std::min((int)((N + LT - 1) / LT), ctx->sm_count * 2));
+    const size_t bytes = sizeof(double) * (size_t)N * 6 + sizeof(float) * (size_t)N * 4 +
+                         sizeof(double) * (NGRID + 2 * (size_t)chunks_max * NGRID + 2 * NGRID + 2) + 1024;
+    KP_TRY(kp_alloc(ctx, &ctx->lam_ws, bytes));
+  }
+  char* wp = (char*)ctx->lam_ws;
+  auto take = [&](size_t bytes) {
+    void* q = wp;
+    wp += (bytes + 255) & ~(size_t)255;
+    return q;
+  };
+  double* B64 = (double*)take(sizeof(double) * N);
+  double* T = (double*)take(sizeof(double) * N);
+  double* bh = (double*)take(sizeof(double) * N);
+  double* s2 = (double*)take(sizeof(double) * N);
+  double* xh = (double*)take(sizeof(double) * N);
+  float* s2f = (float*)take(sizeof(float) * N);
+  float* sgf = (float*)take(sizeof(float) * N);
+  float* bhf = (float*)take(sizeof(float) * N);
+  float* xhf = (float*)take(sizeof(float) * N);
+  double* lam2_dev = (double*)take(sizeof(double) * NGRID);
   const int chunks = std::max(1, std::min((int)((N + LT - 1) / LT), ctx->sm_count * 2));
-  KP_TRY(kp_alloc(ctx, (void**)&part, sizeof(double) * 2 * (size_t)chunks * NGRID));
-  KP_TRY(kp_alloc(ctx, (void**)&sums, sizeof(double) * 2 * NGRID));
-  KP_TRY(kp_alloc(ctx, (void**)&ext, sizeof(double) * 2));
+  double* part = (double*)take(sizeof(double) * 2 * (size_t)chunks * NGRID);
+  double* sums = (double*)take(sizeof(double) * 2 * NGRID);
+  double* ext = (double*)take(sizeof(double) * 2);
+  if (method != KP_LAMBDA_OPT) {
+    xh = nullptr;
+    xhf = nullptr;
+  }
 
   // coefficients in the KP basis: Y^ = U_c^T Y U_r (or V for x_true)
   auto kp_coeffs = [&](const void* img, const double* Lc, const double* Rr, double* out) -> kp_status {
@@ -321,11 +337,7 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
     return simt_gemm<double>(ctx, g2);
   };
   KP_TRY(kp_coeffs(b, ctx->Uc, ctx->Ur, bh));
-  if (method == KP_LAMBDA_OPT) {
-    KP_TRY(kp_alloc(ctx, (void**)&xh, sizeof(double) * N));
-    KP_TRY(kp_alloc(ctx, (void**)&xhf, sizeof(float) * N));
-    KP_TRY(kp_coeffs(x_true, ctx->Vc, ctx->Vr, xh));
-  }
+  if (method == KP_LAMBDA_OPT) KP_TRY(kp_coeffs(x_true, ctx->Vc, ctx->Vr, xh));
   k_prep<<<gr, 256, 0, st>>>(ctx->Sigma64, bh, xh, N, s2, s2f, sgf, bhf, xhf);
   KP_LAUNCHED(ctx);
   k_absmax_min<<<1, 1024, 0, st>>>(ctx->Sigma64, N, ext);
@@ -551,12 +563,7 @@ extern "C" kp_status choose_lambda(kp_ctx* ctx, const void* b, kp_lambda_method 
     return KP_EINVAL;
   }
   KP_TRY(kp_enter(ctx));
-  size_t nalloc = ctx->allocs.size();
   kp_status s = choose_lambda_impl(ctx, b, method, param, x_true, lambda_out);
-  // release this call's scratch
-  cudaStreamSynchronize(ctx->stream);
-  for (size_t i = nalloc; i < ctx->allocs.size(); ++i) cudaFree(ctx->allocs[i]);
-  ctx->allocs.resize(nalloc);
   kp_status l = kp_leave(ctx);
   return s != KP_OK ? s : l;
 }

@@ -72,13 +72,9 @@ static void pairs_for(kp_ctx* ctx, int mode, GemmDesc& g) {
   }
 }
 
-static int choose_splits(kp_ctx* ctx, int M, int N, int steps) {
-  if (ctx->splitk_override > 0) return std::min(ctx->splitk_override, steps);
-  const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
-  int s = (ctx->sm_count + tiles - 1) / tiles;
-  s = std::max(1, std::min(s, 4));
-  return std::min(s, steps);
-}
+// split-K factor for the square GEMMs: 0 lets the GEMM plan pick enough
+// (tile, split) units to fill the GPU
+static int square_splits(kp_ctx* ctx) { return ctx->splitk_override > 0 ? ctx->splitk_override : 0; }
 
 // GEMM descriptors of the operator: which = 0..3 (G1..G4)
 static GemmDesc op_desc(kp_ctx* ctx, int which, int mode, const void* bptr) {
@@ -216,9 +212,7 @@ kp_status ops_prepare(kp_ctx* ctx) {
       for (int w = 0; w < 4; ++w) {
         const void* bptr = w == 0 ? (mode == OP_INNER ? ctx->w_img2 : ctx->w_img3) : (w == 2 ? ctx->w_img : nullptr);
         GemmDesc g = op_desc(ctx, w, mode, bptr);
-        const int bk = 64;
-        const int steps = g.npairs * g.nkron * ((g.K + bk - 1) / bk);
-        const int splits = (w == 1 || w == 3) ? choose_splits(ctx, g.M, g.N, steps) : 1;
+        const int splits = (w == 1 || w == 3) ? square_splits(ctx) : 1;
         KP_TRY(tc_plan_create(ctx, g, TC_BF16, splits, &os->G[mode][w]));
       }
     }
@@ -227,9 +221,7 @@ kp_status ops_prepare(kp_ctx* ctx) {
     const int kind = ctx->pc_prec == KP_BF16 ? TC_BF16 : (ctx->pc_prec == KP_F16 ? TC_F16 : TC_E4M3);
     for (int w = 0; w < 4; ++w) {
       GemmDesc g = pc_desc(ctx, w);
-      const int bk = kind == TC_E4M3 ? 128 : 64;
-      const int steps = g.npairs * ((g.K + bk - 1) / bk);
-      KP_TRY(tc_plan_create(ctx, g, kind, choose_splits(ctx, g.M, g.N, steps), &os->P[w]));
+      KP_TRY(tc_plan_create(ctx, g, kind, square_splits(ctx), &os->P[w]));
     }
   }
   return KP_OK;

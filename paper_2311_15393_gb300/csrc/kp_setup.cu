@@ -208,10 +208,12 @@ static int grid_for(kp_ctx* ctx, long long n) {
 
 static bool is_tc(kp_prec p) { return p == KP_BF16 || p == KP_BF16X3 || p == KP_F16 || p == KP_E4M3; }
 
-// projected spectrum factor: d[k][i] = diag(U^T F^(k) V)_i for square n
-static kp_status projected_diag(kp_ctx* ctx, const double* F, const double* U, const double* V, int n, int rank,
-                                double* d, double* tmp) {
-  for (int k = 0; k < rank; ++k) {
+// projected spectrum factor: d[k][i] = diag(U^T F^(k) V)_i for square n; for
+// k = 0 (the factor the SVD is of) that diagonal is the singular values
+static kp_status projected_diag(kp_ctx* ctx, const double* F, const double* U, const double* V, const double* s,
+                                int n, int rank, double* d, double* tmp) {
+  KP_CUDA(cudaMemcpyAsync(d, s, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  for (int k = 1; k < rank; ++k) {
     GemmDesc g;
     g.M = n;
     g.N = n;
@@ -372,8 +374,8 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
     KP_TRY(kp_alloc(ctx, (void**)&dr, sizeof(double) * (size_t)rk * n_c));
     if (sigma == KP_SIGMA_PROJECTED) {
       KP_TRY(kp_alloc(ctx, (void**)&tmp, sizeof(double) * (size_t)nmax * nmax));
-      KP_TRY(projected_diag(ctx, ctx->Ac64, ctx->Uc, ctx->Vc, n_r, rank, dc, tmp));
-      KP_TRY(projected_diag(ctx, ctx->Ar64, ctx->Ur, ctx->Vr, n_c, rank, dr, tmp));
+      KP_TRY(projected_diag(ctx, ctx->Ac64, ctx->Uc, ctx->Vc, ctx->sc, n_r, rank, dc, tmp));
+      KP_TRY(projected_diag(ctx, ctx->Ar64, ctx->Ur, ctx->Vr, ctx->sr, n_c, rank, dr, tmp));
     } else {
       KP_CUDA(cudaMemcpyAsync(dc, ctx->sc, sizeof(double) * n_r, cudaMemcpyDeviceToDevice, st));
       KP_CUDA(cudaMemcpyAsync(dr, ctx->sr, sizeof(double) * n_c, cudaMemcpyDeviceToDevice, st));

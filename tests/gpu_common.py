@@ -86,7 +86,7 @@ def emulate_minv(kp, Sigma, R, lam, fmt):
     R scaled by 2^e (amax(R) 2^e in [1/2, 1)) and rounded (bf16 factors as
     hi + lo pairs); each GEMM output
     rounded to fp32 then to the narrow format; S applied as
-    lam^2 / (Sigma^2 + lam^2) in the P2 output; 1 / (lam^2 2^e) at the end."""
+    lam^2 / (Sigma^2 + lam^2) (FP32) in the P2 output; 1 / (lam^2 2^e) at the end."""
     rd = lp.ROUND[fmt]
     am = np.max(np.abs(lp.to_fp32(R)))
     m, e = np.frexp(1.0 / am)
@@ -99,7 +99,8 @@ def emulate_minv(kp, Sigma, R, lam, fmt):
         Vc, Vr = rd(kp.Vc), rd(kp.Vr)
     T1 = rd(lp.to_fp32(Vc.T @ Rq))
     S32 = lp.to_fp32(Sigma)
-    fac = lp.to_fp32(lam * lam / (S32.astype(np.float64) ** 2 + lam * lam))
+    l2 = lp.to_fp32(lam * lam)
+    fac = lp.to_fp32(l2 / lp.to_fp32(S32 * S32 + l2))   # FP32 on the GPU
     W = rd(lp.to_fp32(lp.to_fp32(T1 @ Vr) * fac))
     T3 = rd(lp.to_fp32(Vc @ W))
     inv = lp.to_fp32(1.0 / (lam * lam * s))
