@@ -298,6 +298,17 @@ __global__ void k_mgs2(double* __restrict__ Q, int m, int p) {
   }
 }
 
+// count entries with F[i][j] != F[j][i] (exact comparison)
+__global__ void k_asym_count(const double* __restrict__ F, int n, unsigned int* __restrict__ count) {
+  const long long tot = (long long)n * n;
+  unsigned int local = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (i < j && F[t] != F[(long long)j * n + i]) ++local;
+  }
+  if (local) atomicAdd(count, local);
+}
+
 // count pairs (i < j) of the Gram matrix G = W^T W that still need a rotation
 // (same test as k_jacobi_round: relative and absolute floors)
 __global__ void k_gram_violations(const double* __restrict__ G, int n, double tol, double floor,
@@ -444,9 +455,10 @@ kp_status jacobi_svd(kp_ctx* ctx, const double* A, int m, int n, double* U, doub
 // transform C that nearly diagonalises it: one-sided Jacobi on F C with V
 // starting at C (so V ends as C Q, exact for any orthogonal C); the
 // transform only shortens the sweeps (DCT-II for reflexive BC, DST-I for
-// zero BC).  A second run on F^T gives U as accumulated rotations, hence
-// orthonormal also where sigma is below the noise floor; its columns are
-// sign-aligned with F v_i / sigma_i of the first run.
+// zero BC).  U must be orthonormal also where sigma is below the noise floor:
+// for a symmetric F it is V with column signs; otherwise a second run on F^T
+// gives U as accumulated rotations.  Either way its columns are sign-aligned
+// with F v_i / sigma_i of the first run.
 kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, double* U, double* s, double* V,
                      int* sweeps_out) {
   cudaStream_t st = ctx->stream;
@@ -481,12 +493,27 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
   KP_TRY(mul(F_rm, W));
   KP_CUDA(cudaMemcpyAsync(Vw, C, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
   KP_TRY(jacobi_run(ctx, W, n, n, Vw, U1, s, V, &sw1));
-  // run 2: F^T = V' S U^T  (F^T row-major = F column-major = transpose of F_rm)
-  k_transpose_cm<<<g, 256, 0, st>>>(F_rm, n, n, FT_rm);
+  // A symmetric factor F = Q L Q^T (reflexive BC with a PSF symmetric about its
+  // centre gives one) has U = V sign(L): the columns of U1 = F V / sigma are
+  // +-V where sigma is above rounding level, and any sign pairs with sigma ~ 0.
+  unsigned int* cnt;
+  KP_TRY(kp_alloc(ctx, (void**)&cnt, sizeof(unsigned int)));
+  KP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st));
+  k_asym_count<<<g, 256, 0, st>>>(F_rm, n, cnt);
   KP_LAUNCHED(ctx);
-  KP_TRY(mul(FT_rm, W));
-  KP_CUDA(cudaMemcpyAsync(Vw, C, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
-  KP_TRY(jacobi_run(ctx, W, n, n, Vw, FT_rm /* scratch */, s2, U, &sw2));
+  unsigned int asym = 1;
+  KP_CUDA(cudaMemcpyAsync(&asym, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  KP_CUDA(cudaStreamSynchronize(st));
+  if (asym == 0) {
+    KP_CUDA(cudaMemcpyAsync(U, V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+  } else {
+    // run 2: F^T = V' S U^T  (F^T row-major = F column-major = transpose of F_rm)
+    k_transpose_cm<<<g, 256, 0, st>>>(F_rm, n, n, FT_rm);
+    KP_LAUNCHED(ctx);
+    KP_TRY(mul(FT_rm, W));
+    KP_CUDA(cudaMemcpyAsync(Vw, C, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+    KP_TRY(jacobi_run(ctx, W, n, n, Vw, FT_rm /* scratch */, s2, U, &sw2));
+  }
   k_align_signs<<<n, JT, 0, st>>>(U, U1, n);
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());

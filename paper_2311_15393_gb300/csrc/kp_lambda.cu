@@ -11,10 +11,12 @@
 // (the lam^4 factors of GCV cancel, so the phi form equals eq. GCVTikSVD and
 // keeps every term bounded).  Minimisation: the 400 log-spaced grid values
 // are evaluated in one launch (FP32 terms, FP64 block sums), the best grid
-// point is re-checked in FP64 with its neighbours, then golden-section search
-// in log lam over the two adjacent cells, FP64 throughout.  The discrepancy
-// root is bracketed by decades in log lam and refined by Illinois regula
-// falsi with bisection safeguards.
+// point is re-checked in FP64 with its neighbours, then refined in the two
+// adjacent cells in FP64: GCV / wGCV by Newton on log G in t = log lam with
+// analytic derivatives of the sums (one pass gives all six), bisection as
+// safeguard; the optimal-error lambda by golden-section search.  The
+// discrepancy root is bracketed by decades in log lam and refined by the
+// same safeguarded Newton (D' > 0).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -169,6 +171,56 @@ __global__ void __launch_bounds__(LT) k_lam_eval64(LamData d, const double* __re
   }
 }
 
+// FP64 sums and their first two derivatives in t = log(lam) at one lambda,
+// for the residual family (phi = lam^2 / d, psi = sigma^2 / d = 1 - phi):
+//   s1 = sum phi^2 b^2          s1' = sum 4 phi^2 psi b^2     s1'' = sum 8 phi^2 psi (2 - 3 phi) b^2
+//   s2 = sum (1 - w + w phi)    s2' = w sum 2 phi psi         s2'' = w sum 4 phi psi (1 - 2 phi)
+__global__ void __launch_bounds__(LT) k_lam_deriv64(LamData d, double lam2, double* __restrict__ part) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const double w = d.omega;
+  for (long long i = blockIdx.x * (long long)LT + threadIdx.x; i < d.n; i += (long long)gridDim.x * LT) {
+    const double s2 = d.s2[i], b = d.bh[i];
+    const double rd = 1.0 / (s2 + lam2);
+    const double phi = lam2 * rd, psi = s2 * rd, b2 = b * b;
+    const double pp = phi * psi;
+    acc[0] = fma(phi * phi, b2, acc[0]);
+    acc[1] += 1.0 - w + w * phi;
+    acc[2] = fma(4.0 * phi * pp, b2, acc[2]);
+    acc[3] += 2.0 * w * pp;
+    acc[4] = fma(8.0 * phi * pp * (2.0 - 3.0 * phi), b2, acc[4]);
+    acc[5] += 4.0 * w * pp * (1.0 - 2.0 * phi);
+  }
+  __shared__ double sh[LT / 32][6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double v = lwarp_sum(acc[k]);
+    if (lane == 0) sh[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double t = 0;
+    for (int q = 0; q < LT / 32; ++q) t += sh[q][threadIdx.x];
+    part[(long long)blockIdx.x * 6 + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_sum6_finish(const double* __restrict__ part, int nchunks, double* __restrict__ out) {
+  __shared__ double sh[6][256];
+  for (int k = 0; k < 6; ++k) {
+    double a = 0;
+    for (int c = threadIdx.x; c < nchunks; c += blockDim.x) a += part[(long long)c * 6 + k];
+    sh[k][threadIdx.x] = a;
+  }
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
 __global__ void k_prep(const double* __restrict__ Sigma, const double* __restrict__ bh, const double* __restrict__ xh,
                        long long n, double* __restrict__ s2, float* __restrict__ s2f, float* __restrict__ sgf,
                        float* __restrict__ bhf, float* __restrict__ xhf) {
@@ -242,6 +294,18 @@ static kp_status eval64(LamCtx& L, const double* lams, int k, double* s1, double
     s1[i] = h[2 * i];
     s2[i] = h[2 * i + 1];
   }
+  return KP_OK;
+}
+
+// s[0..5] = (s1, s2, s1', s2', s1'', s2'') at lam
+static kp_status deriv64(LamCtx& L, double lam, double* s6) {
+  kp_ctx* ctx = L.ctx;
+  k_lam_deriv64<<<L.chunks, LT, 0, ctx->stream>>>(L.d, lam * lam, L.part);
+  KP_LAUNCHED(ctx);
+  k_sum6_finish<<<1, 256, 0, ctx->stream>>>(L.part, L.chunks, L.sums);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaMemcpyAsync(s6, L.sums, sizeof(double) * 6, cudaMemcpyDeviceToHost, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
   return KP_OK;
 }
 
@@ -414,29 +478,20 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
       kp_set_error("choose_lambda: discrepancy bracket failed");
       return KP_ENOROOT;
     }
-    // Illinois regula falsi with bisection safeguard in t = log lambda
-    int side = 0;
+    // safeguarded Newton in t = log lambda (D' = s1' > 0), bisection when a
+    // step leaves the bracket
     double t = 0.5 * (tl + th);
     for (int it = 0; it < 200; ++it) {
-      double tn = th - fh * (th - tl) / (fh - fl);
+      double s6[6];
+      KP_TRY(deriv64(L, std::exp(t), s6));
+      const double D = s6[0] - eps * eps, Dp = s6[2];
+      if (D == 0.0) break;
+      if (D < 0) tl = t; else th = t;
+      double tn = (Dp > 0) ? t - D / Dp : 0.5 * (tl + th);
       if (!(tn > tl && tn < th)) tn = 0.5 * (tl + th);
-      if (it % 8 == 7) tn = 0.5 * (tl + th);  // guarantees progress
-      double fn;
-      KP_TRY(f64_at(L, lm, std::exp(tn), Nd, eps, &fn));
+      const bool done = std::fabs(tn - t) <= 1e-14 * std::max(1.0, std::fabs(t)) || th - tl <= 1e-15 * std::max(1.0, std::fabs(t));
       t = tn;
-      if (fn == 0.0) break;
-      if (fn < 0) {
-        tl = tn;
-        fl = fn;
-        if (side == -1) fh *= 0.5;
-        side = -1;
-      } else {
-        th = tn;
-        fh = fn;
-        if (side == 1) fl *= 0.5;
-        side = 1;
-      }
-      if (th - tl <= 1e-15 * std::max(1.0, std::fabs(t))) break;
+      if (done) break;
     }
     *lambda_out = std::exp(t);
     return KP_OK;
@@ -512,8 +567,35 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
       }
     }
   }
-  // golden-section search in log lambda over [t_{best-1}, t_{best+1}]
   double a = tg[std::max(best - 1, 0)], c = tg[std::min(best + 1, NGRID - 1)];
+  if (lm == LM_GCV || lm == LM_WGCV) {
+    // safeguarded Newton on g(t) = log s1 - 2 log s2 (= log G - log N) in
+    // t = log lambda over [t_{best-1}, t_{best+1}], from the best grid point
+    double t = tg[best];
+    for (int it = 0; it < 100; ++it) {
+      double s6[6];
+      KP_TRY(deriv64(L, std::exp(t), s6));
+      if (!(s6[1] > 0.0) || !(s6[0] > 0.0)) {  // below the wGCV lower limit: move right
+        a = t;
+        t = 0.5 * (a + c);
+        continue;
+      }
+      const double r1 = s6[2] / s6[0], r2 = s6[3] / s6[1];
+      const double gp = r1 - 2.0 * r2;
+      const double gpp = s6[4] / s6[0] - r1 * r1 - 2.0 * (s6[5] / s6[1] - r2 * r2);
+      if (gp > 0) c = t; else a = t;
+      double tn = (gpp > 0) ? t - gp / gpp : 0.5 * (a + c);
+      if (!(tn > a && tn < c)) tn = 0.5 * (a + c);
+      const bool done = std::fabs(tn - t) <= 1e-13 * std::max(1.0, std::fabs(t)) || c - a <= 1e-13 * std::max(1.0, std::fabs(t));
+      t = tn;
+      if (done || gp == 0.0) break;
+    }
+    double ft;
+    KP_TRY(f64_at(L, lm, std::exp(t), Nd, eps, &ft));
+    *lambda_out = std::exp(ft <= bv ? t : tg[best]);
+    return KP_OK;
+  }
+  // optimal-error lambda: golden-section search in log lambda over the cell pair
   const double gr_ = 0.5 * (std::sqrt(5.0) - 1.0);
   double x1 = c - gr_ * (c - a), x2 = a + gr_ * (c - a), f1, f2;
   KP_TRY(f64_at(L, lm, std::exp(x1), Nd, eps, &f1));
