@@ -212,7 +212,16 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     operators, 0 = off for the F64 operator)
  *   "check_every"     iterations between host convergence checks (default 4)
  *   "jacobi_tol"      one-sided Jacobi rotation threshold (default 1e-15)
- *   "jacobi_max_sweeps" (default 40) */
+ *   "jacobi_max_sweeps" (default 40)
+ *   "splitk"          > 0: fixed split-K factor of the square tensor-core
+ *                     GEMMs (default 0 = chosen per shape)
+ *   "setup_fp64"      nonzero: keep the O(n^3) products of kp_setup and of
+ *                     choose_lambda's spectral coefficients in FP64 also for
+ *                     FP32 vectors.  By default they run in FP32 when
+ *                     vec_prec is KP_F32 (factor SVD products and Gram test
+ *                     at FP32 tolerance, rotations in FP64), which moves the
+ *                     chosen lambda by ~1e-6 relative; FP64 vectors always
+ *                     use FP64.  Takes effect at the next kp_setup. */
 kp_status kp_set_option(kp_ctx* ctx, const char* name, double value);
 
 /* Number of this library's kernel launches issued on the context since the

@@ -5,6 +5,8 @@
 #include <cstring>
 #include <string>
 
+#include <algorithm>
+
 #include "kp_internal.h"
 
 static thread_local std::string g_last_error;
@@ -39,15 +41,35 @@ extern "C" const char* kp_status_str(kp_status s) {
 
 kp_status kp_alloc(kp_ctx* ctx, void** p, size_t bytes) {
   *p = nullptr;
-  if (bytes == 0) bytes = 16;
+  bytes = (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
+  // smallest pooled block that fits and wastes at most half of itself
+  auto it = ctx->pool.lower_bound(bytes);
+  if (it != ctx->pool.end() && it->first <= 2 * bytes) {
+    *p = it->second;
+    ctx->allocs.emplace_back(it->second, it->first);
+    ctx->pool.erase(it);
+    return KP_OK;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess && !ctx->pool.empty()) {  // give the pool back and retry once
+    cudaGetLastError();
+    kp_pool_release(ctx);
+    e = cudaMalloc(p, bytes);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
+    *p = nullptr;
     kp_set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     return KP_ENOMEM;
   }
-  ctx->allocs.push_back(*p);
+  ctx->allocs.emplace_back(*p, bytes);
   return KP_OK;
+}
+
+void kp_pool_release(kp_ctx* ctx) {
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& b : ctx->pool) cudaFree(b.second);
+  ctx->pool.clear();
 }
 
 void tc_plans_free(kp_ctx* ctx);
@@ -72,10 +94,11 @@ kp_status kp_leave(kp_ctx* ctx) {
 void kp_free_all(kp_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ops_state_free(ctx);
-  for (void* p : ctx->allocs) cudaFree(p);
+  for (auto& b : ctx->allocs) ctx->pool.emplace(b.second, b.first);
   ctx->allocs.clear();
   tc_plans_free(ctx);
   ctx->lam_ws = nullptr;
+  ctx->Uc32 = ctx->Ur32 = ctx->Vc32 = ctx->Vr32 = nullptr;
   ctx->ready = false;
 }
 
@@ -153,6 +176,7 @@ extern "C" void kp_destroy(kp_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   kp_free_all(ctx);
+  kp_pool_release(ctx);
   if (ctx->ctx_block) cudaFree(ctx->ctx_block);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
@@ -191,6 +215,8 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
     ctx->jacobi_max_sweeps = (int)value;
   } else if (!strcmp(name, "splitk")) {
     ctx->splitk_override = (int)value;
+  } else if (!strcmp(name, "setup_fp64")) {
+    ctx->force_setup_fp64 = value != 0.0;
   } else {
     kp_set_error("kp_set_option: unknown option '%s'", name);
     return KP_EINVAL;

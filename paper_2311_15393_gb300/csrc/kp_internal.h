@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "../../include/kpsvd.h"
@@ -118,9 +120,17 @@ struct kp_ctx {
   int jacobi_max_sweeps = 40;
   int splitk_override = 0;  // > 0: fixed split-K factor for the square GEMMs
 
-  // device allocations: ctx_block lives with the context, allocs with the problem
+  // device allocations: ctx_block lives with the context, allocs with the
+  // problem; a new kp_setup returns the previous problem's blocks to `pool`,
+  // from which kp_alloc serves requests before calling cudaMalloc
   void* ctx_block = nullptr;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;
+  std::multimap<size_t, void*> pool;
+  // FP32 arithmetic for the O(n^3) products of the setup and of the spectral
+  // coefficients (factor SVD products, projected spectrum, U^T B U): on for
+  // FP32 vectors unless the "setup_fp64" option is set
+  bool setup_fp32 = false;
+  bool force_setup_fp64 = false;
   int* dev_status = nullptr;     // device status word
   double* dscal = nullptr;       // device scalars (see kp_solver.cu)
   double* red_part = nullptr;    // reduction partials
@@ -136,6 +146,8 @@ struct kp_ctx {
   double *Uc = nullptr, *Vc = nullptr, *sc = nullptr;  // col-major n_r x n_r
   double* Sigma64 = nullptr;  // n_r x n_c col-major
   float* Sigma32 = nullptr;
+  // FP32 copies of the factor bases (setup_fp32 only), col-major
+  float *Uc32 = nullptr, *Ur32 = nullptr, *Vc32 = nullptr, *Vr32 = nullptr;
 
   // operator factors in the four GEMM layouts (T = op type, or bf16 slices)
   void* opAc = nullptr;   // G1: [slice][k][i'][i] = A_c^(k)[i', i]
@@ -175,7 +187,8 @@ struct kp_ctx {
 
 // allocation helper: registers the pointer with the context
 kp_status kp_alloc(kp_ctx* ctx, void** p, size_t bytes);
-void kp_free_all(kp_ctx* ctx);
+void kp_free_all(kp_ctx* ctx);    // problem blocks -> pool
+void kp_pool_release(kp_ctx* ctx);  // cudaFree the pool
 
 // ---------------------------------------------------------------- kernels (host launchers)
 // SIMT GEMM (double or float)

@@ -18,12 +18,15 @@
 // below the rounding noise every column carries (without this absolute
 // floor, columns of singular values below eps ||A|| never settle).  Then
 // sigma_i = |a_i|, u_i = a_i / sigma_i, and the triplets are sorted by
-// decreasing sigma.
+// decreasing sigma.  For FP32 vectors the blur-factor SVDs take their O(n^3)
+// products (the transform F C and the Gram test) in FP32 and use eps = 2^-23
+// in both thresholds; rotations stay FP64.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "kp_internal.h"
+#include "kp_vec.cuh"
 
 namespace {
 
@@ -203,7 +206,8 @@ __global__ void k_transform(int n, int kind, double* __restrict__ C) {
 }
 
 // B (n x m col-major) = A^T for A m x n col-major
-__global__ void k_transpose_cm(const double* __restrict__ A, int m, int n, double* __restrict__ B) {
+template <typename T>
+__global__ void k_transpose_cm(const T* __restrict__ A, int m, int n, T* __restrict__ B) {
   long long tot = (long long)m * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % m), j = (int)(t / m);
@@ -245,59 +249,6 @@ __global__ void k_sumsq(const double* __restrict__ A, long long n, double* out) 
   }
 }
 
-// Orthonormalise the p columns of Q (m x p col-major) in place: modified
-// Gram-Schmidt, each projection done twice; a column that vanishes (rank
-// deficiency) is replaced by a unit vector e_t and orthogonalised again.
-// One block.
-__global__ void k_mgs2(double* __restrict__ Q, int m, int p) {
-  __shared__ double sh[JT / 32];
-  __shared__ double tot;
-  auto bsum = [&](double v) -> double {
-    v = jwarp_sum(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int w = 0; w < JT / 32; ++w) t += sh[w];
-      tot = t;
-    }
-    __syncthreads();
-    return tot;
-  };
-  for (int k = 0; k < p; ++k) {
-    double* qk = Q + (long long)k * m;
-    double n0 = 0;
-    for (int r = threadIdx.x; r < m; r += JT) n0 = fma(qk[r], qk[r], n0);
-    n0 = sqrt(bsum(n0));
-    for (int attempt = 0; attempt < 3; ++attempt) {
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int j = 0; j < k; ++j) {
-          const double* qj = Q + (long long)j * m;
-          double d = 0;
-          for (int r = threadIdx.x; r < m; r += JT) d = fma(qj[r], qk[r], d);
-          d = bsum(d);
-          for (int r = threadIdx.x; r < m; r += JT) qk[r] -= d * qj[r];
-          __syncthreads();
-        }
-      }
-      double nk = 0;
-      for (int r = threadIdx.x; r < m; r += JT) nk = fma(qk[r], qk[r], nk);
-      nk = sqrt(bsum(nk));
-      if (nk > 1e-10 * n0 && nk > 0) {
-        for (int r = threadIdx.x; r < m; r += JT) qk[r] /= nk;
-        __syncthreads();
-        break;
-      }
-      // rank deficient: restart from a unit vector
-      const int t = (int)(((long long)(k + 1) * 7919 + attempt * 104729) % m);
-      for (int r = threadIdx.x; r < m; r += JT) qk[r] = (r == t) ? 1.0 : 0.0;
-      n0 = 1.0;
-      __syncthreads();
-    }
-  }
-}
-
 // count entries with F[i][j] != F[j][i] (exact comparison)
 __global__ void k_asym_count(const double* __restrict__ F, int n, unsigned int* __restrict__ count) {
   const long long tot = (long long)n * n;
@@ -311,7 +262,8 @@ __global__ void k_asym_count(const double* __restrict__ F, int n, unsigned int* 
 
 // count pairs (i < j) of the Gram matrix G = W^T W that still need a rotation
 // (same test as k_jacobi_round: relative and absolute floors)
-__global__ void k_gram_violations(const double* __restrict__ G, int n, double tol, double floor,
+template <typename T>
+__global__ void k_gram_violations(const T* __restrict__ G, int n, double tol, double floor,
                                   unsigned int* __restrict__ count) {
   const long long tot = (long long)n * n;
   unsigned int local = 0;
@@ -324,12 +276,257 @@ __global__ void k_gram_violations(const double* __restrict__ G, int n, double to
   if (local) atomicAdd(count, local);
 }
 
+
+// out[j + k ldo] = sum_i X[i + j ldx] Y[i + k ldy] for j < ncol, k < p: the
+// tall-skinny products of the subspace iteration, one warp per column j
+constexpr int SK_CHUNK = 8;
+__global__ void __launch_bounds__(256) k_skinny_tn(const double* __restrict__ X, long long ldx,
+                                                   const double* __restrict__ Y, long long ldy, int m, int ncol,
+                                                   int p, double* __restrict__ out, long long ldo) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= ncol) return;
+  const double* x = X + warp * ldx;
+  for (int k0 = 0; k0 < p; k0 += SK_CHUNK) {
+    const int kn = min(SK_CHUNK, p - k0);
+    double acc[SK_CHUNK];
+#pragma unroll
+    for (int q = 0; q < SK_CHUNK; ++q) acc[q] = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      const double xv = x[i];
+#pragma unroll
+      for (int q = 0; q < SK_CHUNK; ++q)
+        if (q < kn) acc[q] = fma(xv, Y[i + (long long)(k0 + q) * ldy], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < SK_CHUNK; ++q) acc[q] = jwarp_sum(acc[q]);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < SK_CHUNK; ++q)
+        if (q < kn) out[warp + (long long)(k0 + q) * ldo] = acc[q];
+  }
+}
+
+// out (m x r col-major) = Q (m x p col-major) B[:, :r] (B p x p col-major)
+__global__ void k_small_right(const double* __restrict__ Q, int m, int p, const double* __restrict__ B, int r,
+                              double* __restrict__ out) {
+  const long long tot = (long long)m * r;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % m), c = (int)(t / m);
+    double acc = 0.0;
+    for (int j = 0; j < p; ++j) acc = fma(Q[i + (long long)j * m], B[j + (long long)c * p], acc);
+    out[t] = acc;
+  }
+}
+
+// Orthonormalise the p columns of Q (m x p col-major) in place by classical
+// Gram-Schmidt with each projection done twice (CGS2: all dots against the
+// previous columns in one block reduction); a column that vanishes (rank
+// deficiency) is replaced by a unit vector e_t and orthogonalised again.
+// One block of CG_T threads.
+constexpr int CG_T = 512;
+constexpr int CG_CH = 16;  // dots per block reduction
+__global__ void __launch_bounds__(CG_T) k_cgs2(double* __restrict__ Q, int m, int p) {
+  __shared__ double sh[CG_T / 32][CG_CH + 1];
+  __shared__ double dsh[CG_CH];
+  __shared__ double tot;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  auto bsum = [&](double v) -> double {
+    v = jwarp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid][0] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int w = 0; w < CG_T / 32; ++w) t += sh[w][0];
+      tot = t;
+    }
+    __syncthreads();
+    return tot;
+  };
+  for (int k = 0; k < p; ++k) {
+    double* qk = Q + (long long)k * m;
+    double n0 = 0;
+    for (int r = threadIdx.x; r < m; r += CG_T) n0 = fma(qk[r], qk[r], n0);
+    n0 = sqrt(bsum(n0));
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int j0 = 0; j0 < k; j0 += CG_CH) {
+          const int jn = min(CG_CH, k - j0);
+          double d[CG_CH];
+#pragma unroll
+          for (int q = 0; q < CG_CH; ++q) d[q] = 0.0;
+          for (int r = threadIdx.x; r < m; r += CG_T) {
+            const double x = qk[r];
+#pragma unroll
+            for (int q = 0; q < CG_CH; ++q)
+              if (q < jn) d[q] = fma(Q[r + (long long)(j0 + q) * m], x, d[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < CG_CH; ++q) {
+            const double v = jwarp_sum(d[q]);
+            if (lane == 0) sh[wid][q] = v;
+          }
+          __syncthreads();
+          if (threadIdx.x < jn) {
+            double t = 0;
+            for (int w = 0; w < CG_T / 32; ++w) t += sh[w][threadIdx.x];
+            dsh[threadIdx.x] = t;
+          }
+          __syncthreads();
+          for (int r = threadIdx.x; r < m; r += CG_T) {
+            double x = qk[r];
+            for (int q = 0; q < jn; ++q) x = fma(-dsh[q], Q[r + (long long)(j0 + q) * m], x);
+            qk[r] = x;
+          }
+          __syncthreads();
+        }
+      }
+      double nk = 0;
+      for (int r = threadIdx.x; r < m; r += CG_T) nk = fma(qk[r], qk[r], nk);
+      nk = sqrt(bsum(nk));
+      if (nk > 1e-10 * n0 && nk > 0) {
+        for (int r = threadIdx.x; r < m; r += CG_T) qk[r] /= nk;
+        __syncthreads();
+        break;
+      }
+      const int t = (int)(((long long)(k + 1) * 7919 + attempt * 104729) % m);
+      for (int r = threadIdx.x; r < m; r += CG_T) qk[r] = (r == t) ? 1.0 : 0.0;
+      n0 = 1.0;
+      __syncthreads();
+    }
+  }
+}
+
+// One-sided Jacobi SVD of a narrow A (m x p col-major, p <= 32) held in
+// shared memory by one block: the same rotations, thresholds and round-robin
+// order as the multi-block sweep, every sweep in this launch, one warp per
+// pair.  Writes U = A V / sigma (m x p), sigma (p) and V (p x p) sorted by
+// decreasing sigma; *status = 1 if max_sweeps sweeps did not converge.
+constexpr int SJ_T = 1024;
+constexpr int SJ_MAXP = 32;
+__global__ void __launch_bounds__(SJ_T) k_jacobi_small(const double* __restrict__ A, int m, int p, double tol_in,
+                                                       int max_sweeps, double* __restrict__ U,
+                                                       double* __restrict__ s_out, double* __restrict__ V_out,
+                                                       int* __restrict__ status) {
+  extern __shared__ double smem_d[];
+  double* W = smem_d;                    // m x p
+  double* V = W + (long long)m * p;      // p x p
+  __shared__ double red[SJ_T / 32];
+  __shared__ double sg[SJ_MAXP];
+  __shared__ int perm[SJ_MAXP];
+  __shared__ unsigned int rot;
+  __shared__ double floor_sh;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double f2 = 0.0;
+  for (long long t = threadIdx.x; t < (long long)m * p; t += SJ_T) {
+    const double x = A[t];
+    W[t] = x;
+    f2 = fma(x, x, f2);
+  }
+  for (int t = threadIdx.x; t < p * p; t += SJ_T) V[t] = (t / p == t % p) ? 1.0 : 0.0;
+  f2 = jwarp_sum(f2);
+  if (lane == 0) red[wid] = f2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < SJ_T / 32; ++w) t += red[w];
+    floor_sh = (double)m * 2.220446049250313e-16 * sqrt(t);
+  }
+  __syncthreads();
+  const double floor = floor_sh;
+  const double tol = fmax(tol_in, (double)m * 2.220446049250313e-16);
+  const int npad = p + (p & 1);
+  int sweep = 0;
+  bool done = npad < 2;
+  for (; !done && sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rot = 0u;
+    __syncthreads();
+    for (int round = 0; round < npad - 1; ++round) {
+      if (wid < npad / 2) {
+        int i = rr_player(wid, round, npad);
+        int j = rr_player(npad - 1 - wid, round, npad);
+        if (i > j) {
+          const int t = i;
+          i = j;
+          j = t;
+        }
+        if (j < p) {
+          double* a = W + (long long)i * m;
+          double* b = W + (long long)j * m;
+          double al = 0.0, be = 0.0, ga = 0.0;
+          for (int r = lane; r < m; r += 32) {
+            const double x = a[r], y = b[r];
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
+          al = jwarp_sum(al);
+          be = jwarp_sum(be);
+          ga = jwarp_sum(ga);
+          if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be) && fabs(ga) > floor * sqrt(fmax(al, be))) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+            for (int r = lane; r < m; r += 32) {
+              const double x = a[r], y = b[r];
+              a[r] = c * x - sn * y;
+              b[r] = sn * x + c * y;
+            }
+            double* va = V + (long long)i * p;
+            double* vb = V + (long long)j * p;
+            for (int r = lane; r < p; r += 32) {
+              const double x = va[r], y = vb[r];
+              va[r] = c * x - sn * y;
+              vb[r] = sn * x + c * y;
+            }
+            if (lane == 0) atomicAdd(&rot, 1u);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    done = rot == 0u;
+    __syncthreads();
+  }
+  if (!done && threadIdx.x == 0) *status = 1;
+  // sigma = column norms, then sort (descending; ties keep the smaller index)
+  for (int c = wid; c < p; c += SJ_T / 32) {
+    double v = 0.0;
+    for (int r = lane; r < m; r += 32) v = fma(W[(long long)c * m + r], W[(long long)c * m + r], v);
+    v = jwarp_sum(v);
+    if (lane == 0) sg[c] = sqrt(v);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < p; ++c) perm[c] = c;
+    for (int a = 1; a < p; ++a) {
+      const int x = perm[a];
+      int b = a - 1;
+      while (b >= 0 && sg[perm[b]] < sg[x]) {
+        perm[b + 1] = perm[b];
+        --b;
+      }
+      perm[b + 1] = x;
+    }
+  }
+  __syncthreads();
+  for (int c = wid; c < p; c += SJ_T / 32) {
+    const int src = perm[c];
+    const double sv = sg[src];
+    const double inv = sv > 0.0 ? 1.0 / sv : 0.0;
+    for (int r = lane; r < m; r += 32) U[(long long)c * m + r] = W[(long long)src * m + r] * inv;
+    for (int r = lane; r < p; r += 32) V_out[(long long)c * p + r] = V[(long long)src * p + r];
+    if (lane == 0) s_out[c] = sv;
+  }
+}
+
 }  // namespace
 
 // Sweeps on W (m x n col-major, in place) accumulating into V (n x n,
 // holding its initial value); then sigma, sorting, U = W / sigma.
 static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, double* U, double* s, double* V,
-                            int* sweeps_out) {
+                            int* sweeps_out, bool fast = false) {
   cudaStream_t st = ctx->stream;
   double *sw = nullptr, *nrm = nullptr;
   int* perm = nullptr;
@@ -338,53 +535,57 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
   KP_TRY(kp_alloc(ctx, (void**)&perm, sizeof(int) * n));
   KP_TRY(kp_alloc(ctx, (void**)&cnt, sizeof(unsigned int)));
   KP_TRY(kp_alloc(ctx, (void**)&nrm, sizeof(double)));
-  // noise floor m eps ||A||_F
+  // noise floor m eps ||A||_F; eps is the unit of the arithmetic W came from
+  // (FP32 when the products of the setup run in FP32)
   k_sumsq<<<1, 1024, 0, st>>>(W, (long long)m * n, nrm);
   KP_LAUNCHED(ctx);
   double fro2 = 0.0;
   KP_CUDA(cudaMemcpyAsync(&fro2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
   KP_CUDA(cudaStreamSynchronize(st));
-  const double eps = 2.220446049250313e-16;
+  const double eps = fast ? 1.1920928955078125e-07 : 2.220446049250313e-16;
   const double floor = (double)m * eps * sqrt(fro2);
+  // pairs count as orthogonal at |gamma| <= tol sqrt(alpha beta); below m eps
+  // the inner products are rounding noise and rotations would never stop
+  const double tol = std::max(ctx->jacobi_tol, (double)m * eps);
   const int npad = n + (n & 1);
   int sweeps = 0;
   if (npad >= 2) {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    k_zero_u32<<<1, 1, 0, st>>>(cnt);
-    // pairs count as orthogonal at |gamma| <= tol sqrt(alpha beta); below m eps
-    // the inner products are rounding noise and rotations would never stop
-    const double tol = std::max(ctx->jacobi_tol, (double)m * eps);
-    for (int round = 0; round < npad - 1; ++round)
-      k_jacobi_round<<<npad / 2, JT, 0, st>>>(W, Vw, m, n, npad, round, tol, floor, cnt);
-    cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    if (ce != cudaSuccess) {
-      kp_set_error("jacobi_svd: capture failed: %s", cudaGetErrorString(ce));
-      return KP_ECUDA;
-    }
-    KP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
     // Before the first sweep, and instead of a sweep that would only confirm
     // convergence, count the pairs that need a rotation on G = W^T W (one
-    // FP64 GEMM): a sweep over a matrix with no such pair rotates nothing.
+    // GEMM): a sweep over a matrix with no such pair rotates nothing.
     double* G = nullptr;
-    KP_TRY(kp_alloc(ctx, (void**)&G, sizeof(double) * (size_t)n * n));
+    float *G32 = nullptr, *W32 = nullptr;
+    if (fast) {
+      KP_TRY(kp_alloc(ctx, (void**)&G32, sizeof(float) * (size_t)n * n));
+      KP_TRY(kp_alloc(ctx, (void**)&W32, sizeof(float) * (size_t)m * n));
+    } else {
+      KP_TRY(kp_alloc(ctx, (void**)&G, sizeof(double) * (size_t)n * n));
+    }
     auto gram_clean = [&](bool* clean) -> kp_status {
       GemmDesc gd;  // G[i][j] = sum_r W[r, i] W[r, j]
       gd.M = n;
       gd.N = n;
       gd.K = m;
-      gd.A.ptr = W;
       gd.A.ld = m;
-      gd.B.ptr = W;
       gd.B.ld = m;
       gd.epi.mode = EPI_T;
-      gd.epi.out = G;
       gd.epi.ldd = n;
-      KP_TRY(simt_gemm<double>(ctx, gd));
-      KP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st));
       const int gb = std::max(1, std::min((int)(((long long)n * n + 255) / 256), ctx->sm_count * 8));
-      k_gram_violations<<<gb, 256, 0, st>>>(G, n, tol, floor, cnt);
+      KP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st));
+      if (fast) {
+        KP_TRY(convert_f64_to_f32(ctx, W, W32, (long long)m * n));
+        gd.A.ptr = W32;
+        gd.B.ptr = W32;
+        gd.epi.out = G32;
+        KP_TRY(simt_gemm<float>(ctx, gd));
+        k_gram_violations<float><<<gb, 256, 0, st>>>(G32, n, tol, floor, cnt);
+      } else {
+        gd.A.ptr = W;
+        gd.B.ptr = W;
+        gd.epi.out = G;
+        KP_TRY(simt_gemm<double>(ctx, gd));
+        k_gram_violations<double><<<gb, 256, 0, st>>>(G, n, tol, floor, cnt);
+      }
       KP_LAUNCHED(ctx);
       unsigned int h = 0;
       KP_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
@@ -396,18 +597,40 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
     bool clean = false;
     KP_TRY(gram_clean(&clean));
     if (clean) h_cnt = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    kp_status gst = KP_OK;
     for (sweeps = 0; !clean && sweeps < ctx->jacobi_max_sweeps; ++sweeps) {
-      KP_CUDA(cudaGraphLaunch(exec, st));
+      if (!exec) {  // one sweep (n - 1 rounds) as a graph, built at the first sweep
+        KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        k_zero_u32<<<1, 1, 0, st>>>(cnt);
+        for (int round = 0; round < npad - 1; ++round)
+          k_jacobi_round<<<npad / 2, JT, 0, st>>>(W, Vw, m, n, npad, round, tol, floor, cnt);
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (ce != cudaSuccess) {
+          kp_set_error("jacobi_svd: sweep graph capture failed: %s", cudaGetErrorString(ce));
+          gst = KP_ECUDA;
+          break;
+        }
+      }
+      cudaError_t ce = cudaGraphLaunch(exec, st);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_cnt, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+      if (ce != cudaSuccess) {
+        kp_set_error("jacobi_svd: sweep failed: %s", cudaGetErrorString(ce));
+        gst = KP_ECUDA;
+        break;
+      }
       ctx->launches += npad;
-      KP_CUDA(cudaMemcpyAsync(&h_cnt, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-      KP_CUDA(cudaStreamSynchronize(st));
       if (h_cnt == 0) {
         ++sweeps;
         break;
       }
       // few rotations: the next sweep is likely only a confirmation
       if ((long long)h_cnt * 8 < (long long)npad) {
-        KP_TRY(gram_clean(&clean));
+        gst = gram_clean(&clean);
+        if (gst != KP_OK) break;
         if (clean) {
           h_cnt = 0;
           ++sweeps;
@@ -415,8 +638,9 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
         }
       }
     }
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    KP_TRY(gst);
     if (h_cnt != 0) {
       kp_set_error("jacobi_svd: no convergence after %d sweeps (%u rotations in the last)", sweeps, h_cnt);
       return KP_ENOCONV;
@@ -462,6 +686,7 @@ kp_status jacobi_svd(kp_ctx* ctx, const double* A, int m, int n, double* U, doub
 kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, double* U, double* s, double* V,
                      int* sweeps_out) {
   cudaStream_t st = ctx->stream;
+  const bool fast = ctx->setup_fp32;
   const long long nn = (long long)n * n;
   double *C, *W, *Vw, *FT_rm, *U1, *s2;
   KP_TRY(kp_alloc(ctx, (void**)&C, sizeof(double) * nn));
@@ -470,29 +695,45 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
   KP_TRY(kp_alloc(ctx, (void**)&FT_rm, sizeof(double) * nn));
   KP_TRY(kp_alloc(ctx, (void**)&U1, sizeof(double) * nn));
   KP_TRY(kp_alloc(ctx, (void**)&s2, sizeof(double) * n));
+  float *C32 = nullptr, *F32 = nullptr, *W32 = nullptr;
+  if (fast) {
+    KP_TRY(kp_alloc(ctx, (void**)&C32, sizeof(float) * nn));
+    KP_TRY(kp_alloc(ctx, (void**)&F32, sizeof(float) * nn));
+    KP_TRY(kp_alloc(ctx, (void**)&W32, sizeof(float) * nn));
+  }
   const int g = std::max(1, std::min((int)((nn + 255) / 256), ctx->sm_count * 16));
   k_transform<<<g, 256, 0, st>>>(n, transform, C);
   KP_LAUNCHED(ctx);
-  // W (col-major) = F C, computed as the row-major product D[k][i] = sum_j C[j,k] F[i,j]
+  if (fast) KP_TRY(convert_f64_to_f32(ctx, C, C32, nn));
+  // W (col-major) = X C for X given row-major, computed as the row-major
+  // product D[k][i] = sum_j C[j,k] X[i,j]; FP32 products are widened to FP64
   auto mul = [&](const double* X_rm, double* out) -> kp_status {
     GemmDesc gd;
     gd.M = n;
     gd.N = n;
     gd.K = n;
-    gd.A.ptr = C;
     gd.A.ld = n;
-    gd.B.ptr = X_rm;
     gd.B.ld = n;
     gd.epi.mode = EPI_T;
-    gd.epi.out = out;
     gd.epi.ldd = n;
+    if (fast) {
+      KP_TRY(convert_f64_to_f32(ctx, X_rm, F32, nn));
+      gd.A.ptr = C32;
+      gd.B.ptr = F32;
+      gd.epi.out = W32;
+      KP_TRY(simt_gemm<float>(ctx, gd));
+      return convert_f32_to_f64(ctx, W32, out, nn);
+    }
+    gd.A.ptr = C;
+    gd.B.ptr = X_rm;
+    gd.epi.out = out;
     return simt_gemm<double>(ctx, gd);
   };
   int sw1 = 0, sw2 = 0;
   // run 1: F = U1 S V^T
   KP_TRY(mul(F_rm, W));
   KP_CUDA(cudaMemcpyAsync(Vw, C, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
-  KP_TRY(jacobi_run(ctx, W, n, n, Vw, U1, s, V, &sw1));
+  KP_TRY(jacobi_run(ctx, W, n, n, Vw, U1, s, V, &sw1, fast));
   // A symmetric factor F = Q L Q^T (reflexive BC with a PSF symmetric about its
   // centre gives one) has U = V sign(L): the columns of U1 = F V / sigma are
   // +-V where sigma is above rounding level, and any sign pairs with sigma ~ 0.
@@ -508,11 +749,11 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
     KP_CUDA(cudaMemcpyAsync(U, V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
   } else {
     // run 2: F^T = V' S U^T  (F^T row-major = F column-major = transpose of F_rm)
-    k_transpose_cm<<<g, 256, 0, st>>>(F_rm, n, n, FT_rm);
+    k_transpose_cm<double><<<g, 256, 0, st>>>(F_rm, n, n, FT_rm);
     KP_LAUNCHED(ctx);
     KP_TRY(mul(FT_rm, W));
     KP_CUDA(cudaMemcpyAsync(Vw, C, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
-    KP_TRY(jacobi_run(ctx, W, n, n, Vw, FT_rm /* scratch */, s2, U, &sw2));
+    KP_TRY(jacobi_run(ctx, W, n, n, Vw, FT_rm /* scratch */, s2, U, &sw2, fast));
   }
   k_align_signs<<<n, JT, 0, st>>>(U, U1, n);
   KP_LAUNCHED(ctx);
@@ -521,104 +762,89 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
   return KP_OK;
 }
 
-// Leading r singular triplets of W (m x n col-major, m >= n) by subspace
-// iteration: Q <- orth(W (W^T Q)) with p = min(n, r + 8) columns, started
-// from the lowest-frequency DCT-II columns, until the Ritz values
-// sigma_1..sigma_r of Q^T W change by less than 4 eps relative (at most 200
-// iterations); then the SVD of the p x n matrix Q^T W by one-sided Jacobi.
-// Outputs: U (m x r), s (r), V (n x r) col-major, s descending.
 kp_status topr_svd(kp_ctx* ctx, const double* W, int m, int n, int r, double* U, double* s, double* V,
                    int* iters_out) {
   cudaStream_t st = ctx->stream;
   const int p = std::min(n, r + 8);
-  double *Q, *Z, *Uz, *sz, *Vz, *C;
+  double *Q, *Z, *Uz, *sz, *Vz, *WT;
   KP_TRY(kp_alloc(ctx, (void**)&Q, sizeof(double) * (size_t)m * p));
   KP_TRY(kp_alloc(ctx, (void**)&Z, sizeof(double) * (size_t)n * p));
   KP_TRY(kp_alloc(ctx, (void**)&Uz, sizeof(double) * (size_t)n * p));
   KP_TRY(kp_alloc(ctx, (void**)&sz, sizeof(double) * p));
   KP_TRY(kp_alloc(ctx, (void**)&Vz, sizeof(double) * (size_t)p * p));
-  KP_TRY(kp_alloc(ctx, (void**)&C, sizeof(double) * (size_t)m * m));
-  double* WT;  // W^T (n x m col-major) = W row-major
-  KP_TRY(kp_alloc(ctx, (void**)&WT, sizeof(double) * (size_t)m * n));
+  KP_TRY(kp_alloc(ctx, (void**)&WT, sizeof(double) * (size_t)m * n));  // W^T (n x m col-major)
   const int g = std::max(1, std::min((int)(((long long)m * n + 255) / 256), ctx->sm_count * 16));
-  k_transpose_cm<<<g, 256, 0, st>>>(W, m, n, WT);
-  k_transform<<<g, 256, 0, st>>>(m, 0, C);  // first p columns: smooth start vectors
-  ctx->launches += 2;
-  KP_CUDA(cudaMemcpyAsync(Q, C, sizeof(double) * (size_t)m * p, cudaMemcpyDeviceToDevice, st));
-  // Z (n x p col-major) = W^T Q : row-major D[k][j] = sum_i Q[i,k] W[i,j]
-  auto mulZ = [&]() -> kp_status {
-    GemmDesc gd;
-    gd.M = p;
-    gd.N = n;
-    gd.K = m;
-    gd.A.ptr = Q;
-    gd.A.ld = m;
-    gd.B.ptr = W;
-    gd.B.ld = m;
-    gd.epi.mode = EPI_T;
-    gd.epi.out = Z;
-    gd.epi.ldd = n;
-    return simt_gemm<double>(ctx, gd);
-  };
-  // Q (m x p col-major) = W Z : row-major D[k][i] = sum_j Z[j,k] W[i,j]
-  auto mulY = [&]() -> kp_status {
-    GemmDesc gd;
-    gd.M = p;
-    gd.N = m;
-    gd.K = n;
-    gd.A.ptr = Z;
-    gd.A.ld = n;
-    gd.B.ptr = WT;
-    gd.B.ld = n;
-    gd.epi.mode = EPI_T;
-    gd.epi.out = Q;
-    gd.epi.ldd = m;
-    return simt_gemm<double>(ctx, gd);
+  k_transpose_cm<double><<<g, 256, 0, st>>>(W, m, n, WT);
+  KP_LAUNCHED(ctx);
+  {  // start vectors: the first p columns of the m x m DCT-II matrix (smooth)
+    double* C;
+    KP_TRY(kp_alloc(ctx, (void**)&C, sizeof(double) * (size_t)m * m));
+    k_transform<<<g, 256, 0, st>>>(m, 0, C);
+    KP_LAUNCHED(ctx);
+    KP_CUDA(cudaMemcpyAsync(Q, C, sizeof(double) * (size_t)m * p, cudaMemcpyDeviceToDevice, st));
+  }
+  // the Ritz step: one-block Jacobi when Z fits in shared memory
+  const size_t small_smem = sizeof(double) * ((size_t)n * p + (size_t)p * p);
+  const bool small = p <= SJ_MAXP && small_smem <= 200 * 1024;
+  int* jstat = nullptr;
+  if (small) {
+    KP_TRY(kp_alloc(ctx, (void**)&jstat, sizeof(int)));
+    KP_CUDA(cudaMemsetAsync(jstat, 0, sizeof(int), st));
+    KP_CUDA(cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
+  }
+  auto skinny = [&](const double* X, int rows, int ncol, const double* Y, double* out) -> kp_status {
+    const long long threads = (long long)ncol * 32;
+    k_skinny_tn<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(X, rows, Y, rows, rows, ncol, p, out, ncol);
+    KP_LAUNCHED(ctx);
+    return KP_OK;
   };
   std::vector<double> prev(r, 0.0), cur(r, 0.0);
   int it = 0;
   const int maxit = 200;
   for (it = 0; it < maxit; ++it) {
-    k_mgs2<<<1, JT, 0, st>>>(Q, m, p);
+    k_cgs2<<<1, CG_T, 0, st>>>(Q, m, p);
     KP_LAUNCHED(ctx);
-    KP_TRY(mulZ());  // Z = W^T Q = (Q^T W)^T
-    // Ritz values: singular values of Z (n x p)
-    KP_TRY(jacobi_svd(ctx, Z, n, p, Uz, sz, Vz, nullptr));
+    KP_TRY(skinny(W, m, n, Q, Z));  // Z (n x p) = W^T Q
+    // Ritz values: singular values of Z
+    if (small) {
+      k_jacobi_small<<<1, SJ_T, small_smem, st>>>(Z, n, p, ctx->jacobi_tol, ctx->jacobi_max_sweeps, Uz, sz, Vz,
+                                                  jstat);
+      KP_LAUNCHED(ctx);
+    } else {
+      KP_TRY(jacobi_svd(ctx, Z, n, p, Uz, sz, Vz, nullptr));
+    }
     KP_CUDA(cudaMemcpyAsync(cur.data(), sz, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
     KP_CUDA(cudaStreamSynchronize(st));
     double d = 0.0;
     for (int k = 0; k < r; ++k) d = std::max(d, std::fabs(cur[k] - prev[k]) / std::max(cur[0], 1e-300));
     if (it > 0 && d <= 4 * 2.220446049250313e-16) break;
     prev = cur;
-    KP_TRY(mulY());  // Q = W Z
+    // Q (m x p) = W U_z, the span of W Z, with its columns already in the
+    // order of the Ritz values: after orthonormalisation the next Z is
+    // nearly orthogonal and its Jacobi step takes few sweeps
+    KP_TRY(skinny(WT, n, m, Uz, Q));
   }
   if (it == maxit) {
     kp_set_error("topr_svd: subspace iteration did not settle in %d iterations", maxit);
     return KP_ENOCONV;
   }
+  if (small) {
+    int h = 0;
+    KP_CUDA(cudaMemcpyAsync(&h, jstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KP_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+      kp_set_error("topr_svd: Ritz-step Jacobi did not converge in %d sweeps", ctx->jacobi_max_sweeps);
+      return KP_ENOCONV;
+    }
+  }
   // Z = W^T Q = V_W S (Q^T U_W)^T: Jacobi on Z gave Uz (normalised Z V_z ->
   // right singular vectors of W), sz, Vz (p x p); left vectors U = Q Vz.
   KP_CUDA(cudaMemcpyAsync(V, Uz, sizeof(double) * (size_t)n * r, cudaMemcpyDeviceToDevice, st));
   KP_CUDA(cudaMemcpyAsync(s, sz, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
-  {
-    // U (m x r col-major) = Q Vz[:, :r] : row-major D[k][i] = sum_j Vz[j,k] Q[i,j]
-    double* QT;
-    KP_TRY(kp_alloc(ctx, (void**)&QT, sizeof(double) * (size_t)m * p));
-    k_transpose_cm<<<g, 256, 0, st>>>(Q, m, p, QT);
-    KP_LAUNCHED(ctx);
-    GemmDesc gd;
-    gd.M = r;
-    gd.N = m;
-    gd.K = p;
-    gd.A.ptr = Vz;
-    gd.A.ld = p;
-    gd.B.ptr = QT;
-    gd.B.ld = p;
-    gd.epi.mode = EPI_T;
-    gd.epi.out = U;
-    gd.epi.ldd = m;
-    KP_TRY(simt_gemm<double>(ctx, gd));
-  }
+  const int gr = std::max(1, std::min((int)(((long long)m * r + 255) / 256), ctx->sm_count * 16));
+  k_small_right<<<gr, 256, 0, st>>>(Q, m, p, Vz, r, U);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
   if (iters_out) *iters_out = it + 1;
   return KP_OK;
 }

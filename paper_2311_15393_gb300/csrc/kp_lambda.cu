@@ -365,8 +365,44 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
     xhf = nullptr;
   }
 
-  // coefficients in the KP basis: Y^ = U_c^T Y U_r (or V for x_true)
+  // coefficients in the KP basis: Y^ = U_c^T Y U_r (or V for x_true); in
+  // FP32 from FP32 images when the setup kept FP32 copies of the bases
+  auto kp_coeffs32 = [&](const float* img, const float* Lc, const float* Rr, double* out) -> kp_status {
+    float* T32 = (float*)T;  // T holds N doubles: room for two FP32 images
+    float* O32 = T32 + N;
+    GemmDesc g1;
+    g1.M = n_r;
+    g1.N = n_c;
+    g1.K = n_r;
+    g1.A.ptr = Lc;
+    g1.A.ld = n_r;
+    g1.B.ptr = img;
+    g1.B.ld = n_r;
+    g1.epi.mode = EPI_T;
+    g1.epi.out = T32;
+    g1.epi.ldd = n_c;
+    KP_TRY(simt_gemm<float>(ctx, g1));
+    GemmDesc g2;
+    g2.M = n_c;
+    g2.N = n_r;
+    g2.K = n_c;
+    g2.A.ptr = Rr;
+    g2.A.ld = n_c;
+    g2.B.ptr = T32;
+    g2.B.ld = n_c;
+    g2.epi.mode = EPI_T;
+    g2.epi.out = O32;
+    g2.epi.ldd = n_r;
+    KP_TRY(simt_gemm<float>(ctx, g2));
+    k_to_f64<float><<<gr, 256, 0, st>>>(O32, N, out);
+    KP_LAUNCHED(ctx);
+    return KP_OK;
+  };
   auto kp_coeffs = [&](const void* img, const double* Lc, const double* Rr, double* out) -> kp_status {
+    if (!f64 && ctx->Uc32) {
+      const bool u = Lc == ctx->Uc;
+      return kp_coeffs32((const float*)img, u ? ctx->Uc32 : ctx->Vc32, u ? ctx->Ur32 : ctx->Vr32, out);
+    }
     const double* src;
     if (f64) {
       src = (const double*)img;

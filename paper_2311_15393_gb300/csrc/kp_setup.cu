@@ -158,10 +158,12 @@ __global__ void k_narrow64(const double* __restrict__ in, int n, int transpose, 
 }
 
 // d[i] = sum_a U[a + n i] * T[a * n + i]   (U col-major, T row-major)
-__global__ void k_coldot(const double* __restrict__ U, const double* __restrict__ T, int n, double* __restrict__ d) {
+template <typename T_>
+__global__ void k_coldot(const T_* __restrict__ U, const T_* __restrict__ T, int n, double* __restrict__ d) {
   const int i = blockIdx.x;
   double acc = 0.0;
-  for (int a = threadIdx.x; a < n; a += blockDim.x) acc = fma(U[(long long)i * n + a], T[(long long)a * n + i], acc);
+  for (int a = threadIdx.x; a < n; a += blockDim.x)
+    acc = fma((double)U[(long long)i * n + a], (double)T[(long long)a * n + i], acc);
   __shared__ double sh[256];
   sh[threadIdx.x] = acc;
   __syncthreads();
@@ -209,24 +211,39 @@ static int grid_for(kp_ctx* ctx, long long n) {
 static bool is_tc(kp_prec p) { return p == KP_BF16 || p == KP_BF16X3 || p == KP_F16 || p == KP_E4M3; }
 
 // projected spectrum factor: d[k][i] = diag(U^T F^(k) V)_i for square n; for
-// k = 0 (the factor the SVD is of) that diagonal is the singular values
-static kp_status projected_diag(kp_ctx* ctx, const double* F, const double* U, const double* V, const double* s,
-                                int n, int rank, double* d, double* tmp) {
+// k = 0 (the factor the SVD is of) that diagonal is the singular values.
+// The terms k >= 1 are one stacked product [F^(1); ...; F^(rank-1)] V, in
+// FP32 (U32, V32 given) or FP64.
+static kp_status projected_diag(kp_ctx* ctx, const double* F, const double* U, const double* V, const float* U32,
+                                const float* V32, const double* s, int n, int rank, double* d, void* tmp,
+                                float* F32) {
   KP_CUDA(cudaMemcpyAsync(d, s, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-  for (int k = 1; k < rank; ++k) {
-    GemmDesc g;
-    g.M = n;
-    g.N = n;
-    g.K = n;
-    g.A.ptr = F + (long long)k * n * n;
-    g.A.ld = n;
-    g.B.ptr = V;  // B[i][b] = V[b, i] (col-major V)
-    g.B.ld = n;
-    g.epi.mode = EPI_T;
-    g.epi.out = tmp;
-    g.epi.ldd = n;
+  if (rank < 2) return KP_OK;
+  const long long blk = (long long)n * n;
+  GemmDesc g;
+  g.M = (rank - 1) * n;
+  g.N = n;
+  g.K = n;
+  g.A.ld = n;
+  g.B.ld = n;  // B[i][b] = V[b, i] (col-major V)
+  g.epi.mode = EPI_T;
+  g.epi.out = tmp;
+  g.epi.ldd = n;
+  if (U32) {
+    KP_TRY(convert_f64_to_f32(ctx, F + blk, F32, (rank - 1) * blk));
+    g.A.ptr = F32;
+    g.B.ptr = V32;
+    KP_TRY(simt_gemm<float>(ctx, g));
+  } else {
+    g.A.ptr = F + blk;
+    g.B.ptr = V;
     KP_TRY(simt_gemm<double>(ctx, g));
-    k_coldot<<<n, 256, 0, ctx->stream>>>(U, tmp, n, d + (long long)k * n);
+  }
+  for (int k = 1; k < rank; ++k) {
+    if (U32)
+      k_coldot<float><<<n, 256, 0, ctx->stream>>>(U32, (const float*)tmp + (k - 1) * blk, n, d + (long long)k * n);
+    else
+      k_coldot<double><<<n, 256, 0, ctx->stream>>>(U, (const double*)tmp + (k - 1) * blk, n, d + (long long)k * n);
     KP_LAUNCHED(ctx);
   }
   KP_CUDA(cudaGetLastError());
@@ -298,6 +315,7 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
   ctx->pc_prec = pc_prec;
   ctx->vec_prec = vec_prec;
   ctx->sigma_mode = sigma;
+  ctx->setup_fp32 = vec_prec == KP_F32 && !ctx->force_setup_fp64;
   KP_CUDA(cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), ctx->stream));
 
   cudaStream_t st = ctx->stream;
@@ -362,20 +380,38 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
   const int transform = reflexive ? 0 : 1;
   KP_TRY(factor_svd(ctx, ctx->Ar64, n_c, transform, ctx->Ur, ctx->sr, ctx->Vr, nullptr));
   KP_TRY(factor_svd(ctx, ctx->Ac64, n_r, transform, ctx->Uc, ctx->sc, ctx->Vc, nullptr));
+  if (ctx->setup_fp32) {
+    KP_TRY(kp_alloc(ctx, (void**)&ctx->Uc32, sizeof(float) * (size_t)n_r * n_r));
+    KP_TRY(kp_alloc(ctx, (void**)&ctx->Vc32, sizeof(float) * (size_t)n_r * n_r));
+    KP_TRY(kp_alloc(ctx, (void**)&ctx->Ur32, sizeof(float) * (size_t)n_c * n_c));
+    KP_TRY(kp_alloc(ctx, (void**)&ctx->Vr32, sizeof(float) * (size_t)n_c * n_c));
+    KP_TRY(convert_f64_to_f32(ctx, ctx->Uc, ctx->Uc32, (long long)n_r * n_r));
+    KP_TRY(convert_f64_to_f32(ctx, ctx->Vc, ctx->Vc32, (long long)n_r * n_r));
+    KP_TRY(convert_f64_to_f32(ctx, ctx->Ur, ctx->Ur32, (long long)n_c * n_c));
+    KP_TRY(convert_f64_to_f32(ctx, ctx->Vr, ctx->Vr32, (long long)n_c * n_c));
+  }
 
   // ---- 5: KP spectrum
   KP_TRY(kp_alloc(ctx, (void**)&ctx->Sigma64, sizeof(double) * N));
   KP_TRY(kp_alloc(ctx, (void**)&ctx->Sigma32, sizeof(float) * N));
   {
-    double *dc, *dr, *tmp;
+    double *dc, *dr;
+    void* tmp = nullptr;
+    float* F32 = nullptr;
     const int nmax = std::max(n_r, n_c);
     const int rk = sigma == KP_SIGMA_PROJECTED ? rank : 1;
     KP_TRY(kp_alloc(ctx, (void**)&dc, sizeof(double) * (size_t)rk * n_r));
     KP_TRY(kp_alloc(ctx, (void**)&dr, sizeof(double) * (size_t)rk * n_c));
     if (sigma == KP_SIGMA_PROJECTED) {
-      KP_TRY(kp_alloc(ctx, (void**)&tmp, sizeof(double) * (size_t)nmax * nmax));
-      KP_TRY(projected_diag(ctx, ctx->Ac64, ctx->Uc, ctx->Vc, ctx->sc, n_r, rank, dc, tmp));
-      KP_TRY(projected_diag(ctx, ctx->Ar64, ctx->Ur, ctx->Vr, ctx->sr, n_c, rank, dr, tmp));
+      const size_t stack = (size_t)std::max(rank - 1, 1) * nmax * nmax;
+      if (ctx->setup_fp32) {
+        KP_TRY(kp_alloc(ctx, &tmp, sizeof(float) * stack));
+        KP_TRY(kp_alloc(ctx, (void**)&F32, sizeof(float) * stack));
+      } else {
+        KP_TRY(kp_alloc(ctx, &tmp, sizeof(double) * stack));
+      }
+      KP_TRY(projected_diag(ctx, ctx->Ac64, ctx->Uc, ctx->Vc, ctx->Uc32, ctx->Vc32, ctx->sc, n_r, rank, dc, tmp, F32));
+      KP_TRY(projected_diag(ctx, ctx->Ar64, ctx->Ur, ctx->Vr, ctx->Ur32, ctx->Vr32, ctx->sr, n_c, rank, dr, tmp, F32));
     } else {
       KP_CUDA(cudaMemcpyAsync(dc, ctx->sc, sizeof(double) * n_r, cudaMemcpyDeviceToDevice, st));
       KP_CUDA(cudaMemcpyAsync(dr, ctx->sr, sizeof(double) * n_c, cudaMemcpyDeviceToDevice, st));

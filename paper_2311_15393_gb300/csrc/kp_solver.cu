@@ -25,69 +25,6 @@
 #include "kp_ops.h"
 #include "kp_vec.cuh"
 
-namespace {
-
-// device scalar slots (ctx->dscal)
-enum {
-  S_RR = 0, S_AMAX = 1, S_PQ = 2, S_ALPHA = 3, S_ZR = 4, S_ZRNEW = 5, S_ZROLD = 6, S_BETA = 7,
-  S_RR0 = 8, S_RMAX = 9, S_TOL2 = 10, S_DELTA2 = 11
-};
-// device flag slots (ctx->dflags)
-enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4 };
-enum { R_CONV = 1, R_REPLACE = 2, R_MAXIT = 4, R_BREAKDOWN = 8, R_NUMERIC = 16 };
-
-__device__ __forceinline__ bool is_paused(const int* f) { return *(volatile const int*)f != 0; }
-
-__global__ void k_alpha(double* s, int* f) {
-  if (is_paused(f)) return;
-  const double pq = s[S_PQ], zr = s[S_ZR];
-  if (!isfinite(pq) || !isfinite(zr)) {
-    f[F_REASON] |= R_NUMERIC;
-    f[F_PAUSE] = 1;
-    return;
-  }
-  if (!(pq > 0.0) || !(zr > 0.0)) {
-    f[F_REASON] |= R_BREAKDOWN;
-    f[F_PAUSE] = 1;
-    return;
-  }
-  s[S_ALPHA] = zr / pq;
-}
-
-__global__ void k_check(double* s, int* f, double* hist, int hist_cap) {
-  if (is_paused(f)) return;
-  const int it = ++f[F_ITER];
-  const double rr = s[S_RR];
-  if (it < hist_cap) hist[it] = sqrt(rr / s[S_RR0]);
-  int reason = 0;
-  if (!isfinite(rr)) reason |= R_NUMERIC;
-  else if (rr <= s[S_TOL2]) reason |= R_CONV;
-  else if (s[S_DELTA2] > 0.0 && rr < s[S_DELTA2] * s[S_RMAX]) reason |= R_REPLACE;
-  if (it >= f[F_MAXIT]) reason |= R_MAXIT;
-  if (reason) {
-    f[F_REASON] |= reason;
-    f[F_PAUSE] = 1;
-  }
-}
-
-__global__ void k_beta(double* s, int* f) {
-  if (is_paused(f)) return;
-  const double zn = s[S_ZRNEW], zo = s[S_ZROLD], zr = s[S_ZR];
-  if (!isfinite(zn) || !isfinite(zo)) {
-    f[F_REASON] |= R_NUMERIC;
-    f[F_PAUSE] = 1;
-    return;
-  }
-  if (!(zn > 0.0)) {
-    f[F_REASON] |= R_BREAKDOWN;
-    f[F_PAUSE] = 1;
-    return;
-  }
-  s[S_BETA] = f[F_FLEX] ? (zn - zo) / zr : zn / zr;
-  s[S_ZR] = zn;
-}
-
-}  // namespace
 
 struct SolveBufs {
   void *r, *r_old, *p, *q, *z, *rhs;
@@ -110,13 +47,17 @@ static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
   const bool f64 = ctx->vec_prec == KP_F64;
   const int* fl = ctx->dflags;
   double* s = ctx->dscal;
+  PostOp pa;  // alpha = zr / p^T K p, by the last block of the dot product
+  pa.kind = POST_ALPHA;
+  pa.s = s;
+  pa.f = ctx->dflags;
+  PostOp pc = pa;  // iteration count, history and stopping flags, after the update
+  pc.kind = POST_CHECK;
+  pc.hist = ctx->hist;
+  pc.hist_cap = ctx->hist_cap;
   KP_TRY(op_apply_K(ctx, B.p, B.q, lam2, op_inner_slices(ctx) > 0, fl));
-  KP_TRY(dot2_dev(ctx, B.p, B.q, nullptr, N, f64, s + S_PQ, fl));
-  k_alpha<<<1, 1, 0, ctx->stream>>>(s, ctx->dflags);
-  KP_LAUNCHED(ctx);
-  KP_TRY(update_xr_dev(ctx, x, B.r, B.r_old, B.p, B.q, N, f64, s + S_ALPHA, s + S_RR, fl));
-  k_check<<<1, 1, 0, ctx->stream>>>(s, ctx->dflags, ctx->hist, ctx->hist_cap);
-  KP_LAUNCHED(ctx);
+  KP_TRY(dot2_dev(ctx, B.p, B.q, nullptr, N, f64, s + S_PQ, fl, pa));
+  KP_TRY(update_xr_dev(ctx, x, B.r, B.r_old, B.p, B.q, N, f64, s + S_ALPHA, s + S_RR, fl, pc));
   KP_CUDA(cudaGetLastError());
   return KP_OK;
 }
@@ -128,9 +69,11 @@ static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2) {
   const int* fl = ctx->dflags;
   double* s = ctx->dscal;
   KP_TRY(pc_apply(ctx, B.r, B.z, lam2, s + S_RR, fl));
-  KP_TRY(dot2_dev(ctx, B.z, B.r, B.r_old, N, f64, s + S_ZRNEW, fl));
-  k_beta<<<1, 1, 0, ctx->stream>>>(s, ctx->dflags);
-  KP_LAUNCHED(ctx);
+  PostOp pb;  // beta and zr, by the last block of the dot products
+  pb.kind = POST_BETA;
+  pb.s = s;
+  pb.f = ctx->dflags;
+  KP_TRY(dot2_dev(ctx, B.z, B.r, B.r_old, N, f64, s + S_ZRNEW, fl, pb));
   const int sl = op_inner_slices(ctx);
   KP_TRY(p_update_dev(ctx, B.p, B.z, N, f64, s + S_BETA, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N, fl));
   return KP_OK;

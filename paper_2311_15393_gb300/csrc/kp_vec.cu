@@ -1,11 +1,18 @@
 // Vector kernels of the (F)PCG loop and helper reductions.
 //
-// Every inner product and norm is accumulated in FP64 as a tree: per-thread
-// partial sums, warp shuffles, a block reduction, per-block partials, and a
-// final ordered reduction by the last block to finish.  The result does not
-// depend on block scheduling.  This is the GPU form of the pairwise
-// summation the paper uses to limit rounding-error growth in inner products
-// (Section 4).
+// Every inner product and norm is accumulated as a tree: per-thread partial
+// sums, warp shuffles, a block reduction, per-block partials, and a final
+// ordered reduction by the last block to finish, in FP64 from the warp level
+// up.  The result does not depend on block scheduling.  This is the GPU form
+// of the pairwise summation the paper uses to limit rounding-error growth in
+// inner products (Section 4).  FP32 vectors are processed in FP32 (16-byte
+// loads; per-thread partial sums over at most 64 elements before they are
+// added into FP64): FP64 arithmetic runs at a small fraction of the FP32 rate
+// on this GPU and would bound these memory-bound kernels.  The last block of
+// a reduction can run the scalar step of the iteration (alpha, the
+// convergence test, beta) on the final values, saving a launch.
+#include <type_traits>
+
 #include "kp_vec.cuh"
 
 namespace kpv {
@@ -23,9 +30,11 @@ __device__ __forceinline__ double warp_max(double v) {
 
 // Block-level reduction of NV sums (+ optional max in slot NV-1 when
 // last_is_max) and the cross-block ordered finish.  blockDim.x == VEC_THREADS.
+__device__ void run_post(const PostOp& po, const double* vals);
+
 template <int NV>
 __device__ void reduce_finish(double (&v)[NV], bool last_is_max, double* partials, unsigned int* counter,
-                              double* out, int nout) {
+                              double* out, int nout, const PostOp& po = PostOp()) {
   __shared__ double sh[VEC_THREADS / 32][NV];
   __shared__ bool s_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -76,15 +85,66 @@ __device__ void reduce_finish(double (&v)[NV], bool last_is_max, double* partial
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 0; i < nout; ++i) {
+    double fin[NV];
+    for (int i = 0; i < NV; ++i) {
       const bool mx = last_is_max && i == NV - 1;
       double t = sh[0][i];
       for (int w = 1; w < VEC_THREADS / 32; ++w) t = mx ? fmax(t, sh[w][i]) : t + sh[w][i];
-      out[i] = t;
+      fin[i] = t;
+      if (i < nout) out[i] = t;
     }
     *counter = 0u;
+    if (po.kind != POST_NONE) run_post(po, fin);
   }
 }
+
+// scalar steps of the iteration (see PostOp); vals = the reduction's results
+__device__ void run_post(const PostOp& po, const double* vals) {
+  double* s = po.s;
+  int* f = po.f;
+  if (po.kind == POST_ALPHA) {  // vals[0] = p^T K p
+    const double pq = vals[0], zr = s[S_ZR];
+    if (!isfinite(pq) || !isfinite(zr)) {
+      f[F_REASON] |= R_NUMERIC;
+      f[F_PAUSE] = 1;
+    } else if (!(pq > 0.0) || !(zr > 0.0)) {
+      f[F_REASON] |= R_BREAKDOWN;
+      f[F_PAUSE] = 1;
+    } else {
+      s[S_ALPHA] = zr / pq;
+    }
+  } else if (po.kind == POST_CHECK) {  // vals[0] = ||r||^2
+    const int it = ++f[F_ITER];
+    const double rr = vals[0];
+    if (it < po.hist_cap) po.hist[it] = sqrt(rr / s[S_RR0]);
+    int reason = 0;
+    if (!isfinite(rr)) reason |= R_NUMERIC;
+    else if (rr <= s[S_TOL2]) reason |= R_CONV;
+    else if (s[S_DELTA2] > 0.0 && rr < s[S_DELTA2] * s[S_RMAX]) reason |= R_REPLACE;
+    if (it >= f[F_MAXIT]) reason |= R_MAXIT;
+    if (reason) {
+      f[F_REASON] |= reason;
+      f[F_PAUSE] = 1;
+    }
+  } else if (po.kind == POST_BETA) {  // vals[0] = z^T r, vals[1] = z^T r_old
+    const double zn = vals[0], zo = vals[1], zr = s[S_ZR];
+    if (!isfinite(zn) || !isfinite(zo)) {
+      f[F_REASON] |= R_NUMERIC;
+      f[F_PAUSE] = 1;
+    } else if (!(zn > 0.0)) {
+      f[F_REASON] |= R_BREAKDOWN;
+      f[F_PAUSE] = 1;
+    } else {
+      s[S_BETA] = f[F_FLEX] ? (zn - zo) / zr : zn / zr;
+      s[S_ZR] = zn;
+    }
+  }
+}
+
+// 16-byte access to element 4 i of an FP32 vector
+__device__ __forceinline__ float4 ld4(const float* p, long long i) { return reinterpret_cast<const float4*>(p)[i]; }
+__device__ __forceinline__ void st4(float* p, long long i, float4 v) { reinterpret_cast<float4*>(p)[i] = v; }
+constexpr int FLUSH = 16;  // float4 packets per thread between FP64 flushes
 
 __device__ __forceinline__ bool paused(const int* flags) { return flags != nullptr && *(volatile const int*)flags != 0; }
 
@@ -92,16 +152,48 @@ __device__ __forceinline__ bool paused(const int* flags) { return flags != nullp
 // out[0] = a.b ; if c != null, out[1] = a.c
 template <typename T>
 __global__ void __launch_bounds__(VEC_THREADS) k_dot2(const T* __restrict__ a, const T* __restrict__ b,
-                                                      const T* __restrict__ c, long long n, double* partials,
-                                                      unsigned int* counter, double* out, const int* flags) {
+                                                      const T* __restrict__ c, long long n, int vec4,
+                                                      double* partials, unsigned int* counter, double* out,
+                                                      const int* flags, PostOp po) {
   if (paused(flags)) return;
   double v[2] = {0.0, 0.0};
-  for (long long i = blockIdx.x * (long long)VEC_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * VEC_THREADS) {
-    double ai = (double)a[i];
-    v[0] = fma(ai, (double)b[i], v[0]);
-    if (c) v[1] = fma(ai, (double)c[i], v[1]);
+  const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
+  long long i0 = tid;
+  if constexpr (std::is_same<T, float>::value) {
+    if (vec4) {
+      const long long n4 = n >> 2;
+      float f0 = 0.f, f1 = 0.f;
+      int cnt = 0;
+      for (long long i = tid; i < n4; i += stride) {
+        const float4 x = ld4(a, i), y = ld4(b, i);
+        f0 = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, f0))));
+        if (c) {
+          const float4 z = ld4(c, i);
+          f1 = fmaf(x.x, z.x, fmaf(x.y, z.y, fmaf(x.z, z.z, fmaf(x.w, z.w, f1))));
+        }
+        if (++cnt == FLUSH) {
+          v[0] += f0;
+          v[1] += f1;
+          f0 = f1 = 0.f;
+          cnt = 0;
+        }
+      }
+      v[0] += f0;
+      v[1] += f1;
+      i0 = 4 * n4 + tid;
+    }
+    for (long long i = i0; i < n; i += stride) {
+      v[0] += (double)(a[i] * b[i]);
+      if (c) v[1] += (double)(a[i] * c[i]);
+    }
+  } else {
+    for (long long i = i0; i < n; i += stride) {
+      const double ai = (double)a[i];
+      v[0] = fma(ai, (double)b[i], v[0]);
+      if (c) v[1] = fma(ai, (double)c[i], v[1]);
+    }
   }
-  reduce_finish<2>(v, false, partials, counter, out, c ? 2 : 1);
+  reduce_finish<2>(v, false, partials, counter, out, c ? 2 : 1, po);
 }
 
 // y = alpha*x + beta*y (scalars from host); used by setup / hooks
@@ -116,40 +208,122 @@ __global__ void k_axpby(const T* __restrict__ x, T* __restrict__ y, long long n,
 template <typename T>
 __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T* __restrict__ r,
                                                            T* __restrict__ r_old, const T* __restrict__ p,
-                                                           const T* __restrict__ q, long long n,
+                                                           const T* __restrict__ q, long long n, int vec4,
                                                            const double* __restrict__ alpha_dev, double* partials,
-                                                           unsigned int* counter, double* out, const int* flags) {
+                                                           unsigned int* counter, double* out, const int* flags,
+                                                           PostOp po) {
   if (paused(flags)) return;
-  const double alpha = *alpha_dev;
   double v[2] = {0.0, 0.0};
-  for (long long i = blockIdx.x * (long long)VEC_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * VEC_THREADS) {
-    T ri = r[i];
-    x[i] = (T)((double)x[i] + alpha * (double)p[i]);
-    r_old[i] = ri;
-    T rn = (T)((double)ri - alpha * (double)q[i]);
-    r[i] = rn;
-    double d = (double)rn;
-    v[0] = fma(d, d, v[0]);
-    v[1] = fmax(v[1], fabs(d));
+  const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
+  if constexpr (std::is_same<T, float>::value) {
+    const float al = (float)*alpha_dev;
+    long long i0 = tid;
+    float rr = 0.f, am = 0.f;
+    int cnt = 0;
+    if (vec4) {
+      const long long n4 = n >> 2;
+      for (long long i = tid; i < n4; i += stride) {
+        const float4 xi = ld4(x, i), ri = ld4(r, i), pi = ld4(p, i), qi = ld4(q, i);
+        st4(x, i, make_float4(fmaf(al, pi.x, xi.x), fmaf(al, pi.y, xi.y), fmaf(al, pi.z, xi.z), fmaf(al, pi.w, xi.w)));
+        st4(r_old, i, ri);
+        const float4 rn = make_float4(fmaf(-al, qi.x, ri.x), fmaf(-al, qi.y, ri.y), fmaf(-al, qi.z, ri.z),
+                                      fmaf(-al, qi.w, ri.w));
+        st4(r, i, rn);
+        rr = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, rr))));
+        am = fmaxf(am, fmaxf(fmaxf(fabsf(rn.x), fabsf(rn.y)), fmaxf(fabsf(rn.z), fabsf(rn.w))));
+        if (++cnt == FLUSH) {
+          v[0] += rr;
+          rr = 0.f;
+          cnt = 0;
+        }
+      }
+      i0 = 4 * n4 + tid;
+    }
+    for (long long i = i0; i < n; i += stride) {
+      const float ri = r[i];
+      x[i] = fmaf(al, p[i], x[i]);
+      r_old[i] = ri;
+      const float rn = fmaf(-al, q[i], ri);
+      r[i] = rn;
+      rr = fmaf(rn, rn, rr);
+      am = fmaxf(am, fabsf(rn));
+    }
+    v[0] += rr;
+    v[1] = am;
+  } else {
+    const double alpha = *alpha_dev;
+    for (long long i = tid; i < n; i += stride) {
+      T ri = r[i];
+      x[i] = (T)((double)x[i] + alpha * (double)p[i]);
+      r_old[i] = ri;
+      T rn = (T)((double)ri - alpha * (double)q[i]);
+      r[i] = rn;
+      double d = (double)rn;
+      v[0] = fma(d, d, v[0]);
+      v[1] = fmax(v[1], fabs(d));
+    }
   }
-  reduce_finish<2>(v, true, partials, counter, out, 2);
+  reduce_finish<2>(v, true, partials, counter, out, 2, po);
 }
 
 // p = z + beta p ; optional bf16 split copy of p (slices written at stride)
 template <typename T>
-__global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long n, const double* __restrict__ beta_dev,
-                           __nv_bfloat16* __restrict__ ps, int slices, long long sstride, const int* flags) {
+__global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long n, int vec4,
+                           const double* __restrict__ beta_dev, __nv_bfloat16* __restrict__ ps, int slices,
+                           long long sstride, const int* flags) {
   if (paused(flags)) return;
-  const double beta = beta_dev ? *beta_dev : 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    T pn = (T)((double)z[i] + beta * (double)p[i]);
-    p[i] = pn;
-    if (ps) {
-      float v = (float)pn;
-      for (int s = 0; s < slices; ++s) {
-        __nv_bfloat16 h = __float2bfloat16_rn(v);
-        ps[s * sstride + i] = h;
-        v -= __bfloat162float(h);
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  if constexpr (std::is_same<T, float>::value) {
+    const float be = beta_dev ? (float)*beta_dev : 0.f;
+    long long i0 = tid;
+    if (vec4) {
+      const long long n4 = n >> 2;
+      for (long long i = tid; i < n4; i += stride) {
+        const float4 pi = ld4(p, i), zi = ld4(z, i);
+        float4 pn = make_float4(fmaf(be, pi.x, zi.x), fmaf(be, pi.y, zi.y), fmaf(be, pi.z, zi.z), fmaf(be, pi.w, zi.w));
+        st4(p, i, pn);
+        if (ps) {
+          float w[4] = {pn.x, pn.y, pn.z, pn.w};
+          for (int sl = 0; sl < slices; ++sl) {
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(w[0], w[1]);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(w[2], w[3]);
+            uint2 pk;
+            pk.x = *reinterpret_cast<uint32_t*>(&h0);
+            pk.y = *reinterpret_cast<uint32_t*>(&h1);
+            *reinterpret_cast<uint2*>(ps + sl * sstride + 4 * i) = pk;
+            w[0] -= __bfloat162float(h0.x);
+            w[1] -= __bfloat162float(h0.y);
+            w[2] -= __bfloat162float(h1.x);
+            w[3] -= __bfloat162float(h1.y);
+          }
+        }
+      }
+      i0 = 4 * n4 + tid;
+    }
+    for (long long i = i0; i < n; i += stride) {
+      const float pn = fmaf(be, p[i], z[i]);
+      p[i] = pn;
+      if (ps) {
+        float v = pn;
+        for (int sl = 0; sl < slices; ++sl) {
+          __nv_bfloat16 h = __float2bfloat16_rn(v);
+          ps[sl * sstride + i] = h;
+          v -= __bfloat162float(h);
+        }
+      }
+    }
+  } else {
+    const double beta = beta_dev ? *beta_dev : 0.0;
+    for (long long i = tid; i < n; i += stride) {
+      T pn = (T)((double)z[i] + beta * (double)p[i]);
+      p[i] = pn;
+      if (ps) {
+        float v = (float)pn;
+        for (int sl = 0; sl < slices; ++sl) {
+          __nv_bfloat16 h = __float2bfloat16_rn(v);
+          ps[sl * sstride + i] = h;
+          v -= __bfloat162float(h);
+        }
       }
     }
   }
@@ -179,13 +353,31 @@ __device__ __forceinline__ float pow2_scale(double amax, double target) {
   return (float)ldexp(1.0, e - 1);
 }
 template <typename T, typename N>
-__global__ void k_quantize(const T* __restrict__ r, long long n, const double* __restrict__ stat, double target,
-                           double lam2, N* __restrict__ out, float* __restrict__ inv_out, const int* flags) {
+__global__ void k_quantize(const T* __restrict__ r, long long n, int vec4, const double* __restrict__ stat,
+                           double target, double lam2, N* __restrict__ out, float* __restrict__ inv_out,
+                           const int* flags) {
   if (paused(flags)) return;
-  const float s = pow2_scale(stat[1], target);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *inv_out = (float)(1.0 / (lam2 * (double)s));
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = to_narrow<N>((float)r[i] * s);
+  __shared__ float s_sh;
+  if (threadIdx.x == 0) {
+    s_sh = pow2_scale(stat[1], target);
+    if (blockIdx.x == 0) *inv_out = (float)(1.0 / (lam2 * (double)s_sh));
+  }
+  __syncthreads();
+  const float s = s_sh;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  long long i0 = tid;
+  if (vec4) {
+    const long long n4 = n >> 2;
+    for (long long i = tid; i < n4; i += stride) {
+      const float4 v = ld4((const float*)r, i);
+      out[4 * i + 0] = to_narrow<N>(v.x * s);
+      out[4 * i + 1] = to_narrow<N>(v.y * s);
+      out[4 * i + 2] = to_narrow<N>(v.z * s);
+      out[4 * i + 3] = to_narrow<N>(v.w * s);
+    }
+    i0 = 4 * n4 + tid;
+  }
+  for (long long i = i0; i < n; i += stride) out[i] = to_narrow<N>((float)r[i] * s);
 }
 
 // amax only (for one-off applies outside the loop)
@@ -193,10 +385,28 @@ template <typename T>
 __global__ void __launch_bounds__(VEC_THREADS) k_norm_amax(const T* __restrict__ x, long long n, double* partials,
                                                            unsigned int* counter, double* out) {
   double v[2] = {0.0, 0.0};
-  for (long long i = blockIdx.x * (long long)VEC_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * VEC_THREADS) {
-    double d = (double)x[i];
-    v[0] = fma(d, d, v[0]);
-    v[1] = fmax(v[1], fabs(d));
+  const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
+  if constexpr (std::is_same<T, float>::value) {
+    float rr = 0.f, am = 0.f;
+    int cnt = 0;
+    for (long long i = tid; i < n; i += stride) {
+      const float d = x[i];
+      rr = fmaf(d, d, rr);
+      am = fmaxf(am, fabsf(d));
+      if (++cnt == 4 * FLUSH) {
+        v[0] += rr;
+        rr = 0.f;
+        cnt = 0;
+      }
+    }
+    v[0] += rr;
+    v[1] = am;
+  } else {
+    for (long long i = tid; i < n; i += stride) {
+      double d = (double)x[i];
+      v[0] = fma(d, d, v[0]);
+      v[1] = fmax(v[1], fabs(d));
+    }
   }
   reduce_finish<2>(v, true, partials, counter, out, 2);
 }
@@ -220,15 +430,22 @@ int vec_grid(kp_ctx* ctx, long long n) {
   return (int)b;
 }
 
+static int aligned16(const void* a, const void* b = nullptr, const void* c = nullptr, const void* d = nullptr,
+                     const void* e = nullptr) {
+  const uintptr_t m = (uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d | (uintptr_t)e;
+  return (m & 15) == 0 ? 1 : 0;
+}
+
 kp_status dot2_dev(kp_ctx* ctx, const void* a, const void* b, const void* c, long long n, bool f64, double* out,
-                   const int* flags) {
+                   const int* flags, PostOp post) {
   int g = vec_grid(ctx, n);
   if (f64)
-    k_dot2<double><<<g, VEC_THREADS, 0, ctx->stream>>>((const double*)a, (const double*)b, (const double*)c, n,
-                                                       ctx->red_part, ctx->red_count, out, flags);
+    k_dot2<double><<<g, VEC_THREADS, 0, ctx->stream>>>((const double*)a, (const double*)b, (const double*)c, n, 0,
+                                                       ctx->red_part, ctx->red_count, out, flags, post);
   else
     k_dot2<float><<<g, VEC_THREADS, 0, ctx->stream>>>((const float*)a, (const float*)b, (const float*)c, n,
-                                                      ctx->red_part, ctx->red_count, out, flags);
+                                                      aligned16(a, b, c), ctx->red_part, ctx->red_count, out, flags,
+                                                      post);
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -254,16 +471,17 @@ kp_status norm2_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* o
 }
 
 kp_status update_xr_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* p, const void* q, long long n,
-                        bool f64, const double* alpha_dev, double* out2, const int* flags) {
+                        bool f64, const double* alpha_dev, double* out2, const int* flags, PostOp post) {
   int g = vec_grid(ctx, n);
   if (f64)
     k_update_xr<double><<<g, VEC_THREADS, 0, ctx->stream>>>((double*)x, (double*)r, (double*)r_old, (const double*)p,
-                                                            (const double*)q, n, alpha_dev, ctx->red_part,
-                                                            ctx->red_count, out2, flags);
+                                                            (const double*)q, n, 0, alpha_dev, ctx->red_part,
+                                                            ctx->red_count, out2, flags, post);
   else
     k_update_xr<float><<<g, VEC_THREADS, 0, ctx->stream>>>((float*)x, (float*)r, (float*)r_old, (const float*)p,
-                                                           (const float*)q, n, alpha_dev, ctx->red_part,
-                                                           ctx->red_count, out2, flags);
+                                                           (const float*)q, n, aligned16(x, r, r_old, p, q),
+                                                           alpha_dev, ctx->red_part, ctx->red_count, out2, flags,
+                                                           post);
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -273,11 +491,12 @@ kp_status p_update_dev(kp_ctx* ctx, void* p, const void* z, long long n, bool f6
                        __nv_bfloat16* ps, int slices, long long sstride, const int* flags) {
   int g = vec_grid(ctx, n);
   if (f64)
-    k_p_update<double><<<g, VEC_THREADS, 0, ctx->stream>>>((double*)p, (const double*)z, n, beta_dev, ps, slices,
+    k_p_update<double><<<g, VEC_THREADS, 0, ctx->stream>>>((double*)p, (const double*)z, n, 0, beta_dev, ps, slices,
                                                            sstride, flags);
   else
-    k_p_update<float><<<g, VEC_THREADS, 0, ctx->stream>>>((float*)p, (const float*)z, n, beta_dev, ps, slices,
-                                                          sstride, flags);
+    k_p_update<float><<<g, VEC_THREADS, 0, ctx->stream>>>(
+        (float*)p, (const float*)z, n, aligned16(p, z) && (((uintptr_t)ps & 7) == 0) && (sstride % 4 == 0), beta_dev,
+        ps, slices, sstride, flags);
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -303,14 +522,15 @@ kp_status quantize_dev(kp_ctx* ctx, const void* r, long long n, bool f64, const 
     return KP_ENOTSUP;
   }
   const float* rf = (const float*)r;
+  const int v4 = aligned16(r);
   if (narrow == NT_BF16)
-    k_quantize<float, __nv_bfloat16><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, stat, target, lam2,
+    k_quantize<float, __nv_bfloat16><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, v4, stat, target, lam2,
                                                                           (__nv_bfloat16*)out, inv_out, flags);
   else if (narrow == NT_F16)
-    k_quantize<float, __half><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, stat, target, lam2, (__half*)out, inv_out,
-                                                                   flags);
+    k_quantize<float, __half><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, v4, stat, target, lam2, (__half*)out,
+                                                                   inv_out, flags);
   else
-    k_quantize<float, __nv_fp8_e4m3><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, stat, target, lam2,
+    k_quantize<float, __nv_fp8_e4m3><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, v4, stat, target, lam2,
                                                                           (__nv_fp8_e4m3*)out, inv_out, flags);
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
