@@ -215,6 +215,13 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *   "jacobi_max_sweeps" (default 40)
  *   "splitk"          > 0: fixed split-K factor of the square tensor-core
  *                     GEMMs (default 0 = chosen per shape)
+ *   "tc_bn"           64, 128 or 256: fixed tensor-core tile width (default 0 =
+ *                     chosen per shape)
+ *   "tc_ctas_per_sm"  1 or 2: fixed CTAs per SM for 128-wide tiles (default 0)
+ *                     The three tile options take effect at the next kp_setup.
+ *   "pdl"             0: launch the iteration's kernels without programmatic
+ *                     dependent launch (default 1: each kernel's launch and
+ *                     prologue overlap the tail of the previous one)
  *   "setup_fp64"      nonzero: keep the O(n^3) products of kp_setup and of
  *                     choose_lambda's spectral coefficients in FP64 also for
  *                     FP32 vectors.  By default they run in FP32 when

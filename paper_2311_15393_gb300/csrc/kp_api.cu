@@ -215,6 +215,12 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
     ctx->jacobi_max_sweeps = (int)value;
   } else if (!strcmp(name, "splitk")) {
     ctx->splitk_override = (int)value;
+  } else if (!strcmp(name, "pdl")) {
+    ctx->pdl = value != 0.0;
+  } else if (!strcmp(name, "tc_bn")) {
+    ctx->tc_bn_override = (int)value;
+  } else if (!strcmp(name, "tc_ctas_per_sm")) {
+    ctx->tc_cps_override = (int)value;
   } else if (!strcmp(name, "setup_fp64")) {
     ctx->force_setup_fp64 = value != 0.0;
   } else {

@@ -11,9 +11,9 @@
 // bf16 slices (hi + lo + ...) and sum slice products to recover FP32-level
 // accuracy where needed.
 //
-// Persistent kernel, one CTA per SM.  Work units are (128 x BN output tile,
-// K split) pairs handed out round-robin over the grid:
-//   warp 0      TMA producer (one thread): STAGES-deep shared-memory ring
+// Persistent kernel, one or two CTAs per SM.  Work units are (128 x BN
+// output tile, K split) pairs handed out round-robin over the grid:
+//   warp 0      TMA producer (lanes 0 / 1: A / B tiles): STAGES-deep ring
 //   warp 1      TMEM allocation + MMA issuer (one thread)
 //   warps 2..5  epilogue: tcgen05.ld TMEM -> registers -> fused output
 // The accumulator is double-buffered in TMEM (2 x BN columns), so the
@@ -35,13 +35,23 @@ namespace {
 constexpr int TBM = 128;
 constexpr int TC_THREADS = 192;
 
-template <int BN>
+// Tile configurations: 128 x BN output tiles, CPS CTAs resident per SM.  The
+// shared-memory ring is as deep as ~192 KiB per SM allows: the loads of a
+// k-step take about a microsecond to arrive, so a deep ring (bytes in
+// flight) is what keeps the tensor pipe fed.
+//   BN 256, 1 CTA/SM: 4 x 48 KiB     BN 128, 1 CTA/SM: 6 x 32 KiB
+//   BN 128, 2 CTAs/SM: 3 x 32 KiB each (one's prologue / epilogue overlaps
+//   the other's main loop)            BN 64, 1 CTA/SM: 8 x 24 KiB
+// Narrow tiles give the square n x n products enough tiles to occupy the
+// SMs without splitting K (split-K partials cost more than they save here).
+template <int BN, int CPS>
 struct TcCfg {
+  static_assert(CPS == 1 || (CPS == 2 && BN <= 128), "TMEM holds 2 x BN columns per CTA");
   static constexpr int A_BYTES = TBM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int STAGES = BN == 256 ? 4 : 3;
-  static constexpr int CTAS_PER_SM = BN == 256 ? 1 : 2;  // 2 x (96 KiB ring, 256 TMEM columns) per SM
+  static constexpr int STAGES = (196608 / CPS) / STAGE;
+  static constexpr int CTAS_PER_SM = CPS;
   static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 512 /*barriers*/;
   static constexpr int TMEM_COLS = 2 * BN;
 };
@@ -52,7 +62,8 @@ struct TcParams {
   int sa[KP_MAX_PAIRS], sb[KP_MAX_PAIRS];
   int kblocks;      // ceil(K / BK)
   int splits;       // split-K factor over the (pair, term, kblock) steps
-  int steps_total;  // npairs * nkron * kblocks
+  int steps_total;  // npairs * nkron * kblocks (npairs * kblocks when batched)
+  int batch_rows;   // > 0: term index = tile row / batch_rows, no sum over terms
   int tiles_m, tiles_n, units;
   uint32_t idesc;
   EpiParams epi;
@@ -337,15 +348,17 @@ __device__ __forceinline__ Unit decode_unit(const TcParams& p, int u, int bn) {
   return r;
 }
 
-template <int KIND, int BN>
-__global__ void __launch_bounds__(TC_THREADS, TcCfg<BN>::CTAS_PER_SM)
+template <int KIND, int BN, int CPS>
+__global__ void __launch_bounds__(TC_THREADS, CPS)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
-  using C = TcCfg<BN>;
-  if (p.flags && *(volatile const int*)p.flags) return;
+  using C = TcCfg<BN, CPS>;
   if (threadIdx.x == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
   }
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
+  if (p.flags && *(volatile const int*)p.flags) return;
   extern __shared__ unsigned char smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE);
@@ -384,29 +397,45 @@ __global__ void __launch_bounds__(TC_THREADS, TcCfg<BN>::CTAS_PER_SM)
   const int ksh = KIND == TC_E4M3 ? 0 : 1;  // K elements per 128-byte row: 128 >> ksh
 
   if (warp == 0) {
-    if (lane == 0) {
-      // ---------------- TMA producer
+    if (lane < 2) {
+      // ---------------- TMA producer: lane 0 owns the barriers and loads the
+      // A tile, lane 1 loads the B tile (both issued by one instruction)
+      const CUtensorMap* map = lane == 0 ? &tmA : &tmB;
+      const int nk = p.batch_rows ? 1 : p.nkron;
       int it = 0;
-      for (int u = blockIdx.x; u < p.units && !*(volatile int*)&s_abort; u += gridDim.x) {
+      bool run = true;
+      for (int u = blockIdx.x; run && u < p.units && !*(volatile int*)&s_abort; u += gridDim.x) {
         const Unit w = decode_unit(p, u, BN);
+        const int tb = p.batch_rows ? w.m0 / p.batch_rows : 0;
+        const int row0 = lane == 0 ? w.m0 - tb * p.batch_rows : w.n0;
+        int kb = w.step0 % p.kblocks;
+        const int rest = w.step0 / p.kblocks;
+        int k = rest % nk, pr = rest / nk;
         for (int j = 0; j < w.nsteps; ++j, ++it) {
-          const int stp = w.step0 + j;
-          const int kb = stp % p.kblocks;
-          const int rest = stp / p.kblocks;
-          const int k = rest % p.nkron;
-          const int pr = rest / p.nkron;
           const int s = it % C::STAGES;
           const uint32_t ph = (it / C::STAGES) & 1;
-          if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, p.status)) {
-            s_abort = 1;
+          const uint32_t fb = smem_u32(&full[s]);
+          int okw = 1;
+          if (lane == 0) {
+            okw = mbar_wait(smem_u32(&empty[s]), ph ^ 1, p.status) ? 1 : 0;
+            if (okw) mbar_expect_tx(fb, C::STAGE);
+          }
+          okw = __shfl_sync(0x3u, okw, 0);
+          if (!okw) {
+            if (lane == 0) s_abort = 1;
+            run = false;
             break;
           }
-          const uint32_t fb = smem_u32(&full[s]);
-          mbar_expect_tx(fb, C::STAGE);
-          const int kc = (kb * 128) >> ksh;
-          const uint32_t sa = smem_u32(smem + s * C::STAGE);
-          tma_load_3d(sa, &tmA, kc, w.m0, p.sa[pr] * p.a_terms + k, fb);
-          tma_load_3d(sa + C::A_BYTES, &tmB, kc, w.n0, p.sb[pr] * p.b_terms + k, fb);
+          const int term = (lane == 0 ? p.sa[pr] * p.a_terms : p.sb[pr] * p.b_terms) + (p.batch_rows ? tb : k);
+          const uint32_t dst = smem_u32(smem + s * C::STAGE) + (lane == 0 ? 0u : (uint32_t)C::A_BYTES);
+          tma_load_3d(dst, map, (kb * 128) >> ksh, row0, term, fb);
+          if (++kb == p.kblocks) {
+            kb = 0;
+            if (++k == nk) {
+              k = 0;
+              ++pr;
+            }
+          }
         }
       }
     }
@@ -535,6 +564,7 @@ struct TcGemmPlan {
   TcParams params;
   int kind;
   int bn;
+  int cps;
   dim3 grid;
 };
 
@@ -616,9 +646,33 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
     kp_set_error("tc_plan_create: K * element size must be a multiple of 16 bytes (K=%d)", g.K);
     return KP_ENOTSUP;
   }
-  // 128 x 128 tiles, two CTAs per SM so that one's prologue / epilogue
-  // overlaps the other's main loop (128 x 256 kept for very wide outputs)
-  const int bn = (g.N >= 256 && (long long)((g.M + TBM - 1) / TBM) * ((g.N + 255) / 256) >= 4LL * ctx->sm_count) ? 256 : 128;
+  // Tile shape, CTAs per SM and K split.  Wide tiles (most work per byte
+  // staged) when they alone give most SMs a tile; else 128-wide tiles, with
+  // K split so that about one unit lands on each SM (each split keeping at
+  // least 8 k-steps), two CTAs per SM when the tiles outnumber the SMs.
+  const int sms = ctx->sm_count;
+  const int bk_ = 128 / esize;
+  if (g.batch_rows > 0 && (g.batch_rows % TBM != 0 || g.M != g.batch_rows * g.nkron)) {
+    kp_set_error("tc_plan_create: batched rows must be a multiple of %d and M = terms x rows", TBM);
+    return KP_EINVAL;
+  }
+  const int steps_all = g.npairs * (g.batch_rows > 0 ? 1 : g.nkron) * ((g.K + bk_ - 1) / bk_);
+  const int tm = (g.M + TBM - 1) / TBM;
+  auto tiles_of = [&](int w) { return tm * ((g.N + w - 1) / w); };
+  int bn = 64;
+  if (g.N >= 256 && 4 * tiles_of(256) >= 3 * sms)
+    bn = 256;
+  else if (g.N >= 128 && 4 * tiles_of(128) >= 3 * sms)
+    bn = 128;
+  if (ctx->tc_bn_override == 64 || ctx->tc_bn_override == 128 || ctx->tc_bn_override == 256)
+    bn = ctx->tc_bn_override;
+  const int tiles_bn = tiles_of(bn);
+  int cps = (bn == 128 && tiles_bn > sms) ? 2 : 1;
+  if (bn == 128 && (ctx->tc_cps_override == 1 || ctx->tc_cps_override == 2)) cps = ctx->tc_cps_override;
+  if (splits < 1) {  // K split only when even 64-wide tiles leave most SMs idle
+    splits = 1;
+    if (2 * tiles_bn < sms) splits = std::max(1, std::min({4, sms / tiles_bn, steps_all / 16}));
+  }
   TcGemmPlan* pl = new TcGemmPlan();
   kp_status st = make_map(&pl->mapA, g.A, kind, TBM);
   if (st == KP_OK) st = make_map(&pl->mapB, g.B, kind, bn);
@@ -640,16 +694,11 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
   }
   const int bk = 128 / esize;
   p.kblocks = (g.K + bk - 1) / bk;
-  p.steps_total = g.npairs * g.nkron * p.kblocks;
+  p.batch_rows = g.batch_rows;
+  p.steps_total = g.npairs * (g.batch_rows > 0 ? 1 : g.nkron) * p.kblocks;
   p.tiles_m = (g.M + TBM - 1) / TBM;
   p.tiles_n = (g.N + bn - 1) / bn;
   const int tiles = p.tiles_m * p.tiles_n;
-  if (splits < 1) {  // split K only for few tiles and long K (>= 32 steps per split)
-    splits = 1;
-    const int slots = 2 * ctx->sm_count;
-    if (2 * tiles < slots && p.steps_total >= 64)
-      splits = std::max(1, std::min({4, p.steps_total / 32, (slots + tiles - 1) / tiles}));
-  }
   splits = std::min(splits, p.steps_total);
   p.splits = splits;
   p.units = tiles * splits;
@@ -676,7 +725,8 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
   }
   pl->kind = kind;
   pl->bn = bn;
-  pl->grid = dim3(std::min(p.units, ctx->sm_count * (bn == 256 ? 1 : 2)), 1, 1);
+  pl->cps = cps;
+  pl->grid = dim3(std::min(p.units, ctx->sm_count * cps), 1, 1);
   ctx->tc_plans.push_back(pl);
   *out = pl;
   return KP_OK;
@@ -692,17 +742,25 @@ void tc_plan_set_runtime(TcGemmPlan* plan, const float* alpha_dev, const int* fl
   plan->params.flags = flags;
 }
 
-template <int KIND, int BN>
+template <int KIND, int BN, int CPS>
 static kp_status launch_kind(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
+  using C = TcCfg<BN, CPS>;
   static bool attr_set = false;
   if (!attr_set) {
-    KP_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TcCfg<BN>::SMEM));
+    KP_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     attr_set = true;
   }
-  tc_gemm_kernel<KIND, BN><<<pl->grid, TC_THREADS, TcCfg<BN>::SMEM, ctx->stream>>>(pl->mapA, pl->mapB, p);
+  KP_CUDA(kp_launch(ctx, tc_gemm_kernel<KIND, BN, CPS>, pl->grid, dim3(TC_THREADS), C::SMEM, pl->mapA, pl->mapB, p));
   KP_LAUNCHED(ctx);
   return KP_OK;
+}
+
+template <int KIND>
+static kp_status launch_cfg(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
+  if (pl->bn == 256) return launch_kind<KIND, 256, 1>(ctx, pl, p);
+  if (pl->bn == 64) return launch_kind<KIND, 64, 1>(ctx, pl, p);
+  if (pl->cps == 2) return launch_kind<KIND, 128, 2>(ctx, pl, p);
+  return launch_kind<KIND, 128, 1>(ctx, pl, p);
 }
 
 kp_status tc_plan_run(kp_ctx* ctx, TcGemmPlan* pl, const EpiParams* epi_override) {
@@ -711,14 +769,13 @@ kp_status tc_plan_run(kp_ctx* ctx, TcGemmPlan* pl, const EpiParams* epi_override
     p.epi = *epi_override;
     if (p.epi.ld_aux == 0) p.epi.ld_aux = p.epi.ldd;
   }
-  const bool wide = pl->bn == 256;
   kp_status st;
   if (pl->kind == TC_BF16)
-    st = wide ? launch_kind<TC_BF16, 256>(ctx, pl, p) : launch_kind<TC_BF16, 128>(ctx, pl, p);
+    st = launch_cfg<TC_BF16>(ctx, pl, p);
   else if (pl->kind == TC_F16)
-    st = wide ? launch_kind<TC_F16, 256>(ctx, pl, p) : launch_kind<TC_F16, 128>(ctx, pl, p);
+    st = launch_cfg<TC_F16>(ctx, pl, p);
   else
-    st = wide ? launch_kind<TC_E4M3, 256>(ctx, pl, p) : launch_kind<TC_E4M3, 128>(ctx, pl, p);
+    st = launch_cfg<TC_E4M3>(ctx, pl, p);
   KP_TRY(st);
   KP_CUDA(cudaGetLastError());
   return KP_OK;

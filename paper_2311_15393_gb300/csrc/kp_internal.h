@@ -38,6 +38,15 @@ void kp_set_error(const char* fmt, ...);
 // device status word bits (written by kernels, read by the host at sync points)
 enum : int { DEV_ERR_TIMEOUT = 1, DEV_ERR_NUMERIC = 2, DEV_ERR_BREAKDOWN = 4, DEV_ERR_BOUNDS = 8 };
 
+// Programmatic dependent launch.  Kernels of the iteration are launched with
+// programmatic stream serialization, so a kernel's launch and prologue
+// overlap the tail of the one before it.  Each such kernel executes
+// KP_PDL_WAIT() (wait until the preceding grid has completed and its writes
+// are visible) before it reads or writes anything another kernel touches,
+// and before any early return; KP_PDL_TRIGGER() lets the next grid launch.
+#define KP_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+#define KP_PDL_TRIGGER() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
+
 // bounded spin limit for device-side waits (each try_wait already suspends
 // for a hardware-defined interval, so this is a few seconds at most)
 constexpr long long KP_SPIN_LIMIT = 1LL << 24;
@@ -90,6 +99,10 @@ struct GemmDesc {
   GemmOp A, B;
   EpiParams epi;
   const int* flags = nullptr;  // when non-null and *flags != 0 the launch does nothing
+  // > 0: batched over terms instead of summed: output rows [k * batch_rows,
+  // (k + 1) * batch_rows) are the product with term k alone (M = nkron *
+  // batch_rows); the caller sums the per-term outputs
+  int batch_rows = 0;
 };
 
 // ---------------------------------------------------------------- context
@@ -118,7 +131,10 @@ struct kp_ctx {
   int check_every = 4;
   double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD
   int jacobi_max_sweeps = 40;
+  bool pdl = true;           // programmatic dependent launch in the iteration
   int splitk_override = 0;  // > 0: fixed split-K factor for the square GEMMs
+  int tc_bn_override = 0;   // 128 / 256: fixed tensor-core tile width
+  int tc_cps_override = 0;  // 1 / 2: fixed CTAs per SM for 128-wide tiles
 
   // device allocations: ctx_block lives with the context, allocs with the
   // problem; a new kp_setup returns the previous problem's blocks to `pool`,
@@ -184,6 +200,24 @@ struct kp_ctx {
   // prepared tensor-core GEMM plans
   std::vector<TcGemmPlan*> tc_plans;
 };
+
+// launch with programmatic stream serialization (when ctx->pdl); the kernel
+// must begin with KP_PDL_WAIT()
+template <typename... KArgs, typename... Args>
+inline cudaError_t kp_launch(const kp_ctx* ctx, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = ctx->pdl ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // allocation helper: registers the pointer with the context
 kp_status kp_alloc(kp_ctx* ctx, void** p, size_t bytes);

@@ -27,6 +27,7 @@
 namespace {
 struct OpsState {
   TcGemmPlan* G[2][4] = {{nullptr}};  // [mode][gemm]
+  bool batched = false;               // G2 / G4 write per-term outputs, summed by k_term_reduce
   TcGemmPlan* P[4] = {nullptr};
   float* inv_slot = nullptr;          // device scale for P4
   double* stat = nullptr;             // device [rr, amax] scratch
@@ -167,6 +168,73 @@ static GemmDesc pc_desc(kp_ctx* ctx, int which) {
   return g;
 }
 
+// Sum of the per-term outputs of a batched G2 / G4 with the fused epilogue of
+// the image-shaped product: out = alpha sum_k Z_k + beta aux, as FP32 or as
+// bf16 slices (hi, lo, ...).  Z holds `terms` blocks of nel FP32 values; the
+// terms are added in order.
+__global__ void k_term_reduce(const float* __restrict__ Z, int terms, long long nel, float alpha, float beta,
+                              const float* __restrict__ aux, int slices_mode, void* __restrict__ out, int slices,
+                              long long sstride, int vec, const int* flags) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
+  if (flags && *(volatile const int*)flags) return;
+  if (!vec) {  // out / aux not 16-byte aligned: one element at a time
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nel; i += (long long)gridDim.x * blockDim.x) {
+      float a = Z[i];
+      for (int k = 1; k < terms; ++k) a += Z[k * nel + i];
+      float v = alpha * a;
+      if (aux) v = fmaf(beta, aux[i], v);
+      if (!slices_mode) {
+        ((float*)out)[i] = v;
+      } else {
+        for (int sl = 0; sl < slices; ++sl) {
+          const __nv_bfloat16 h = __float2bfloat16_rn(v);
+          ((__nv_bfloat16*)out)[sl * sstride + i] = h;
+          v -= __bfloat162float(h);
+        }
+      }
+    }
+    return;
+  }
+  const long long n4 = nel >> 2;
+  const float4* Z4 = reinterpret_cast<const float4*>(Z);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    float4 a = Z4[i];
+    for (int k = 1; k < terms; ++k) {
+      const float4 t = Z4[k * n4 + i];
+      a.x += t.x;
+      a.y += t.y;
+      a.z += t.z;
+      a.w += t.w;
+    }
+    float v[4] = {alpha * a.x, alpha * a.y, alpha * a.z, alpha * a.w};
+    if (aux) {
+      const float4 t = reinterpret_cast<const float4*>(aux)[i];
+      v[0] = fmaf(beta, t.x, v[0]);
+      v[1] = fmaf(beta, t.y, v[1]);
+      v[2] = fmaf(beta, t.z, v[2]);
+      v[3] = fmaf(beta, t.w, v[3]);
+    }
+    if (!slices_mode) {
+      reinterpret_cast<float4*>(out)[i] = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      __nv_bfloat16* o = (__nv_bfloat16*)out + 4 * i;
+      for (int sl = 0; sl < slices; ++sl) {
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t*>(&h0);
+        pk.y = *reinterpret_cast<uint32_t*>(&h1);
+        *reinterpret_cast<uint2*>(o + sl * sstride) = pk;
+        v[0] -= __bfloat162float(h0.x);
+        v[1] -= __bfloat162float(h0.y);
+        v[2] -= __bfloat162float(h1.x);
+        v[3] -= __bfloat162float(h1.y);
+      }
+    }
+  }
+}
+
 kp_status ops_prepare(kp_ctx* ctx) {
   const int n_r = ctx->n_r, n_c = ctx->n_c, r = ctx->rank;
   const long long N = (long long)n_r * n_c;
@@ -208,11 +276,21 @@ kp_status ops_prepare(kp_ctx* ctx) {
   KP_TRY(kp_alloc(ctx, (void**)&ctx->w_split, sizeof(float) * ctx->w_split_elems));
 
   if (op_is_tc(ctx)) {
+    // G2 / G4 as one GEMM over the stacked per-term products (4x the tiles
+    // of the term sum, no K split) when the per-term outputs fit the split
+    // workspace; k_term_reduce adds them with the fused epilogue
+    os->batched = r >= 2 && n_c % 128 == 0 && n_r % 4 == 0 && (long long)r * N <= ctx->w_split_elems &&
+                  ctx->splitk_override == 0;
     for (int mode = 0; mode < 2; ++mode) {
       for (int w = 0; w < 4; ++w) {
         const void* bptr = w == 0 ? (mode == OP_INNER ? ctx->w_img2 : ctx->w_img3) : (w == 2 ? ctx->w_img : nullptr);
         GemmDesc g = op_desc(ctx, w, mode, bptr);
-        const int splits = (w == 1 || w == 3) ? square_splits(ctx) : 1;
+        int splits = (w == 1 || w == 3) ? square_splits(ctx) : 1;
+        if ((w == 1 || w == 3) && os->batched) {
+          g.batch_rows = n_c;
+          g.M = r * n_c;
+          splits = 1;
+        }
         KP_TRY(tc_plan_create(ctx, g, TC_BF16, splits, &os->G[mode][w]));
       }
     }
@@ -241,9 +319,24 @@ static kp_status simt_op(kp_ctx* ctx, int which, const void* bptr, EpiParams e, 
 
 static kp_status run_op(kp_ctx* ctx, int which, int mode, const void* bptr, const EpiParams& e, const int* flags) {
   if (op_is_tc(ctx)) {
-    TcGemmPlan* pl = ops(ctx)->G[mode][which];
+    OpsState* os = ops(ctx);
+    TcGemmPlan* pl = os->G[mode][which];
     tc_plan_set_runtime(pl, nullptr, flags);
-    return tc_plan_run(ctx, pl, &e);
+    if (!(os->batched && (which == 1 || which == 3))) return tc_plan_run(ctx, pl, &e);
+    // per-term FP32 outputs into the split workspace, then the term sum
+    EpiParams ez;
+    ez.mode = EPI_F32;
+    ez.out = ctx->w_split;
+    ez.ldd = ctx->n_r;
+    KP_TRY(tc_plan_run(ctx, pl, &ez));
+    const long long nel = (long long)ctx->n_r * ctx->n_c;
+    const int g = std::max(1, std::min((int)((nel / 4 + 255) / 256), ctx->sm_count * 8));
+    const int vec = ((((uintptr_t)e.out | (uintptr_t)e.aux) & 15) == 0 && (e.slice_stride % 4) == 0) ? 1 : 0;
+    KP_CUDA(kp_launch(ctx, k_term_reduce, dim3(g), dim3(256), 0, (const float*)ctx->w_split, ctx->rank, nel,
+                      (float)e.alpha, (float)e.beta, (const float*)e.aux, e.mode == EPI_SLICES ? 1 : 0, e.out,
+                      e.slices, e.slice_stride, vec, flags));
+    KP_LAUNCHED(ctx);
+    return KP_OK;
   }
   if (vec64(ctx)) return simt_op<double>(ctx, which, bptr, e, flags);
   return simt_op<float>(ctx, which, bptr, e, flags);

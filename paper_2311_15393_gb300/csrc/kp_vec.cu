@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_dot2(const T* __restrict__ a, c
                                                       const T* __restrict__ c, long long n, int vec4,
                                                       double* partials, unsigned int* counter, double* out,
                                                       const int* flags, PostOp po) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
   if (paused(flags)) return;
   double v[2] = {0.0, 0.0};
   const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
@@ -212,6 +214,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T*
                                                            const double* __restrict__ alpha_dev, double* partials,
                                                            unsigned int* counter, double* out, const int* flags,
                                                            PostOp po) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
   if (paused(flags)) return;
   double v[2] = {0.0, 0.0};
   const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
@@ -271,6 +275,8 @@ template <typename T>
 __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long n, int vec4,
                            const double* __restrict__ beta_dev, __nv_bfloat16* __restrict__ ps, int slices,
                            long long sstride, const int* flags) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
   if (paused(flags)) return;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
   if constexpr (std::is_same<T, float>::value) {
@@ -333,6 +339,8 @@ __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long
 template <typename T>
 __global__ void k_split(const T* __restrict__ x, long long n, __nv_bfloat16* __restrict__ out, int slices,
                         long long sstride) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     float v = (float)x[i];
     for (int s = 0; s < slices; ++s) {
@@ -356,6 +364,8 @@ template <typename T, typename N>
 __global__ void k_quantize(const T* __restrict__ r, long long n, int vec4, const double* __restrict__ stat,
                            double target, double lam2, N* __restrict__ out, float* __restrict__ inv_out,
                            const int* flags) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
   if (paused(flags)) return;
   __shared__ float s_sh;
   if (threadIdx.x == 0) {
@@ -384,6 +394,8 @@ __global__ void k_quantize(const T* __restrict__ r, long long n, int vec4, const
 template <typename T>
 __global__ void __launch_bounds__(VEC_THREADS) k_norm_amax(const T* __restrict__ x, long long n, double* partials,
                                                            unsigned int* counter, double* out) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
   double v[2] = {0.0, 0.0};
   const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
   if constexpr (std::is_same<T, float>::value) {
@@ -440,12 +452,12 @@ kp_status dot2_dev(kp_ctx* ctx, const void* a, const void* b, const void* c, lon
                    const int* flags, PostOp post) {
   int g = vec_grid(ctx, n);
   if (f64)
-    k_dot2<double><<<g, VEC_THREADS, 0, ctx->stream>>>((const double*)a, (const double*)b, (const double*)c, n, 0,
-                                                       ctx->red_part, ctx->red_count, out, flags, post);
+    KP_CUDA(kp_launch(ctx, k_dot2<double>, dim3(g), dim3(VEC_THREADS), 0, (const double*)a, (const double*)b, (const double*)c, n, 0,
+                                                       ctx->red_part, ctx->red_count, out, flags, post));
   else
-    k_dot2<float><<<g, VEC_THREADS, 0, ctx->stream>>>((const float*)a, (const float*)b, (const float*)c, n,
+    KP_CUDA(kp_launch(ctx, k_dot2<float>, dim3(g), dim3(VEC_THREADS), 0, (const float*)a, (const float*)b, (const float*)c, n,
                                                       aligned16(a, b, c), ctx->red_part, ctx->red_count, out, flags,
-                                                      post);
+                                                      post));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -458,9 +470,9 @@ kp_status dot_dev(kp_ctx* ctx, const void* x, const void* y, long long n, bool f
 kp_status norm_amax_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out2) {
   int g = vec_grid(ctx, n);
   if (f64)
-    k_norm_amax<double><<<g, VEC_THREADS, 0, ctx->stream>>>((const double*)x, n, ctx->red_part, ctx->red_count, out2);
+    KP_CUDA(kp_launch(ctx, k_norm_amax<double>, dim3(g), dim3(VEC_THREADS), 0, (const double*)x, n, ctx->red_part, ctx->red_count, out2));
   else
-    k_norm_amax<float><<<g, VEC_THREADS, 0, ctx->stream>>>((const float*)x, n, ctx->red_part, ctx->red_count, out2);
+    KP_CUDA(kp_launch(ctx, k_norm_amax<float>, dim3(g), dim3(VEC_THREADS), 0, (const float*)x, n, ctx->red_part, ctx->red_count, out2));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -474,14 +486,14 @@ kp_status update_xr_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* 
                         bool f64, const double* alpha_dev, double* out2, const int* flags, PostOp post) {
   int g = vec_grid(ctx, n);
   if (f64)
-    k_update_xr<double><<<g, VEC_THREADS, 0, ctx->stream>>>((double*)x, (double*)r, (double*)r_old, (const double*)p,
+    KP_CUDA(kp_launch(ctx, k_update_xr<double>, dim3(g), dim3(VEC_THREADS), 0, (double*)x, (double*)r, (double*)r_old, (const double*)p,
                                                             (const double*)q, n, 0, alpha_dev, ctx->red_part,
-                                                            ctx->red_count, out2, flags, post);
+                                                            ctx->red_count, out2, flags, post));
   else
-    k_update_xr<float><<<g, VEC_THREADS, 0, ctx->stream>>>((float*)x, (float*)r, (float*)r_old, (const float*)p,
+    KP_CUDA(kp_launch(ctx, k_update_xr<float>, dim3(g), dim3(VEC_THREADS), 0, (float*)x, (float*)r, (float*)r_old, (const float*)p,
                                                            (const float*)q, n, aligned16(x, r, r_old, p, q),
                                                            alpha_dev, ctx->red_part, ctx->red_count, out2, flags,
-                                                           post);
+                                                           post));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -491,12 +503,12 @@ kp_status p_update_dev(kp_ctx* ctx, void* p, const void* z, long long n, bool f6
                        __nv_bfloat16* ps, int slices, long long sstride, const int* flags) {
   int g = vec_grid(ctx, n);
   if (f64)
-    k_p_update<double><<<g, VEC_THREADS, 0, ctx->stream>>>((double*)p, (const double*)z, n, 0, beta_dev, ps, slices,
-                                                           sstride, flags);
+    KP_CUDA(kp_launch(ctx, k_p_update<double>, dim3(g), dim3(VEC_THREADS), 0, (double*)p, (const double*)z, n, 0, beta_dev, ps, slices,
+                                                           sstride, flags));
   else
-    k_p_update<float><<<g, VEC_THREADS, 0, ctx->stream>>>(
+    KP_CUDA(kp_launch(ctx, k_p_update<float>, dim3(g), dim3(VEC_THREADS), 0, 
         (float*)p, (const float*)z, n, aligned16(p, z) && (((uintptr_t)ps & 7) == 0) && (sstride % 4 == 0), beta_dev,
-        ps, slices, sstride, flags);
+        ps, slices, sstride, flags));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -505,9 +517,9 @@ kp_status p_update_dev(kp_ctx* ctx, void* p, const void* z, long long n, bool f6
 kp_status split_bf16(kp_ctx* ctx, const void* x, bool f64, long long n, void* out, int slices, long long sstride) {
   int g = vec_grid(ctx, n);
   if (f64)
-    k_split<double><<<g, VEC_THREADS, 0, ctx->stream>>>((const double*)x, n, (__nv_bfloat16*)out, slices, sstride);
+    KP_CUDA(kp_launch(ctx, k_split<double>, dim3(g), dim3(VEC_THREADS), 0, (const double*)x, n, (__nv_bfloat16*)out, slices, sstride));
   else
-    k_split<float><<<g, VEC_THREADS, 0, ctx->stream>>>((const float*)x, n, (__nv_bfloat16*)out, slices, sstride);
+    KP_CUDA(kp_launch(ctx, k_split<float>, dim3(g), dim3(VEC_THREADS), 0, (const float*)x, n, (__nv_bfloat16*)out, slices, sstride));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -524,14 +536,14 @@ kp_status quantize_dev(kp_ctx* ctx, const void* r, long long n, bool f64, const 
   const float* rf = (const float*)r;
   const int v4 = aligned16(r);
   if (narrow == NT_BF16)
-    k_quantize<float, __nv_bfloat16><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, v4, stat, target, lam2,
-                                                                          (__nv_bfloat16*)out, inv_out, flags);
+    KP_CUDA(kp_launch(ctx, k_quantize<float, __nv_bfloat16>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2,
+                                                                          (__nv_bfloat16*)out, inv_out, flags));
   else if (narrow == NT_F16)
-    k_quantize<float, __half><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, v4, stat, target, lam2, (__half*)out,
-                                                                   inv_out, flags);
+    KP_CUDA(kp_launch(ctx, k_quantize<float, __half>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2, (__half*)out,
+                                                                   inv_out, flags));
   else
-    k_quantize<float, __nv_fp8_e4m3><<<g, VEC_THREADS, 0, ctx->stream>>>(rf, n, v4, stat, target, lam2,
-                                                                          (__nv_fp8_e4m3*)out, inv_out, flags);
+    KP_CUDA(kp_launch(ctx, k_quantize<float, __nv_fp8_e4m3>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2,
+                                                                          (__nv_fp8_e4m3*)out, inv_out, flags));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;

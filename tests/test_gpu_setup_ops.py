@@ -46,6 +46,37 @@ def test_setup_fp64_matches_oracle(kpsvd, case):
         np.testing.assert_allclose(svd["Ur"] @ np.diag(svd["sr"]) @ svd["Vr"].T, A1, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("case", CASES[1:], ids=lambda c: f"{c[0]}-{c[2]}-{c[3]}-r{c[4]}")
+def test_setup_fp32_products_match_oracle(kpsvd, case):
+    """FP32 vectors: the O(n^3) products of the setup run in FP32 (rotations in
+    FP64); the KP-SVD then agrees with the oracle to FP32 level, and with the
+    all-FP64 setup ("setup_fp64" option) likewise."""
+    name, n, shape, bc, rank = case
+    pr = OracleProblem(name, n=n, shape=shape, bc=bc, rank=rank)
+    out = {}
+    for fp64 in (0, 1):
+        ctx = kpsvd.KpContext(0)
+        ctx.kp_set_option("setup_fp64", fp64)
+        P = pr.P
+        ctx.kp_setup(kpsvd.to_device(P.psf), P.n_r, P.n_c, P.center, P.bc, P.op_rank, "f32", "f32", "f32")
+        out[fp64] = (ctx.kp_get_kpsvd(), ctx.kp_get_spectrum())
+        ctx.close()
+    svd, Sg = out[0]
+    u32 = 2.0 ** -23
+    n_max = max(pr.P.n_r, pr.P.n_c)
+    np.testing.assert_allclose(svd["sr"], pr.kp.sr, rtol=0, atol=8 * n_max * u32 * pr.kp.sr[0])
+    np.testing.assert_allclose(svd["sc"], pr.kp.sc, rtol=0, atol=8 * n_max * u32 * pr.kp.sc[0])
+    smax = np.abs(pr.kp.Sigma).max()
+    np.testing.assert_allclose(Sg, pr.kp.Sigma, rtol=0, atol=8 * n_max * u32 * smax)
+    np.testing.assert_allclose(Sg, out[1][1], rtol=0, atol=8 * n_max * u32 * smax)
+    for side in ("r", "c"):
+        A1 = pr.op.Ar[0] if side == "r" else pr.op.Ac[0]
+        U, S, V = svd["U" + side], svd["s" + side], svd["V" + side]
+        np.testing.assert_allclose(U @ np.diag(S) @ V.T, A1, rtol=0, atol=8 * n_max * u32 * S[0])
+        np.testing.assert_allclose(U.T @ U, np.eye(U.shape[0]), rtol=0, atol=1e-4)
+        np.testing.assert_allclose(V.T @ V, np.eye(V.shape[0]), rtol=0, atol=1e-4)
+
+
 @pytest.mark.parametrize("vec", ["f64", "f32"])
 @pytest.mark.parametrize("case", CASES[1:3], ids=lambda c: f"{c[2]}-{c[3]}")
 def test_apply_A_and_K(kpsvd, case, vec):
