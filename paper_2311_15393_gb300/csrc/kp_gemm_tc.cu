@@ -181,7 +181,7 @@ __device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d
 // All indexing is at compile time (the values stay in registers); full
 // segments use 16-byte vector accesses, ragged ones predicated scalars.
 __device__ __forceinline__ void epi_store32(const EpiParams& e, float scale_dev, int gm, int gn0, int N,
-                                            float (&v)[32]) {
+                                            float (&v)[32], float& tmax) {
   const int cnt = min(32, N - gn0);
   if (cnt <= 0) return;
   const long long base = (long long)gm * e.ldd + gn0;
@@ -208,7 +208,7 @@ __device__ __forceinline__ void epi_store32(const EpiParams& e, float scale_dev,
         if (c < cnt) v[c] = fmaf(bt, aux[abase + c], v[c]);
     }
   }
-  if (e.mode == EPI_NARROW && e.sigma32) {
+  if ((e.mode == EPI_NARROW || e.mode == EPI_F32) && e.sigma32) {
     // S' = lam^2 / (sigma^2 + lam^2) in FP32 (it scales a value about to be
     // rounded to 16 or 8 bits; FP64 arithmetic is slow on this part)
     const float l2 = (float)e.lam2;
@@ -232,6 +232,11 @@ __device__ __forceinline__ void epi_store32(const EpiParams& e, float scale_dev,
     }
   }
   if (e.mode == EPI_F32) {
+    if (e.amax_bits) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < cnt) tmax = fmaxf(tmax, fabsf(v[c]));
+    }
     float* out = (float*)e.out + base;
     if (vec) {
 #pragma unroll
@@ -488,6 +493,7 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
       tc_fence_after();
       const int gm = w.m0 + row;
       const bool row_ok = gm < p.M;
+      float tmax = 0.f;
       if (p.splits == 1) {
 #pragma unroll 1
         for (int chunk = 0; chunk < BN / 32; ++chunk) {
@@ -499,10 +505,15 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
             for (int c = 0; c < 32; ++c) acc[c] = 0.f;
           }
           const int gn0 = w.n0 + chunk * 32;
-          if (row_ok && gn0 < p.N) epi_store32(p.epi, sdev, gm, gn0, p.N, acc);
+          if (row_ok && gn0 < p.N) epi_store32(p.epi, sdev, gm, gn0, p.N, acc, tmax);
         }
         tc_fence_before();
         mbar_arrive(smem_u32(&tempty[buf]));
+        if (p.epi.amax_bits) {  // one atomic per warp and unit
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+          if (lane == 0 && tmax > 0.f) atomicMax(p.epi.amax_bits, __float_as_uint(tmax));
+        }
       } else {
         // split-K: FP32 partial, then the last split to arrive finishes the tile
 #pragma unroll 1
@@ -540,8 +551,13 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
 #pragma unroll
               for (int c = 0; c < 32; ++c) acc[c] = 0.f;
               for (int s = 0; s < p.splits; ++s) partial_add32(p.ws + ((long long)s * p.M + gm) * p.N + gn0, cnt, acc);
-              epi_store32(p.epi, sdev, gm, gn0, p.N, acc);
+              epi_store32(p.epi, sdev, gm, gn0, p.N, acc, tmax);
             }
+          }
+          if (p.epi.amax_bits) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+            if (lane == 0 && tmax > 0.f) atomicMax(p.epi.amax_bits, __float_as_uint(tmax));
           }
         }
         epi_bar();  // s_last is reused by the next unit

@@ -88,6 +88,7 @@ struct EpiParams {
   const double* sigma64 = nullptr;
   double lam2 = 0.0;
   int narrow = NT_BF16;
+  unsigned int* amax_bits = nullptr;  // EPI_F32: atomicMax of max |out| (bits of a non-negative float)
 };
 
 struct GemmDesc {

@@ -30,6 +30,8 @@ struct OpsState {
   bool batched = false;               // G2 / G4 write per-term outputs, summed by k_term_reduce
   TcGemmPlan* P[4] = {nullptr};
   float* inv_slot = nullptr;          // device scale for P4
+  float* e4m3_slots = nullptr;        // E4M3: [0] 1/(lam^2 s_R s_V^2), [1..3] stage scales g
+  unsigned int* amax8 = nullptr;      // E4M3: per-stage max |T| of the FP32 GEMM outputs
   double* stat = nullptr;             // device [rr, amax] scratch
 };
 }  // namespace
@@ -243,6 +245,9 @@ kp_status ops_prepare(kp_ctx* ctx) {
   OpsState* os = new OpsState();
   ctx->ops_state = os;
   KP_TRY(kp_alloc(ctx, (void**)&os->inv_slot, 16));
+  KP_TRY(kp_alloc(ctx, (void**)&os->e4m3_slots, 16));
+  KP_TRY(kp_alloc(ctx, (void**)&os->amax8, 16));
+  KP_CUDA(cudaMemsetAsync(os->amax8, 0, 16, ctx->stream));
   KP_TRY(kp_alloc(ctx, (void**)&os->stat, 4 * sizeof(double)));
   // solver vectors and scratch images
   for (int i = 0; i < 8; ++i) KP_TRY(kp_alloc(ctx, &ctx->vbuf[i], vs * N));
@@ -299,7 +304,7 @@ kp_status ops_prepare(kp_ctx* ctx) {
     const int kind = ctx->pc_prec == KP_BF16 ? TC_BF16 : (ctx->pc_prec == KP_F16 ? TC_F16 : TC_E4M3);
     for (int w = 0; w < 4; ++w) {
       GemmDesc g = pc_desc(ctx, w);
-      KP_TRY(tc_plan_create(ctx, g, kind, square_splits(ctx), &os->P[w]));
+      KP_TRY(tc_plan_create(ctx, g, kind, kind == TC_E4M3 ? 1 : square_splits(ctx), &os->P[w]));
     }
   }
   return KP_OK;
@@ -473,9 +478,38 @@ kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const doubl
     stat = os->stat;
   }
   const int nt = ctx->pc_prec == KP_BF16 ? NT_BF16 : (ctx->pc_prec == KP_F16 ? NT_F16 : NT_E4M3);
-  // E4M3 factors carry power-of-two scales; undo them in the last GEMM
-  const double fscale = (double)ctx->pc_vscale_c * ctx->pc_vscale_r;
-  KP_TRY(quantize_dev(ctx, r, N, false, stat, nt, lam2 * fscale * fscale, ctx->pc_in, os->inv_slot, flags));
+  if (nt == NT_E4M3) {
+    // FP8: E4M3 holds only [2^-9, 448], so every stage is rescaled: the GEMMs
+    // write FP32 with their max |.| (fused in the epilogue), k_quant8 scales
+    // by a power of two g into [224, 448) and rounds; the factors' scales
+    // s_V, the residual's s_R and the g's are undone in the last GEMM
+    const double fscale = (double)ctx->pc_vscale_c * ctx->pc_vscale_r;
+    KP_TRY(quantize_dev(ctx, r, N, false, stat, nt, lam2 * fscale * fscale, ctx->pc_in, os->e4m3_slots, flags,
+                        os->amax8, 3));
+    for (int w = 0; w < 3; ++w) {
+      EpiParams e;
+      e.mode = EPI_F32;
+      e.out = ctx->pc_f32;
+      e.ldd = w == 0 || w == 2 ? ctx->n_c : ctx->n_r;
+      e.amax_bits = os->amax8 + w;
+      if (w == 1) {
+        e.sigma32 = ctx->Sigma32;
+        e.lam2 = lam2;
+      }
+      tc_plan_set_runtime(os->P[w], nullptr, flags);
+      KP_TRY(tc_plan_run(ctx, os->P[w], &e));
+      void* dst = w == 0 ? ctx->pc_t1 : (w == 1 ? ctx->pc_t2 : ctx->pc_t3);
+      KP_TRY(quant8_dev(ctx, ctx->pc_f32, N, os->amax8 + w, os->e4m3_slots + 1, w, os->e4m3_slots, os->inv_slot, dst,
+                        flags));
+    }
+    EpiParams e;
+    e.mode = EPI_F32;
+    e.out = z;
+    e.ldd = ctx->n_r;
+    tc_plan_set_runtime(os->P[3], os->inv_slot, flags);
+    return tc_plan_run(ctx, os->P[3], &e);
+  }
+  KP_TRY(quantize_dev(ctx, r, N, false, stat, nt, lam2, ctx->pc_in, os->inv_slot, flags));
   for (int w = 0; w < 4; ++w) {
     EpiParams e;
     e.ldd = w == 0 || w == 2 ? ctx->n_c : ctx->n_r;

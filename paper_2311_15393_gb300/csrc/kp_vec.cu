@@ -363,14 +363,17 @@ __device__ __forceinline__ float pow2_scale(double amax, double target) {
 template <typename T, typename N>
 __global__ void k_quantize(const T* __restrict__ r, long long n, int vec4, const double* __restrict__ stat,
                            double target, double lam2, N* __restrict__ out, float* __restrict__ inv_out,
-                           const int* flags) {
+                           unsigned int* __restrict__ reset, int nreset, const int* flags) {
   KP_PDL_WAIT();
   KP_PDL_TRIGGER();
   if (paused(flags)) return;
   __shared__ float s_sh;
   if (threadIdx.x == 0) {
     s_sh = pow2_scale(stat[1], target);
-    if (blockIdx.x == 0) *inv_out = (float)(1.0 / (lam2 * (double)s_sh));
+    if (blockIdx.x == 0) {
+      *inv_out = (float)(1.0 / (lam2 * (double)s_sh));
+      for (int i = 0; i < nreset; ++i) reset[i] = 0u;  // per-stage amax slots of this apply
+    }
   }
   __syncthreads();
   const float s = s_sh;
@@ -388,6 +391,42 @@ __global__ void k_quantize(const T* __restrict__ r, long long n, int vec4, const
     i0 = 4 * n4 + tid;
   }
   for (long long i = i0; i < n; i += stride) out[i] = to_narrow<N>((float)r[i] * s);
+}
+
+// One stage of the E4M3 preconditioner solve: the stage's FP32 GEMM output
+// (max |.| accumulated by the GEMM epilogue into *amax_bits) is scaled by a
+// power of two g putting its maximum into [224, 448) and rounded to E4M3;
+// g is kept in gs[stage].  The last stage also writes the scale of the final
+// product, inv_out = base / (g_0 g_1 g_2).
+__global__ void k_quant8(const float* __restrict__ in, long long n, int vec4, const unsigned int* __restrict__ amax_bits,
+                         float* __restrict__ gs, int stage, const float* __restrict__ base, float* __restrict__ inv_out,
+                         __nv_fp8_e4m3* __restrict__ out, const int* flags) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
+  if (paused(flags)) return;
+  __shared__ float g_sh;
+  if (threadIdx.x == 0) {
+    const float am = __uint_as_float(*amax_bits);
+    g_sh = pow2_scale((double)am, 448.0);
+    if (blockIdx.x == 0) {
+      gs[stage] = g_sh;
+      if (stage == 2) *inv_out = *base / (gs[0] * gs[1] * g_sh);
+    }
+  }
+  __syncthreads();
+  const float g = g_sh;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  long long i0 = tid;
+  if (vec4) {
+    const long long n4 = n >> 2;
+    for (long long i = tid; i < n4; i += stride) {
+      const float4 v = ld4(in, i);
+      const __nv_fp8x4_e4m3 q(make_float4(v.x * g, v.y * g, v.z * g, v.w * g));
+      reinterpret_cast<__nv_fp8x4_e4m3*>(out)[i] = q;
+    }
+    i0 = 4 * n4 + tid;
+  }
+  for (long long i = i0; i < n; i += stride) out[i] = __nv_fp8_e4m3(in[i] * g);
 }
 
 // amax only (for one-off applies outside the loop)
@@ -525,8 +564,18 @@ kp_status split_bf16(kp_ctx* ctx, const void* x, bool f64, long long n, void* ou
   return KP_OK;
 }
 
+kp_status quant8_dev(kp_ctx* ctx, const float* in, long long n, const unsigned int* amax_bits, float* gs, int stage,
+                     const float* base, float* inv_out, void* out, const int* flags) {
+  int g = vec_grid(ctx, n);
+  const int v4 = aligned16(in) && (((uintptr_t)out & 3) == 0);
+  KP_CUDA(kp_launch(ctx, k_quant8, dim3(g), dim3(VEC_THREADS), 0, in, n, v4, amax_bits, gs, stage, base, inv_out,
+                    (__nv_fp8_e4m3*)out, flags));
+  KP_LAUNCHED(ctx);
+  return KP_OK;
+}
+
 kp_status quantize_dev(kp_ctx* ctx, const void* r, long long n, bool f64, const double* stat, int narrow,
-                       double lam2, void* out, float* inv_out, const int* flags) {
+                       double lam2, void* out, float* inv_out, const int* flags, unsigned int* reset, int nreset) {
   int g = vec_grid(ctx, n);
   double target = narrow == NT_E4M3 ? 448.0 : 1.0;
   if (f64) {
@@ -537,13 +586,13 @@ kp_status quantize_dev(kp_ctx* ctx, const void* r, long long n, bool f64, const 
   const int v4 = aligned16(r);
   if (narrow == NT_BF16)
     KP_CUDA(kp_launch(ctx, k_quantize<float, __nv_bfloat16>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2,
-                                                                          (__nv_bfloat16*)out, inv_out, flags));
+                                                                          (__nv_bfloat16*)out, inv_out, reset, nreset, flags));
   else if (narrow == NT_F16)
     KP_CUDA(kp_launch(ctx, k_quantize<float, __half>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2, (__half*)out,
-                                                                   inv_out, flags));
+                                                                   inv_out, reset, nreset, flags));
   else
     KP_CUDA(kp_launch(ctx, k_quantize<float, __nv_fp8_e4m3>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2,
-                                                                          (__nv_fp8_e4m3*)out, inv_out, flags));
+                                                                          (__nv_fp8_e4m3*)out, inv_out, reset, nreset, flags));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;

@@ -43,7 +43,10 @@ kp_status update_xr_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* 
 kp_status p_update_dev(kp_ctx* ctx, void* p, const void* z, long long n, bool f64, const double* beta_dev,
                        __nv_bfloat16* ps, int slices, long long sstride, const int* flags);
 kp_status quantize_dev(kp_ctx* ctx, const void* r, long long n, bool f64, const double* stat, int narrow,
-                       double lam2, void* out, float* inv_out, const int* flags);
+                       double lam2, void* out, float* inv_out, const int* flags, unsigned int* reset = nullptr,
+                       int nreset = 0);
+kp_status quant8_dev(kp_ctx* ctx, const float* in, long long n, const unsigned int* amax_bits, float* gs, int stage,
+                     const float* base, float* inv_out, void* out, const int* flags);
 kp_status axpby_dev(kp_ctx* ctx, const void* x, void* y, long long n, bool f64, double alpha, double beta);
 kp_status convert_f64_to_f32(kp_ctx* ctx, const double* x, float* y, long long n);
 kp_status convert_f32_to_f64(kp_ctx* ctx, const float* x, double* y, long long n);

@@ -81,12 +81,52 @@ def emulate_apply_A_bf16(op, X):
     return lp.to_fp32(sum(Wk @ bf(Ar).T for Wk, Ar in zip(W, op.Ar)))
 
 
+def pow2_scale(amax, target):
+    """2^e with amax * 2^e in [target / 2, target) (1 when amax is 0)."""
+    if not amax > 0:
+        return 1.0
+    m, e = np.frexp(target / amax)
+    return float(np.ldexp(1.0, e - 1))
+
+
+def emulate_minv_e4m3(kp, Sigma, R, lam):
+    """E4M3 preconditioner solve with the GPU's rounding points: per-factor
+    power-of-two scales (max |V| s_V in [224, 448)), R scaled the same way,
+    every GEMM accumulated exactly then rounded to fp32, each of the first
+    three outputs rescaled by a power of two from its own max |.| and rounded
+    to e4m3; the scales are undone at the end (in fp32)."""
+    f32, q = lp.to_fp32, lp.to_e4m3
+    sc, sr = pow2_scale(np.abs(kp.Vc).max(), 448.0), pow2_scale(np.abs(kp.Vr).max(), 448.0)
+    Vc, Vr = q(f32(kp.Vc * sc)), q(f32(kp.Vr * sr))
+    R32 = f32(R)
+    s_R = pow2_scale(np.abs(R32).max(), 448.0)
+    Rq = q(f32(R32 * s_R))
+    base = f32(1.0 / (lam * lam * (sc * sr) ** 2 * s_R))
+    S32 = f32(Sigma)
+    l2 = f32(lam * lam)
+    fac = f32(l2 / f32(S32 * S32 + l2))
+    g = []
+    T1 = f32(Vc.T @ Rq)
+    g.append(pow2_scale(np.abs(T1).max(), 448.0))
+    T1q = q(f32(T1 * g[0]))
+    W = f32(f32(T1q @ Vr) * fac)
+    g.append(pow2_scale(np.abs(W).max(), 448.0))
+    Wq = q(f32(W * g[1]))
+    T3 = f32(Vc @ Wq)
+    g.append(pow2_scale(np.abs(T3).max(), 448.0))
+    T3q = q(f32(T3 * g[2]))
+    inv = f32(base / f32(f32(g[0] * g[1]) * g[2]))
+    return f32(f32(T3q @ Vr.T) * inv)
+
+
 def emulate_minv(kp, Sigma, R, lam, fmt):
     """Reduced-precision preconditioner solve with the GPU's rounding points:
     R scaled by 2^e (amax(R) 2^e in [1/2, 1)) and rounded (bf16 factors as
     hi + lo pairs); each GEMM output
     rounded to fp32 then to the narrow format; S applied as
     lam^2 / (Sigma^2 + lam^2) (FP32) in the P2 output; 1 / (lam^2 2^e) at the end."""
+    if fmt == "e4m3":
+        return emulate_minv_e4m3(kp, Sigma, R, lam)
     rd = lp.ROUND[fmt]
     am = np.max(np.abs(lp.to_fp32(R)))
     m, e = np.frexp(1.0 / am)

@@ -148,7 +148,7 @@ def test_tensor_core_accurate_operator(kpsvd, n):
         assert rel(kpsvd.from_device(b, n, n), pr.B) < 2e-6
 
 
-@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+@pytest.mark.parametrize("fmt", ["f16", "bf16", "e4m3"])
 @pytest.mark.parametrize("n", [64, 256])
 def test_tensor_core_preconditioner_vs_emulation(kpsvd, fmt, n):
     """Reduced-precision KP-SVD solve equals its emulation (same rounded
@@ -168,7 +168,7 @@ def test_tensor_core_preconditioner_vs_emulation(kpsvd, fmt, n):
         Z = kpsvd.from_device(z, n, n)
         # the only differences are FP32 accumulation order flipping a rounding
         # at the same points: bounded by half a unit of the narrow format
-        u = 2.0 ** -11 if fmt == "f16" else 2.0 ** -8
+        u = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8, "e4m3": 2.0 ** -4}[fmt]
         assert rel(Z, emulate_minv(pr.kp, pr.kp.Sigma, R, lam, fmt)) < 0.5 * u
 
 
@@ -188,3 +188,24 @@ def test_tensor_core_preconditioner_vs_fp64(kpsvd, fmt, n):
         Z = kpsvd.from_device(z, n, n)
         Z64 = okp.precond_apply(pr.kp, okp.precond_scale(pr.kp.Sigma, lam), R)
         assert rel(Z, Z64) < 5e-3
+
+
+@pytest.mark.parametrize("n", [64, 256])
+def test_e4m3_preconditioner_vs_fp64(kpsvd, n):
+    """FP8 (E4M3) single apply against FP64.  The four GEMMs round eight
+    operands (R, T1, W, T3 and the two factors twice) to E4M3, unit roundoff
+    u = 2^-4; eight independent roundings give a relative error of about
+    sqrt(8) u / sqrt(3) ~ 0.1 (the FP64 emulation of the same rounding points
+    gives 0.073 here), above the 3e-2 a single FP8 rounding would allow."""
+    pr = OracleProblem("deblur256_fp32", n=n, rank=3)
+    lam = 0.02
+    with setup_ctx(kpsvd, pr, "f32", "e4m3", "f32") as ctx:
+        R = synth.random_matrix(n, n, 5)
+        r = kpsvd.to_device(R, torch.float32)
+        z = torch.empty_like(r)
+        ctx.kp_apply_Minv(r, z, lam)
+        Z = kpsvd.from_device(z, n, n)
+        Z64 = okp.precond_apply(pr.kp, okp.precond_scale(pr.kp.Sigma, lam), R)
+        err = rel(Z, Z64)
+        assert err < np.sqrt(8.0) * 2.0 ** -4 / np.sqrt(3.0)
+        assert abs(err - rel(emulate_minv(pr.kp, pr.kp.Sigma, R, lam, "e4m3"), Z64)) < 0.01

@@ -115,6 +115,24 @@ def test_reduced_precision_fpcg_reaches_oracle_solution(kpsvd, op, pc):
         assert info.iters <= io.iters + 3
 
 
+def test_e4m3_fpcg_reaches_oracle_solution(kpsvd):
+    """256 x 256: FPCG with the FP8 (E4M3) preconditioner, whose every apply
+    is ~7% off the FP64 one, still reaches the oracle's x_lambda to 1e-4
+    (flexible PCG treats the inexact preconditioner as variable); it needs
+    more iterations than FP16."""
+    pr = OracleProblem("deblur256_fp32")
+    lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
+    tol = 1e-7
+    x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam)
+    _, io = opcg.tik_pcg(pr.op, pr.kp, pr.B, lam, tol, 500, True)
+    with setup_ctx(kpsvd, pr, "bf16", "e4m3", "f32") as ctx:
+        x, info = run(kpsvd, ctx, pr, lam, tol, 500, True, "f32")
+        print(f"e4m3 FPCG iterations {info.iters} (oracle FP64 {io.iters})")
+        assert info.status == kpsvd.KP_OK
+        assert rel(x, x_star) < 1e-4
+        assert info.iters <= 3 * io.iters
+
+
 def test_edge_cases(kpsvd):
     pr = OracleProblem("deblur256_fp32", n=64, rank=2)
     with setup_ctx(kpsvd, pr, "f64", "f64", "f64") as ctx:
