@@ -98,6 +98,7 @@ void kp_free_all(kp_ctx* ctx) {
   ctx->allocs.clear();
   tc_plans_free(ctx);
   ctx->lam_ws = nullptr;
+  ctx->lam_sigma_ready = false;
   ctx->Uc32 = ctx->Ur32 = ctx->Vc32 = ctx->Vr32 = nullptr;
   ctx->ready = false;
 }

@@ -186,6 +186,8 @@ struct kp_ctx {
   void* w_img3 = nullptr;    // x slices (accurate operator input)
   double* hist = nullptr;    // residual history (device)
   void* lam_ws = nullptr;    // choose_lambda scratch (allocated at its first call)
+  bool lam_sigma_ready = false;  // spectrum-only part of lam_ws filled (once per setup)
+  double lam_sigma_ext[2] = {0.0, 0.0};  // max |Sigma|, min |Sigma| > 0
   int hist_cap = 0;
   float* w_split = nullptr;  // split-K partials
   long long w_split_elems = 0;

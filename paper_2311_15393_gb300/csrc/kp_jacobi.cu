@@ -188,21 +188,43 @@ __global__ void k_gather(const double* __restrict__ W, const double* __restrict_
 }
 
 // orthogonal transform that nearly diagonalises the blur factors:
-// DCT-II (reflexive BC) or DST-I (zero BC), column-major n x n
-__global__ void k_transform(int n, int kind, double* __restrict__ C) {
-  long long tot = (long long)n * n;
+// DCT-II (reflexive BC) or DST-I (zero BC), column-major n x n.  The entries
+// are scale * trig(pi q / P) for an integer q reduced mod 2P, so one table of
+// 2P values (k_trig_table) serves all n^2 entries.
+//   DCT-II: C[j][k] = sqrt(2/n) cos(pi (2j+1) k / (2n)) (k = 0 row x 1/sqrt 2), P = 2n
+//   DST-I:  C[j][k] = sqrt(2/(n+1)) sin(pi (j+1)(k+1) / (n+1)),                 P = n+1
+__global__ void k_trig_table(int P, int kind, double* __restrict__ tab) {
   const double pi = 3.141592653589793238462643;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * P; q += gridDim.x * blockDim.x)
+    tab[q] = kind == 0 ? cos(pi * q / P) : sin(pi * q / P);
+}
+__global__ void k_transform(int n, int kind, const double* __restrict__ tab, double scale, double* __restrict__ C) {
+  const long long tot = (long long)n * n;
+  const long long P2 = kind == 0 ? 4LL * n : 2LL * (n + 1);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(t % n), k = (int)(t / n);
-    double v;
+    const long long j = t % n, k = t / n;
     if (kind == 0) {
-      v = sqrt(2.0 / n) * cos(pi * (2.0 * j + 1.0) * k / (2.0 * n));
-      if (k == 0) v *= 0.70710678118654752440;
+      const double v = scale * tab[((2 * j + 1) * k) % P2];
+      C[t] = k == 0 ? v * 0.70710678118654752440 : v;
     } else {
-      v = sqrt(2.0 / (n + 1.0)) * sin(pi * (j + 1.0) * (k + 1.0) / (n + 1.0));
+      C[t] = scale * tab[((j + 1) * (k + 1)) % P2];
     }
-    C[t] = v;
   }
+}
+
+// fill C (n x n) with the transform: table, then the gather
+static kp_status make_transform(kp_ctx* ctx, int n, int kind, double* C) {
+  const int P = kind == 0 ? 2 * n : n + 1;
+  double* tab = nullptr;
+  KP_TRY(kp_alloc(ctx, (void**)&tab, sizeof(double) * 2 * (size_t)P));
+  k_trig_table<<<(2 * P + 255) / 256, 256, 0, ctx->stream>>>(P, kind, tab);
+  const long long nn = (long long)n * n;
+  const int g = std::max(1, std::min((int)((nn + 255) / 256), ctx->sm_count * 16));
+  const double scale = kind == 0 ? std::sqrt(2.0 / n) : std::sqrt(2.0 / (n + 1.0));
+  k_transform<<<g, 256, 0, ctx->stream>>>(n, kind, tab, scale, C);
+  ctx->launches += 2;
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
 }
 
 // B (n x m col-major) = A^T for A m x n col-major
@@ -235,20 +257,6 @@ __global__ void k_align_signs(double* __restrict__ U, const double* __restrict__
     for (int r = threadIdx.x; r < m; r += blockDim.x) U[(long long)c * m + r] = -U[(long long)c * m + r];
 }
 
-__global__ void k_sumsq(const double* __restrict__ A, long long n, double* out) {
-  double v = 0.0;
-  for (long long t = threadIdx.x; t < n; t += blockDim.x) v = fma(A[t], A[t], v);
-  __shared__ double sh[1024 / 32];
-  v = jwarp_sum(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += sh[w];
-    *out = t;
-  }
-}
-
 // count entries with F[i][j] != F[j][i] (exact comparison)
 __global__ void k_asym_count(const double* __restrict__ F, int n, unsigned int* __restrict__ count) {
   const long long tot = (long long)n * n;
@@ -270,8 +278,10 @@ __global__ void k_gram_violations(const T* __restrict__ G, int n, double tol, do
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % n), j = (int)(t / n);
     if (i >= j) continue;
-    const double ga = G[t], al = G[(long long)i * n + i], be = G[(long long)j * n + j];
-    if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be) && fabs(ga) > floor * sqrt(fmax(al, be))) ++local;
+    // |g| > tol sqrt(a b) and |g| > floor sqrt(max(a, b)), compared squared
+    const T ga = G[t], al = G[(long long)i * n + i], be = G[(long long)j * n + j];
+    const T g2 = ga * ga;
+    if (ga != T(0) && g2 > T(tol * tol) * al * be && g2 > T(floor * floor) * (al > be ? al : be)) ++local;
   }
   if (local) atomicAdd(count, local);
 }
@@ -323,10 +333,12 @@ __global__ void k_small_right(const double* __restrict__ Q, int m, int p, const 
 // Gram-Schmidt with each projection done twice (CGS2: all dots against the
 // previous columns in one block reduction); a column that vanishes (rank
 // deficiency) is replaced by a unit vector e_t and orthogonalised again.
-// One block of CG_T threads.
-constexpr int CG_T = 512;
+// With R non-null, also the triangular factor of Q_in = Q_out R (p x p
+// col-major; a vanished column keeps its small remaining norm on the
+// diagonal).  One block of CG_T threads.
+constexpr int CG_T = 128;  // few threads: the FP64 warp reductions, not the dots, bound this kernel
 constexpr int CG_CH = 16;  // dots per block reduction
-__global__ void __launch_bounds__(CG_T) k_cgs2(double* __restrict__ Q, int m, int p) {
+__global__ void __launch_bounds__(CG_T) k_cgs2(double* __restrict__ Q, int m, int p, double* __restrict__ R) {
   __shared__ double sh[CG_T / 32][CG_CH + 1];
   __shared__ double dsh[CG_CH];
   __shared__ double tot;
@@ -364,14 +376,20 @@ __global__ void __launch_bounds__(CG_T) k_cgs2(double* __restrict__ Q, int m, in
           }
 #pragma unroll
           for (int q = 0; q < CG_CH; ++q) {
-            const double v = jwarp_sum(d[q]);
-            if (lane == 0) sh[wid][q] = v;
+            if (q < jn) {  // uniform over the block
+              const double v = jwarp_sum(d[q]);
+              if (lane == 0) sh[wid][q] = v;
+            }
           }
           __syncthreads();
           if (threadIdx.x < jn) {
             double t = 0;
             for (int w = 0; w < CG_T / 32; ++w) t += sh[w][threadIdx.x];
             dsh[threadIdx.x] = t;
+            if (R && attempt == 0) {
+              double* rr = R + (long long)k * p + j0 + threadIdx.x;
+              *rr = (pass == 0 ? 0.0 : *rr) + t;
+            }
           }
           __syncthreads();
           for (int r = threadIdx.x; r < m; r += CG_T) {
@@ -385,8 +403,13 @@ __global__ void __launch_bounds__(CG_T) k_cgs2(double* __restrict__ Q, int m, in
       double nk = 0;
       for (int r = threadIdx.x; r < m; r += CG_T) nk = fma(qk[r], qk[r], nk);
       nk = sqrt(bsum(nk));
+      if (R && attempt == 0 && threadIdx.x == 0) {
+        for (int j = k + 1; j < p; ++j) R[(long long)k * p + j] = 0.0;
+        R[(long long)k * p + k] = nk;
+      }
       if (nk > 1e-10 * n0 && nk > 0) {
-        for (int r = threadIdx.x; r < m; r += CG_T) qk[r] /= nk;
+        const double inv = 1.0 / nk;  // one FP64 division per column, not per entry
+        for (int r = threadIdx.x; r < m; r += CG_T) qk[r] *= inv;
         __syncthreads();
         break;
       }
@@ -537,8 +560,7 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
   KP_TRY(kp_alloc(ctx, (void**)&nrm, sizeof(double)));
   // noise floor m eps ||A||_F; eps is the unit of the arithmetic W came from
   // (FP32 when the products of the setup run in FP32)
-  k_sumsq<<<1, 1024, 0, st>>>(W, (long long)m * n, nrm);
-  KP_LAUNCHED(ctx);
+  KP_TRY(dot_dev(ctx, W, W, (long long)m * n, true, nrm));
   double fro2 = 0.0;
   KP_CUDA(cudaMemcpyAsync(&fro2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
   KP_CUDA(cudaStreamSynchronize(st));
@@ -702,8 +724,7 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
     KP_TRY(kp_alloc(ctx, (void**)&W32, sizeof(float) * nn));
   }
   const int g = std::max(1, std::min((int)((nn + 255) / 256), ctx->sm_count * 16));
-  k_transform<<<g, 256, 0, st>>>(n, transform, C);
-  KP_LAUNCHED(ctx);
+  KP_TRY(make_transform(ctx, n, transform, C));
   if (fast) KP_TRY(convert_f64_to_f32(ctx, C, C32, nn));
   // W (col-major) = X C for X given row-major, computed as the row-major
   // product D[k][i] = sum_j C[j,k] X[i,j]; FP32 products are widened to FP64
@@ -779,19 +800,22 @@ kp_status topr_svd(kp_ctx* ctx, const double* W, int m, int n, int r, double* U,
   {  // start vectors: the first p columns of the m x m DCT-II matrix (smooth)
     double* C;
     KP_TRY(kp_alloc(ctx, (void**)&C, sizeof(double) * (size_t)m * m));
-    k_transform<<<g, 256, 0, st>>>(m, 0, C);
-    KP_LAUNCHED(ctx);
+    KP_TRY(make_transform(ctx, m, 0, C));
     KP_CUDA(cudaMemcpyAsync(Q, C, sizeof(double) * (size_t)m * p, cudaMemcpyDeviceToDevice, st));
   }
-  // the Ritz step: one-block Jacobi when Z fits in shared memory
-  const size_t small_smem = sizeof(double) * ((size_t)n * p + (size_t)p * p);
-  const bool small = p <= SJ_MAXP && small_smem <= 200 * 1024;
+  // the Ritz step for p <= 32: Z = Q_z R_z (CGS2), then the one-block Jacobi
+  // SVD of the p x p factor R_z = U_R S V_R^T, so that U_z = Q_z U_R, V_z = V_R
+  const bool small = p <= SJ_MAXP;
+  const size_t small_smem = sizeof(double) * 2 * (size_t)p * p;
   int* jstat = nullptr;
+  double *Rz = nullptr, *UR = nullptr;
   if (small) {
     KP_TRY(kp_alloc(ctx, (void**)&jstat, sizeof(int)));
+    KP_TRY(kp_alloc(ctx, (void**)&Rz, sizeof(double) * (size_t)p * p));
+    KP_TRY(kp_alloc(ctx, (void**)&UR, sizeof(double) * (size_t)p * p));
     KP_CUDA(cudaMemsetAsync(jstat, 0, sizeof(int), st));
-    KP_CUDA(cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
   }
+  const int gz = std::max(1, std::min((int)(((long long)n * p + 255) / 256), ctx->sm_count * 4));
   auto skinny = [&](const double* X, int rows, int ncol, const double* Y, double* out) -> kp_status {
     const long long threads = (long long)ncol * 32;
     k_skinny_tn<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(X, rows, Y, rows, rows, ncol, p, out, ncol);
@@ -802,14 +826,16 @@ kp_status topr_svd(kp_ctx* ctx, const double* W, int m, int n, int r, double* U,
   int it = 0;
   const int maxit = 200;
   for (it = 0; it < maxit; ++it) {
-    k_cgs2<<<1, CG_T, 0, st>>>(Q, m, p);
+    k_cgs2<<<1, CG_T, 0, st>>>(Q, m, p, nullptr);
     KP_LAUNCHED(ctx);
     KP_TRY(skinny(W, m, n, Q, Z));  // Z (n x p) = W^T Q
     // Ritz values: singular values of Z
     if (small) {
-      k_jacobi_small<<<1, SJ_T, small_smem, st>>>(Z, n, p, ctx->jacobi_tol, ctx->jacobi_max_sweeps, Uz, sz, Vz,
+      k_cgs2<<<1, CG_T, 0, st>>>(Z, n, p, Rz);  // Z <- Q_z
+      k_jacobi_small<<<1, SJ_T, small_smem, st>>>(Rz, p, p, ctx->jacobi_tol, ctx->jacobi_max_sweeps, UR, sz, Vz,
                                                   jstat);
-      KP_LAUNCHED(ctx);
+      k_small_right<<<gz, 256, 0, st>>>(Z, n, p, UR, p, Uz);
+      ctx->launches += 3;
     } else {
       KP_TRY(jacobi_svd(ctx, Z, n, p, Uz, sz, Vz, nullptr));
     }

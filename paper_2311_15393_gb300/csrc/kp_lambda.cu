@@ -27,7 +27,7 @@
 namespace {
 
 constexpr int NGRID = 400;
-constexpr int GPB = 8;  // grid values per block
+constexpr int GPB = 16;  // grid values per block
 constexpr int LT = 256;
 
 enum LMethod { LM_GCV = 0, LM_WGCV = 1, LM_DISC = 2, LM_OPT = 3, LM_TRACE = 4 };
@@ -46,28 +46,58 @@ struct LamData {
   int method;
 };
 
+// 1 / x in FP64 from an FP32 reciprocal and two Newton steps (FP64 division
+// is a long instruction sequence on this part); x > 0
+__device__ __forceinline__ double drcp(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ float drcp(float x) { return __frcp_rn(x); }
+
 // per-element contributions (s1, s2) of the sums for one lambda
 template <typename T>
 __device__ __forceinline__ void terms(int method, T s2, T sg, T bh, T xh, T lam2, T omega, T& a, T& b) {
-  const T d = s2 + lam2;
-  const T phi = lam2 / d;
+  const T rd = drcp(s2 + lam2);
+  const T phi = lam2 * rd;
   switch (method) {
     case LM_OPT: {
-      const T e = sg * bh / d - xh;
+      const T e = sg * bh * rd - xh;
       a = e * e;
       b = T(0);
       break;
     }
     case LM_TRACE:
       a = T(0);
-      b = ((T(1) - omega) * s2 + lam2) / d;
+      b = ((T(1) - omega) * s2 + lam2) * rd;
       break;
     default: {  // GCV / wGCV / discrepancy share the residual sum
       const T pb = phi * bh;
       a = pb * pb;
-      b = ((T(1) - omega) * s2 + lam2) / d;
+      b = ((T(1) - omega) * s2 + lam2) * rd;
       break;
     }
+  }
+}
+// FP32 form for the grid scan: one reciprocal per term (the grid only
+// brackets the minimum; the FP64 forms above decide it)
+__device__ __forceinline__ void terms_grid(int method, float s2, float sg, float bh, float xh, float lam2, float omega,
+                                           float& a, float& b) {
+  const float rd = __frcp_rn(s2 + lam2);
+  if (method == LM_OPT) {
+    const float e = sg * bh * rd - xh;
+    a = e * e;
+    b = 0.f;
+  } else if (method == LM_TRACE) {
+    a = 0.f;
+    b = fmaf(1.f - omega, s2, lam2) * rd;
+  } else {
+    const float pb = lam2 * rd * bh;
+    a = pb * pb;
+    b = fmaf(1.f - omega, s2, lam2) * rd;
   }
 }
 
@@ -90,24 +120,32 @@ __global__ void __launch_bounds__(LT) k_lam_grid(LamData d, const double* __rest
     acc_b[q] = 0.f;
   }
   const float om = (float)d.omega;
+  const bool opt = d.method == LM_OPT;
   for (long long i = blockIdx.x * (long long)LT + threadIdx.x; i < d.n; i += (long long)gridDim.x * LT) {
-    const float s2 = d.s2f[i], sg = d.sgf[i], bh = d.bhf[i], xh = d.xhf ? d.xhf[i] : 0.f;
+    const float s2 = d.s2f[i], bh = d.bhf[i];
+    const float sg = opt ? d.sgf[i] : 0.f, xh = opt ? d.xhf[i] : 0.f;
 #pragma unroll
     for (int q = 0; q < GPB; ++q) {
       float a, b;
-      terms<float>(d.method, s2, sg, bh, xh, l2[q], om, a, b);
+      terms_grid(d.method, s2, sg, bh, xh, l2[q], om, a, b);
       acc_a[q] += a;
       acc_b[q] += b;
     }
   }
+  // warp sums in FP32 (the grid only brackets the minimum), block sums in FP64
   __shared__ double sh[LT / 32][GPB][2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < GPB; ++q) {
-    double a = lwarp_sum((double)acc_a[q]), b = lwarp_sum((double)acc_b[q]);
+    float a = acc_a[q], b = acc_b[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
     if (lane == 0) {
-      sh[wid][q][0] = a;
-      sh[wid][q][1] = b;
+      sh[wid][q][0] = (double)a;
+      sh[wid][q][1] = (double)b;
     }
   }
   __syncthreads();
@@ -180,7 +218,7 @@ __global__ void __launch_bounds__(LT) k_lam_deriv64(LamData d, double lam2, doub
   const double w = d.omega;
   for (long long i = blockIdx.x * (long long)LT + threadIdx.x; i < d.n; i += (long long)gridDim.x * LT) {
     const double s2 = d.s2[i], b = d.bh[i];
-    const double rd = 1.0 / (s2 + lam2);
+    const double rd = drcp(s2 + lam2);
     const double phi = lam2 * rd, psi = s2 * rd, b2 = b * b;
     const double pp = phi * psi;
     acc[0] = fma(phi * phi, b2, acc[0]);
@@ -221,14 +259,20 @@ __global__ void k_sum6_finish(const double* __restrict__ part, int nchunks, doub
   if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void k_prep(const double* __restrict__ Sigma, const double* __restrict__ bh, const double* __restrict__ xh,
-                       long long n, double* __restrict__ s2, float* __restrict__ s2f, float* __restrict__ sgf,
-                       float* __restrict__ bhf, float* __restrict__ xhf) {
+// spectrum-only arrays (once per kp_setup)
+__global__ void k_prep_sigma(const double* __restrict__ Sigma, long long n, double* __restrict__ s2,
+                             float* __restrict__ s2f, float* __restrict__ sgf) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double s = Sigma[i];
     s2[i] = s * s;
     s2f[i] = (float)(s * s);
     sgf[i] = (float)s;
+  }
+}
+// coefficient arrays (every call)
+__global__ void k_prep_coeffs(const double* __restrict__ bh, const double* __restrict__ xh, long long n,
+                              float* __restrict__ bhf, float* __restrict__ xhf) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     bhf[i] = (float)bh[i];
     if (xh) xhf[i] = (float)xh[i];
   }
@@ -240,15 +284,38 @@ __global__ void k_to_f64(const T* __restrict__ x, long long n, double* __restric
     y[i] = (double)x[i];
 }
 
-__global__ void k_absmax_min(const double* __restrict__ S, long long n, double* out) {
-  // out[0] = max |S|, out[1] = min |S| over |S| > 0 (single block)
+// per-block max |S| and min |S| over |S| > 0 (part[2 b], part[2 b + 1]);
+// then one block combines the partials
+__global__ void k_absmax_min_part(const double* __restrict__ S, long long n, double* __restrict__ part) {
   double mx = 0.0, mn = INFINITY;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    double a = fabs(S[i]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double a = fabs(S[i]);
     mx = fmax(mx, a);
     if (a > 0) mn = fmin(mn, a);
   }
-  __shared__ double smx[1024], smn[1024];
+  __shared__ double smx[256], smn[256];
+  smx[threadIdx.x] = mx;
+  smn[threadIdx.x] = mn;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + o]);
+      smn[threadIdx.x] = fmin(smn[threadIdx.x], smn[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = smx[0];
+    part[2 * blockIdx.x + 1] = smn[0];
+  }
+}
+__global__ void k_absmax_min_finish(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  double mx = 0.0, mn = INFINITY;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    mx = fmax(mx, part[2 * i]);
+    mn = fmin(mn, part[2 * i + 1]);
+  }
+  __shared__ double smx[256], smn[256];
   smx[threadIdx.x] = mx;
   smn[threadIdx.x] = mn;
   __syncthreads();
@@ -436,15 +503,24 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
     g2.epi.ldd = n_r;
     return simt_gemm<double>(ctx, g2);
   };
+  if (!ctx->lam_sigma_ready) {  // spectrum-only arrays and bounds, once per setup
+    k_prep_sigma<<<gr, 256, 0, st>>>(ctx->Sigma64, N, s2, s2f, sgf);
+    KP_LAUNCHED(ctx);
+    const int nb = std::max(1, std::min((int)((N + 255) / 256), ctx->sm_count * 4));
+    k_absmax_min_part<<<nb, 256, 0, st>>>(ctx->Sigma64, N, part);
+    k_absmax_min_finish<<<1, 256, 0, st>>>(part, nb, ext);
+    ctx->launches += 2;
+    KP_CUDA(cudaMemcpyAsync(ctx->lam_sigma_ext, ext, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  }
   KP_TRY(kp_coeffs(b, ctx->Uc, ctx->Ur, bh));
   if (method == KP_LAMBDA_OPT) KP_TRY(kp_coeffs(x_true, ctx->Vc, ctx->Vr, xh));
-  k_prep<<<gr, 256, 0, st>>>(ctx->Sigma64, bh, xh, N, s2, s2f, sgf, bhf, xhf);
+  k_prep_coeffs<<<gr, 256, 0, st>>>(bh, xh, N, bhf, xhf);
   KP_LAUNCHED(ctx);
-  k_absmax_min<<<1, 1024, 0, st>>>(ctx->Sigma64, N, ext);
-  KP_LAUNCHED(ctx);
-  double he[2];
-  KP_CUDA(cudaMemcpyAsync(he, ext, sizeof(he), cudaMemcpyDeviceToHost, st));
-  KP_CUDA(cudaStreamSynchronize(st));
+  if (!ctx->lam_sigma_ready) {
+    KP_CUDA(cudaStreamSynchronize(st));
+    ctx->lam_sigma_ready = true;
+  }
+  const double* he = ctx->lam_sigma_ext;
   const double smax = he[0];
   const double smin = std::isfinite(he[1]) ? he[1] : smax;
   if (!(smax > 0)) {
@@ -608,7 +684,7 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
     // safeguarded Newton on g(t) = log s1 - 2 log s2 (= log G - log N) in
     // t = log lambda over [t_{best-1}, t_{best+1}], from the best grid point
     double t = tg[best];
-    for (int it = 0; it < 100; ++it) {
+    for (int it = 0; it < 60; ++it) {
       double s6[6];
       KP_TRY(deriv64(L, std::exp(t), s6));
       if (!(s6[1] > 0.0) || !(s6[0] > 0.0)) {  // below the wGCV lower limit: move right
@@ -622,7 +698,7 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
       if (gp > 0) c = t; else a = t;
       double tn = (gpp > 0) ? t - gp / gpp : 0.5 * (a + c);
       if (!(tn > a && tn < c)) tn = 0.5 * (a + c);
-      const bool done = std::fabs(tn - t) <= 1e-13 * std::max(1.0, std::fabs(t)) || c - a <= 1e-13 * std::max(1.0, std::fabs(t));
+      const bool done = std::fabs(tn - t) <= 1e-12 * std::max(1.0, std::fabs(t)) || c - a <= 1e-12 * std::max(1.0, std::fabs(t));
       t = tn;
       if (done || gp == 0.0) break;
     }

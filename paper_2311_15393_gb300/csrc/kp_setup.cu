@@ -138,10 +138,13 @@ __global__ void k_split64(const double* __restrict__ in, int n, int blocks, int 
     } else {
       v = in[t];
     }
+    // slices of the FP32-rounded value, split in FP32 (exact: three bf16
+    // slices hold the 24-bit significand; FP64 arithmetic is slow here)
+    float f = (float)v;
     for (int s = 0; s < slices; ++s) {
-      __nv_bfloat16 h = __double2bfloat16(v);
+      const __nv_bfloat16 h = __float2bfloat16_rn(f);
       out[s * sstride + t] = h;
-      v -= (double)__bfloat162float(h);
+      f -= __bfloat162float(h);
     }
   }
 }
