@@ -178,6 +178,9 @@ extern "C" void kp_destroy(kp_ctx* ctx) {
   cudaSetDevice(ctx->device);
   kp_free_all(ctx);
   kp_pool_release(ctx);
+  if (ctx->hmirror) cudaFreeHost(ctx->hmirror);
+  for (auto& e : ctx->ev_blk)
+    if (e) cudaEventDestroy(e);
   if (ctx->ctx_block) cudaFree(ctx->ctx_block);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);

@@ -133,6 +133,8 @@ struct kp_ctx {
   double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD
   int jacobi_max_sweeps = 40;
   bool pdl = true;           // programmatic dependent launch in the iteration
+  void* hmirror = nullptr;   // pinned host copies of the solver flags / scalars (2 slots)
+  cudaEvent_t ev_blk[2] = {nullptr, nullptr};
   int splitk_override = 0;  // > 0: fixed split-K factor for the square GEMMs
   int tc_bn_override = 0;   // 128 / 256: fixed tensor-core tile width
   int tc_cps_override = 0;  // 1 / 2: fixed CTAs per SM for 128-wide tiles

@@ -174,12 +174,24 @@ static GemmDesc pc_desc(kp_ctx* ctx, int which) {
 // the image-shaped product: out = alpha sum_k Z_k + beta aux, as FP32 or as
 // bf16 slices (hi, lo, ...).  Z holds `terms` blocks of nel FP32 values; the
 // terms are added in order.
-__global__ void k_term_reduce(const float* __restrict__ Z, int terms, long long nel, float alpha, float beta,
-                              const float* __restrict__ aux, int slices_mode, void* __restrict__ out, int slices,
-                              long long sstride, int vec, const int* flags) {
+// With dot non-null (FP32 output), also dot = sum out * aux (p^T q of the
+// iteration) by the deterministic tree of the vector kernels, and the scalar
+// step po by its last block.
+struct TermDot {
+  double* out = nullptr;
+  double* partials = nullptr;
+  unsigned int* counter = nullptr;
+  PostOp po;
+};
+
+__global__ void __launch_bounds__(VEC_THREADS)
+    k_term_reduce(const float* __restrict__ Z, int terms, long long nel, float alpha, float beta,
+                  const float* __restrict__ aux, int slices_mode, void* __restrict__ out, int slices, long long sstride,
+                  int vec, TermDot td, const int* flags) {
   KP_PDL_WAIT();
   KP_PDL_TRIGGER();
   if (flags && *(volatile const int*)flags) return;
+  float dh[1] = {0.f}, dl[1] = {0.f};  // p^T q as a double-float pair
   if (!vec) {  // out / aux not 16-byte aligned: one element at a time
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nel; i += (long long)gridDim.x * blockDim.x) {
       float a = Z[i];
@@ -188,6 +200,7 @@ __global__ void k_term_reduce(const float* __restrict__ Z, int terms, long long 
       if (aux) v = fmaf(beta, aux[i], v);
       if (!slices_mode) {
         ((float*)out)[i] = v;
+        if (td.out) kpv::df_add_prod(dh[0], dl[0], v, aux[i]);
       } else {
         for (int sl = 0; sl < slices; ++sl) {
           const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -196,6 +209,7 @@ __global__ void k_term_reduce(const float* __restrict__ Z, int terms, long long 
         }
       }
     }
+    if (td.out) kpv::reduce_finish_df<1>(dh, dl, false, td.partials, td.counter, td.out, 1, td.po);
     return;
   }
   const long long n4 = nel >> 2;
@@ -219,6 +233,13 @@ __global__ void k_term_reduce(const float* __restrict__ Z, int terms, long long 
     }
     if (!slices_mode) {
       reinterpret_cast<float4*>(out)[i] = make_float4(v[0], v[1], v[2], v[3]);
+      if (td.out) {
+        const float4 t = reinterpret_cast<const float4*>(aux)[i];
+        kpv::df_add_prod(dh[0], dl[0], v[0], t.x);
+        kpv::df_add_prod(dh[0], dl[0], v[1], t.y);
+        kpv::df_add_prod(dh[0], dl[0], v[2], t.z);
+        kpv::df_add_prod(dh[0], dl[0], v[3], t.w);
+      }
     } else {
       __nv_bfloat16* o = (__nv_bfloat16*)out + 4 * i;
       for (int sl = 0; sl < slices; ++sl) {
@@ -235,6 +256,7 @@ __global__ void k_term_reduce(const float* __restrict__ Z, int terms, long long 
       }
     }
   }
+  if (td.out) kpv::reduce_finish_df<1>(dh, dl, false, td.partials, td.counter, td.out, 1, td.po);
 }
 
 kp_status ops_prepare(kp_ctx* ctx) {
@@ -322,7 +344,9 @@ static kp_status simt_op(kp_ctx* ctx, int which, const void* bptr, EpiParams e, 
   return simt_gemm<T>(ctx, g);
 }
 
-static kp_status run_op(kp_ctx* ctx, int which, int mode, const void* bptr, const EpiParams& e, const int* flags) {
+static kp_status run_op(kp_ctx* ctx, int which, int mode, const void* bptr, const EpiParams& e, const int* flags,
+                        const TermDot* td = nullptr, bool* dot_done = nullptr) {
+  if (dot_done) *dot_done = false;
   if (op_is_tc(ctx)) {
     OpsState* os = ops(ctx);
     TcGemmPlan* pl = os->G[mode][which];
@@ -335,11 +359,16 @@ static kp_status run_op(kp_ctx* ctx, int which, int mode, const void* bptr, cons
     ez.ldd = ctx->n_r;
     KP_TRY(tc_plan_run(ctx, pl, &ez));
     const long long nel = (long long)ctx->n_r * ctx->n_c;
-    const int g = std::max(1, std::min((int)((nel / 4 + 255) / 256), ctx->sm_count * 8));
+    const int g = std::max(1, std::min((int)((nel / 4 + VEC_THREADS - 1) / VEC_THREADS), ctx->sm_count * 8));
     const int vec = ((((uintptr_t)e.out | (uintptr_t)e.aux) & 15) == 0 && (e.slice_stride % 4) == 0) ? 1 : 0;
-    KP_CUDA(kp_launch(ctx, k_term_reduce, dim3(g), dim3(256), 0, (const float*)ctx->w_split, ctx->rank, nel,
+    TermDot t;
+    if (td && e.mode == EPI_F32 && e.aux) {
+      t = *td;
+      if (dot_done) *dot_done = true;
+    }
+    KP_CUDA(kp_launch(ctx, k_term_reduce, dim3(g), dim3(VEC_THREADS), 0, (const float*)ctx->w_split, ctx->rank, nel,
                       (float)e.alpha, (float)e.beta, (const float*)e.aux, e.mode == EPI_SLICES ? 1 : 0, e.out,
-                      e.slices, e.slice_stride, vec, flags));
+                      e.slices, e.slice_stride, vec, t, flags));
     KP_LAUNCHED(ctx);
     return KP_OK;
   }
@@ -414,7 +443,9 @@ kp_status op_apply(kp_ctx* ctx, const void* x, void* y, int transpose, int mode)
   return KP_OK;
 }
 
-kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_slices_ready, const int* flags) {
+kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_slices_ready, const int* flags,
+                     double* pq_out, const PostOp* pq_post, bool* pq_done) {
+  if (pq_done) *pq_done = false;
   const void* bx = p;
   if (op_is_tc(ctx)) {
     if (!p_slices_ready) KP_TRY(stage_input(ctx, p, OP_INNER, &bx));
@@ -424,6 +455,15 @@ kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_sl
   KP_TRY(run_op(ctx, 0, OP_INNER, bx, epi_stack(ctx, OP_INNER), flags));
   KP_TRY(run_op(ctx, 1, OP_INNER, nullptr, epi_img(ctx, OP_INNER, ctx->w_img, tc, 1.0, 0.0, nullptr), flags));
   KP_TRY(run_op(ctx, 2, OP_INNER, ctx->w_img, epi_stack(ctx, OP_INNER), flags));
+  if (pq_out) {  // p^T q (and the alpha step) fused into the term sum when G4 is batched
+    TermDot td;
+    td.out = pq_out;
+    td.partials = ctx->red_part;
+    td.counter = ctx->red_count;
+    if (pq_post) td.po = *pq_post;
+    KP_TRY(run_op(ctx, 3, OP_INNER, nullptr, epi_img(ctx, OP_INNER, q, false, 1.0, lam2, p), flags, &td, pq_done));
+    return KP_OK;
+  }
   KP_TRY(run_op(ctx, 3, OP_INNER, nullptr, epi_img(ctx, OP_INNER, q, false, 1.0, lam2, p), flags));
   return KP_OK;
 }

@@ -13,7 +13,11 @@ kp_status op_apply(kp_ctx* ctx, const void* x, void* y, int transpose, int mode)
 // q = (A^T A + lam2 I) p in the inner operator precision.  For tensor-core
 // operators `p_slices_ready` says the bf16 slices of p are already in
 // ctx->w_img2 (written by the p update); otherwise they are made here.
-kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_slices_ready, const int* flags);
+// With pq_out, p^T q may be computed on the way (and pq_post run on it);
+// *pq_done says whether it was (else the caller computes it).
+struct PostOp;
+kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_slices_ready, const int* flags,
+                     double* pq_out = nullptr, const PostOp* pq_post = nullptr, bool* pq_done = nullptr);
 
 // r = A^T (b - A x) - lam2 x with the accurate operator
 kp_status op_true_residual(kp_ctx* ctx, const void* b, const void* x, void* r, double lam2, const int* flags);

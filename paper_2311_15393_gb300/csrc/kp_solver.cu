@@ -55,8 +55,9 @@ static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
   pc.kind = POST_CHECK;
   pc.hist = ctx->hist;
   pc.hist_cap = ctx->hist_cap;
-  KP_TRY(op_apply_K(ctx, B.p, B.q, lam2, op_inner_slices(ctx) > 0, fl));
-  KP_TRY(dot2_dev(ctx, B.p, B.q, nullptr, N, f64, s + S_PQ, fl, pa));
+  bool fused = false;
+  KP_TRY(op_apply_K(ctx, B.p, B.q, lam2, op_inner_slices(ctx) > 0, fl, s + S_PQ, &pa, &fused));
+  if (!fused) KP_TRY(dot2_dev(ctx, B.p, B.q, nullptr, N, f64, s + S_PQ, fl, pa));
   KP_TRY(update_xr_dev(ctx, x, B.r, B.r_old, B.p, B.q, N, f64, s + S_ALPHA, s + S_RR, fl, pc));
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -189,12 +190,40 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
         return KP_ECUDA;
       }
       KP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-      bool done = false;
-      while (!done) {
+      // Blocks are launched one ahead: while block k runs, block k + 1 is
+      // queued, and the host inspects block k's flags (copied to pinned
+      // memory behind it) without leaving the GPU idle.  If block k paused,
+      // block k + 1 runs as no-ops (every kernel sees the pause flag).
+      struct Mirror {
+        HostFlags f;
+        int pad[3];
+        double s[12];
+      };
+      if (!ctx->hmirror) KP_CUDA(cudaHostAlloc(&ctx->hmirror, 2 * sizeof(Mirror), cudaHostAllocDefault));
+      for (auto& e : ctx->ev_blk)
+        if (!e) KP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      Mirror* mir = static_cast<Mirror*>(ctx->hmirror);
+      auto launch_block = [&](int slot) -> kp_status {
         KP_CUDA(cudaGraphLaunch(exec, st));
         ctx->launches += per_block;
-        KP_TRY(read_flags(ctx, &hf, hs));
-        if (!hf.pause) continue;
+        KP_CUDA(cudaMemcpyAsync(&mir[slot].f, ctx->dflags, sizeof(HostFlags), cudaMemcpyDeviceToHost, st));
+        KP_CUDA(cudaMemcpyAsync(mir[slot].s, ctx->dscal, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        KP_CUDA(cudaEventRecord(ctx->ev_blk[slot], st));
+        return KP_OK;
+      };
+      int cur = 0;
+      KP_TRY(launch_block(cur));
+      bool done = false;
+      while (!done) {
+        KP_TRY(launch_block(cur ^ 1));
+        KP_CUDA(cudaEventSynchronize(ctx->ev_blk[cur]));
+        hf = mir[cur].f;
+        std::copy(mir[cur].s, mir[cur].s + 12, hs);
+        if (!hf.pause) {
+          cur ^= 1;
+          continue;
+        }
+        KP_CUDA(cudaStreamSynchronize(st));  // drain the no-op block behind it
         iters = hf.iter;
         final_rr = hs[S_RR];
         if (hf.reason & R_NUMERIC) {
@@ -235,6 +264,8 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
         KP_CUDA(cudaMemcpyAsync(ctx->dflags, zero2, sizeof(zero2), cudaMemcpyHostToDevice, st));
         KP_TRY(half_b(ctx, B, lam2));
         KP_CUDA(cudaStreamSynchronize(st));
+        cur = 0;
+        KP_TRY(launch_block(cur));
       }
       cudaGraphExecDestroy(exec);
       cudaGraphDestroy(graph);

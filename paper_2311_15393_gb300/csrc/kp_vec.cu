@@ -17,136 +17,11 @@
 
 namespace kpv {
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Block-level reduction of NV sums (+ optional max in slot NV-1 when
-// last_is_max) and the cross-block ordered finish.  blockDim.x == VEC_THREADS.
-__device__ void run_post(const PostOp& po, const double* vals);
-
-template <int NV>
-__device__ void reduce_finish(double (&v)[NV], bool last_is_max, double* partials, unsigned int* counter,
-                              double* out, int nout, const PostOp& po = PostOp()) {
-  __shared__ double sh[VEC_THREADS / 32][NV];
-  __shared__ bool s_last;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    const bool mx = last_is_max && i == NV - 1;
-    v[i] = mx ? warp_max(v[i]) : warp_sum(v[i]);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) sh[wid][i] = v[i];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < NV; ++i) {
-      const bool mx = last_is_max && i == NV - 1;
-      double t = sh[0][i];
-      for (int w = 1; w < VEC_THREADS / 32; ++w) t = mx ? fmax(t, sh[w][i]) : t + sh[w][i];
-      partials[blockIdx.x * NV + i] = t;
-    }
-    __threadfence();
-    unsigned int prev = atomicAdd(counter, 1u);
-    s_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double acc[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += VEC_THREADS) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      const bool mx = last_is_max && i == NV - 1;
-      double pv = ((volatile double*)partials)[b * NV + i];
-      acc[i] = mx ? fmax(acc[i], pv) : acc[i] + pv;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    const bool mx = last_is_max && i == NV - 1;
-    acc[i] = mx ? warp_max(acc[i]) : warp_sum(acc[i]);
-  }
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) sh[wid][i] = acc[i];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double fin[NV];
-    for (int i = 0; i < NV; ++i) {
-      const bool mx = last_is_max && i == NV - 1;
-      double t = sh[0][i];
-      for (int w = 1; w < VEC_THREADS / 32; ++w) t = mx ? fmax(t, sh[w][i]) : t + sh[w][i];
-      fin[i] = t;
-      if (i < nout) out[i] = t;
-    }
-    *counter = 0u;
-    if (po.kind != POST_NONE) run_post(po, fin);
-  }
-}
-
-// scalar steps of the iteration (see PostOp); vals = the reduction's results
-__device__ void run_post(const PostOp& po, const double* vals) {
-  double* s = po.s;
-  int* f = po.f;
-  if (po.kind == POST_ALPHA) {  // vals[0] = p^T K p
-    const double pq = vals[0], zr = s[S_ZR];
-    if (!isfinite(pq) || !isfinite(zr)) {
-      f[F_REASON] |= R_NUMERIC;
-      f[F_PAUSE] = 1;
-    } else if (!(pq > 0.0) || !(zr > 0.0)) {
-      f[F_REASON] |= R_BREAKDOWN;
-      f[F_PAUSE] = 1;
-    } else {
-      s[S_ALPHA] = zr / pq;
-    }
-  } else if (po.kind == POST_CHECK) {  // vals[0] = ||r||^2
-    const int it = ++f[F_ITER];
-    const double rr = vals[0];
-    if (it < po.hist_cap) po.hist[it] = sqrt(rr / s[S_RR0]);
-    int reason = 0;
-    if (!isfinite(rr)) reason |= R_NUMERIC;
-    else if (rr <= s[S_TOL2]) reason |= R_CONV;
-    else if (s[S_DELTA2] > 0.0 && rr < s[S_DELTA2] * s[S_RMAX]) reason |= R_REPLACE;
-    if (it >= f[F_MAXIT]) reason |= R_MAXIT;
-    if (reason) {
-      f[F_REASON] |= reason;
-      f[F_PAUSE] = 1;
-    }
-  } else if (po.kind == POST_BETA) {  // vals[0] = z^T r, vals[1] = z^T r_old
-    const double zn = vals[0], zo = vals[1], zr = s[S_ZR];
-    if (!isfinite(zn) || !isfinite(zo)) {
-      f[F_REASON] |= R_NUMERIC;
-      f[F_PAUSE] = 1;
-    } else if (!(zn > 0.0)) {
-      f[F_REASON] |= R_BREAKDOWN;
-      f[F_PAUSE] = 1;
-    } else {
-      s[S_BETA] = f[F_FLEX] ? (zn - zo) / zr : zn / zr;
-      s[S_ZR] = zn;
-    }
-  }
-}
-
 // 16-byte access to element 4 i of an FP32 vector
 __device__ __forceinline__ float4 ld4(const float* p, long long i) { return reinterpret_cast<const float4*>(p)[i]; }
 __device__ __forceinline__ void st4(float* p, long long i, float4 v) { reinterpret_cast<float4*>(p)[i] = v; }
 constexpr int FLUSH = 16;  // float4 packets per thread between FP64 flushes
 
-__device__ __forceinline__ bool paused(const int* flags) { return flags != nullptr && *(volatile const int*)flags != 0; }
 
 // ------------------------------------------------------------- dot products
 // out[0] = a.b ; if c != null, out[1] = a.c
@@ -162,40 +37,38 @@ __global__ void __launch_bounds__(VEC_THREADS) k_dot2(const T* __restrict__ a, c
   const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
   long long i0 = tid;
   if constexpr (std::is_same<T, float>::value) {
+    float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
     if (vec4) {
       const long long n4 = n >> 2;
-      float f0 = 0.f, f1 = 0.f;
-      int cnt = 0;
       for (long long i = tid; i < n4; i += stride) {
         const float4 x = ld4(a, i), y = ld4(b, i);
-        f0 = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, f0))));
+        df_add_prod(hi[0], lo[0], x.x, y.x);
+        df_add_prod(hi[0], lo[0], x.y, y.y);
+        df_add_prod(hi[0], lo[0], x.z, y.z);
+        df_add_prod(hi[0], lo[0], x.w, y.w);
         if (c) {
           const float4 z = ld4(c, i);
-          f1 = fmaf(x.x, z.x, fmaf(x.y, z.y, fmaf(x.z, z.z, fmaf(x.w, z.w, f1))));
-        }
-        if (++cnt == FLUSH) {
-          v[0] += f0;
-          v[1] += f1;
-          f0 = f1 = 0.f;
-          cnt = 0;
+          df_add_prod(hi[1], lo[1], x.x, z.x);
+          df_add_prod(hi[1], lo[1], x.y, z.y);
+          df_add_prod(hi[1], lo[1], x.z, z.z);
+          df_add_prod(hi[1], lo[1], x.w, z.w);
         }
       }
-      v[0] += f0;
-      v[1] += f1;
       i0 = 4 * n4 + tid;
     }
     for (long long i = i0; i < n; i += stride) {
-      v[0] += (double)(a[i] * b[i]);
-      if (c) v[1] += (double)(a[i] * c[i]);
+      df_add_prod(hi[0], lo[0], a[i], b[i]);
+      if (c) df_add_prod(hi[1], lo[1], a[i], c[i]);
     }
+    reduce_finish_df<2>(hi, lo, false, partials, counter, out, c ? 2 : 1, po);
   } else {
     for (long long i = i0; i < n; i += stride) {
       const double ai = (double)a[i];
       v[0] = fma(ai, (double)b[i], v[0]);
       if (c) v[1] = fma(ai, (double)c[i], v[1]);
     }
+    reduce_finish<2>(v, false, partials, counter, out, c ? 2 : 1, po);
   }
-  reduce_finish<2>(v, false, partials, counter, out, c ? 2 : 1, po);
 }
 
 // y = alpha*x + beta*y (scalars from host); used by setup / hooks
@@ -222,8 +95,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T*
   if constexpr (std::is_same<T, float>::value) {
     const float al = (float)*alpha_dev;
     long long i0 = tid;
-    float rr = 0.f, am = 0.f;
-    int cnt = 0;
+    float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};  // ||r||^2 (double-float), amax(r)
     if (vec4) {
       const long long n4 = n >> 2;
       for (long long i = tid; i < n4; i += stride) {
@@ -233,13 +105,11 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T*
         const float4 rn = make_float4(fmaf(-al, qi.x, ri.x), fmaf(-al, qi.y, ri.y), fmaf(-al, qi.z, ri.z),
                                       fmaf(-al, qi.w, ri.w));
         st4(r, i, rn);
-        rr = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, rr))));
-        am = fmaxf(am, fmaxf(fmaxf(fabsf(rn.x), fabsf(rn.y)), fmaxf(fabsf(rn.z), fabsf(rn.w))));
-        if (++cnt == FLUSH) {
-          v[0] += rr;
-          rr = 0.f;
-          cnt = 0;
-        }
+        df_add_prod(hi[0], lo[0], rn.x, rn.x);
+        df_add_prod(hi[0], lo[0], rn.y, rn.y);
+        df_add_prod(hi[0], lo[0], rn.z, rn.z);
+        df_add_prod(hi[0], lo[0], rn.w, rn.w);
+        hi[1] = fmaxf(hi[1], fmaxf(fmaxf(fabsf(rn.x), fabsf(rn.y)), fmaxf(fabsf(rn.z), fabsf(rn.w))));
       }
       i0 = 4 * n4 + tid;
     }
@@ -249,12 +119,12 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T*
       r_old[i] = ri;
       const float rn = fmaf(-al, q[i], ri);
       r[i] = rn;
-      rr = fmaf(rn, rn, rr);
-      am = fmaxf(am, fabsf(rn));
+      df_add_prod(hi[0], lo[0], rn, rn);
+      hi[1] = fmaxf(hi[1], fabsf(rn));
     }
-    v[0] += rr;
-    v[1] = am;
+    reduce_finish_df<2>(hi, lo, true, partials, counter, out, 2, po);
   } else {
+    double v[2] = {0.0, 0.0};
     const double alpha = *alpha_dev;
     for (long long i = tid; i < n; i += stride) {
       T ri = r[i];
@@ -266,8 +136,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T*
       v[0] = fma(d, d, v[0]);
       v[1] = fmax(v[1], fabs(d));
     }
+    reduce_finish<2>(v, true, partials, counter, out, 2, po);
   }
-  reduce_finish<2>(v, true, partials, counter, out, 2, po);
 }
 
 // p = z + beta p ; optional bf16 split copy of p (slices written at stride)
@@ -438,28 +308,21 @@ __global__ void __launch_bounds__(VEC_THREADS) k_norm_amax(const T* __restrict__
   double v[2] = {0.0, 0.0};
   const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
   if constexpr (std::is_same<T, float>::value) {
-    float rr = 0.f, am = 0.f;
-    int cnt = 0;
+    float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
     for (long long i = tid; i < n; i += stride) {
       const float d = x[i];
-      rr = fmaf(d, d, rr);
-      am = fmaxf(am, fabsf(d));
-      if (++cnt == 4 * FLUSH) {
-        v[0] += rr;
-        rr = 0.f;
-        cnt = 0;
-      }
+      df_add_prod(hi[0], lo[0], d, d);
+      hi[1] = fmaxf(hi[1], fabsf(d));
     }
-    v[0] += rr;
-    v[1] = am;
+    reduce_finish_df<2>(hi, lo, true, partials, counter, out, 2);
   } else {
     for (long long i = tid; i < n; i += stride) {
       double d = (double)x[i];
       v[0] = fma(d, d, v[0]);
       v[1] = fmax(v[1], fabs(d));
     }
+    reduce_finish<2>(v, true, partials, counter, out, 2);
   }
-  reduce_finish<2>(v, true, partials, counter, out, 2);
 }
 
 template <typename A, typename B>

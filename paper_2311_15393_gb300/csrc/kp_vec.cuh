@@ -50,3 +50,269 @@ kp_status quant8_dev(kp_ctx* ctx, const float* in, long long n, const unsigned i
 kp_status axpby_dev(kp_ctx* ctx, const void* x, void* y, long long n, bool f64, double alpha, double beta);
 kp_status convert_f64_to_f32(kp_ctx* ctx, const double* x, float* y, long long n);
 kp_status convert_f32_to_f64(kp_ctx* ctx, const float* x, double* y, long long n);
+
+// ---------------------------------------------------------------- device reductions
+// (shared by the vector kernels and the operator's fused term sum)
+namespace kpv {
+
+__device__ __forceinline__ bool paused(const int* flags) { return flags != nullptr && *(volatile const int*)flags != 0; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-level reduction of NV sums (+ optional max in slot NV-1 when
+// last_is_max) and the cross-block ordered finish.  blockDim.x == VEC_THREADS.
+__device__ inline void run_post(const PostOp& po, const double* vals);
+
+// Double-float (hi + lo in FP32) accumulation: FP64 instructions run at a
+// small fraction of the FP32 rate on this GPU, so per-element and per-warp
+// sums are kept as unevaluated pairs of floats (error-free transformations:
+// TwoSum, and the exact FMA residual of each product), ~2^-44 relative, and
+// only the per-warp results are converted to FP64.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b) {
+  const float p = a * b;
+  lo += fmaf(a, b, -p);
+  df_add(hi, lo, p);
+}
+__device__ __forceinline__ void df_warp_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    float l = lo + ol;
+    df_add(hi, l, oh);
+    const float t = hi + l;  // renormalise
+    lo = l - (t - hi);
+    hi = t;
+  }
+}
+
+// Block-level reduction of NV sums (+ optional max in slot NV-1 when
+// last_is_max) and the cross-block ordered finish.  blockDim.x == VEC_THREADS.
+// wv: this warp's values (used in lane 0).
+template <int NV>
+__device__ inline void reduce_tail(const double (&wv)[NV], bool last_is_max, double* partials, unsigned int* counter,
+                                   double* out, int nout, const PostOp& po) {
+  __shared__ double sh[VEC_THREADS / 32][NV];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[wid][i] = wv[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NV; ++i) {
+      const bool mx = last_is_max && i == NV - 1;
+      double t = sh[0][i];
+      for (int w = 1; w < VEC_THREADS / 32; ++w) t = mx ? fmax(t, sh[w][i]) : t + sh[w][i];
+      partials[blockIdx.x * NV + i] = t;
+    }
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // all of this thread's partials are loaded before any is used (L2 loads,
+  // in flight together), then combined in block order
+  constexpr int MAXP = 8;
+  double pv[MAXP][NV];
+#pragma unroll
+  for (int u = 0; u < MAXP; ++u) {
+    const int b = threadIdx.x + u * VEC_THREADS;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) pv[u][i] = b < (int)gridDim.x ? __ldcg(partials + b * NV + i) : 0.0;
+  }
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const bool mx = last_is_max && i == NV - 1;
+    acc[i] = 0.0;
+#pragma unroll
+    for (int u = 0; u < MAXP; ++u) acc[i] = mx ? fmax(acc[i], pv[u][i]) : acc[i] + pv[u][i];
+  }
+  for (int b = threadIdx.x + MAXP * VEC_THREADS; b < (int)gridDim.x; b += VEC_THREADS) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const bool mx = last_is_max && i == NV - 1;
+      const double q = __ldcg(partials + b * NV + i);
+      acc[i] = mx ? fmax(acc[i], q) : acc[i] + q;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const bool mx = last_is_max && i == NV - 1;
+    acc[i] = mx ? warp_max(acc[i]) : warp_sum(acc[i]);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[wid][i] = acc[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double fin[NV];
+    for (int i = 0; i < NV; ++i) {
+      const bool mx = last_is_max && i == NV - 1;
+      double t = sh[0][i];
+      for (int w = 1; w < VEC_THREADS / 32; ++w) t = mx ? fmax(t, sh[w][i]) : t + sh[w][i];
+      fin[i] = t;
+      if (i < nout) out[i] = t;
+    }
+    *counter = 0u;
+    if (po.kind != POST_NONE) run_post(po, fin);
+  }
+}
+
+template <int NV>
+__device__ inline void reduce_finish(double (&v)[NV], bool last_is_max, double* partials, unsigned int* counter,
+                                     double* out, int nout, const PostOp& po = PostOp()) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const bool mx = last_is_max && i == NV - 1;
+    v[i] = mx ? warp_max(v[i]) : warp_sum(v[i]);
+  }
+  reduce_tail<NV>(v, last_is_max, partials, counter, out, nout, po);
+}
+
+// The same from per-thread double-float sums (a max slot keeps its value in
+// hi), kept as float pairs through the block and grid levels; only the final
+// values become FP64 (thread 0 of the last block).  partials: 8 bytes per
+// value and block, as (hi, lo) float pairs.
+template <int NV>
+__device__ inline void df_block_sum(float (&hi)[NV], float (&lo)[NV], bool last_is_max) {
+  __shared__ float2 shp[VEC_THREADS / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    if (last_is_max && i == NV - 1) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) hi[i] = fmaxf(hi[i], __shfl_xor_sync(0xffffffffu, hi[i], o));
+      lo[i] = 0.f;
+    } else {
+      df_warp_sum(hi[i], lo[i]);
+    }
+    if (lane == 0) shp[wid][i] = make_float2(hi[i], lo[i]);
+  }
+  __syncthreads();
+  if (wid == 0) {  // warp 0 combines the warps' pairs (all lanes take part)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const float2 t = lane < VEC_THREADS / 32 ? shp[lane][i] : make_float2(0.f, 0.f);
+      hi[i] = t.x;
+      lo[i] = t.y;
+      if (last_is_max && i == NV - 1) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hi[i] = fmaxf(hi[i], __shfl_xor_sync(0xffffffffu, hi[i], o));
+      } else {
+        df_warp_sum(hi[i], lo[i]);
+      }
+    }
+  }
+}
+
+template <int NV>
+__device__ inline void reduce_finish_df(float (&hi)[NV], float (&lo)[NV], bool last_is_max, double* partials,
+                                        unsigned int* counter, double* out, int nout, const PostOp& po = PostOp()) {
+  __shared__ bool s_last;
+  float2* pp = reinterpret_cast<float2*>(partials);
+  df_block_sum<NV>(hi, lo, last_is_max);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) pp[blockIdx.x * NV + i] = make_float2(hi[i], lo[i]);
+    __threadfence();
+    s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    hi[i] = 0.f;
+    lo[i] = 0.f;
+  }
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += VEC_THREADS) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const float2 t = __ldcg(pp + b * NV + i);
+      if (last_is_max && i == NV - 1) {
+        hi[i] = fmaxf(hi[i], t.x);
+      } else {
+        lo[i] += t.y;
+        df_add(hi[i], lo[i], t.x);
+      }
+    }
+  }
+  __syncthreads();  // shared pairs of the first pass are read before they are reused
+  df_block_sum<NV>(hi, lo, last_is_max);
+  if (threadIdx.x == 0) {
+    double fin[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      fin[i] = (double)hi[i] + (double)lo[i];
+      if (i < nout) out[i] = fin[i];
+    }
+    *counter = 0u;
+    if (po.kind != POST_NONE) run_post(po, fin);
+  }
+}
+
+// scalar steps of the iteration (see PostOp); vals = the reduction's results
+__device__ inline void run_post(const PostOp& po, const double* vals) {
+  double* s = po.s;
+  int* f = po.f;
+  if (po.kind == POST_ALPHA) {  // vals[0] = p^T K p
+    const double pq = vals[0], zr = s[S_ZR];
+    if (!isfinite(pq) || !isfinite(zr)) {
+      f[F_REASON] |= R_NUMERIC;
+      f[F_PAUSE] = 1;
+    } else if (!(pq > 0.0) || !(zr > 0.0)) {
+      f[F_REASON] |= R_BREAKDOWN;
+      f[F_PAUSE] = 1;
+    } else {
+      s[S_ALPHA] = zr / pq;
+    }
+  } else if (po.kind == POST_CHECK) {  // vals[0] = ||r||^2
+    const int it = ++f[F_ITER];
+    const double rr = vals[0];
+    if (it < po.hist_cap) po.hist[it] = sqrt(rr / s[S_RR0]);
+    int reason = 0;
+    if (!isfinite(rr)) reason |= R_NUMERIC;
+    else if (rr <= s[S_TOL2]) reason |= R_CONV;
+    else if (s[S_DELTA2] > 0.0 && rr < s[S_DELTA2] * s[S_RMAX]) reason |= R_REPLACE;
+    if (it >= f[F_MAXIT]) reason |= R_MAXIT;
+    if (reason) {
+      f[F_REASON] |= reason;
+      f[F_PAUSE] = 1;
+    }
+  } else if (po.kind == POST_BETA) {  // vals[0] = z^T r, vals[1] = z^T r_old
+    const double zn = vals[0], zo = vals[1], zr = s[S_ZR];
+    if (!isfinite(zn) || !isfinite(zo)) {
+      f[F_REASON] |= R_NUMERIC;
+      f[F_PAUSE] = 1;
+    } else if (!(zn > 0.0)) {
+      f[F_REASON] |= R_BREAKDOWN;
+      f[F_PAUSE] = 1;
+    } else {
+      s[S_BETA] = f[F_FLEX] ? (zn - zo) / zr : zn / zr;
+      s[S_ZR] = zn;
+    }
+  }
+}
+
+}  // namespace kpv
