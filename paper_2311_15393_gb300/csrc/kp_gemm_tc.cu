@@ -361,9 +361,6 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
   }
-  KP_PDL_WAIT();
-  KP_PDL_TRIGGER();
-  if (p.flags && *(volatile const int*)p.flags) return;
   extern __shared__ unsigned char smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE);
@@ -400,8 +397,14 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int ksh = KIND == TC_E4M3 ? 0 : 1;  // K elements per 128-byte row: 128 >> ksh
+  // the prologue above overlaps the previous kernel; its results are needed from here on
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
+  const bool skip = p.flags && *(volatile const int*)p.flags;
 
-  if (warp == 0) {
+  if (skip) {
+    // paused: nothing to do but release TMEM below
+  } else if (warp == 0) {
     if (lane < 2) {
       // ---------------- TMA producer: lane 0 owns the barriers and loads the
       // A tile, lane 1 loads the B tile (both issued by one instruction)

@@ -26,6 +26,25 @@
 #include "kp_vec.cuh"
 
 
+namespace {
+// after a reliable update requested mid-run: record ||r_true|| in the
+// history and either resume (clear the pause) or stop as converged (the
+// true residual already meets the tolerance: F_REASON = R_CONV | R_TRUE)
+constexpr int R_TRUE = 32;
+__global__ void k_after_replace(double* s, int* f, double* hist, int hist_cap) {
+  const double rr = s[S_RR];
+  const int it = f[F_ITER];
+  if (it < hist_cap) hist[it] = sqrt(rr / s[S_RR0]);
+  if (rr <= s[S_TOL2]) {
+    f[F_REASON] = R_CONV | R_TRUE;
+    f[F_PAUSE] = 1;
+  } else {
+    f[F_REASON] = 0;
+    f[F_PAUSE] = 0;
+  }
+}
+}  // namespace
+
 struct SolveBufs {
   void *r, *r_old, *p, *q, *z, *rhs;
 };
@@ -235,6 +254,22 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
           kp_set_error("tik_pcg: breakdown (p^T K p <= 0 or z^T r <= 0) at iteration %d", iters);
           result = KP_EBREAKDOWN;
           break;
+        }
+        if (hf.reason & R_TRUE) {  // converged on a true residual computed without a host check
+          result = KP_OK;
+          break;
+        }
+        if (hf.reason == R_REPLACE) {
+          // reliable update in the middle of the run: replace, check and
+          // resume on the device, with no host round trip
+          KP_TRY(replace_residual(ctx, B, b, x, lam2));
+          ++repl;
+          k_after_replace<<<1, 1, 0, st>>>(ctx->dscal, ctx->dflags, ctx->hist, ctx->hist_cap);
+          KP_LAUNCHED(ctx);
+          KP_TRY(half_b(ctx, B, lam2));
+          cur = 0;
+          KP_TRY(launch_block(cur));
+          continue;
         }
         bool need_replace = reliable && (hf.reason & (R_CONV | R_REPLACE | R_MAXIT));
         if (need_replace) {
