@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=25)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--op", default="bf16", choices=["bf16", "bf16x3", "f32"])
@@ -160,10 +160,37 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def sources_digest():
+    """sha256 over the CUDA sources (names and contents, sorted)."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2311_15393_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def kapply_traffic(n, r):
+    """DRAM bytes of one K application from the committed ncu capture
+    (profiles/kapply_deblur1024_traffic.json), or None when the kernels have
+    changed since it was taken or the workload differs."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "kapply_deblur1024_traffic.json")) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("sources_sha256") != sources_digest() or t.get("n") != n or t.get("rank") != r:
+        return None
+    return t.get("dram_bytes_per_k_application")
+
+
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(P, iters_per_solve):
+def oracle_sample(P, iters_per_solve, k=3):
     """Bounded sample of the step on the host cores with the FP64 oracle:
-    setup, GCV lambda for one noise level, 3 FPCG iterations; extrapolated to
+    setup, GCV lambda for one noise level, k FPCG iterations; extrapolated to
     one step (setup + 2 x (lambda + iters_per_solve iterations))."""
     import numpy as np
     from oracle import forward, kpsvd as okp, kron, lam as olam, pcg as opcg
@@ -175,7 +202,6 @@ def oracle_sample(P, iters_per_solve):
     t2 = time.perf_counter()
     lam = olam.choose_lambda(kp, B, "gcv")
     t3 = time.perf_counter()
-    k = 3
     opcg.tik_pcg(op, kp, B, lam, 0.0, k, True)
     t4 = time.perf_counter()
     t_setup, t_lam, t_it = t1 - t0, t3 - t2, (t4 - t3) / (k + 1)  # + A^T b and z0 ~ one iteration
@@ -388,12 +414,15 @@ def run_ours(args, ws, rank, local, dist):
                                  f"{it64} iterations and scaled to the iteration count of the mixed solve"}
             ctx64.close()
 
-    # roofline of the operator GEMMs (dominant in the solve): 2 M N K flops each
+    # roofline of the dominant kernel family, the operator's tcgen05 GEMMs, per
+    # K application (4 GEMMs of 2 (r n_r) n_c n_r flops each, with the two term
+    # sums and the bf16 split of p that belong to one application)
     r = P.op_rank
-    flops_kapply = 4 * 2.0 * r * n_r * n_r * n_c   # G1..G4: 2 (r n_r) n_c n_r each (square: 8 r n^3)
+    flops_kapply = 4 * 2.0 * r * n_r * n_r * n_c
     pk_, how = peaks()
-    peak_tf = pk_.get("bf16_tflops")   # burst figure: the GEMMs are timed alone
+    peak_tf = pk_.get("bf16_tflops")   # burst figure: the K application is timed alone
     achieved = flops_kapply / (kapply_ms * 1e-3) / 1e12
+    traffic = kapply_traffic(n_r, r)
     last = infos[-1]
     result = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -406,10 +435,12 @@ def run_ours(args, ws, rank, local, dist):
                    "step": "kp_setup + 2 x (choose_lambda GCV + tik_pcg FPCG)"},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "operator GEMMs (tcgen05 bf16, 4 per K application)", "bound": "tensor",
-                     "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved / peak_tf,
-                     "traffic": None, "peak_source": how + " bf16_tflops (burst)",
-                     "flops_per_launch": flops_kapply / 4, "ms_per_launch": kapply_ms / 4},
+        "roofline": {"kernel": "K application: 4 tcgen05 BF16 GEMMs (+2 FP32 term sums, 1 bf16 split of p)",
+                     "bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tf, "traffic": traffic,
+                     "peak_source": how + " bf16_tflops (burst)",
+                     "flops_per_launch": flops_kapply, "ms_per_launch": kapply_ms,
+                     "launch": "one K application (7 kernels)"},
         "clocks": clk,
         "phases_ms": {k: (statistics.mean(v) if v else None) for k, v in phase.items()},
         "solves": [{"lambda": lam, "iters": inf.iters, "replacements": inf.replacements,
@@ -420,12 +451,13 @@ def run_ours(args, ws, rank, local, dist):
     ctx.close()
     if rank == 0 and not args.no_cpu_baseline:
         iters = max(inf.iters for _, inf in last)
-        smp = oracle_sample(P, iters)
+        k_cpu = 100
+        smp = oracle_sample(P, iters, k_cpu)
         result["cpu_baseline"] = {"value": 2.0 / smp["step_s"], "unit": "solves/s", "cores": blas_threads(),
                                   "kind": "oracle",
-                                  "sample": "FP64 oracle setup + GCV lambda (one noise level) + 3 FPCG iterations "
-                                            f"({smp['sample_s']:.1f} s), extrapolated to setup + 2 x (lambda + "
-                                            f"{iters} iterations)"}
+                                  "sample": f"FP64 oracle setup + GCV lambda (one noise level) + {k_cpu} FPCG "
+                                            f"iterations ({smp['sample_s']:.1f} s), extrapolated to setup + 2 x "
+                                            f"(lambda + {iters} iterations)"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0
