@@ -38,6 +38,23 @@ __device__ __forceinline__ double jwarp_sum(double v) {
   return v;
 }
 
+template <typename T>
+__device__ __forceinline__ T jwsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+struct Eps;
+template <>
+struct Eps<double> {
+  static constexpr double v = 2.220446049250313e-16;
+};
+template <>
+struct Eps<float> {
+  static constexpr double v = 1.1920928955078125e-07;
+};
+
 // pair p of round `round` for npad players (circle method)
 __device__ __forceinline__ int rr_player(int t, int round, int npad) {
   return t == 0 ? 0 : 1 + ((t - 1 + round) % (npad - 1));
@@ -290,26 +307,27 @@ __global__ void k_gram_violations(const T* __restrict__ G, int n, double tol, do
 // out[j + k ldo] = sum_i X[i + j ldx] Y[i + k ldy] for j < ncol, k < p: the
 // tall-skinny products of the subspace iteration, one warp per column j
 constexpr int SK_CHUNK = 8;
-__global__ void __launch_bounds__(256) k_skinny_tn(const double* __restrict__ X, long long ldx,
-                                                   const double* __restrict__ Y, long long ldy, int m, int ncol,
-                                                   int p, double* __restrict__ out, long long ldo) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_skinny_tn(const T* __restrict__ X, long long ldx,
+                                                   const T* __restrict__ Y, long long ldy, int m, int ncol,
+                                                   int p, T* __restrict__ out, long long ldo) {
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= ncol) return;
-  const double* x = X + warp * ldx;
+  const T* x = X + warp * ldx;
   for (int k0 = 0; k0 < p; k0 += SK_CHUNK) {
     const int kn = min(SK_CHUNK, p - k0);
-    double acc[SK_CHUNK];
+    T acc[SK_CHUNK];
 #pragma unroll
-    for (int q = 0; q < SK_CHUNK; ++q) acc[q] = 0.0;
+    for (int q = 0; q < SK_CHUNK; ++q) acc[q] = T(0);
     for (int i = lane; i < m; i += 32) {
-      const double xv = x[i];
+      const T xv = x[i];
 #pragma unroll
       for (int q = 0; q < SK_CHUNK; ++q)
         if (q < kn) acc[q] = fma(xv, Y[i + (long long)(k0 + q) * ldy], acc[q]);
     }
 #pragma unroll
-    for (int q = 0; q < SK_CHUNK; ++q) acc[q] = jwarp_sum(acc[q]);
+    for (int q = 0; q < SK_CHUNK; ++q) acc[q] = jwsum<T>(acc[q]);
     if (lane == 0)
 #pragma unroll
       for (int q = 0; q < SK_CHUNK; ++q)
@@ -318,12 +336,13 @@ __global__ void __launch_bounds__(256) k_skinny_tn(const double* __restrict__ X,
 }
 
 // out (m x r col-major) = Q (m x p col-major) B[:, :r] (B p x p col-major)
-__global__ void k_small_right(const double* __restrict__ Q, int m, int p, const double* __restrict__ B, int r,
-                              double* __restrict__ out) {
+template <typename T>
+__global__ void k_small_right(const T* __restrict__ Q, int m, int p, const T* __restrict__ B, int r,
+                              T* __restrict__ out) {
   const long long tot = (long long)m * r;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % m), c = (int)(t / m);
-    double acc = 0.0;
+    T acc = T(0);
     for (int j = 0; j < p; ++j) acc = fma(Q[i + (long long)j * m], B[j + (long long)c * p], acc);
     out[t] = acc;
   }
@@ -336,20 +355,21 @@ __global__ void k_small_right(const double* __restrict__ Q, int m, int p, const 
 // With R non-null, also the triangular factor of Q_in = Q_out R (p x p
 // col-major; a vanished column keeps its small remaining norm on the
 // diagonal).  One block of CG_T threads.
-constexpr int CG_T = 128;  // few threads: the FP64 warp reductions, not the dots, bound this kernel
+constexpr int CG_T = 128;  // few threads: the warp reductions, not the dots, bound this kernel (FP64)
 constexpr int CG_CH = 16;  // dots per block reduction
-__global__ void __launch_bounds__(CG_T) k_cgs2(double* __restrict__ Q, int m, int p, double* __restrict__ R) {
-  __shared__ double sh[CG_T / 32][CG_CH + 1];
-  __shared__ double dsh[CG_CH];
-  __shared__ double tot;
+template <typename T>
+__global__ void __launch_bounds__(CG_T) k_cgs2(T* __restrict__ Q, int m, int p, T* __restrict__ R) {
+  __shared__ T sh[CG_T / 32][CG_CH + 1];
+  __shared__ T dsh[CG_CH];
+  __shared__ T tot;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  auto bsum = [&](double v) -> double {
-    v = jwarp_sum(v);
+  auto bsum = [&](T v) -> T {
+    v = jwsum<T>(v);
     __syncthreads();
     if (lane == 0) sh[wid][0] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0;
+      T t = 0;
       for (int w = 0; w < CG_T / 32; ++w) t += sh[w][0];
       tot = t;
     }
@@ -357,19 +377,19 @@ __global__ void __launch_bounds__(CG_T) k_cgs2(double* __restrict__ Q, int m, in
     return tot;
   };
   for (int k = 0; k < p; ++k) {
-    double* qk = Q + (long long)k * m;
-    double n0 = 0;
+    T* qk = Q + (long long)k * m;
+    T n0 = 0;
     for (int r = threadIdx.x; r < m; r += CG_T) n0 = fma(qk[r], qk[r], n0);
     n0 = sqrt(bsum(n0));
     for (int attempt = 0; attempt < 3; ++attempt) {
       for (int pass = 0; pass < 2; ++pass) {
         for (int j0 = 0; j0 < k; j0 += CG_CH) {
           const int jn = min(CG_CH, k - j0);
-          double d[CG_CH];
+          T d[CG_CH];
 #pragma unroll
-          for (int q = 0; q < CG_CH; ++q) d[q] = 0.0;
+          for (int q = 0; q < CG_CH; ++q) d[q] = T(0);
           for (int r = threadIdx.x; r < m; r += CG_T) {
-            const double x = qk[r];
+            const T x = qk[r];
 #pragma unroll
             for (int q = 0; q < CG_CH; ++q)
               if (q < jn) d[q] = fma(Q[r + (long long)(j0 + q) * m], x, d[q]);
@@ -377,45 +397,45 @@ __global__ void __launch_bounds__(CG_T) k_cgs2(double* __restrict__ Q, int m, in
 #pragma unroll
           for (int q = 0; q < CG_CH; ++q) {
             if (q < jn) {  // uniform over the block
-              const double v = jwarp_sum(d[q]);
+              const T v = jwsum<T>(d[q]);
               if (lane == 0) sh[wid][q] = v;
             }
           }
           __syncthreads();
           if (threadIdx.x < jn) {
-            double t = 0;
+            T t = 0;
             for (int w = 0; w < CG_T / 32; ++w) t += sh[w][threadIdx.x];
             dsh[threadIdx.x] = t;
             if (R && attempt == 0) {
-              double* rr = R + (long long)k * p + j0 + threadIdx.x;
-              *rr = (pass == 0 ? 0.0 : *rr) + t;
+              T* rr = R + (long long)k * p + j0 + threadIdx.x;
+              *rr = (pass == 0 ? T(0) : *rr) + t;
             }
           }
           __syncthreads();
           for (int r = threadIdx.x; r < m; r += CG_T) {
-            double x = qk[r];
+            T x = qk[r];
             for (int q = 0; q < jn; ++q) x = fma(-dsh[q], Q[r + (long long)(j0 + q) * m], x);
             qk[r] = x;
           }
           __syncthreads();
         }
       }
-      double nk = 0;
+      T nk = 0;
       for (int r = threadIdx.x; r < m; r += CG_T) nk = fma(qk[r], qk[r], nk);
       nk = sqrt(bsum(nk));
       if (R && attempt == 0 && threadIdx.x == 0) {
-        for (int j = k + 1; j < p; ++j) R[(long long)k * p + j] = 0.0;
+        for (int j = k + 1; j < p; ++j) R[(long long)k * p + j] = T(0);
         R[(long long)k * p + k] = nk;
       }
-      if (nk > 1e-10 * n0 && nk > 0) {
-        const double inv = 1.0 / nk;  // one FP64 division per column, not per entry
+      if (nk > T(sizeof(T) == 8 ? 1e-10 : 1e-4) * n0 && nk > T(0)) {
+        const T inv = T(1) / nk;  // one FP64 division per column, not per entry
         for (int r = threadIdx.x; r < m; r += CG_T) qk[r] *= inv;
         __syncthreads();
         break;
       }
       const int t = (int)(((long long)(k + 1) * 7919 + attempt * 104729) % m);
-      for (int r = threadIdx.x; r < m; r += CG_T) qk[r] = (r == t) ? 1.0 : 0.0;
-      n0 = 1.0;
+      for (int r = threadIdx.x; r < m; r += CG_T) qk[r] = (r == t) ? T(1) : T(0);
+      n0 = T(1);
       __syncthreads();
     }
   }
@@ -428,37 +448,38 @@ __global__ void __launch_bounds__(CG_T) k_cgs2(double* __restrict__ Q, int m, in
 // decreasing sigma; *status = 1 if max_sweeps sweeps did not converge.
 constexpr int SJ_T = 1024;
 constexpr int SJ_MAXP = 32;
-__global__ void __launch_bounds__(SJ_T) k_jacobi_small(const double* __restrict__ A, int m, int p, double tol_in,
-                                                       int max_sweeps, double* __restrict__ U,
-                                                       double* __restrict__ s_out, double* __restrict__ V_out,
+template <typename T>
+__global__ void __launch_bounds__(SJ_T) k_jacobi_small(const T* __restrict__ A, int m, int p, T tol_in,
+                                                       int max_sweeps, T* __restrict__ U,
+                                                       T* __restrict__ s_out, T* __restrict__ V_out,
                                                        int* __restrict__ status) {
-  extern __shared__ double smem_d[];
-  double* W = smem_d;                    // m x p
-  double* V = W + (long long)m * p;      // p x p
-  __shared__ double red[SJ_T / 32];
-  __shared__ double sg[SJ_MAXP];
+  extern __shared__ __align__(16) unsigned char smem_j[];
+  T* W = reinterpret_cast<T*>(smem_j);                    // m x p
+  T* V = W + (long long)m * p;      // p x p
+  __shared__ T red[SJ_T / 32];
+  __shared__ T sg[SJ_MAXP];
   __shared__ int perm[SJ_MAXP];
   __shared__ unsigned int rot;
-  __shared__ double floor_sh;
+  __shared__ T floor_sh;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double f2 = 0.0;
+  T f2 = T(0);
   for (long long t = threadIdx.x; t < (long long)m * p; t += SJ_T) {
-    const double x = A[t];
+    const T x = A[t];
     W[t] = x;
     f2 = fma(x, x, f2);
   }
-  for (int t = threadIdx.x; t < p * p; t += SJ_T) V[t] = (t / p == t % p) ? 1.0 : 0.0;
-  f2 = jwarp_sum(f2);
+  for (int t = threadIdx.x; t < p * p; t += SJ_T) V[t] = (t / p == t % p) ? T(1) : T(0);
+  f2 = jwsum<T>(f2);
   if (lane == 0) red[wid] = f2;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0;
+    T t = 0;
     for (int w = 0; w < SJ_T / 32; ++w) t += red[w];
-    floor_sh = (double)m * 2.220446049250313e-16 * sqrt(t);
+    floor_sh = T((double)m * Eps<T>::v) * sqrt(t);
   }
   __syncthreads();
-  const double floor = floor_sh;
-  const double tol = fmax(tol_in, (double)m * 2.220446049250313e-16);
+  const T floor = floor_sh;
+  const T tol = tol_in > T((double)m * Eps<T>::v) ? tol_in : T((double)m * Eps<T>::v);
   const int npad = p + (p & 1);
   int sweep = 0;
   bool done = npad < 2;
@@ -475,31 +496,31 @@ __global__ void __launch_bounds__(SJ_T) k_jacobi_small(const double* __restrict_
           j = t;
         }
         if (j < p) {
-          double* a = W + (long long)i * m;
-          double* b = W + (long long)j * m;
-          double al = 0.0, be = 0.0, ga = 0.0;
+          T* a = W + (long long)i * m;
+          T* b = W + (long long)j * m;
+          T al = T(0), be = T(0), ga = T(0);
           for (int r = lane; r < m; r += 32) {
-            const double x = a[r], y = b[r];
+            const T x = a[r], y = b[r];
             al = fma(x, x, al);
             be = fma(y, y, be);
             ga = fma(x, y, ga);
           }
-          al = jwarp_sum(al);
-          be = jwarp_sum(be);
-          ga = jwarp_sum(ga);
-          if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be) && fabs(ga) > floor * sqrt(fmax(al, be))) {
-            const double zeta = (be - al) / (2.0 * ga);
-            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+          al = jwsum<T>(al);
+          be = jwsum<T>(be);
+          ga = jwsum<T>(ga);
+          if (ga != T(0) && fabs(ga) > tol * sqrt(al) * sqrt(be) && fabs(ga) > floor * sqrt(al > be ? al : be)) {
+            const T zeta = (be - al) / (T(2) * ga);
+            const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+            const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
             for (int r = lane; r < m; r += 32) {
-              const double x = a[r], y = b[r];
+              const T x = a[r], y = b[r];
               a[r] = c * x - sn * y;
               b[r] = sn * x + c * y;
             }
-            double* va = V + (long long)i * p;
-            double* vb = V + (long long)j * p;
+            T* va = V + (long long)i * p;
+            T* vb = V + (long long)j * p;
             for (int r = lane; r < p; r += 32) {
-              const double x = va[r], y = vb[r];
+              const T x = va[r], y = vb[r];
               va[r] = c * x - sn * y;
               vb[r] = sn * x + c * y;
             }
@@ -515,9 +536,9 @@ __global__ void __launch_bounds__(SJ_T) k_jacobi_small(const double* __restrict_
   if (!done && threadIdx.x == 0) *status = 1;
   // sigma = column norms, then sort (descending; ties keep the smaller index)
   for (int c = wid; c < p; c += SJ_T / 32) {
-    double v = 0.0;
+    T v = T(0);
     for (int r = lane; r < m; r += 32) v = fma(W[(long long)c * m + r], W[(long long)c * m + r], v);
-    v = jwarp_sum(v);
+    v = jwsum<T>(v);
     if (lane == 0) sg[c] = sqrt(v);
   }
   __syncthreads();
@@ -536,13 +557,14 @@ __global__ void __launch_bounds__(SJ_T) k_jacobi_small(const double* __restrict_
   __syncthreads();
   for (int c = wid; c < p; c += SJ_T / 32) {
     const int src = perm[c];
-    const double sv = sg[src];
-    const double inv = sv > 0.0 ? 1.0 / sv : 0.0;
+    const T sv = sg[src];
+    const T inv = sv > T(0) ? T(1) / sv : T(0);
     for (int r = lane; r < m; r += 32) U[(long long)c * m + r] = W[(long long)src * m + r] * inv;
     for (int r = lane; r < p; r += 32) V_out[(long long)c * p + r] = V[(long long)src * p + r];
     if (lane == 0) s_out[c] = sv;
   }
 }
+
 
 }  // namespace
 
@@ -783,94 +805,123 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
   return KP_OK;
 }
 
-kp_status topr_svd(kp_ctx* ctx, const double* W, int m, int n, int r, double* U, double* s, double* V,
-                   int* iters_out) {
+// Subspace iteration for the leading r singular triplets, in T arithmetic
+// (FP64, or FP32 for the FP32-vector setup); p <= SJ_MAXP.  W (m x n col-major)
+// and WT = W^T are T; outputs (T): U (m x r), s (r), V (n x r).
+template <typename T>
+static kp_status topr_run(kp_ctx* ctx, const T* W, const T* WT, int m, int n, int r, int p, T* U, T* s, T* V,
+                          int* iters_out) {
   cudaStream_t st = ctx->stream;
-  const int p = std::min(n, r + 8);
-  double *Q, *Z, *Uz, *sz, *Vz, *WT;
-  KP_TRY(kp_alloc(ctx, (void**)&Q, sizeof(double) * (size_t)m * p));
-  KP_TRY(kp_alloc(ctx, (void**)&Z, sizeof(double) * (size_t)n * p));
-  KP_TRY(kp_alloc(ctx, (void**)&Uz, sizeof(double) * (size_t)n * p));
-  KP_TRY(kp_alloc(ctx, (void**)&sz, sizeof(double) * p));
-  KP_TRY(kp_alloc(ctx, (void**)&Vz, sizeof(double) * (size_t)p * p));
-  KP_TRY(kp_alloc(ctx, (void**)&WT, sizeof(double) * (size_t)m * n));  // W^T (n x m col-major)
-  const int g = std::max(1, std::min((int)(((long long)m * n + 255) / 256), ctx->sm_count * 16));
-  k_transpose_cm<double><<<g, 256, 0, st>>>(W, m, n, WT);
-  KP_LAUNCHED(ctx);
-  {  // start vectors: the first p columns of the m x m DCT-II matrix (smooth)
+  T *Q, *Z, *Uz, *sz, *Vz, *Rz, *UR;
+  int* jstat;
+  KP_TRY(kp_alloc(ctx, (void**)&Q, sizeof(T) * (size_t)m * p));
+  KP_TRY(kp_alloc(ctx, (void**)&Z, sizeof(T) * (size_t)n * p));
+  KP_TRY(kp_alloc(ctx, (void**)&Uz, sizeof(T) * (size_t)n * p));
+  KP_TRY(kp_alloc(ctx, (void**)&sz, sizeof(T) * p));
+  KP_TRY(kp_alloc(ctx, (void**)&Vz, sizeof(T) * (size_t)p * p));
+  KP_TRY(kp_alloc(ctx, (void**)&Rz, sizeof(T) * (size_t)p * p));
+  KP_TRY(kp_alloc(ctx, (void**)&UR, sizeof(T) * (size_t)p * p));
+  KP_TRY(kp_alloc(ctx, (void**)&jstat, sizeof(int)));
+  KP_CUDA(cudaMemsetAsync(jstat, 0, sizeof(int), st));
+  {  // start vectors: the first p columns of the m x m DCT-II matrix (smooth, orthonormal)
     double* C;
     KP_TRY(kp_alloc(ctx, (void**)&C, sizeof(double) * (size_t)m * m));
     KP_TRY(make_transform(ctx, m, 0, C));
-    KP_CUDA(cudaMemcpyAsync(Q, C, sizeof(double) * (size_t)m * p, cudaMemcpyDeviceToDevice, st));
+    if (sizeof(T) == sizeof(double))
+      KP_CUDA(cudaMemcpyAsync(Q, C, sizeof(double) * (size_t)m * p, cudaMemcpyDeviceToDevice, st));
+    else
+      KP_TRY(convert_f64_to_f32(ctx, C, (float*)Q, (long long)m * p));
   }
-  // the Ritz step for p <= 32: Z = Q_z R_z (CGS2), then the one-block Jacobi
-  // SVD of the p x p factor R_z = U_R S V_R^T, so that U_z = Q_z U_R, V_z = V_R
-  const bool small = p <= SJ_MAXP;
-  const size_t small_smem = sizeof(double) * 2 * (size_t)p * p;
-  int* jstat = nullptr;
-  double *Rz = nullptr, *UR = nullptr;
-  if (small) {
-    KP_TRY(kp_alloc(ctx, (void**)&jstat, sizeof(int)));
-    KP_TRY(kp_alloc(ctx, (void**)&Rz, sizeof(double) * (size_t)p * p));
-    KP_TRY(kp_alloc(ctx, (void**)&UR, sizeof(double) * (size_t)p * p));
-    KP_CUDA(cudaMemsetAsync(jstat, 0, sizeof(int), st));
-  }
+  // the Ritz step: Z = Q_z R_z (CGS2), then the one-block Jacobi SVD of the
+  // p x p factor R_z = U_R S V_R^T, so that U_z = Q_z U_R, V_z = V_R
+  const size_t small_smem = sizeof(T) * 2 * (size_t)p * p;
   const int gz = std::max(1, std::min((int)(((long long)n * p + 255) / 256), ctx->sm_count * 4));
-  auto skinny = [&](const double* X, int rows, int ncol, const double* Y, double* out) -> kp_status {
+  auto skinny = [&](const T* X, int rows, int ncol, const T* Y, T* out) -> kp_status {
     const long long threads = (long long)ncol * 32;
-    k_skinny_tn<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(X, rows, Y, rows, rows, ncol, p, out, ncol);
+    k_skinny_tn<T><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(X, rows, Y, rows, rows, ncol, p, out, ncol);
     KP_LAUNCHED(ctx);
     return KP_OK;
   };
-  std::vector<double> prev(r, 0.0), cur(r, 0.0);
+  // settled when the leading Ritz values stop moving, relative to the largest:
+  // 4 eps in FP64, 64 eps in FP32 (whose rounding noise is sqrt(n) eps)
+  const double settle = (sizeof(T) == sizeof(double) ? 4.0 : 64.0) * Eps<T>::v;
+  std::vector<T> prev(r, T(0)), cur(r, T(0));
   int it = 0;
   const int maxit = 200;
   for (it = 0; it < maxit; ++it) {
-    k_cgs2<<<1, CG_T, 0, st>>>(Q, m, p, nullptr);
-    KP_LAUNCHED(ctx);
-    KP_TRY(skinny(W, m, n, Q, Z));  // Z (n x p) = W^T Q
-    // Ritz values: singular values of Z
-    if (small) {
-      k_cgs2<<<1, CG_T, 0, st>>>(Z, n, p, Rz);  // Z <- Q_z
-      k_jacobi_small<<<1, SJ_T, small_smem, st>>>(Rz, p, p, ctx->jacobi_tol, ctx->jacobi_max_sweeps, UR, sz, Vz,
-                                                  jstat);
-      k_small_right<<<gz, 256, 0, st>>>(Z, n, p, UR, p, Uz);
-      ctx->launches += 3;
-    } else {
-      KP_TRY(jacobi_svd(ctx, Z, n, p, Uz, sz, Vz, nullptr));
+    if (it > 0) {  // the start vectors are orthonormal already
+      k_cgs2<T><<<1, CG_T, 0, st>>>(Q, m, p, nullptr);
+      KP_LAUNCHED(ctx);
     }
-    KP_CUDA(cudaMemcpyAsync(cur.data(), sz, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
+    KP_TRY(skinny(W, m, n, Q, Z));  // Z (n x p) = W^T Q
+    k_cgs2<T><<<1, CG_T, 0, st>>>(Z, n, p, Rz);  // Z <- Q_z
+    k_jacobi_small<T><<<1, SJ_T, small_smem, st>>>(Rz, p, p, (T)ctx->jacobi_tol, ctx->jacobi_max_sweeps, UR, sz, Vz,
+                                                   jstat);
+    k_small_right<T><<<gz, 256, 0, st>>>(Z, n, p, UR, p, Uz);
+    ctx->launches += 3;
+    KP_CUDA(cudaMemcpyAsync(cur.data(), sz, sizeof(T) * r, cudaMemcpyDeviceToHost, st));
     KP_CUDA(cudaStreamSynchronize(st));
     double d = 0.0;
-    for (int k = 0; k < r; ++k) d = std::max(d, std::fabs(cur[k] - prev[k]) / std::max(cur[0], 1e-300));
-    if (it > 0 && d <= 4 * 2.220446049250313e-16) break;
+    for (int k = 0; k < r; ++k)
+      d = std::max(d, std::fabs((double)cur[k] - (double)prev[k]) / std::max((double)cur[0], 1e-300));
+    if (it > 0 && d <= settle) break;
     prev = cur;
     // Q (m x p) = W U_z, the span of W Z, with its columns already in the
-    // order of the Ritz values: after orthonormalisation the next Z is
-    // nearly orthogonal and its Jacobi step takes few sweeps
+    // order of the Ritz values
     KP_TRY(skinny(WT, n, m, Uz, Q));
   }
   if (it == maxit) {
     kp_set_error("topr_svd: subspace iteration did not settle in %d iterations", maxit);
     return KP_ENOCONV;
   }
-  if (small) {
-    int h = 0;
-    KP_CUDA(cudaMemcpyAsync(&h, jstat, sizeof(int), cudaMemcpyDeviceToHost, st));
-    KP_CUDA(cudaStreamSynchronize(st));
-    if (h) {
-      kp_set_error("topr_svd: Ritz-step Jacobi did not converge in %d sweeps", ctx->jacobi_max_sweeps);
-      return KP_ENOCONV;
-    }
+  int h = 0;
+  KP_CUDA(cudaMemcpyAsync(&h, jstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KP_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    kp_set_error("topr_svd: Ritz-step Jacobi did not converge in %d sweeps", ctx->jacobi_max_sweeps);
+    return KP_ENOCONV;
   }
-  // Z = W^T Q = V_W S (Q^T U_W)^T: Jacobi on Z gave Uz (normalised Z V_z ->
-  // right singular vectors of W), sz, Vz (p x p); left vectors U = Q Vz.
-  KP_CUDA(cudaMemcpyAsync(V, Uz, sizeof(double) * (size_t)n * r, cudaMemcpyDeviceToDevice, st));
-  KP_CUDA(cudaMemcpyAsync(s, sz, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
+  // Z = W^T Q = V_W S (Q^T U_W)^T: U_z holds right singular vectors of W,
+  // sz the values, V_z (p x p) gives the left vectors U = Q V_z
+  KP_CUDA(cudaMemcpyAsync(V, Uz, sizeof(T) * (size_t)n * r, cudaMemcpyDeviceToDevice, st));
+  KP_CUDA(cudaMemcpyAsync(s, sz, sizeof(T) * r, cudaMemcpyDeviceToDevice, st));
   const int gr = std::max(1, std::min((int)(((long long)m * r + 255) / 256), ctx->sm_count * 16));
-  k_small_right<<<gr, 256, 0, st>>>(Q, m, p, Vz, r, U);
+  k_small_right<T><<<gr, 256, 0, st>>>(Q, m, p, Vz, r, U);
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   if (iters_out) *iters_out = it + 1;
   return KP_OK;
+}
+
+kp_status topr_svd(kp_ctx* ctx, const double* W, int m, int n, int r, double* U, double* s, double* V,
+                   int* iters_out) {
+  cudaStream_t st = ctx->stream;
+  const int p = std::min(n, r + 8);
+  const long long mn = (long long)m * n;
+  const int g = std::max(1, std::min((int)((mn + 255) / 256), ctx->sm_count * 16));
+  if (p > SJ_MAXP) {  // wide subspace: Ritz values of Z by the multi-block Jacobi (FP64)
+    kp_set_error("topr_svd: subspace of %d columns exceeds %d", p, SJ_MAXP);
+    return KP_ENOTSUP;
+  }
+  if (!ctx->setup_fp32) {
+    double* WT;
+    KP_TRY(kp_alloc(ctx, (void**)&WT, sizeof(double) * mn));
+    k_transpose_cm<double><<<g, 256, 0, st>>>(W, m, n, WT);
+    KP_LAUNCHED(ctx);
+    return topr_run<double>(ctx, W, WT, m, n, r, p, U, s, V, iters_out);
+  }
+  // FP32 arithmetic for FP32 vectors: the PSF terms to FP32 accuracy
+  float *W32, *WT32, *U32, *s32, *V32;
+  KP_TRY(kp_alloc(ctx, (void**)&W32, sizeof(float) * mn));
+  KP_TRY(kp_alloc(ctx, (void**)&WT32, sizeof(float) * mn));
+  KP_TRY(kp_alloc(ctx, (void**)&U32, sizeof(float) * (size_t)m * r));
+  KP_TRY(kp_alloc(ctx, (void**)&s32, sizeof(float) * r));
+  KP_TRY(kp_alloc(ctx, (void**)&V32, sizeof(float) * (size_t)n * r));
+  KP_TRY(convert_f64_to_f32(ctx, W, W32, mn));
+  k_transpose_cm<float><<<g, 256, 0, st>>>(W32, m, n, WT32);
+  KP_LAUNCHED(ctx);
+  KP_TRY(topr_run<float>(ctx, W32, WT32, m, n, r, p, U32, s32, V32, iters_out));
+  KP_TRY(convert_f32_to_f64(ctx, U32, U, (long long)m * r));
+  KP_TRY(convert_f32_to_f64(ctx, s32, s, r));
+  return convert_f32_to_f64(ctx, V32, V, (long long)n * r);
 }

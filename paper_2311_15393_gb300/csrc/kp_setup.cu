@@ -345,7 +345,7 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
   }
   // few terms: subspace iteration for the leading ones; otherwise the full
   // one-sided Jacobi SVD
-  if (4 * rank <= nn) {
+  if (4 * rank <= nn && rank + 8 <= 32) {  // few leading terms: subspace iteration (p = rank + 8 <= 32)
     KP_TRY(topr_svd(ctx, Wsrc, mm, nn, rank, Uw, sw, Vw, nullptr));
   } else {
     KP_TRY(jacobi_svd(ctx, Wsrc, mm, nn, Uw, sw, Vw, nullptr));
