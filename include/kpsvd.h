@@ -210,7 +210,7 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *   "reliable_delta"  factor by which ||r|| must fall before a reliable
  *                     residual update (default 0.1 for F32 / BF16 / BF16X3
  *                     operators, 0 = off for the F64 operator)
- *   "check_every"     iterations between host convergence checks (default 4)
+ *   "check_every"     iterations between host convergence checks (default 2)
  *   "jacobi_tol"      one-sided Jacobi rotation threshold (default 1e-15)
  *   "jacobi_max_sweeps" (default 40)
  *   "splitk"          > 0: fixed split-K factor of the square tensor-core
@@ -218,6 +218,8 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *   "tc_bn"           64, 128 or 256: fixed tensor-core tile width (default 0 =
  *                     chosen per shape)
  *   "tc_ctas_per_sm"  1 or 2: fixed CTAs per SM for 128-wide tiles (default 0)
+ *   "tc_kblocks_per_stage" 1 or 2: k-blocks per shared-memory ring stage
+ *                     (default 0 = 2, or 1 with two CTAs per SM)
  *                     The three tile options take effect at the next kp_setup.
  *   "pdl"             0: launch the iteration's kernels without programmatic
  *                     dependent launch (default 1: each kernel's launch and

@@ -223,6 +223,8 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
     ctx->pdl = value != 0.0;
   } else if (!strcmp(name, "tc_bn")) {
     ctx->tc_bn_override = (int)value;
+  } else if (!strcmp(name, "tc_kblocks_per_stage")) {
+    ctx->tc_kps_override = (int)value;
   } else if (!strcmp(name, "tc_ctas_per_sm")) {
     ctx->tc_cps_override = (int)value;
   } else if (!strcmp(name, "setup_fp64")) {

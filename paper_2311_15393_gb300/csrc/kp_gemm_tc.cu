@@ -44,16 +44,20 @@ constexpr int TC_THREADS = 192;
 //   the other's main loop)            BN 64, 1 CTA/SM: 8 x 24 KiB
 // Narrow tiles give the square n x n products enough tiles to occupy the
 // SMs without splitting K (split-K partials cost more than they save here).
-template <int BN, int CPS>
+// A ring stage holds KPS k-blocks (each an A and a B tile of 128-byte rows):
+// the producer and MMA threads pay their per-stage costs (barrier waits,
+// commits, loop control) once per KPS k-blocks.
+template <int BN, int CPS, int KPS = 1>
 struct TcCfg {
   static_assert(CPS == 1 || (CPS == 2 && BN <= 128), "TMEM holds 2 x BN columns per CTA");
   static constexpr int A_BYTES = TBM * 128;
   static constexpr int B_BYTES = BN * 128;
-  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int KB_BYTES = A_BYTES + B_BYTES;  // one k-block
+  static constexpr int STAGE = KPS * KB_BYTES;
   static constexpr int STAGES = (196608 / CPS) / STAGE;
-  static constexpr int CTAS_PER_SM = CPS;
   static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 512 /*barriers*/;
   static constexpr int TMEM_COLS = 2 * BN;
+  static_assert(STAGES >= 2, "ring too shallow");
 };
 
 struct TcParams {
@@ -353,10 +357,10 @@ __device__ __forceinline__ Unit decode_unit(const TcParams& p, int u, int bn) {
   return r;
 }
 
-template <int KIND, int BN, int CPS>
+template <int KIND, int BN, int CPS, int KPS>
 __global__ void __launch_bounds__(TC_THREADS, CPS)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
-  using C = TcCfg<BN, CPS>;
+  using C = TcCfg<BN, CPS, KPS>;
   if (threadIdx.x == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
@@ -405,44 +409,46 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
   if (skip) {
     // paused: nothing to do but release TMEM below
   } else if (warp == 0) {
-    if (lane < 2) {
-      // ---------------- TMA producer: lane 0 owns the barriers and loads the
-      // A tile, lane 1 loads the B tile (both issued by one instruction)
-      const CUtensorMap* map = lane == 0 ? &tmA : &tmB;
+    if (lane < 2 * KPS) {
+      // ---------------- TMA producer: lane 2q loads the A tile, lane 2q + 1
+      // the B tile of k-block q of the stage (all issued by one instruction);
+      // lane 0 owns the barriers
+      const bool isB = lane & 1;
+      const int q = lane >> 1;
+      const CUtensorMap* map = isB ? &tmB : &tmA;
       const int nk = p.batch_rows ? 1 : p.nkron;
+      const unsigned mask = (1u << (2 * KPS)) - 1u;
       int it = 0;
       bool run = true;
       for (int u = blockIdx.x; run && u < p.units && !*(volatile int*)&s_abort; u += gridDim.x) {
         const Unit w = decode_unit(p, u, BN);
         const int tb = p.batch_rows ? w.m0 / p.batch_rows : 0;
-        const int row0 = lane == 0 ? w.m0 - tb * p.batch_rows : w.n0;
-        int kb = w.step0 % p.kblocks;
-        const int rest = w.step0 / p.kblocks;
-        int k = rest % nk, pr = rest / nk;
-        for (int j = 0; j < w.nsteps; ++j, ++it) {
+        const int row0 = isB ? w.n0 : w.m0 - tb * p.batch_rows;
+        for (int j = 0; j * KPS < w.nsteps; ++j, ++it) {
           const int s = it % C::STAGES;
           const uint32_t ph = (it / C::STAGES) & 1;
           const uint32_t fb = smem_u32(&full[s]);
+          const int nkb = min(KPS, w.nsteps - j * KPS);  // k-blocks in this stage
           int okw = 1;
           if (lane == 0) {
             okw = mbar_wait(smem_u32(&empty[s]), ph ^ 1, p.status) ? 1 : 0;
-            if (okw) mbar_expect_tx(fb, C::STAGE);
+            if (okw) mbar_expect_tx(fb, (uint32_t)(nkb * C::KB_BYTES));
           }
-          okw = __shfl_sync(0x3u, okw, 0);
+          okw = __shfl_sync(mask, okw, 0);
           if (!okw) {
             if (lane == 0) s_abort = 1;
             run = false;
             break;
           }
-          const int term = (lane == 0 ? p.sa[pr] * p.a_terms : p.sb[pr] * p.b_terms) + (p.batch_rows ? tb : k);
-          const uint32_t dst = smem_u32(smem + s * C::STAGE) + (lane == 0 ? 0u : (uint32_t)C::A_BYTES);
-          tma_load_3d(dst, map, (kb * 128) >> ksh, row0, term, fb);
-          if (++kb == p.kblocks) {
-            kb = 0;
-            if (++k == nk) {
-              k = 0;
-              ++pr;
-            }
+          if (q < nkb) {
+            const int stp = w.step0 + j * KPS + q;
+            const int kb = stp % p.kblocks;
+            const int rest = stp / p.kblocks;
+            const int k = rest % nk, pr = rest / nk;
+            const int term = (isB ? p.sb[pr] * p.b_terms : p.sa[pr] * p.a_terms) + (p.batch_rows ? tb : k);
+            const uint32_t dst =
+                smem_u32(smem + s * C::STAGE + q * C::KB_BYTES) + (isB ? (uint32_t)C::A_BYTES : 0u);
+            tma_load_3d(dst, map, (kb * 128) >> ksh, row0, term, fb);
           }
         }
       }
@@ -461,7 +467,7 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * BN);
         bool ok = true;
-        for (int j = 0; j < w.nsteps; ++j, ++it) {
+        for (int j = 0; j * KPS < w.nsteps; ++j, ++it) {
           const int s = it % C::STAGES;
           const uint32_t ph = (it / C::STAGES) & 1;
           if (*(volatile int*)&s_abort || !mbar_wait(smem_u32(&full[s]), ph, p.status)) {
@@ -470,12 +476,18 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(smem + s * C::STAGE);
-          const uint32_t b0 = a0 + C::A_BYTES;
+          const int nkb = min(KPS, w.nsteps - j * KPS);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)  // 4 x 32 bytes of K per 128-byte row
-            mma_issue<KIND>(d, make_sdesc(a0 + kk * 32), make_sdesc(b0 + kk * 32), p.idesc,
-                            (j > 0 || kk > 0) ? 1u : 0u);
+          for (int q = 0; q < KPS; ++q) {
+            if (q < nkb) {
+              const uint32_t a0 = smem_u32(smem + s * C::STAGE + q * C::KB_BYTES);
+              const uint32_t b0 = a0 + C::A_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)  // 4 x 32 bytes of K per 128-byte row
+                mma_issue<KIND>(d, make_sdesc(a0 + kk * 32), make_sdesc(b0 + kk * 32), p.idesc,
+                                (j > 0 || q > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
           mma_commit(smem_u32(&empty[s]));
         }
         mma_commit(smem_u32(&tfull[buf]));
@@ -584,6 +596,7 @@ struct TcGemmPlan {
   int kind;
   int bn;
   int cps;
+  int kps;
   dim3 grid;
 };
 
@@ -745,6 +758,10 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
   pl->kind = kind;
   pl->bn = bn;
   pl->cps = cps;
+  // k-blocks per ring stage: 2 (the producer's and MMA thread's per-stage
+  // costs otherwise bound the main loop), except for two CTAs per SM
+  pl->kps = (bn == 128 && cps == 2) ? 1 : 2;
+  if (ctx->tc_kps_override == 1 || (ctx->tc_kps_override == 2 && !(bn == 128 && cps == 2))) pl->kps = ctx->tc_kps_override;
   pl->grid = dim3(std::min(p.units, ctx->sm_count * cps), 1, 1);
   ctx->tc_plans.push_back(pl);
   *out = pl;
@@ -761,25 +778,27 @@ void tc_plan_set_runtime(TcGemmPlan* plan, const float* alpha_dev, const int* fl
   plan->params.flags = flags;
 }
 
-template <int KIND, int BN, int CPS>
+template <int KIND, int BN, int CPS, int KPS>
 static kp_status launch_kind(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
-  using C = TcCfg<BN, CPS>;
+  using C = TcCfg<BN, CPS, KPS>;
   static bool attr_set = false;
   if (!attr_set) {
-    KP_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    KP_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN, CPS, KPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 C::SMEM));
     attr_set = true;
   }
-  KP_CUDA(kp_launch(ctx, tc_gemm_kernel<KIND, BN, CPS>, pl->grid, dim3(TC_THREADS), C::SMEM, pl->mapA, pl->mapB, p));
+  KP_CUDA(kp_launch(ctx, tc_gemm_kernel<KIND, BN, CPS, KPS>, pl->grid, dim3(TC_THREADS), C::SMEM, pl->mapA, pl->mapB,
+                    p));
   KP_LAUNCHED(ctx);
   return KP_OK;
 }
 
 template <int KIND>
 static kp_status launch_cfg(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
-  if (pl->bn == 256) return launch_kind<KIND, 256, 1>(ctx, pl, p);
-  if (pl->bn == 64) return launch_kind<KIND, 64, 1>(ctx, pl, p);
-  if (pl->cps == 2) return launch_kind<KIND, 128, 2>(ctx, pl, p);
-  return launch_kind<KIND, 128, 1>(ctx, pl, p);
+  if (pl->bn == 256) return pl->kps == 2 ? launch_kind<KIND, 256, 1, 2>(ctx, pl, p) : launch_kind<KIND, 256, 1, 1>(ctx, pl, p);
+  if (pl->bn == 64) return pl->kps == 2 ? launch_kind<KIND, 64, 1, 2>(ctx, pl, p) : launch_kind<KIND, 64, 1, 1>(ctx, pl, p);
+  if (pl->cps == 2) return launch_kind<KIND, 128, 2, 1>(ctx, pl, p);
+  return pl->kps == 2 ? launch_kind<KIND, 128, 1, 2>(ctx, pl, p) : launch_kind<KIND, 128, 1, 1>(ctx, pl, p);
 }
 
 kp_status tc_plan_run(kp_ctx* ctx, TcGemmPlan* pl, const EpiParams* epi_override) {

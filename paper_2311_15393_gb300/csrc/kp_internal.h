@@ -129,7 +129,7 @@ struct kp_ctx {
 
   // options
   double reliable_delta = -1.0;  // < 0: default for the operator precision
-  int check_every = 4;
+  int check_every = 2;
   double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD
   int jacobi_max_sweeps = 40;
   bool pdl = true;           // programmatic dependent launch in the iteration
@@ -138,6 +138,7 @@ struct kp_ctx {
   int splitk_override = 0;  // > 0: fixed split-K factor for the square GEMMs
   int tc_bn_override = 0;   // 128 / 256: fixed tensor-core tile width
   int tc_cps_override = 0;  // 1 / 2: fixed CTAs per SM for 128-wide tiles
+  int tc_kps_override = 0;  // 1 / 2: fixed k-blocks per ring stage
 
   // device allocations: ctx_block lives with the context, allocs with the
   // problem; a new kp_setup returns the previous problem's blocks to `pool`,
