@@ -218,8 +218,9 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *   "tc_bn"           64, 128 or 256: fixed tensor-core tile width (default 0 =
  *                     chosen per shape)
  *   "tc_ctas_per_sm"  1 or 2: fixed CTAs per SM for 128-wide tiles (default 0)
- *   "tc_kblocks_per_stage" 1 or 2: k-blocks per shared-memory ring stage
- *                     (default 0 = 2, or 1 with two CTAs per SM)
+ *   "tc_kblocks_per_stage" 1, 2 or 4 (4: 64-wide tiles only): k-blocks per
+ *                     shared-memory ring stage (default 0 = 4 for 64-wide
+ *                     tiles, 1 with two CTAs per SM, else 2)
  *                     The three tile options take effect at the next kp_setup.
  *   "pdl"             0: launch the iteration's kernels without programmatic
  *                     dependent launch (default 1: each kernel's launch and

@@ -758,10 +758,13 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
   pl->kind = kind;
   pl->bn = bn;
   pl->cps = cps;
-  // k-blocks per ring stage: 2 (the producer's and MMA thread's per-stage
-  // costs otherwise bound the main loop), except for two CTAs per SM
-  pl->kps = (bn == 128 && cps == 2) ? 1 : 2;
-  if (ctx->tc_kps_override == 1 || (ctx->tc_kps_override == 2 && !(bn == 128 && cps == 2))) pl->kps = ctx->tc_kps_override;
+  // k-blocks per ring stage: 2, or 4 for 64-wide tiles (the producer's and
+  // MMA thread's per-stage costs otherwise bound the main loop); 1 with two
+  // CTAs per SM
+  pl->kps = bn == 64 ? 4 : ((bn == 128 && cps == 2) ? 1 : 2);
+  if (ctx->tc_kps_override == 1 || (ctx->tc_kps_override == 2 && !(bn == 128 && cps == 2)) ||
+      (ctx->tc_kps_override == 4 && bn == 64))
+    pl->kps = ctx->tc_kps_override;
   pl->grid = dim3(std::min(p.units, ctx->sm_count * cps), 1, 1);
   ctx->tc_plans.push_back(pl);
   *out = pl;
@@ -796,7 +799,10 @@ static kp_status launch_kind(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
 template <int KIND>
 static kp_status launch_cfg(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
   if (pl->bn == 256) return pl->kps == 2 ? launch_kind<KIND, 256, 1, 2>(ctx, pl, p) : launch_kind<KIND, 256, 1, 1>(ctx, pl, p);
-  if (pl->bn == 64) return pl->kps == 2 ? launch_kind<KIND, 64, 1, 2>(ctx, pl, p) : launch_kind<KIND, 64, 1, 1>(ctx, pl, p);
+  if (pl->bn == 64) {
+    if (pl->kps == 4) return launch_kind<KIND, 64, 1, 4>(ctx, pl, p);
+    return pl->kps == 2 ? launch_kind<KIND, 64, 1, 2>(ctx, pl, p) : launch_kind<KIND, 64, 1, 1>(ctx, pl, p);
+  }
   if (pl->cps == 2) return launch_kind<KIND, 128, 2, 1>(ctx, pl, p);
   return pl->kps == 2 ? launch_kind<KIND, 128, 1, 2>(ctx, pl, p) : launch_kind<KIND, 128, 1, 1>(ctx, pl, p);
 }
