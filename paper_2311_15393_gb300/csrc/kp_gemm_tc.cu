@@ -401,38 +401,67 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int ksh = KIND == TC_E4M3 ? 0 : 1;  // K elements per 128-byte row: 128 >> ksh
-  // the prologue above overlaps the previous kernel; its results are needed from here on
-  KP_PDL_WAIT();
-  KP_PDL_TRIGGER();
-  const bool skip = p.flags && *(volatile const int*)p.flags;
-
-  if (skip) {
-    // paused: nothing to do but release TMEM below
-  } else if (warp == 0) {
-    if (lane < 2 * KPS) {
-      // ---------------- TMA producer: lane 2q loads the A tile, lane 2q + 1
-      // the B tile of k-block q of the stage (all issued by one instruction);
-      // lane 0 owns the barriers
-      const bool isB = lane & 1;
-      const int q = lane >> 1;
-      const CUtensorMap* map = isB ? &tmB : &tmA;
-      const int nk = p.batch_rows ? 1 : p.nkron;
-      const unsigned mask = (1u << (2 * KPS)) - 1u;
-      int it = 0;
+  // The prologue above overlaps the previous kernel (programmatic dependent
+  // launch).  The A operand of every GEMM here is a constant factor, so the
+  // producer also loads the A tiles of the first ring stages before waiting
+  // for the previous kernel; everything else waits first.
+  bool skip = false;
+  if (warp == 0 && lane < 2 * KPS) {
+    // ---------------- TMA producer: lane 2q loads the A tile, lane 2q + 1
+    // the B tile of k-block q of the stage (all issued by one instruction);
+    // lane 0 owns the barriers
+    const bool isB = lane & 1;
+    const int q = lane >> 1;
+    const CUtensorMap* map = isB ? &tmB : &tmA;
+    const int nk = p.batch_rows ? 1 : p.nkron;
+    const unsigned mask = (1u << (2 * KPS)) - 1u;
+    auto load = [&](const Unit& w, int j, int s, bool a_side) {
+      // this lane's tile of stage j of unit w (A lanes when a_side, else B lanes)
+      const int nkb = min(KPS, w.nsteps - j * KPS);
+      if (q >= nkb || isB == a_side) return;
+      const int tb = p.batch_rows ? w.m0 / p.batch_rows : 0;
+      const int row0 = isB ? w.n0 : w.m0 - tb * p.batch_rows;
+      const int stp = w.step0 + j * KPS + q;
+      const int kb = stp % p.kblocks;
+      const int rest = stp / p.kblocks;
+      const int k = rest % nk, pr = rest / nk;
+      const int term = (isB ? p.sb[pr] * p.b_terms : p.sa[pr] * p.a_terms) + (p.batch_rows ? tb : k);
+      const uint32_t dst = smem_u32(smem + s * C::STAGE + q * C::KB_BYTES) + (isB ? (uint32_t)C::A_BYTES : 0u);
+      tma_load_3d(dst, map, (kb * 128) >> ksh, row0, term, smem_u32(&full[s]));
+    };
+    // prefetch: the first ring stages of the first unit (fresh barriers, free slots)
+    int npre = 0;
+    Unit w0;
+    if ((int)blockIdx.x < p.units) {
+      w0 = decode_unit(p, blockIdx.x, BN);
+      npre = min(C::STAGES, (w0.nsteps + KPS - 1) / KPS);
+      for (int j = 0; j < npre; ++j) {
+        if (lane == 0) mbar_expect_tx(smem_u32(&full[j]), (uint32_t)(min(KPS, w0.nsteps - j * KPS) * C::KB_BYTES));
+        __syncwarp(mask);
+        load(w0, j, j, true);
+      }
+    }
+    KP_PDL_WAIT();
+    KP_PDL_TRIGGER();
+    skip = p.flags && *(volatile const int*)p.flags;
+    // the B tiles of the prefetched stages (also when paused: the stages must fill before the CTA exits)
+    for (int j = 0; j < npre; ++j) load(w0, j, j, false);
+    if (skip) {
+      if (lane == 0)
+        for (int j = 0; j < npre; ++j) mbar_wait(smem_u32(&full[j]), 0, p.status);
+    } else {
+      int it = npre;
       bool run = true;
       for (int u = blockIdx.x; run && u < p.units && !*(volatile int*)&s_abort; u += gridDim.x) {
         const Unit w = decode_unit(p, u, BN);
-        const int tb = p.batch_rows ? w.m0 / p.batch_rows : 0;
-        const int row0 = isB ? w.n0 : w.m0 - tb * p.batch_rows;
-        for (int j = 0; j * KPS < w.nsteps; ++j, ++it) {
+        for (int j = u == (int)blockIdx.x ? npre : 0; j * KPS < w.nsteps; ++j, ++it) {
           const int s = it % C::STAGES;
           const uint32_t ph = (it / C::STAGES) & 1;
-          const uint32_t fb = smem_u32(&full[s]);
           const int nkb = min(KPS, w.nsteps - j * KPS);  // k-blocks in this stage
           int okw = 1;
           if (lane == 0) {
             okw = mbar_wait(smem_u32(&empty[s]), ph ^ 1, p.status) ? 1 : 0;
-            if (okw) mbar_expect_tx(fb, (uint32_t)(nkb * C::KB_BYTES));
+            if (okw) mbar_expect_tx(smem_u32(&full[s]), (uint32_t)(nkb * C::KB_BYTES));
           }
           okw = __shfl_sync(mask, okw, 0);
           if (!okw) {
@@ -440,19 +469,19 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
             run = false;
             break;
           }
-          if (q < nkb) {
-            const int stp = w.step0 + j * KPS + q;
-            const int kb = stp % p.kblocks;
-            const int rest = stp / p.kblocks;
-            const int k = rest % nk, pr = rest / nk;
-            const int term = (isB ? p.sb[pr] * p.b_terms : p.sa[pr] * p.a_terms) + (p.batch_rows ? tb : k);
-            const uint32_t dst =
-                smem_u32(smem + s * C::STAGE + q * C::KB_BYTES) + (isB ? (uint32_t)C::A_BYTES : 0u);
-            tma_load_3d(dst, map, (kb * 128) >> ksh, row0, term, fb);
-          }
+          load(w, j, s, true);
+          load(w, j, s, false);
         }
       }
     }
+  } else {
+    KP_PDL_WAIT();
+    KP_PDL_TRIGGER();
+    skip = p.flags && *(volatile const int*)p.flags;
+  }
+
+  if (skip || warp == 0) {
+    // paused, or the producer (done above): nothing more before the teardown
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
