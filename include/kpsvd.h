@@ -211,6 +211,12 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     residual update (default 0.1 for F32 / BF16 / BF16X3
  *                     operators, 0 = off for the F64 operator)
  *   "check_every"     iterations between host convergence checks (default 2)
+ *   "cg_fuse"         1 (default): with a BF16 / BF16X3 operator, an F16 / BF16
+ *                     preconditioner and FP32 vectors, the x / r update also
+ *                     writes the preconditioner's narrow input, scaled by a
+ *                     power of two from the bound max|r| + |alpha| max|q|
+ *                     (no separate quantisation pass); 0: separate pass
+ *                     scaled from the exact max|r|
  *   "jacobi_tol"      one-sided Jacobi rotation threshold (default 1e-15)
  *   "jacobi_max_sweeps" (default 40)
  *   "splitk"          > 0: fixed split-K factor of the square tensor-core

@@ -205,6 +205,12 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
       return KP_EINVAL;
     }
     ctx->check_every = (int)value;
+  } else if (!strcmp(name, "cg_fuse")) {
+    if (value != 0 && value != 1) {
+      kp_set_error("cg_fuse must be 0 or 1");
+      return KP_EINVAL;
+    }
+    ctx->cg_fuse = value != 0;
   } else if (!strcmp(name, "jacobi_tol")) {
     if (!(value > 0 && value < 1e-3)) {
       kp_set_error("jacobi_tol must be in (0, 1e-3)");

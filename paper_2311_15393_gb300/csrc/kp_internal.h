@@ -130,6 +130,7 @@ struct kp_ctx {
   // options
   double reliable_delta = -1.0;  // < 0: default for the operator precision
   int check_every = 2;
+  bool cg_fuse = true;  // the x / r update also writes the preconditioner's narrow input (where possible)
   double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD
   int jacobi_max_sweeps = 40;
   bool pdl = true;           // programmatic dependent launch in the iteration

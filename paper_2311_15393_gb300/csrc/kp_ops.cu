@@ -177,12 +177,25 @@ static GemmDesc pc_desc(kp_ctx* ctx, int which) {
 // With dot non-null (FP32 output), also dot = sum out * aux (p^T q of the
 // iteration) by the deterministic tree of the vector kernels, and the scalar
 // step po by its last block.
+// With qmax also max |out| into out[1].
 struct TermDot {
   double* out = nullptr;
   double* partials = nullptr;
   unsigned int* counter = nullptr;
   PostOp po;
+  int qmax = 0;
 };
+
+// the term sum's dot (and max) reduction: one double-float sum, or a sum
+// and a max
+__device__ __forceinline__ void term_dot_finish(float (&dh)[2], float (&dl)[2], const TermDot& td) {
+  if (td.qmax) {
+    kpv::reduce_finish_df<2>(dh, dl, true, td.partials, td.counter, td.out, 2, td.po);
+  } else {
+    float h1[1] = {dh[0]}, l1[1] = {dl[0]};
+    kpv::reduce_finish_df<1>(h1, l1, false, td.partials, td.counter, td.out, 1, td.po);
+  }
+}
 
 __global__ void __launch_bounds__(VEC_THREADS)
     k_term_reduce(const float* __restrict__ Z, int terms, long long nel, float alpha, float beta,
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(VEC_THREADS)
   KP_PDL_WAIT();
   KP_PDL_TRIGGER();
   if (flags && *(volatile const int*)flags) return;
-  float dh[1] = {0.f}, dl[1] = {0.f};  // p^T q as a double-float pair
+  float dh[2] = {0.f, 0.f}, dl[2] = {0.f, 0.f};  // p^T q as a double-float pair; max |q| in dh[1]
   if (!vec) {  // out / aux not 16-byte aligned: one element at a time
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nel; i += (long long)gridDim.x * blockDim.x) {
       float a = Z[i];
@@ -200,7 +213,10 @@ __global__ void __launch_bounds__(VEC_THREADS)
       if (aux) v = fmaf(beta, aux[i], v);
       if (!slices_mode) {
         ((float*)out)[i] = v;
-        if (td.out) kpv::df_add_prod(dh[0], dl[0], v, aux[i]);
+        if (td.out) {
+          kpv::df_add_prod(dh[0], dl[0], v, aux[i]);
+          dh[1] = fmaxf(dh[1], fabsf(v));
+        }
       } else {
         for (int sl = 0; sl < slices; ++sl) {
           const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -209,7 +225,7 @@ __global__ void __launch_bounds__(VEC_THREADS)
         }
       }
     }
-    if (td.out) kpv::reduce_finish_df<1>(dh, dl, false, td.partials, td.counter, td.out, 1, td.po);
+    if (td.out) term_dot_finish(dh, dl, td);
     return;
   }
   const long long n4 = nel >> 2;
@@ -239,6 +255,7 @@ __global__ void __launch_bounds__(VEC_THREADS)
         kpv::df_add_prod(dh[0], dl[0], v[1], t.y);
         kpv::df_add_prod(dh[0], dl[0], v[2], t.z);
         kpv::df_add_prod(dh[0], dl[0], v[3], t.w);
+        dh[1] = fmaxf(dh[1], fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3]))));
       }
     } else {
       __nv_bfloat16* o = (__nv_bfloat16*)out + 4 * i;
@@ -256,7 +273,7 @@ __global__ void __launch_bounds__(VEC_THREADS)
       }
     }
   }
-  if (td.out) kpv::reduce_finish_df<1>(dh, dl, false, td.partials, td.counter, td.out, 1, td.po);
+  if (td.out) term_dot_finish(dh, dl, td);
 }
 
 kp_status ops_prepare(kp_ctx* ctx) {
@@ -444,7 +461,7 @@ kp_status op_apply(kp_ctx* ctx, const void* x, void* y, int transpose, int mode)
 }
 
 kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_slices_ready, const int* flags,
-                     double* pq_out, const PostOp* pq_post, bool* pq_done) {
+                     double* pq_out, const PostOp* pq_post, bool* pq_done, bool qmax) {
   if (pq_done) *pq_done = false;
   const void* bx = p;
   if (op_is_tc(ctx)) {
@@ -461,6 +478,7 @@ kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_sl
     td.partials = ctx->red_part;
     td.counter = ctx->red_count;
     if (pq_post) td.po = *pq_post;
+    td.qmax = qmax ? 1 : 0;
     KP_TRY(run_op(ctx, 3, OP_INNER, nullptr, epi_img(ctx, OP_INNER, q, false, 1.0, lam2, p), flags, &td, pq_done));
     return KP_OK;
   }
@@ -506,7 +524,8 @@ static kp_status simt_pc(kp_ctx* ctx, const void* r, void* z, double lam2, const
   return KP_OK;
 }
 
-kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat, const int* flags) {
+kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat, const int* flags,
+                   bool narrow_ready) {
   if (!pc_is_tc(ctx)) {
     if (vec64(ctx)) return simt_pc<double>(ctx, r, z, lam2, flags);
     return simt_pc<float>(ctx, r, z, lam2, flags);
@@ -549,7 +568,7 @@ kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const doubl
     tc_plan_set_runtime(os->P[3], os->inv_slot, flags);
     return tc_plan_run(ctx, os->P[3], &e);
   }
-  KP_TRY(quantize_dev(ctx, r, N, false, stat, nt, lam2, ctx->pc_in, os->inv_slot, flags));
+  if (!narrow_ready) KP_TRY(quantize_dev(ctx, r, N, false, stat, nt, lam2, ctx->pc_in, os->inv_slot, flags));
   for (int w = 0; w < 4; ++w) {
     EpiParams e;
     e.ldd = w == 0 || w == 2 ? ctx->n_c : ctx->n_r;
@@ -571,3 +590,12 @@ kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const doubl
   }
   return KP_OK;
 }
+
+// ------------------------------------------------------------- folded quantisation
+bool cg_fusable(kp_ctx* ctx) {
+  if (!ctx->cg_fuse || !op_is_tc(ctx) || !pc_is_tc(ctx) || ctx->vec_prec != KP_F32) return false;
+  if (ctx->pc_prec != KP_F16 && ctx->pc_prec != KP_BF16) return false;
+  return ops(ctx)->batched;
+}
+
+float* cg_inv_slot(kp_ctx* ctx) { return ops(ctx)->inv_slot; }

@@ -14,17 +14,30 @@ kp_status op_apply(kp_ctx* ctx, const void* x, void* y, int transpose, int mode)
 // operators `p_slices_ready` says the bf16 slices of p are already in
 // ctx->w_img2 (written by the p update); otherwise they are made here.
 // With pq_out, p^T q may be computed on the way (and pq_post run on it);
-// *pq_done says whether it was (else the caller computes it).
+// *pq_done says whether it was (else the caller computes it).  With qmax,
+// max |q| goes to pq_out[1] as well (only when *pq_done).
 struct PostOp;
 kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_slices_ready, const int* flags,
-                     double* pq_out = nullptr, const PostOp* pq_post = nullptr, bool* pq_done = nullptr);
+                     double* pq_out = nullptr, const PostOp* pq_post = nullptr, bool* pq_done = nullptr,
+                     bool qmax = false);
 
 // r = A^T (b - A x) - lam2 x with the accurate operator
 kp_status op_true_residual(kp_ctx* ctx, const void* b, const void* x, void* r, double lam2, const int* flags);
 
 // z = M^-1 r.  `stat` points to device [||r||^2, amax(r)] when known (else
 // computed here); `inv_slot` is a device float used for the output scale.
-kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat, const int* flags);
+// narrow_ready (F16 / BF16 preconditioners): ctx->pc_in and the inverse
+// scale slot already hold the narrow copy of r (written by the x / r update).
+kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat, const int* flags,
+                   bool narrow_ready = false);
 
 // number of bf16 slices the inner operator wants for p (0 for SIMT operators)
 int op_inner_slices(kp_ctx* ctx);
+
+// ---- folded quantisation (tensor-core operator with batched term sums,
+// F16 / BF16 preconditioner, FP32 vectors): the K application's term sum
+// also gives max |q|, and the x / r update writes the preconditioner's
+// narrow input with a scale bounded from max |r_old| + |alpha| max |q|
+bool cg_fusable(kp_ctx* ctx);
+// the inverse-scale slot of the narrow preconditioner input
+float* cg_inv_slot(kp_ctx* ctx);

@@ -83,12 +83,13 @@ static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
 }
 
 // second half: z = M^-1 r, beta, p = z + beta p (+ bf16 slices of p)
-static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2) {
+// (narrow_ready: the narrow copy of r for the preconditioner is already made)
+static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2, bool narrow_ready = false) {
   const long long N = (long long)ctx->n_r * ctx->n_c;
   const bool f64 = ctx->vec_prec == KP_F64;
   const int* fl = ctx->dflags;
   double* s = ctx->dscal;
-  KP_TRY(pc_apply(ctx, B.r, B.z, lam2, s + S_RR, fl));
+  KP_TRY(pc_apply(ctx, B.r, B.z, lam2, s + S_RR, fl, narrow_ready));
   PostOp pb;  // beta and zr, by the last block of the dot products
   pb.kind = POST_BETA;
   pb.s = s;
@@ -96,6 +97,34 @@ static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2) {
   KP_TRY(dot2_dev(ctx, B.z, B.r, B.r_old, N, f64, s + S_ZRNEW, fl, pb));
   const int sl = op_inner_slices(ctx);
   KP_TRY(p_update_dev(ctx, B.p, B.z, N, f64, s + S_BETA, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N, fl));
+  return KP_OK;
+}
+
+// The first half with the quantisation of r folded into the x / r update
+// (cg_fusable): the K application's term sum also gives max |q|, so the
+// update writes the preconditioner's narrow input with a scale bounded from
+// max |r_old| + |alpha| max |q| >= max |r_new|, known before the update.
+static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  const int* fl = ctx->dflags;
+  double* s = ctx->dscal;
+  PostOp pa;
+  pa.kind = POST_ALPHA;
+  pa.s = s;
+  pa.f = ctx->dflags;
+  PostOp pc = pa;
+  pc.kind = POST_CHECK;
+  pc.hist = ctx->hist;
+  pc.hist_cap = ctx->hist_cap;
+  bool fused = false;
+  KP_TRY(op_apply_K(ctx, B.p, B.q, lam2, true, fl, s + S_QPQ, &pa, &fused, true));
+  if (!fused) {
+    kp_set_error("tik_pcg: folded iteration without a fused term sum");
+    return KP_ENOTSUP;
+  }
+  const int nt = ctx->pc_prec == KP_BF16 ? NT_BF16 : NT_F16;
+  KP_TRY(update_xr_q_dev(ctx, x, B.r, B.r_old, B.p, B.q, N, s + S_ALPHA, s + S_RR, s + S_QMAX, nt, lam2, ctx->pc_in,
+                         cg_inv_slot(ctx), fl, pc));
   return KP_OK;
 }
 
@@ -136,6 +165,7 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
   // default: reliable updates for every operator below FP64
   double delta = ctx->reliable_delta >= 0 ? ctx->reliable_delta : (ctx->op_prec == KP_F64 ? 0.0 : 0.1);
   const bool reliable = delta > 0.0;
+  const bool folded = cg_fusable(ctx);
 
   cudaEvent_t e0, e1;
   KP_CUDA(cudaEventCreate(&e0));
@@ -197,8 +227,8 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
       KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       kp_status cs = KP_OK;
       for (int i = 0; i < blk && cs == KP_OK; ++i) {
-        cs = half_a(ctx, B, x, lam2);
-        if (cs == KP_OK) cs = half_b(ctx, B, lam2);
+        cs = folded ? half_a_folded(ctx, B, x, lam2) : half_a(ctx, B, x, lam2);
+        if (cs == KP_OK) cs = half_b(ctx, B, lam2, folded);
       }
       cudaError_t ce = cudaStreamEndCapture(st, &graph);
       const long long per_block = ctx->launches - l0;

@@ -263,6 +263,79 @@ __global__ void k_quantize(const T* __restrict__ r, long long n, int vec4, const
   for (long long i = i0; i < n; i += stride) out[i] = to_narrow<N>((float)r[i] * s);
 }
 
+// two narrow values packed in 32 bits (low half first)
+template <typename NQ>
+__device__ __forceinline__ uint32_t pack2(float a, float b);
+template <>
+__device__ __forceinline__ uint32_t pack2<__half>(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <>
+__device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// x += alpha p ; r_old = r ; r -= alpha q ; ||r||^2, max |r| (as k_update_xr)
+// and the preconditioner input out = narrow(r * s) in the same pass.  The
+// scale s is a power of two from the bound max |r| + |alpha| max |q| >=
+// max |r_new|, both known before the update, so no extra pass over r is
+// needed; the bound (not the exact max) only moves values down in the
+// narrow type's range.  out2[1] (max |r| of the previous update) is read by
+// every block before the last block overwrites it.
+template <typename NQ>
+__global__ void __launch_bounds__(VEC_THREADS)
+    k_update_xr_q(float* __restrict__ x, float* __restrict__ r, float* __restrict__ r_old, const float* __restrict__ p,
+                  const float* __restrict__ q, long long n, int vec4, const double* __restrict__ alpha_dev,
+                  const double* __restrict__ qmax_dev, double lam2, NQ* __restrict__ out, float* __restrict__ inv_out,
+                  double* partials, unsigned int* counter, double* out2, const int* flags, PostOp po) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
+  if (paused(flags)) return;
+  __shared__ float s_sh;
+  if (threadIdx.x == 0) {
+    const double bound = out2[1] + fabs(*alpha_dev) * *qmax_dev;
+    s_sh = pow2_scale(bound * (1.0 + 1e-6), 1.0);
+    if (blockIdx.x == 0) *inv_out = (float)(1.0 / (lam2 * (double)s_sh));
+  }
+  __syncthreads();
+  const float sc = s_sh;
+  const float al = (float)*alpha_dev;
+  const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
+  long long i0 = tid;
+  float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
+  if (vec4) {
+    const long long n4 = n >> 2;
+    for (long long i = tid; i < n4; i += stride) {
+      const float4 xi = ld4(x, i), ri = ld4(r, i), pi = ld4(p, i), qi = ld4(q, i);
+      st4(x, i, make_float4(fmaf(al, pi.x, xi.x), fmaf(al, pi.y, xi.y), fmaf(al, pi.z, xi.z), fmaf(al, pi.w, xi.w)));
+      st4(r_old, i, ri);
+      const float4 rn = make_float4(fmaf(-al, qi.x, ri.x), fmaf(-al, qi.y, ri.y), fmaf(-al, qi.z, ri.z),
+                                    fmaf(-al, qi.w, ri.w));
+      st4(r, i, rn);
+      *reinterpret_cast<uint2*>(out + 4 * i) = make_uint2(pack2<NQ>(rn.x * sc, rn.y * sc), pack2<NQ>(rn.z * sc, rn.w * sc));
+      df_add_prod(hi[0], lo[0], rn.x, rn.x);
+      df_add_prod(hi[0], lo[0], rn.y, rn.y);
+      df_add_prod(hi[0], lo[0], rn.z, rn.z);
+      df_add_prod(hi[0], lo[0], rn.w, rn.w);
+      hi[1] = fmaxf(hi[1], fmaxf(fmaxf(fabsf(rn.x), fabsf(rn.y)), fmaxf(fabsf(rn.z), fabsf(rn.w))));
+    }
+    i0 = 4 * n4 + tid;
+  }
+  for (long long i = i0; i < n; i += stride) {
+    const float ri = r[i];
+    x[i] = fmaf(al, p[i], x[i]);
+    r_old[i] = ri;
+    const float rn = fmaf(-al, q[i], ri);
+    r[i] = rn;
+    out[i] = to_narrow<NQ>(rn * sc);
+    df_add_prod(hi[0], lo[0], rn, rn);
+    hi[1] = fmaxf(hi[1], fabsf(rn));
+  }
+  reduce_finish_df<2>(hi, lo, true, partials, counter, out2, 2, po);
+}
+
 // One stage of the E4M3 preconditioner solve: the stage's FP32 GEMM output
 // (max |.| accumulated by the GEMM epilogue into *amax_bits) is scaled by a
 // power of two g putting its maximum into [224, 448) and rounded to E4M3;
@@ -396,6 +469,28 @@ kp_status update_xr_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* 
                                                            (const float*)q, n, aligned16(x, r, r_old, p, q),
                                                            alpha_dev, ctx->red_part, ctx->red_count, out2, flags,
                                                            post));
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+kp_status update_xr_q_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* p, const void* q, long long n,
+                          const double* alpha_dev, double* out2, const double* qmax_dev, int narrow, double lam2,
+                          void* pc_out, float* inv_out, const int* flags, PostOp post) {
+  const int g = vec_grid(ctx, n);
+  const int v4 = aligned16(x, r, r_old, p, q) && (((uintptr_t)pc_out & 7) == 0);
+  if (narrow == NT_F16)
+    KP_CUDA(kp_launch(ctx, k_update_xr_q<__half>, dim3(g), dim3(VEC_THREADS), 0, (float*)x, (float*)r, (float*)r_old,
+                      (const float*)p, (const float*)q, n, v4, alpha_dev, qmax_dev, lam2, (__half*)pc_out, inv_out,
+                      ctx->red_part, ctx->red_count, out2, flags, post));
+  else if (narrow == NT_BF16)
+    KP_CUDA(kp_launch(ctx, k_update_xr_q<__nv_bfloat16>, dim3(g), dim3(VEC_THREADS), 0, (float*)x, (float*)r,
+                      (float*)r_old, (const float*)p, (const float*)q, n, v4, alpha_dev, qmax_dev, lam2,
+                      (__nv_bfloat16*)pc_out, inv_out, ctx->red_part, ctx->red_count, out2, flags, post));
+  else {
+    kp_set_error("update_xr_q: the fused preconditioner input is F16 or BF16");
+    return KP_ENOTSUP;
+  }
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;

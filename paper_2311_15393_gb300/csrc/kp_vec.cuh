@@ -16,7 +16,8 @@ __device__ __forceinline__ __nv_fp8_e4m3 to_narrow<__nv_fp8_e4m3>(float v) { ret
 // device scalar slots (ctx->dscal) and flag slots (ctx->dflags) of the (F)PCG loop
 enum {
   S_RR = 0, S_AMAX = 1, S_PQ = 2, S_ALPHA = 3, S_ZR = 4, S_ZRNEW = 5, S_ZROLD = 6, S_BETA = 7,
-  S_RR0 = 8, S_RMAX = 9, S_TOL2 = 10, S_DELTA2 = 11
+  S_RR0 = 8, S_RMAX = 9, S_TOL2 = 10, S_DELTA2 = 11,
+  S_QPQ = 12, S_QMAX = 13  // fused iteration: p^T q and max |q| (K application's term sum)
 };
 enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4 };
 enum { R_CONV = 1, R_REPLACE = 2, R_MAXIT = 4, R_BREAKDOWN = 8, R_NUMERIC = 16 };
@@ -40,6 +41,13 @@ kp_status dot2_dev(kp_ctx* ctx, const void* a, const void* b, const void* c, lon
 kp_status norm_amax_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out2);
 kp_status update_xr_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* p, const void* q, long long n,
                         bool f64, const double* alpha_dev, double* out2, const int* flags, PostOp post = PostOp());
+// The same update, also writing the preconditioner's input narrow(r * s)
+// (F16 / BF16), with the power of two s taken from a bound on max |r_new|
+// known before the update: max |r| (out2[1], from the previous update) +
+// |alpha| max |q| (*qmax_dev).  Writes *inv_out = 1 / (lam2 s).
+kp_status update_xr_q_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* p, const void* q, long long n,
+                          const double* alpha_dev, double* out2, const double* qmax_dev, int narrow, double lam2,
+                          void* pc_out, float* inv_out, const int* flags, PostOp post);
 kp_status p_update_dev(kp_ctx* ctx, void* p, const void* z, long long n, bool f64, const double* beta_dev,
                        __nv_bfloat16* ps, int slices, long long sstride, const int* flags);
 kp_status quantize_dev(kp_ctx* ctx, const void* r, long long n, bool f64, const double* stat, int narrow,
