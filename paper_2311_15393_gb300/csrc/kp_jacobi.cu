@@ -354,30 +354,66 @@ __global__ void k_small_right(const T* __restrict__ Q, int m, int p, const T* __
 // deficiency) is replaced by a unit vector e_t and orthogonalised again.
 // With R non-null, also the triangular factor of Q_in = Q_out R (p x p
 // col-major; a vanished column keeps its small remaining norm on the
-// diagonal).  One block of CG_T threads.
-constexpr int CG_T = 128;  // few threads: the warp reductions, not the dots, bound this kernel (FP64)
+// diagonal).  One block of CG_T threads runs the column sweeps; with one
+// warp per scheduler it issued an instruction every ~4.4 cycles (measured),
+// so the block is wide (16 warps, each thread ~m / 512 rows) and the warps'
+// reductions overlap.  With `staged`, Q is copied into shared memory (m p
+// elements of dynamic shared memory) and back, so the sweeps read shared
+// memory instead of waiting on global loads.
+constexpr int CG_T = 512;
 constexpr int CG_CH = 16;  // dots per block reduction
+
+// Warp sums of 16 values at once: four halving exchanges (8 + 4 + 2 + 1
+// shuffles) leave each lane pair with one value index, and a last exchange
+// adds the pair: 16 shuffles instead of 16 x 5.  Returns the warp sum of
+// value cg_index(lane); v is consumed.
+__device__ __forceinline__ int cg_index(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
 template <typename T>
-__global__ void __launch_bounds__(CG_T) k_cgs2(T* __restrict__ Q, int m, int p, T* __restrict__ R) {
-  __shared__ T sh[CG_T / 32][CG_CH + 1];
+__device__ __forceinline__ T warp_sum16(T (&v)[CG_CH], int lane) {
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    const bool up = (lane & (2 * h)) != 0;  // exchange across lane bit 2h: keep the upper or lower half
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+constexpr int CG_SMEM_MAX = 200 * 1024;
+template <typename T>
+__global__ void __launch_bounds__(CG_T) k_cgs2(T* __restrict__ Qg, int m, int p, T* __restrict__ R, int staged) {
+  constexpr int NW = CG_T / 32;
+  __shared__ T sh[NW][CG_CH + 1];
   __shared__ T dsh[CG_CH];
   __shared__ T tot;
+  extern __shared__ __align__(16) unsigned char cg_dyn[];
+  const int mp = m * p;
+  T* Q = staged ? reinterpret_cast<T*>(cg_dyn) : Qg;
+  if (staged) {
+    for (int i = threadIdx.x; i < mp; i += CG_T) Q[i] = Qg[i];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   auto bsum = [&](T v) -> T {
     v = jwsum<T>(v);
     __syncthreads();
     if (lane == 0) sh[wid][0] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      T t = 0;
-      for (int w = 0; w < CG_T / 32; ++w) t += sh[w][0];
-      tot = t;
+    if (wid == 0) {
+      T t = lane < NW ? sh[lane][0] : T(0);
+      t = jwsum<T>(t);
+      if (lane == 0) tot = t;
     }
     __syncthreads();
     return tot;
   };
   for (int k = 0; k < p; ++k) {
-    T* qk = Q + (long long)k * m;
+    T* qk = Q + k * m;
     T n0 = 0;
     for (int r = threadIdx.x; r < m; r += CG_T) n0 = fma(qk[r], qk[r], n0);
     n0 = sqrt(bsum(n0));
@@ -385,6 +421,7 @@ __global__ void __launch_bounds__(CG_T) k_cgs2(T* __restrict__ Q, int m, int p, 
       for (int pass = 0; pass < 2; ++pass) {
         for (int j0 = 0; j0 < k; j0 += CG_CH) {
           const int jn = min(CG_CH, k - j0);
+          const T* Qj = Q + j0 * m;
           T d[CG_CH];
 #pragma unroll
           for (int q = 0; q < CG_CH; ++q) d[q] = T(0);
@@ -392,29 +429,26 @@ __global__ void __launch_bounds__(CG_T) k_cgs2(T* __restrict__ Q, int m, int p, 
             const T x = qk[r];
 #pragma unroll
             for (int q = 0; q < CG_CH; ++q)
-              if (q < jn) d[q] = fma(Q[r + (long long)(j0 + q) * m], x, d[q]);
+              if (q < jn) d[q] = fma(Qj[r + q * m], x, d[q]);
           }
-#pragma unroll
-          for (int q = 0; q < CG_CH; ++q) {
-            if (q < jn) {  // uniform over the block
-              const T v = jwsum<T>(d[q]);
-              if (lane == 0) sh[wid][q] = v;
-            }
+          {
+            const T v = warp_sum16<T>(d, lane);
+            if ((lane & 1) == 0) sh[wid][cg_index(lane)] = v;
           }
           __syncthreads();
           if (threadIdx.x < jn) {
             T t = 0;
-            for (int w = 0; w < CG_T / 32; ++w) t += sh[w][threadIdx.x];
+            for (int w = 0; w < NW; ++w) t += sh[w][threadIdx.x];
             dsh[threadIdx.x] = t;
             if (R && attempt == 0) {
-              T* rr = R + (long long)k * p + j0 + threadIdx.x;
+              T* rr = R + k * p + j0 + threadIdx.x;
               *rr = (pass == 0 ? T(0) : *rr) + t;
             }
           }
           __syncthreads();
           for (int r = threadIdx.x; r < m; r += CG_T) {
             T x = qk[r];
-            for (int q = 0; q < jn; ++q) x = fma(-dsh[q], Q[r + (long long)(j0 + q) * m], x);
+            for (int q = 0; q < jn; ++q) x = fma(-dsh[q], Qj[r + q * m], x);
             qk[r] = x;
           }
           __syncthreads();
@@ -424,11 +458,11 @@ __global__ void __launch_bounds__(CG_T) k_cgs2(T* __restrict__ Q, int m, int p, 
       for (int r = threadIdx.x; r < m; r += CG_T) nk = fma(qk[r], qk[r], nk);
       nk = sqrt(bsum(nk));
       if (R && attempt == 0 && threadIdx.x == 0) {
-        for (int j = k + 1; j < p; ++j) R[(long long)k * p + j] = T(0);
-        R[(long long)k * p + k] = nk;
+        for (int j = k + 1; j < p; ++j) R[k * p + j] = T(0);
+        R[k * p + k] = nk;
       }
       if (nk > T(sizeof(T) == 8 ? 1e-10 : 1e-4) * n0 && nk > T(0)) {
-        const T inv = T(1) / nk;  // one FP64 division per column, not per entry
+        const T inv = T(1) / nk;  // one division per column, not per entry
         for (int r = threadIdx.x; r < m; r += CG_T) qk[r] *= inv;
         __syncthreads();
         break;
@@ -438,6 +472,10 @@ __global__ void __launch_bounds__(CG_T) k_cgs2(T* __restrict__ Q, int m, int p, 
       n0 = T(1);
       __syncthreads();
     }
+  }
+  if (staged) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < mp; i += CG_T) Qg[i] = Q[i];
   }
 }
 
@@ -808,6 +846,22 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
 // Subspace iteration for the leading r singular triplets, in T arithmetic
 // (FP64, or FP32 for the FP32-vector setup); p <= SJ_MAXP.  W (m x n col-major)
 // and WT = W^T are T; outputs (T): U (m x r), s (r), V (n x r).
+// CGS2 launch: Q staged in shared memory when m p elements fit
+template <typename T>
+static kp_status cgs2(kp_ctx* ctx, T* Q, int m, int p, T* R) {
+  static bool attr_set = false;
+  const size_t bytes = sizeof(T) * (size_t)m * p;
+  const bool staged = bytes <= (size_t)CG_SMEM_MAX;
+  if (staged && !attr_set) {
+    KP_CUDA(cudaFuncSetAttribute(k_cgs2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, CG_SMEM_MAX));
+    attr_set = true;
+  }
+  k_cgs2<T><<<1, CG_T, staged ? bytes : 0, ctx->stream>>>(Q, m, p, R, staged ? 1 : 0);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
 template <typename T>
 static kp_status topr_run(kp_ctx* ctx, const T* W, const T* WT, int m, int n, int r, int p, T* U, T* s, T* V,
                           int* iters_out) {
@@ -850,11 +904,10 @@ static kp_status topr_run(kp_ctx* ctx, const T* W, const T* WT, int m, int n, in
   const int maxit = 200;
   for (it = 0; it < maxit; ++it) {
     if (it > 0) {  // the start vectors are orthonormal already
-      k_cgs2<T><<<1, CG_T, 0, st>>>(Q, m, p, nullptr);
-      KP_LAUNCHED(ctx);
+      KP_TRY(cgs2<T>(ctx, Q, m, p, nullptr));
     }
     KP_TRY(skinny(W, m, n, Q, Z));  // Z (n x p) = W^T Q
-    k_cgs2<T><<<1, CG_T, 0, st>>>(Z, n, p, Rz);  // Z <- Q_z
+    KP_TRY(cgs2<T>(ctx, Z, n, p, Rz));  // Z <- Q_z
     k_jacobi_small<T><<<1, SJ_T, small_smem, st>>>(Rz, p, p, (T)ctx->jacobi_tol, ctx->jacobi_max_sweeps, UR, sz, Vz,
                                                    jstat);
     k_small_right<T><<<gz, 256, 0, st>>>(Z, n, p, UR, p, Uz);

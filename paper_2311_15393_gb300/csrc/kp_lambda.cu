@@ -664,26 +664,41 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
     }
   }
   // FP64 re-check of the best grid point and its neighbours
+  double t_start;
   {
     int g0 = std::max(0, best - 2), g1 = std::min(NGRID - 1, best + 2);
-    double lams[5], s1v[5], s2v[5];
+    double lams[5], s1v[5], s2v[5], fv[5];
     int k = g1 - g0 + 1;
     for (int i = 0; i < k; ++i) lams[i] = std::exp(tg[g0 + i]);
     KP_TRY(eval64(L, lams, k, s1v, s2v));
     bv = INFINITY;
     for (int i = 0; i < k; ++i) {
-      double f = objective(lm, s1v[i], s2v[i], Nd, eps);
-      if (f <= bv) {
-        bv = f;
+      fv[i] = objective(lm, s1v[i], s2v[i], Nd, eps);
+      if (fv[i] <= bv) {
+        bv = fv[i];
         best = g0 + i;
+      }
+    }
+    // start of the refinement: the vertex of the parabola through the best
+    // point and its two neighbours (in t = log lambda, on log f), when it is
+    // a minimum inside their span; else the best grid point
+    t_start = tg[best];
+    const int ib = best - g0;
+    if (ib > 0 && ib < k - 1 && fv[ib - 1] > 0 && fv[ib] > 0 && fv[ib + 1] > 0) {
+      const double fl = std::log(fv[ib - 1]), f0 = std::log(fv[ib]), fr = std::log(fv[ib + 1]);
+      const double h = tg[best + 1] - tg[best];
+      const double curv = fl - 2.0 * f0 + fr;
+      if (curv > 0 && h > 0) {
+        const double tv = tg[best] + 0.5 * h * (fl - fr) / curv;
+        if (tv > tg[best - 1] && tv < tg[best + 1]) t_start = tv;
       }
     }
   }
   double a = tg[std::max(best - 1, 0)], c = tg[std::min(best + 1, NGRID - 1)];
   if (lm == LM_GCV || lm == LM_WGCV) {
     // safeguarded Newton on g(t) = log s1 - 2 log s2 (= log G - log N) in
-    // t = log lambda over [t_{best-1}, t_{best+1}], from the best grid point
-    double t = tg[best];
+    // t = log lambda over [t_{best-1}, t_{best+1}], from the parabola's vertex
+    double t = t_start;
     for (int it = 0; it < 60; ++it) {
       double s6[6];
       KP_TRY(deriv64(L, std::exp(t), s6));
