@@ -160,16 +160,20 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# the sources of the K application's kernels (tensor-core GEMM, term sums,
+# bf16 split) and the headers they include
+KAPPLY_SOURCES = ("kp_gemm_tc.cu", "kp_internal.h", "kp_ops.cu", "kp_ops.h", "kp_vec.cu", "kp_vec.cuh")
+
+
 def sources_digest():
-    """sha256 over the CUDA sources (names and contents, sorted)."""
+    """sha256 over the K application's CUDA sources (names and contents)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2311_15393_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(name.encode())
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(f.read())
+    for name in KAPPLY_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()
 
 
