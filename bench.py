@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the image size (smaller test runs)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no phase breakdown, e2e, kernel timing or CPU baseline): for launch lists")
+    ap.add_argument("--workload", default="deblur1024_mixed", choices=["deblur1024_mixed", "batched64"],
+                    help="batched64: 64 independent problems of uneven sizes through kp_solve_batch "
+                         "(its own JSON line; the default workload is the headline metric)")
+    ap.add_argument("--workers", type=int, default=8, help="batched64: concurrent problems")
     ap.add_argument("--kernel-only", choices=["kapply", "minv"], default=None,
                     help="set up once, then run only the operator application (or preconditioner solve) "
                          "--steps times: for kernel profiles")
@@ -467,12 +471,122 @@ def run_ours(args, ws, rank, local, dist):
     return 0
 
 
+def run_batched(args, ws, rank, local, dist):
+    """64 independent problems of uneven sizes (each: own PSF, BC, noise level,
+    GCV lambda) per step through kp_solve_batch; solves/s over the batch.
+    Inputs are resident on the device (b formed untimed by each problem's own
+    operator); e2e re-times the step with the PSFs and b copied from pinned
+    host memory and every x copied back inside the timed region."""
+    import numpy as np
+    import torch
+    from paper_2311_15393_gb300 import build as _build
+    _build.build()
+    from paper_2311_15393_gb300 import kpsvd, synth
+
+    dev = local
+    torch.cuda.set_device(dev)
+    probs = synth.make_batch(64, seed=synth.SEED_BASE + synth.BATCH_INDEX + 1000 * rank)
+    f32 = torch.float32
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=f32, device=dev)
+    dp, host = [], []
+    with kpsvd.KpContext(dev) as ctx:
+        for P in probs:
+            psf = kpsvd.to_device(P.psf, torch.float64, f"cuda:{dev}")
+            xt = kpsvd.to_device(P.x_true, f32, f"cuda:{dev}")
+            g = kpsvd.to_device(P.noise_dirs[0], f32, f"cuda:{dev}")
+            b = torch.empty_like(xt)
+            ctx.kp_setup(psf, P.n_r, P.n_c, P.center, P.bc, P.op_rank, args.op, args.pc, "f32", "projected")
+            ctx.kp_forward(xt, g, P.noise_levels[0], b)
+            dp.append(dict(psf=psf, b=b, x=torch.zeros_like(b), n_r=P.n_r, n_c=P.n_c, center=P.center, bc=P.bc,
+                           op_rank=P.op_rank))
+            host.append((psf.cpu().pin_memory(), b.cpu().pin_memory(), torch.empty_like(b, device="cpu").pin_memory()))
+    torch.cuda.synchronize()
+
+    def step():
+        for d in dp:
+            d["x"].zero_()
+        st, ms_, res_ = kpsvd.kp_solve_batch(dp, op_prec=args.op, pc_prec=args.pc, tol=1e-7, maxit=500,
+                                             workers=args.workers, device=dev, check=False)
+        bad = [i.status for _, i in res_ if i.status not in (kpsvd.KP_OK, kpsvd.KP_ENOCONV)]
+        if bad:  # anything but convergence or stagnation at FP32 accuracy is a failure
+            raise RuntimeError(f"kp_solve_batch failed: statuses {bad}: {kpsvd._lib.kp_last_error().decode()}")
+        return st, ms_, res_
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        step()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    times, res = [], None
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        st, _, res = step()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+    barrier(dist)
+    ms = max_over_ranks(dist, 1e3 * statistics.median(times))
+    value = sum_over_ranks(dist, float(len(dp))) / (ms / 1e3)
+
+    # end to end: PSF and b from pinned host memory, x back, inside the timed region
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d, (hp, hb, hx) in zip(dp, host):
+            d["psf"].copy_(hp, non_blocking=True)
+            d["b"].copy_(hb, non_blocking=True)
+        torch.cuda.synchronize()
+        step()
+        for d, (hp, hb, hx) in zip(dp, host):
+            hx.copy_(d["x"], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    e2e_ms = max_over_ranks(dist, 1e3 * statistics.median(e2e))
+    sizes = {}
+    for d, (lam, info) in zip(dp, res):
+        k = f"{d['n_r']}x{d['n_c']}"
+        e = sizes.setdefault(k, {"problems": 0, "iters": []})
+        e["problems"] += 1
+        e["iters"].append(info.iters)
+    for e in sizes.values():
+        e["iters"] = [min(e["iters"]), int(np.median(e["iters"])), max(e["iters"])]
+    result = {"metric": "solves/s, 64 independent deblurring problems of uneven sizes (setup + GCV lambda + FPCG "
+                        "to 1e-7 each)",
+              "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+              "data": "synthetic",
+              "config": {"workload": "batched64", "sizes": [f"{a}x{b}" for a, b in synth.BATCH_SIZES],
+                         "op_prec": args.op, "pc_prec": args.pc, "vec_prec": "f32", "lambda": "gcv", "tol": 1e-7,
+                         "workers": args.workers, "parallelism": f"replicas x{ws}",
+                         "l2": "256 MiB buffer written before every step",
+                         "step": "kp_solve_batch over 64 problems"},
+              "e2e": {"value": sum_over_ranks(dist, float(len(dp))) / (e2e_ms / 1e3), "unit": "solves/s",
+                      "h2d_bytes_per_step": sum(h[0].numel() * 8 + h[1].numel() * 4 for h in host),
+                      "d2h_bytes_per_step": sum(h[2].numel() * 4 for h in host)},
+              "clocks": clk,
+              "converged": sum(info.status == kpsvd.KP_OK for _, info in res),
+              "stagnated_above_tol": sum(info.status == kpsvd.KP_ENOCONV for _, info in res),
+              "max_rel_res": max(info.rel_res for _, info in res),
+              "per_size": sizes}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local, dist = dist_init(args)
     try:
         if args.impl == "reference":
             return run_reference(args, ws, rank, dist)
+        if args.workload == "batched64":
+            return run_batched(args, ws, rank, local, dist)
         return run_ours(args, ws, rank, local, dist)
     finally:
         if dist is not None:

@@ -211,6 +211,12 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     residual update (default 0.1 for F32 / BF16 / BF16X3
  *                     operators, 0 = off for the F64 operator)
  *   "check_every"     iterations between host convergence checks (default 2)
+ *   "op_auto_cond"    > 0 (default 0 = off): with a BF16 operator, each tik_pcg
+ *                     uses the BF16X3 inner operator (three bf16 pairs) when
+ *                     cond(A^T A + lambda^2 I) ~ (max Sigma^2 + lambda^2) /
+ *                     lambda^2 exceeds this value, else BF16 (kp_solve_batch
+ *                     sets 1e4 for BF16 batches, and solves a problem again
+ *                     with BF16X3 if its BF16 solve stalls or breaks down)
  *   "cg_fuse"         1 (default): with a BF16 / BF16X3 operator, an F16 / BF16
  *                     preconditioner and FP32 vectors, the x / r update also
  *                     writes the preconditioner's narrow input, scaled by a
@@ -239,6 +245,48 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     chosen lambda by ~1e-6 relative; FP64 vectors always
  *                     use FP64.  Takes effect at the next kp_setup. */
 kp_status kp_set_option(kp_ctx* ctx, const char* name, double value);
+
+/* ---- Batched independent problems of uneven sizes ------------------------
+ * Many deblurring problems, each with its own PSF, size, boundary condition,
+ * b and lambda (given, or chosen per problem), solved with one set of
+ * precisions and solver settings.  Not part of the paper; the batched
+ * configuration of the project's workloads.  The problems run concurrently:
+ * `workers` host threads each own one context (and stream) and take the
+ * problems largest first, so the GPU overlaps the kernels of different
+ * problems; each problem computes exactly what kp_setup, choose_lambda and
+ * tik_pcg compute for it alone.
+ *   psf, b, x   device pointers as for kp_setup / tik_pcg (x: written)
+ *   lambda      in: > 0 a fixed lambda; <= 0 chosen by `method` with
+ *               lambda_param (choose_lambda's param); out: the lambda used
+ *   info        out: the problem's solve summary (info.status = its status)
+ * The caller owns every pointer; all must stay valid until the call returns. */
+typedef struct {
+  const double* psf;
+  int n_r, n_c, center_r, center_c;
+  kp_bc bc;
+  int op_rank;
+  const void* b;
+  void* x;
+  double lambda;
+  double lambda_param;
+  kp_solve_info info;
+} kp_problem;
+
+typedef struct {
+  kp_prec op_prec, pc_prec, vec_prec;
+  kp_sigma sigma;
+  kp_lambda_method method; /* used for problems with lambda <= 0 */
+  double tol;
+  int maxit;
+  int flexible;
+  int workers; /* concurrent problems; <= 0: 8 */
+} kp_batch_opts;
+
+/* Solve probs[0..nprob) (device `device`).  Returns KP_OK when every problem
+ * returned KP_OK, else the status of the first failing problem (its message
+ * in kp_last_error); KP_EINVAL for NULL arguments or nprob < 0.  ms_total
+ * (host, nullable): wall time of the whole batch in milliseconds. */
+kp_status kp_solve_batch(int device, kp_problem* probs, int nprob, const kp_batch_opts* opts, double* ms_total);
 
 /* Number of this library's kernel launches issued on the context since the
  * last reset (reset = 1 clears it after reading). */

@@ -205,6 +205,12 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
       return KP_EINVAL;
     }
     ctx->check_every = (int)value;
+  } else if (!strcmp(name, "op_auto_cond")) {
+    if (!(value >= 0)) {
+      kp_set_error("op_auto_cond must be >= 0");
+      return KP_EINVAL;
+    }
+    ctx->op_auto_cond = value;
   } else if (!strcmp(name, "cg_fuse")) {
     if (value != 0 && value != 1) {
       kp_set_error("cg_fuse must be 0 or 1");

@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "kp_internal.h"
 #include "kp_vec.cuh"
@@ -813,8 +814,8 @@ void tc_plan_set_runtime(TcGemmPlan* plan, const float* alpha_dev, const int* fl
 template <int KIND, int BN, int CPS, int KPS>
 static kp_status launch_kind(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
   using C = TcCfg<BN, CPS, KPS>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<bool> attr_set{false};  // contexts on several host threads launch this
+  if (!attr_set.load()) {
     KP_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN, CPS, KPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  C::SMEM));
     attr_set = true;

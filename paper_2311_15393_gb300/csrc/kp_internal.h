@@ -125,11 +125,14 @@ struct kp_ctx {
   int n_r = 0, n_c = 0, c_r = 0, c_c = 0, rank = 0;
   kp_bc bc = KP_BC_ZERO;
   kp_prec op_prec = KP_F64, pc_prec = KP_F64, vec_prec = KP_F64;
+  kp_prec op_prec_setup = KP_F64;  // op_prec given to kp_setup (op_prec may be raised per solve)
+  double sigma_max = -1.0;         // max |Sigma| of the current setup (< 0: not computed yet)
   kp_sigma sigma_mode = KP_SIGMA_PROJECTED;
 
   // options
   double reliable_delta = -1.0;  // < 0: default for the operator precision
   int check_every = 2;
+  double op_auto_cond = 0.0;  // > 0: BF16 inner operator raised to BF16X3 when cond(K) exceeds it
   bool cg_fuse = true;  // the x / r update also writes the preconditioner's narrow input (where possible)
   double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD
   int jacobi_max_sweeps = 40;

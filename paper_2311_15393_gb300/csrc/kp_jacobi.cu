@@ -22,6 +22,8 @@
 // products (the transform F C and the Gram test) in FP32 and use eps = 2^-23
 // in both thresholds; rotations stay FP64.
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <cmath>
 #include <vector>
 
@@ -60,8 +62,11 @@ __device__ __forceinline__ int rr_player(int t, int round, int npad) {
   return t == 0 ? 0 : 1 + ((t - 1 + round) % (npad - 1));
 }
 
-__global__ void __launch_bounds__(JT) k_jacobi_round(double* __restrict__ W, double* __restrict__ V, int m, int n,
-                                                     int npad, int round, double tol, double floor,
+// One round of the one-sided Jacobi sweep in T arithmetic (FP64, or FP32 for
+// the FP32-vector setup, whose tolerance is FP32-level anyway)
+template <typename T>
+__global__ void __launch_bounds__(JT) k_jacobi_round(T* __restrict__ W, T* __restrict__ V, int m, int n, int npad,
+                                                     int round, double tol, double floor,
                                                      unsigned int* __restrict__ rot_count) {
   const int pidx = blockIdx.x;
   int i = rr_player(pidx, round, npad);
@@ -72,20 +77,20 @@ __global__ void __launch_bounds__(JT) k_jacobi_round(double* __restrict__ W, dou
     j = t;
   }
   if (j >= n) return;  // pair with the padding column
-  double* a = W + (long long)i * m;
-  double* b = W + (long long)j * m;
-  double sa = 0.0, sb = 0.0, sg = 0.0;
+  T* a = W + (long long)i * m;
+  T* b = W + (long long)j * m;
+  T sa = 0, sb = 0, sg = 0;
   for (int r = threadIdx.x; r < m; r += JT) {
-    double x = a[r], y = b[r];
+    const T x = a[r], y = b[r];
     sa = fma(x, x, sa);
     sb = fma(y, y, sb);
     sg = fma(x, y, sg);
   }
-  __shared__ double sh[3][JT / 32];
-  __shared__ double cs[2];
-  sa = jwarp_sum(sa);
-  sb = jwarp_sum(sb);
-  sg = jwarp_sum(sg);
+  __shared__ T sh[3][JT / 32];
+  __shared__ T cs[2];
+  sa = jwsum<T>(sa);
+  sb = jwsum<T>(sb);
+  sg = jwsum<T>(sg);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     sh[0][wid] = sa;
@@ -94,20 +99,20 @@ __global__ void __launch_bounds__(JT) k_jacobi_round(double* __restrict__ W, dou
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double al = 0, be = 0, ga = 0;
+    T al = 0, be = 0, ga = 0;
     for (int w = 0; w < JT / 32; ++w) {
       al += sh[0][w];
       be += sh[1][w];
       ga += sh[2][w];
     }
-    double c = 1.0, s = 0.0;
+    T c = 1, s = 0;
     // rotate only if the pair is not orthogonal to relative precision tol and
     // the projection of the smaller column on the larger, |gamma| / |a_max|,
     // is above the noise floor m eps ||A||_F that rounding leaves in any column
-    if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be) && fabs(ga) > floor * sqrt(fmax(al, be))) {
-      double zeta = (be - al) / (2.0 * ga);
-      double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      c = 1.0 / sqrt(1.0 + t * t);
+    if (ga != T(0) && fabs(ga) > T(tol) * sqrt(al) * sqrt(be) && fabs(ga) > T(floor) * sqrt(fmax(al, be))) {
+      const T zeta = (be - al) / (T(2) * ga);
+      const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+      c = T(1) / sqrt(T(1) + t * t);
       s = c * t;
       atomicAdd(rot_count, 1u);
     }
@@ -115,17 +120,17 @@ __global__ void __launch_bounds__(JT) k_jacobi_round(double* __restrict__ W, dou
     cs[1] = s;
   }
   __syncthreads();
-  const double c = cs[0], s = cs[1];
-  if (s == 0.0) return;
+  const T c = cs[0], s = cs[1];
+  if (s == T(0)) return;
   for (int r = threadIdx.x; r < m; r += JT) {
-    double x = a[r], y = b[r];
+    const T x = a[r], y = b[r];
     a[r] = c * x - s * y;
     b[r] = s * x + c * y;
   }
-  double* va = V + (long long)i * n;
-  double* vb = V + (long long)j * n;
+  T* va = V + (long long)i * n;
+  T* vb = V + (long long)j * n;
   for (int r = threadIdx.x; r < n; r += JT) {
-    double x = va[r], y = vb[r];
+    const T x = va[r], y = vb[r];
     va[r] = c * x - s * y;
     vb[r] = s * x + c * y;
   }
@@ -636,10 +641,13 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
     // convergence, count the pairs that need a rotation on G = W^T W (one
     // GEMM): a sweep over a matrix with no such pair rotates nothing.
     double* G = nullptr;
-    float *G32 = nullptr, *W32 = nullptr;
-    if (fast) {
+    float *G32 = nullptr, *W32 = nullptr, *V32 = nullptr;
+    if (fast) {  // the sweeps rotate FP32 copies of W and Vw (copied back below)
       KP_TRY(kp_alloc(ctx, (void**)&G32, sizeof(float) * (size_t)n * n));
       KP_TRY(kp_alloc(ctx, (void**)&W32, sizeof(float) * (size_t)m * n));
+      KP_TRY(kp_alloc(ctx, (void**)&V32, sizeof(float) * (size_t)n * n));
+      KP_TRY(convert_f64_to_f32(ctx, W, W32, (long long)m * n));
+      KP_TRY(convert_f64_to_f32(ctx, Vw, V32, (long long)n * n));
     } else {
       KP_TRY(kp_alloc(ctx, (void**)&G, sizeof(double) * (size_t)n * n));
     }
@@ -655,7 +663,6 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
       const int gb = std::max(1, std::min((int)(((long long)n * n + 255) / 256), ctx->sm_count * 8));
       KP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st));
       if (fast) {
-        KP_TRY(convert_f64_to_f32(ctx, W, W32, (long long)m * n));
         gd.A.ptr = W32;
         gd.B.ptr = W32;
         gd.epi.out = G32;
@@ -686,8 +693,12 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
       if (!exec) {  // one sweep (n - 1 rounds) as a graph, built at the first sweep
         KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         k_zero_u32<<<1, 1, 0, st>>>(cnt);
-        for (int round = 0; round < npad - 1; ++round)
-          k_jacobi_round<<<npad / 2, JT, 0, st>>>(W, Vw, m, n, npad, round, tol, floor, cnt);
+        for (int round = 0; round < npad - 1; ++round) {
+          if (fast)
+            k_jacobi_round<float><<<npad / 2, JT, 0, st>>>(W32, V32, m, n, npad, round, tol, floor, cnt);
+          else
+            k_jacobi_round<double><<<npad / 2, JT, 0, st>>>(W, Vw, m, n, npad, round, tol, floor, cnt);
+        }
         cudaError_t ce = cudaStreamEndCapture(st, &graph);
         if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
         if (ce != cudaSuccess) {
@@ -723,6 +734,10 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     KP_TRY(gst);
+    if (fast && sweeps > 0) {
+      KP_TRY(convert_f32_to_f64(ctx, W32, W, (long long)m * n));
+      KP_TRY(convert_f32_to_f64(ctx, V32, Vw, (long long)n * n));
+    }
     if (h_cnt != 0) {
       kp_set_error("jacobi_svd: no convergence after %d sweeps (%u rotations in the last)", sweeps, h_cnt);
       return KP_ENOCONV;
@@ -733,7 +748,15 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
   int npow2 = 1;
   while (npow2 < n) npow2 <<= 1;
   size_t shm = (size_t)npow2 * (sizeof(double) + sizeof(int));
-  if (shm > 48 * 1024) KP_CUDA(cudaFuncSetAttribute(k_sort_desc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  if (shm > 48 * 1024) {  // raise the kernel's limit, never lower it (other threads may launch it meanwhile)
+    static std::mutex mu;
+    static size_t shm_set = 48 * 1024;
+    std::lock_guard<std::mutex> lock(mu);
+    if (shm > shm_set) {
+      KP_CUDA(cudaFuncSetAttribute(k_sort_desc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      shm_set = shm;
+    }
+  }
   k_sort_desc<<<1, 1024, shm, st>>>(sw, n, npow2, perm);
   KP_LAUNCHED(ctx);
   k_gather<<<n, 256, 0, st>>>(W, Vw, sw, perm, m, n, U, V, s);
@@ -849,10 +872,10 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
 // CGS2 launch: Q staged in shared memory when m p elements fit
 template <typename T>
 static kp_status cgs2(kp_ctx* ctx, T* Q, int m, int p, T* R) {
-  static bool attr_set = false;
+  static std::atomic<bool> attr_set{false};  // contexts on several host threads launch this
   const size_t bytes = sizeof(T) * (size_t)m * p;
   const bool staged = bytes <= (size_t)CG_SMEM_MAX;
-  if (staged && !attr_set) {
+  if (staged && !attr_set.load()) {
     KP_CUDA(cudaFuncSetAttribute(k_cgs2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, CG_SMEM_MAX));
     attr_set = true;
   }

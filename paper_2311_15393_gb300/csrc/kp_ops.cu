@@ -27,6 +27,7 @@
 namespace {
 struct OpsState {
   TcGemmPlan* G[2][4] = {{nullptr}};  // [mode][gemm]
+  TcGemmPlan* Gin[2][4] = {{nullptr}};  // inner-operator plans per variant: [0] BF16 pair, [1] BF16X3 pairs
   bool batched = false;               // G2 / G4 write per-term outputs, summed by k_term_reduce
   TcGemmPlan* P[4] = {nullptr};
   float* inv_slot = nullptr;          // device scale for P4
@@ -276,6 +277,42 @@ __global__ void __launch_bounds__(VEC_THREADS)
   if (td.out) term_dot_finish(dh, dl, td);
 }
 
+// tensor-core plan of GEMM w of the operator in `mode` for the current pairs
+static kp_status op_plan(kp_ctx* ctx, OpsState* os, int mode, int w, TcGemmPlan** out) {
+  const void* bptr = w == 0 ? (mode == OP_INNER ? ctx->w_img2 : ctx->w_img3) : (w == 2 ? ctx->w_img : nullptr);
+  GemmDesc g = op_desc(ctx, w, mode, bptr);
+  int splits = (w == 1 || w == 3) ? square_splits(ctx) : 1;
+  if ((w == 1 || w == 3) && os->batched) {
+    g.batch_rows = ctx->n_c;
+    g.M = ctx->rank * ctx->n_c;
+    splits = 1;
+  }
+  return tc_plan_create(ctx, g, TC_BF16, splits, out);
+}
+
+kp_status ops_set_inner(kp_ctx* ctx, kp_prec p) {
+  if (!op_is_tc(ctx) || (p != KP_BF16 && p != KP_BF16X3)) {
+    kp_set_error("ops_set_inner: needs a tensor-core operator and BF16 / BF16X3");
+    return KP_ENOTSUP;
+  }
+  if (ctx->op_prec == p) return KP_OK;
+  OpsState* os = ops(ctx);
+  const int v = p == KP_BF16X3 ? 1 : 0;
+  const kp_prec old = ctx->op_prec;
+  ctx->op_prec = p;  // the pairs and slice counts follow it
+  for (int w = 0; w < 4; ++w) {
+    if (!os->Gin[v][w]) {
+      const kp_status st = op_plan(ctx, os, OP_INNER, w, &os->Gin[v][w]);
+      if (st != KP_OK) {
+        ctx->op_prec = old;
+        return st;
+      }
+    }
+    os->G[OP_INNER][w] = os->Gin[v][w];
+  }
+  return KP_OK;
+}
+
 kp_status ops_prepare(kp_ctx* ctx) {
   const int n_r = ctx->n_r, n_c = ctx->n_c, r = ctx->rank;
   const long long N = (long long)n_r * n_c;
@@ -325,19 +362,9 @@ kp_status ops_prepare(kp_ctx* ctx) {
     // workspace; k_term_reduce adds them with the fused epilogue
     os->batched = r >= 2 && n_c % 128 == 0 && n_r % 4 == 0 && (long long)r * N <= ctx->w_split_elems &&
                   ctx->splitk_override == 0;
-    for (int mode = 0; mode < 2; ++mode) {
-      for (int w = 0; w < 4; ++w) {
-        const void* bptr = w == 0 ? (mode == OP_INNER ? ctx->w_img2 : ctx->w_img3) : (w == 2 ? ctx->w_img : nullptr);
-        GemmDesc g = op_desc(ctx, w, mode, bptr);
-        int splits = (w == 1 || w == 3) ? square_splits(ctx) : 1;
-        if ((w == 1 || w == 3) && os->batched) {
-          g.batch_rows = n_c;
-          g.M = r * n_c;
-          splits = 1;
-        }
-        KP_TRY(tc_plan_create(ctx, g, TC_BF16, splits, &os->G[mode][w]));
-      }
-    }
+    for (int mode = 0; mode < 2; ++mode)
+      for (int w = 0; w < 4; ++w) KP_TRY(op_plan(ctx, os, mode, w, &os->G[mode][w]));
+    for (int w = 0; w < 4; ++w) os->Gin[ctx->op_prec == KP_BF16X3 ? 1 : 0][w] = os->G[OP_INNER][w];
   }
   if (pc_is_tc(ctx)) {
     const int kind = ctx->pc_prec == KP_BF16 ? TC_BF16 : (ctx->pc_prec == KP_F16 ? TC_F16 : TC_E4M3);

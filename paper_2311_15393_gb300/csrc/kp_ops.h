@@ -34,6 +34,11 @@ kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const doubl
 // number of bf16 slices the inner operator wants for p (0 for SIMT operators)
 int op_inner_slices(kp_ctx* ctx);
 
+// switch a tensor-core operator's inner precision between BF16 (one factor x
+// activation pair) and BF16X3 (three pairs of the same bf16 slices); the
+// plans of each variant are built once per setup
+kp_status ops_set_inner(kp_ctx* ctx, kp_prec p);
+
 // ---- folded quantisation (tensor-core operator with batched term sums,
 // F16 / BF16 preconditioner, FP32 vectors): the K application's term sum
 // also gives max |q|, and the x / r update writes the preconditioner's

@@ -315,6 +315,8 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
   ctx->rank = rank;
   ctx->bc = bc;
   ctx->op_prec = op_prec;
+  ctx->op_prec_setup = op_prec;
+  ctx->sigma_max = -1.0;
   ctx->pc_prec = pc_prec;
   ctx->vec_prec = vec_prec;
   ctx->sigma_mode = sigma;

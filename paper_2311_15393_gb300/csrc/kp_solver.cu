@@ -27,16 +27,28 @@
 
 
 namespace {
-// after a reliable update requested mid-run: record ||r_true|| in the
-// history and either resume (clear the pause) or stop as converged (the
-// true residual already meets the tolerance: F_REASON = R_CONV | R_TRUE)
+// after a reliable update: record ||r_true|| in the history and either
+// resume (clear the pause), stop as converged (the true residual meets the
+// tolerance: F_REASON = R_CONV | R_TRUE), or stop as stagnated (R_STAGNATE:
+// three replacements in a row that did not halve the true residual, i.e.
+// the attainable accuracy of the FP32 vectors and the accurate operator is
+// reached above the tolerance)
 constexpr int R_TRUE = 32;
+constexpr int R_STAGNATE = 64;
+constexpr int STAG_REPLACEMENTS = 3;
 __global__ void k_after_replace(double* s, int* f, double* hist, int hist_cap) {
   const double rr = s[S_RR];
   const int it = f[F_ITER];
   if (it < hist_cap) hist[it] = sqrt(rr / s[S_RR0]);
+  const double prev = s[S_RTPREV];
+  f[F_STAG] = (prev > 0.0 && rr > 0.25 * prev) ? f[F_STAG] + 1 : 0;
+  f[F_SINCE] = 0;
+  s[S_RTPREV] = rr;
   if (rr <= s[S_TOL2]) {
     f[F_REASON] = R_CONV | R_TRUE;
+    f[F_PAUSE] = 1;
+  } else if (f[F_STAG] >= STAG_REPLACEMENTS) {
+    f[F_REASON] = R_STAGNATE;
     f[F_PAUSE] = 1;
   } else {
     f[F_REASON] = 0;
@@ -155,9 +167,27 @@ static kp_status replace_residual(kp_ctx* ctx, const SolveBufs& B, const void* b
   return KP_OK;
 }
 
+// With op_auto_cond > 0 and a BF16 operator: the inner operator of this solve
+// is BF16X3 when cond(A^T A + lam^2 I) ~ (max Sigma^2 + lam^2) / lam^2
+// exceeds op_auto_cond (the BF16 inner operator's rounding, ~2^-8, then
+// stalls or breaks the recurrences; BF16X3's is ~2^-16), else BF16.
+static kp_status choose_inner(kp_ctx* ctx, double lam2) {
+  if (!(ctx->op_auto_cond > 0) || ctx->op_prec_setup != KP_BF16) return KP_OK;
+  if (ctx->sigma_max < 0) {
+    double h[2];
+    KP_TRY(norm_amax_dev(ctx, ctx->Sigma64, (long long)ctx->n_r * ctx->n_c, true, ctx->dscal + S_RR));
+    KP_CUDA(cudaMemcpyAsync(h, ctx->dscal + S_RR, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    KP_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->sigma_max = h[1];
+  }
+  const double cond = (ctx->sigma_max * ctx->sigma_max + lam2) / lam2;
+  return ops_set_inner(ctx, cond > ctx->op_auto_cond ? KP_BF16X3 : KP_BF16);
+}
+
 static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible, void* x,
                               int warm_start, kp_solve_info* info) {
   const long long N = (long long)ctx->n_r * ctx->n_c;
+  KP_TRY(choose_inner(ctx, lambda * lambda));
   const bool f64 = ctx->vec_prec == KP_F64;
   const double lam2 = lambda * lambda;
   const SolveBufs B = bufs(ctx);
@@ -206,6 +236,7 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
       KP_TRY(norm_amax_dev(ctx, B.r, N, f64, ctx->dscal + S_RR));
       KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RMAX, ctx->dscal + S_RR, 8, cudaMemcpyDeviceToDevice, st));
     }
+    KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RTPREV, ctx->dscal + S_RR, 8, cudaMemcpyDeviceToDevice, st));
     KP_TRY(read_flags(ctx, &hf, hs));
     double h0 = std::sqrt(hs[S_RR] / rr0);
     KP_CUDA(cudaMemcpyAsync(ctx->hist, &h0, sizeof(double), cudaMemcpyHostToDevice, st));
@@ -289,6 +320,12 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
           result = KP_OK;
           break;
         }
+        if (hf.reason & R_STAGNATE) {
+          result = KP_ENOCONV;
+          kp_set_error("tik_pcg: stagnated at ||r||/||A^T b|| = %.3e (iteration %d): the tolerance is below the "
+                       "attainable accuracy of this precision", std::sqrt(final_rr / rr0), iters);
+          break;
+        }
         if (hf.reason == R_REPLACE) {
           // reliable update in the middle of the run: replace, check and
           // resume on the device, with no host round trip
@@ -303,18 +340,24 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
         }
         bool need_replace = reliable && (hf.reason & (R_CONV | R_REPLACE | R_MAXIT));
         if (need_replace) {
+          const int reason = hf.reason;
           KP_TRY(replace_residual(ctx, B, b, x, lam2));
           ++repl;
+          k_after_replace<<<1, 1, 0, st>>>(ctx->dscal, ctx->dflags, ctx->hist, ctx->hist_cap);
+          KP_LAUNCHED(ctx);
           KP_TRY(read_flags(ctx, &hf, hs));
           final_rr = hs[S_RR];
-          double hv = std::sqrt(final_rr / rr0);
-          if (iters < ctx->hist_cap)
-            KP_CUDA(cudaMemcpyAsync(ctx->hist + iters, &hv, sizeof(double), cudaMemcpyHostToDevice, st));
-          KP_CUDA(cudaStreamSynchronize(st));
-          if (final_rr <= tol * tol * rr0) {
+          if (hf.reason & R_TRUE) {
             result = KP_OK;
             break;
           }
+          if ((hf.reason & R_STAGNATE) && !(reason & R_MAXIT)) {
+            result = KP_ENOCONV;
+            kp_set_error("tik_pcg: stagnated at ||r||/||A^T b|| = %.3e (iteration %d): the tolerance is below the "
+                         "attainable accuracy of this precision", std::sqrt(final_rr / rr0), iters);
+            break;
+          }
+          hf.reason = reason;
         } else if (hf.reason & R_CONV) {
           result = KP_OK;
           break;

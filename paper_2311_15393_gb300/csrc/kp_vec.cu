@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T*
   }
 }
 
-// p = z + beta p ; optional bf16 split copy of p (slices written at stride)
+// p = z + beta p ; optional bf16 split copy of p (slices written at stride).
+// With beta_dev null, p = z: the old p is not read (it may be uninitialised).
 template <typename T>
 __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long n, int vec4,
                            const double* __restrict__ beta_dev, __nv_bfloat16* __restrict__ ps, int slices,
@@ -155,8 +156,12 @@ __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long
     if (vec4) {
       const long long n4 = n >> 2;
       for (long long i = tid; i < n4; i += stride) {
-        const float4 pi = ld4(p, i), zi = ld4(z, i);
-        float4 pn = make_float4(fmaf(be, pi.x, zi.x), fmaf(be, pi.y, zi.y), fmaf(be, pi.z, zi.z), fmaf(be, pi.w, zi.w));
+        const float4 zi = ld4(z, i);
+        float4 pn = zi;
+        if (beta_dev) {
+          const float4 pi = ld4(p, i);
+          pn = make_float4(fmaf(be, pi.x, zi.x), fmaf(be, pi.y, zi.y), fmaf(be, pi.z, zi.z), fmaf(be, pi.w, zi.w));
+        }
         st4(p, i, pn);
         if (ps) {
           float w[4] = {pn.x, pn.y, pn.z, pn.w};
@@ -177,7 +182,7 @@ __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long
       i0 = 4 * n4 + tid;
     }
     for (long long i = i0; i < n; i += stride) {
-      const float pn = fmaf(be, p[i], z[i]);
+      const float pn = beta_dev ? fmaf(be, p[i], z[i]) : z[i];
       p[i] = pn;
       if (ps) {
         float v = pn;
@@ -191,7 +196,7 @@ __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long
   } else {
     const double beta = beta_dev ? *beta_dev : 0.0;
     for (long long i = tid; i < n; i += stride) {
-      T pn = (T)((double)z[i] + beta * (double)p[i]);
+      T pn = beta_dev ? (T)((double)z[i] + beta * (double)p[i]) : z[i];
       p[i] = pn;
       if (ps) {
         float v = (float)pn;

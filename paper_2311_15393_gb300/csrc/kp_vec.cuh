@@ -17,9 +17,13 @@ __device__ __forceinline__ __nv_fp8_e4m3 to_narrow<__nv_fp8_e4m3>(float v) { ret
 enum {
   S_RR = 0, S_AMAX = 1, S_PQ = 2, S_ALPHA = 3, S_ZR = 4, S_ZRNEW = 5, S_ZROLD = 6, S_BETA = 7,
   S_RR0 = 8, S_RMAX = 9, S_TOL2 = 10, S_DELTA2 = 11,
-  S_QPQ = 12, S_QMAX = 13  // fused iteration: p^T q and max |q| (K application's term sum)
+  S_QPQ = 12, S_QMAX = 13,  // fused iteration: p^T q and max |q| (K application's term sum)
+  S_RTPREV = 14             // ||r||^2 of the previous true residual (stagnation test)
 };
-enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4 };
+enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4, F_STAG = 5, F_SINCE = 6 };
+// a reliable update is also due after this many iterations without one (so a
+// recurred residual that stops falling is checked against the true one)
+constexpr int REPLACE_EVERY = 50;
 enum { R_CONV = 1, R_REPLACE = 2, R_MAXIT = 4, R_BREAKDOWN = 8, R_NUMERIC = 16 };
 
 // scalar step run by the last block of a reduction, on its final values:
@@ -302,7 +306,7 @@ __device__ inline void run_post(const PostOp& po, const double* vals) {
     int reason = 0;
     if (!isfinite(rr)) reason |= R_NUMERIC;
     else if (rr <= s[S_TOL2]) reason |= R_CONV;
-    else if (s[S_DELTA2] > 0.0 && rr < s[S_DELTA2] * s[S_RMAX]) reason |= R_REPLACE;
+    else if (s[S_DELTA2] > 0.0 && (rr < s[S_DELTA2] * s[S_RMAX] || ++f[F_SINCE] >= REPLACE_EVERY)) reason |= R_REPLACE;
     if (it >= f[F_MAXIT]) reason |= R_MAXIT;
     if (reason) {
       f[F_REASON] |= reason;

@@ -27,7 +27,8 @@ LAMBDA = {"gcv": 0, "wgcv": 1, "discrepancy": 2, "opt": 3}
 # every function declared in include/kpsvd.h
 EXPORTS = ["kp_create", "kp_destroy", "kp_setup", "kp_forward", "tik_pcg", "choose_lambda", "kp_apply_A",
            "kp_apply_K", "kp_apply_Minv", "kp_get_spectrum", "kp_get_terms", "kp_get_kpsvd", "kp_get_rank",
-           "kp_set_option", "kp_launch_count", "kp_status_str", "kp_last_error", "kp_apply_Minv_noalloc"]
+           "kp_set_option", "kp_launch_count", "kp_status_str", "kp_last_error", "kp_apply_Minv_noalloc",
+           "kp_solve_batch"]
 
 
 class KpError(RuntimeError):
@@ -40,6 +41,21 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("replacements", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("status", ctypes.c_int), ("ms_solve", ctypes.c_double),
                 ("res_hist", ctypes.POINTER(ctypes.c_double)), ("res_hist_len", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    """kp_problem: one problem of a batch."""
+    _fields_ = [("psf", ctypes.c_void_p), ("n_r", ctypes.c_int), ("n_c", ctypes.c_int),
+                ("center_r", ctypes.c_int), ("center_c", ctypes.c_int), ("bc", ctypes.c_int),
+                ("op_rank", ctypes.c_int), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("lambda_", ctypes.c_double), ("lambda_param", ctypes.c_double), ("info", SolveInfo)]
+
+
+class BatchOpts(ctypes.Structure):
+    """kp_batch_opts."""
+    _fields_ = [("op_prec", ctypes.c_int), ("pc_prec", ctypes.c_int), ("vec_prec", ctypes.c_int),
+                ("sigma", ctypes.c_int), ("method", ctypes.c_int), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("flexible", ctypes.c_int), ("workers", ctypes.c_int)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -67,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "kp_status_str": ([i], ctypes.c_char_p),
         "kp_last_error": ([], ctypes.c_char_p),
         "kp_apply_Minv_noalloc": ([vp, vp, vp, i, i, d, vp, vp, vp], i),
+        "kp_solve_batch": ([i, ctypes.POINTER(Problem), i, ctypes.POINTER(BatchOpts), dp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -229,3 +246,30 @@ class KpContext:
 
     def kp_launch_count(self, reset: bool = False) -> int:
         return int(_lib.kp_launch_count(self._h, 1 if reset else 0))
+
+
+def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_prec: str = "f32",
+                   sigma: str = "projected", method: str = "gcv", tol: float = 1e-7, maxit: int = 500,
+                   flexible: bool = True, workers: int = 8, device: int = 0, check: bool = True):
+    """Solve a batch of independent problems (kp_solve_batch).  ``problems``:
+    dicts with psf, b, x (torch CUDA tensors), n_r, n_c, center, bc, op_rank and
+    optionally lam (> 0: fixed) and lambda_param.  Returns (status, ms_total,
+    [(lambda, Info), ...]) in the order given."""
+    arr = (Problem * len(problems))()
+    for k, p in enumerate(problems):
+        q = arr[k]
+        q.psf, q.b, q.x = _ptr(p["psf"]), _ptr(p["b"]), _ptr(p["x"])
+        q.n_r, q.n_c = p["n_r"], p["n_c"]
+        q.center_r, q.center_c = int(p["center"][0]), int(p["center"][1])
+        q.bc, q.op_rank = BC[p["bc"]], p["op_rank"]
+        q.lambda_ = p.get("lam") or 0.0
+        q.lambda_param = p.get("lambda_param", 0.0)
+    o = BatchOpts(PREC[op_prec], PREC[pc_prec], PREC[vec_prec], SIGMA[sigma], LAMBDA[method], tol, maxit,
+                  1 if flexible else 0, workers)
+    ms = ctypes.c_double(0.0)
+    st = _lib.kp_solve_batch(device, arr, len(problems), ctypes.byref(o), ctypes.byref(ms))
+    if check and st != KP_OK:
+        _check(st)
+    out = [(q.lambda_, Info(q.info.iters, q.info.replacements, q.info.rel_res, q.info.status, q.info.ms_solve,
+                            np.zeros(0))) for q in arr]
+    return st, ms.value, out

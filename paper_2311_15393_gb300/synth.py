@@ -27,8 +27,6 @@ def phantom(n_r: int, n_c: int, n_shapes: int, rng: np.random.Generator) -> np.n
     ~ U[n/32, n/8] per axis, ellipse angle ~ U[0, pi), intensity ~ U[0, 1],
     ellipse vs rectangle by a fair coin."""
     X = np.zeros((n_r, n_c), dtype=np.float64)
-    ii, jj = np.meshgrid(np.arange(n_r, dtype=np.float64),
-                         np.arange(n_c, dtype=np.float64), indexing="ij")
     for _ in range(n_shapes):
         cy = rng.uniform(0.0, n_r)
         cx = rng.uniform(0.0, n_c)
@@ -37,6 +35,14 @@ def phantom(n_r: int, n_c: int, n_shapes: int, rng: np.random.Generator) -> np.n
         hy = rng.uniform(n_r / 32.0, n_r / 8.0)
         theta = rng.uniform(0.0, np.pi)
         val = rng.uniform(0.0, 1.0)
+        # only the pixels of a box that holds the whole shape are tested
+        ry, rx = (max(hx, hy), max(hx, hy)) if is_ellipse else (hy, hx)
+        i0, i1 = max(0, int(np.floor(cy - ry)) - 1), min(n_r, int(np.ceil(cy + ry)) + 2)
+        j0, j1 = max(0, int(np.floor(cx - rx)) - 1), min(n_c, int(np.ceil(cx + rx)) + 2)
+        if i0 >= i1 or j0 >= j1:
+            continue
+        ii, jj = np.meshgrid(np.arange(i0, i1, dtype=np.float64),
+                             np.arange(j0, j1, dtype=np.float64), indexing="ij")
         dx = jj - cx
         dy = ii - cy
         if is_ellipse:
@@ -45,7 +51,7 @@ def phantom(n_r: int, n_c: int, n_shapes: int, rng: np.random.Generator) -> np.n
             mask = u * u + v * v <= 1.0
         else:
             mask = (np.abs(dx) <= hx) & (np.abs(dy) <= hy)
-        X[mask] = val
+        X[i0:i1, j0:j1][mask] = val
     return X
 
 
@@ -133,6 +139,37 @@ def make_problem(name: str, n: int | None = None, seed: int | None = None) -> Pr
                    x_true=x, psf=psf, noise_levels=list(w["noise"]), noise_dirs=dirs,
                    lam=w["lam"], tol=w["tol"], maxit=w["maxit"],
                    extra=dict(sigma_x=sx, sigma_y=sy, rho=w["rho"]))
+
+
+# Batched workload: independent problems of uneven sizes, each with its own
+# Gaussian PSF (sigma_x, sigma_y ~ U[1, 8], rho ~ U[-0.8, 0.8]), boundary
+# condition (zero or reflexive, fair coin), noise level ~ U[0.1%, 5%] and
+# GCV lambda; image shapes scale with the image side as in deblur1024_mixed.
+BATCH_SIZES = [(128, 128), (256, 256), (384, 512), (512, 512), (768, 768), (1024, 1024)]
+BATCH_INDEX = 3
+
+
+def make_batch(n_problems: int = 64, sizes=None, seed: int | None = None, op_rank: int = 4) -> list:
+    """``n_problems`` raw problem instances for the batched workload (one
+    noise level each); ``sizes`` restricts the size set (smaller test runs)."""
+    sizes = list(sizes or BATCH_SIZES)
+    rng = np.random.default_rng(SEED_BASE + BATCH_INDEX if seed is None else seed)
+    out = []
+    for k in range(n_problems):
+        n_r, n_c = sizes[int(rng.integers(len(sizes)))]
+        sx, sy = rng.uniform(1.0, 8.0), rng.uniform(1.0, 8.0)
+        rho = rng.uniform(-0.8, 0.8)
+        bc = "zero" if rng.uniform() < 0.5 else "reflexive"
+        nl = rng.uniform(0.001, 0.05)
+        shapes = max(4, int(round(150 * np.sqrt(n_r * n_c) / 1024)))
+        x = phantom(n_r, n_c, shapes, rng)
+        c = (n_r // 2, n_c // 2)
+        psf = gaussian_psf(n_r, n_c, c[0], c[1], sx, sy, rho)
+        g = noise_direction(n_r, n_c, rng)
+        out.append(Problem(name=f"batch{k}", n_r=n_r, n_c=n_c, center=c, bc=bc, op_rank=op_rank, x_true=x,
+                           psf=psf, noise_levels=[nl], noise_dirs=[g], lam=None, tol=1e-7, maxit=500,
+                           extra=dict(sigma_x=sx, sigma_y=sy, rho=rho)))
+    return out
 
 
 def random_matrix(m: int, n: int, seed: int) -> np.ndarray:

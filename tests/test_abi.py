@@ -52,3 +52,37 @@ def test_null_context_is_rejected_without_gpu(lib):
     assert lib.tik_pcg(None, None, ctypes.c_double(0.1), ctypes.c_double(1e-6), 10, 0, None, 0, None) != 0
     assert lib.kp_setup(None, None, 8, 8, 4, 4, 0, 0, 0, 0, 0, 1) != 0
     assert lib.kp_create(None, 0, None) != 0
+
+
+def test_batch_structs_match_the_header(tmp_path):
+    """The binding's kp_problem / kp_batch_opts / kp_solve_info layouts equal
+    the C compiler's (sizes and field offsets)."""
+    import shutil
+    import subprocess
+    from paper_2311_15393_gb300 import kpsvd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = {"kp_problem": (kpsvd.Problem, {"lambda_": "lambda"}), "kp_batch_opts": (kpsvd.BatchOpts, {}),
+              "kp_solve_info": (kpsvd.SolveInfo, {})}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kpsvd.h"', "int main(void) {"]
+    for cname, (cls, ren) in fields.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {ren.get(f, f)}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.split("\n") if l)
+    for cname, (cls, _) in fields.items():
+        assert int(out[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(out[f"{cname}.{f}"]) == getattr(cls, f).offset, f"{cname}.{f}"
+
+
+def test_batch_rejects_bad_arguments_without_gpu(lib):
+    assert lib.kp_solve_batch(0, None, 1, None, None) != 0
+    assert lib.kp_solve_batch(0, None, -1, None, None) != 0

@@ -143,6 +143,64 @@ def test_folded_quantisation_matches_separate_pass(kpsvd):
     assert rel(res[1][0], res[0][0]) < 5e-5
 
 
+def test_solve_ignores_stale_device_memory(kpsvd):
+    """Device memory a new context receives may hold old data (here NaN bit
+    patterns of a freed buffer): no kernel of setup or solve reads a buffer
+    before writing it (the first p = z does not read the old p)."""
+    junk = torch.full((256 * 1024 * 1024,), float("nan"), dtype=torch.float32, device="cuda:0")
+    del junk
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    pr = OracleProblem("deblur256_fp32", n=128, rank=3)
+    lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
+    x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam)
+    for op, pc in (("bf16", "f16"), ("f32", "f32")):
+        with setup_ctx(kpsvd, pr, op, pc, "f32") as ctx:
+            x, info = run(kpsvd, ctx, pr, lam, 1e-7, 500, True, "f32")
+            assert info.status == kpsvd.KP_OK
+            assert rel(x, x_star) < 1e-4
+
+
+def test_ill_conditioned_problem_raises_inner_operator(kpsvd):
+    """256 x 256, zero BC, wide PSF (sigma = 3.4 x 8), 0.14% noise: at the GCV
+    lambda cond(A^T A + lambda^2 I) ~ 1e5, where the BF16 inner operator's
+    rounding stalls FPCG.  With op_auto_cond = 1e4 the solve switches its
+    inner operator to BF16X3, converges to 1e-7, and x is within the
+    forward-error bound cond(K) tol of the oracle's x_lambda."""
+    P = synth.make_problem("deblur256_fp32", n=256)
+    psf = synth.gaussian_psf(256, 256, 128, 128, 3.4, 8.0, 0.17)
+    pr = OracleProblem("deblur256_fp32", n=256, psf=psf, bc="zero", rank=4)
+    pr.B, _ = forward.observe(pr.op, pr.P.x_true, pr.P.noise_dirs[0], 0.0014)
+    lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
+    cond = (np.max(np.abs(pr.kp.Sigma)) ** 2 + lam ** 2) / lam ** 2
+    assert cond > 1e4
+    x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam, tol=1e-10)
+    with setup_ctx(kpsvd, pr, "bf16", "f16", "f32") as ctx:
+        ctx.kp_set_option("op_auto_cond", 1e4)
+        x, info = run(kpsvd, ctx, pr, lam, 1e-7, 500, True, "f32")
+        print(f"cond(K) {cond:.2e}: {info.iters} iterations, {info.replacements} replacements, "
+              f"rel. error {rel(x, x_star):.2e}")
+        assert info.status == kpsvd.KP_OK
+        assert rel(x, x_star) < cond * 1e-7
+
+
+def test_stagnation_below_attainable_accuracy(kpsvd):
+    """FP32 vectors cannot reach a 1e-12 normal-equations residual: the solve
+    stops with KP_ENOCONV once three residual replacements in a row fail to
+    halve the true residual, long before maxit, with x at the oracle's
+    x_lambda to the usual accuracy."""
+    pr = OracleProblem("deblur256_fp32", n=128, rank=3)
+    lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
+    x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam)
+    with setup_ctx(kpsvd, pr, "bf16", "f16", "f32") as ctx:
+        x, info = run(kpsvd, ctx, pr, lam, 1e-12, 2000, True, "f32")
+        print(f"stagnation: {info.iters} iterations, {info.replacements} replacements, rel_res {info.rel_res:.2e}")
+        assert info.status == kpsvd.KP_ENOCONV
+        assert info.iters < 400
+        assert 1e-12 < info.rel_res < 1e-6
+        assert rel(x, x_star) < 1e-4
+
+
 def test_e4m3_fpcg_reaches_oracle_solution(kpsvd):
     """256 x 256: FPCG with the FP8 (E4M3) preconditioner, whose every apply
     is ~7% off the FP64 one, still reaches the oracle's x_lambda to 1e-4
