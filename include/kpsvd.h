@@ -211,6 +211,11 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     residual update (default 0.1 for F32 / BF16 / BF16X3
  *                     operators, 0 = off for the F64 operator)
  *   "check_every"     iterations between host convergence checks (default 2)
+ *   "pc_lambda_ratio" > 0 (default 1): the preconditioner of tik_pcg uses
+ *                     lambda_M = ratio * lambda (eq. PreconSystem has the
+ *                     system's lambda; Section 5.3 suggests a larger one
+ *                     against the error jump of the first iterations); the
+ *                     solution is the same x_lambda
  *   "op_auto_cond"    > 0 (default 0 = off): with a BF16 operator, each tik_pcg
  *                     uses the BF16X3 inner operator (three bf16 pairs) when
  *                     cond(A^T A + lambda^2 I) ~ (max Sigma^2 + lambda^2) /

@@ -69,11 +69,13 @@ def pcg(apply_K, apply_Minv, rhs: np.ndarray, tol: float, maxit: int,
 
 
 def tik_pcg(op: kron.KronOperator, kp: kpsvd.KPSVD | None, B: np.ndarray, lam: float,
-            tol: float, maxit: int, flexible: bool = False, X0=None, callback=None):
-    """KP-SVD preconditioned (F)PCG for the deblurring problem; kp=None gives plain CG."""
+            tol: float, maxit: int, flexible: bool = False, X0=None, callback=None, lam_pc: float | None = None):
+    """KP-SVD preconditioned (F)PCG for the deblurring problem; kp=None gives plain CG.
+    lam_pc: the preconditioner's lambda (default: the system's, eq. PreconSystem;
+    Section 5.3 suggests a larger one against the early error jump)."""
     rhs = kron.apply_AT(op, B)
     if kp is not None:
-        S = kpsvd.precond_scale(kp.Sigma, lam)
+        S = kpsvd.precond_scale(kp.Sigma, lam if lam_pc is None else lam_pc)
         minv = lambda R: kpsvd.precond_apply(kp, S, R)  # noqa: E731
     else:
         minv = lambda R: R.copy()  # noqa: E731

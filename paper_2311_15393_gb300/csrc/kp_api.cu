@@ -7,6 +7,8 @@
 
 #include <algorithm>
 
+#include <cmath>
+
 #include "kp_internal.h"
 
 static thread_local std::string g_last_error;
@@ -205,6 +207,12 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
       return KP_EINVAL;
     }
     ctx->check_every = (int)value;
+  } else if (!strcmp(name, "pc_lambda_ratio")) {
+    if (!(value > 0) || !std::isfinite(value)) {
+      kp_set_error("pc_lambda_ratio must be > 0");
+      return KP_EINVAL;
+    }
+    ctx->pc_lambda_ratio = value;
   } else if (!strcmp(name, "op_auto_cond")) {
     if (!(value >= 0)) {
       kp_set_error("op_auto_cond must be >= 0");

@@ -132,6 +132,7 @@ struct kp_ctx {
   // options
   double reliable_delta = -1.0;  // < 0: default for the operator precision
   int check_every = 2;
+  double pc_lambda_ratio = 1.0;  // preconditioner lambda / system lambda
   double op_auto_cond = 0.0;  // > 0: BF16 inner operator raised to BF16X3 when cond(K) exceeds it
   bool cg_fuse = true;  // the x / r update also writes the preconditioner's narrow input (where possible)
   double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD

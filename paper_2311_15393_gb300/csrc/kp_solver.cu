@@ -96,12 +96,12 @@ static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
 
 // second half: z = M^-1 r, beta, p = z + beta p (+ bf16 slices of p)
 // (narrow_ready: the narrow copy of r for the preconditioner is already made)
-static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2, bool narrow_ready = false) {
+static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2_pc, bool narrow_ready = false) {
   const long long N = (long long)ctx->n_r * ctx->n_c;
   const bool f64 = ctx->vec_prec == KP_F64;
   const int* fl = ctx->dflags;
   double* s = ctx->dscal;
-  KP_TRY(pc_apply(ctx, B.r, B.z, lam2, s + S_RR, fl, narrow_ready));
+  KP_TRY(pc_apply(ctx, B.r, B.z, lam2_pc, s + S_RR, fl, narrow_ready));
   PostOp pb;  // beta and zr, by the last block of the dot products
   pb.kind = POST_BETA;
   pb.s = s;
@@ -116,7 +116,7 @@ static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2, bool narro
 // (cg_fusable): the K application's term sum also gives max |q|, so the
 // update writes the preconditioner's narrow input with a scale bounded from
 // max |r_old| + |alpha| max |q| >= max |r_new|, known before the update.
-static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
+static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2, double lam2_pc) {
   const long long N = (long long)ctx->n_r * ctx->n_c;
   const int* fl = ctx->dflags;
   double* s = ctx->dscal;
@@ -135,7 +135,7 @@ static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double 
     return KP_ENOTSUP;
   }
   const int nt = ctx->pc_prec == KP_BF16 ? NT_BF16 : NT_F16;
-  KP_TRY(update_xr_q_dev(ctx, x, B.r, B.r_old, B.p, B.q, N, s + S_ALPHA, s + S_RR, s + S_QMAX, nt, lam2, ctx->pc_in,
+  KP_TRY(update_xr_q_dev(ctx, x, B.r, B.r_old, B.p, B.q, N, s + S_ALPHA, s + S_RR, s + S_QMAX, nt, lam2_pc, ctx->pc_in,
                          cg_inv_slot(ctx), fl, pc));
   return KP_OK;
 }
@@ -190,6 +190,9 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
   KP_TRY(choose_inner(ctx, lambda * lambda));
   const bool f64 = ctx->vec_prec == KP_F64;
   const double lam2 = lambda * lambda;
+  // the preconditioner's lambda (eq. PreconSystem uses the system's; a larger
+  // one is the remedy Section 5.3 suggests for the early error jump)
+  const double lam2_pc = lam2 * ctx->pc_lambda_ratio * ctx->pc_lambda_ratio;
   const SolveBufs B = bufs(ctx);
   cudaStream_t st = ctx->stream;
   // default: reliable updates for every operator below FP64
@@ -245,7 +248,7 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
       result = KP_OK;
     } else {
       // z0 = M^-1 r0, zr, p0 = z0
-      KP_TRY(pc_apply(ctx, B.r, B.z, lam2, ctx->dscal + S_RR, nullptr));
+      KP_TRY(pc_apply(ctx, B.r, B.z, lam2_pc, ctx->dscal + S_RR, nullptr));
       KP_TRY(dot2_dev(ctx, B.z, B.r, nullptr, N, f64, ctx->dscal + S_ZR, nullptr));
       const int sl = op_inner_slices(ctx);
       KP_TRY(p_update_dev(ctx, B.p, B.z, N, f64, nullptr, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N,
@@ -258,8 +261,8 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
       KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       kp_status cs = KP_OK;
       for (int i = 0; i < blk && cs == KP_OK; ++i) {
-        cs = folded ? half_a_folded(ctx, B, x, lam2) : half_a(ctx, B, x, lam2);
-        if (cs == KP_OK) cs = half_b(ctx, B, lam2, folded);
+        cs = folded ? half_a_folded(ctx, B, x, lam2, lam2_pc) : half_a(ctx, B, x, lam2);
+        if (cs == KP_OK) cs = half_b(ctx, B, lam2_pc, folded);
       }
       cudaError_t ce = cudaStreamEndCapture(st, &graph);
       const long long per_block = ctx->launches - l0;
@@ -333,7 +336,7 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
           ++repl;
           k_after_replace<<<1, 1, 0, st>>>(ctx->dscal, ctx->dflags, ctx->hist, ctx->hist_cap);
           KP_LAUNCHED(ctx);
-          KP_TRY(half_b(ctx, B, lam2));
+          KP_TRY(half_b(ctx, B, lam2_pc));
           cur = 0;
           KP_TRY(launch_block(cur));
           continue;
@@ -370,7 +373,7 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
         // resume: clear the pause, finish the interrupted iteration, continue
         int zero2[2] = {0, 0};
         KP_CUDA(cudaMemcpyAsync(ctx->dflags, zero2, sizeof(zero2), cudaMemcpyHostToDevice, st));
-        KP_TRY(half_b(ctx, B, lam2));
+        KP_TRY(half_b(ctx, B, lam2_pc));
         KP_CUDA(cudaStreamSynchronize(st));
         cur = 0;
         KP_TRY(launch_block(cur));

@@ -37,6 +37,36 @@ def test_fp64_iterates_match_oracle(kpsvd, flexible):
             np.testing.assert_allclose(info.res_hist, io.res_hist, rtol=1e-7)
 
 
+@pytest.mark.parametrize("flexible", [False, True])
+def test_fp64_iterates_with_separate_preconditioner_lambda(kpsvd, flexible):
+    """64 x 64 FP64 workload with the preconditioner built for lambda_M = 3
+    lambda (option pc_lambda_ratio; Section 5.3): the iterates after k steps
+    equal the oracle's with lam_pc = 3 lambda."""
+    pr = OracleProblem("deblur64_fp64")
+    lam = pr.P.lam
+    with setup_ctx(kpsvd, pr, "f64", "f64", "f64") as ctx:
+        ctx.kp_set_option("pc_lambda_ratio", 3.0)
+        for k in [1, 5, 20]:
+            x, info = run(kpsvd, ctx, pr, lam, 0.0, k, flexible, "f64")
+            xo, _ = opcg.tik_pcg(pr.op, pr.kp, pr.B, lam, 0.0, k, flexible, lam_pc=3 * lam)
+            assert info.iters == k
+            assert rel(x, xo) < 1e-9, k
+
+
+def test_separate_preconditioner_lambda_reaches_oracle_solution(kpsvd):
+    """256 x 256, BF16 operator, FP16 preconditioner built for lambda_M = 2
+    lambda: FPCG still reaches the oracle's x_lambda to 1e-4."""
+    pr = OracleProblem("deblur256_fp32")
+    lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
+    x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam)
+    with setup_ctx(kpsvd, pr, "bf16", "f16", "f32") as ctx:
+        ctx.kp_set_option("pc_lambda_ratio", 2.0)
+        x, info = run(kpsvd, ctx, pr, lam, 1e-7, 500, True, "f32")
+        print(f"lambda_M = 2 lambda: {info.iters} iterations")
+        assert info.status == kpsvd.KP_OK
+        assert rel(x, x_star) < 1e-4
+
+
 def test_fp64_workload_stops_by_rule(kpsvd):
     """50 iterations or relative residual 1e-8, whichever comes first."""
     pr = OracleProblem("deblur64_fp64")

@@ -167,3 +167,24 @@ def test_noise_level_is_exact():
     Bt = kron.apply_A(op, X)
     assert abs(np.linalg.norm(B - Bt) / np.linalg.norm(Bt) - 0.05) < 1e-14
     assert abs(enorm - np.linalg.norm(B - Bt)) < 1e-12
+
+
+def test_preconditioner_lambda_changes_the_path_not_the_solution():
+    """A preconditioner built with lambda_M != lambda (Section 5.3's remedy
+    for the early error jump) is still SPD, so (F)PCG converges to the same
+    x_lambda (dense Cholesky); lambda_M = lambda gives the default iterates
+    exactly, and a different lambda_M gives different iterates."""
+    op, _, B = _problem(n=16, bc="reflexive", rank=3)
+    kp = kpsvd.kp_svd(op, "projected")
+    lam = 0.05
+    K = kron.dense_A(op).T @ kron.dense_A(op) + lam * lam * np.eye(256)
+    x_chol = np.linalg.solve(K, kron.vec(kron.apply_AT(op, B)))
+    for flexible in (False, True):
+        x3, info = pcg.tik_pcg(op, kp, B, lam, 1e-13, 500, flexible, lam_pc=3 * lam)
+        assert info.converged
+        assert np.linalg.norm(kron.vec(x3) - x_chol) <= 1e-10 * np.linalg.norm(x_chol)
+        xa, _ = pcg.tik_pcg(op, kp, B, lam, 0.0, 3, flexible)
+        xb, _ = pcg.tik_pcg(op, kp, B, lam, 0.0, 3, flexible, lam_pc=lam)
+        xc, _ = pcg.tik_pcg(op, kp, B, lam, 0.0, 3, flexible, lam_pc=3 * lam)
+        assert np.array_equal(xa, xb)
+        assert np.linalg.norm(xc - xa) > 1e-6 * np.linalg.norm(xa)
