@@ -47,9 +47,14 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the image size (smaller test runs)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no phase breakdown, e2e, kernel timing or CPU baseline): for launch lists")
-    ap.add_argument("--workload", default="deblur1024_mixed", choices=["deblur1024_mixed", "batched64"],
-                    help="batched64: 64 independent problems of uneven sizes through kp_solve_batch "
-                         "(its own JSON line; the default workload is the headline metric)")
+    ap.add_argument("--workload", default="deblur1024_mixed",
+                    choices=["deblur1024_mixed", "batched64", "learned_lambda"],
+                    help="batched64: 64 independent problems of uneven sizes through kp_solve_batch; "
+                         "learned_lambda: train the lambda regressor on generated 256^2 problems and compare it "
+                         "with GCV on new ones (each its own JSON line; the default workload is the headline "
+                         "metric)")
+    ap.add_argument("--train", type=int, default=4096, help="learned_lambda: training problems")
+    ap.add_argument("--eval", type=int, default=512, help="learned_lambda: evaluation problems")
     ap.add_argument("--workers", type=int, default=8, help="batched64: concurrent problems")
     ap.add_argument("--kernel-only", choices=["kapply", "minv"], default=None,
                     help="set up once, then run only the operator application (or preconditioner solve) "
@@ -579,6 +584,111 @@ def run_batched(args, ws, rank, local, dist):
     return 0
 
 
+def run_learned(args, ws, rank, local, dist):
+    """Learned lambda: features (kp_lambda_features) and discrepancy-principle
+    labels (tau = 1.01 times the generator's exact noise norm) of generated
+    256 x 256 problems (PSF and noise as in the batched workload), MLP
+    training (kp_mlp_*), then on new problems lambda from the MLP vs GCV:
+    relative reconstruction error against x_true and FPCG iterations."""
+    import numpy as np
+    import torch
+    from paper_2311_15393_gb300 import build as _build
+    _build.build()
+    from paper_2311_15393_gb300 import kpsvd, synth
+
+    dev = local
+    torch.cuda.set_device(dev)
+    f32 = torch.float32
+    seed0 = synth.SEED_BASE + 4 + 1000 * rank
+    ctx = kpsvd.KpContext(dev)
+    feat = torch.empty(256, dtype=f32, device=dev)
+
+    def prepare(P):
+        psf = kpsvd.to_device(P.psf, torch.float64, f"cuda:{dev}")
+        ctx.kp_setup(psf, P.n_r, P.n_c, P.center, P.bc, P.op_rank, args.op, args.pc, "f32", "projected")
+        xt = kpsvd.to_device(P.x_true, f32, f"cuda:{dev}")
+        b = torch.empty_like(xt)
+        enorm = ctx.kp_forward(xt, kpsvd.to_device(P.noise_dirs[0], f32, f"cuda:{dev}"), P.noise_levels[0], b)
+        ctx.kp_lambda_features(b, feat)
+        return b, enorm, feat.cpu().numpy().copy()
+
+    t0 = time.perf_counter()
+    Xtr, ytr = [], []
+    for P in synth.make_batch(args.train, sizes=[(256, 256)], seed=seed0):
+        b, enorm, f = prepare(P)
+        Xtr.append(f)
+        ytr.append(np.log10(ctx.choose_lambda(b, "discrepancy", 1.01 * enorm)))
+    t_data = time.perf_counter() - t0
+    Xtr, ytr = np.array(Xtr, dtype=np.float64), np.array(ytr)
+    mean, std = Xtr.mean(axis=0), np.maximum(Xtr.std(axis=0), 1e-3)
+    rng = np.random.default_rng(seed0)
+    width, depth, bs = 256, 3, 256
+    sizes = [256] + [width] * depth + [1]
+    vec = [mean, 1.0 / std]
+    for l in range(depth + 1):
+        vec += [rng.standard_normal((sizes[l + 1], sizes[l])).ravel() * np.sqrt(2.0 / sizes[l]), np.zeros(sizes[l + 1])]
+    vec = np.concatenate(vec).astype(np.float32)
+    Xd = torch.tensor(Xtr, dtype=f32, device=dev)
+    yd = torch.tensor(ytr, dtype=f32, device=dev)
+    epochs = 40
+    with kpsvd.Mlp(width, depth, bs, dev) as m:
+        m.set_params(vec)
+        t1 = time.perf_counter()
+        losses = []
+        for ep in range(epochs):
+            perm = torch.tensor(rng.permutation(len(ytr)), device=dev)
+            Xs, ys = Xd[perm], yd[perm]
+            el = [m.train_step(Xs[i:i + bs], ys[i:i + bs], 1e-3) for i in range(0, len(ytr) - bs + 1, bs)]
+            losses.append(float(np.mean(el)))
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t1
+        # evaluation on new problems
+        rows = []
+        out = torch.empty(1, dtype=f32, device=dev)
+        t_inf, t_gcv = 0.0, 0.0
+        for P in synth.make_batch(args.eval, sizes=[(256, 256)], seed=seed0 + 500):
+            b, enorm, f = prepare(P)
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            ctx.kp_lambda_features(b, feat)
+            m.forward(feat.view(1, 256), out)
+            lam_m = float(10.0 ** out.item())
+            tb = time.perf_counter()
+            lam_g = ctx.choose_lambda(b, "gcv")
+            tc = time.perf_counter()
+            t_inf += tb - ta
+            t_gcv += tc - tb
+            lam_d = ctx.choose_lambda(b, "discrepancy", 1.01 * enorm)
+            xt = P.x_true
+            r = {"err_disc_log": abs(np.log10(lam_m / lam_d))}
+            for name, lam in (("mlp", lam_m), ("gcv", lam_g)):
+                x = torch.zeros_like(b)
+                info = ctx.tik_pcg(b, lam, 1e-7, 500, True, x, check=False)
+                X = kpsvd.from_device(x, P.n_r, P.n_c)
+                r[f"err_{name}"] = float(np.linalg.norm(X - xt) / np.linalg.norm(xt))
+                r[f"iters_{name}"] = info.iters
+            rows.append(r)
+    ctx.close()
+    med = lambda k: float(np.median([r[k] for r in rows]))  # noqa: E731
+    mean_ = lambda k: float(np.mean([r[k] for r in rows]))  # noqa: E731
+    result = {"metric": "learned lambda (MLP on KP-spectrum features, trained on discrepancy labels) vs GCV on new "
+                        "256^2 problems: median relative reconstruction error",
+              "value": med("err_mlp"), "unit": "relative error", "higher_is_better": False, "n_gpus": ws,
+              "data": "synthetic", "dtype": "bf16 weights, fp32 accumulation",
+              "config": {"workload": "learned_lambda", "train_problems": len(ytr), "eval_problems": len(rows),
+                         "size": "256x256", "mlp": f"256 -> {width} x {depth} GELU -> 1", "batch": bs,
+                         "epochs": epochs, "optimizer": "Adam lr 1e-3", "label": "discrepancy, tau = 1.01"},
+              "gcv": {"median_err": med("err_gcv"), "mean_iters": mean_("iters_gcv")},
+              "mlp": {"median_err": med("err_mlp"), "mean_iters": mean_("iters_mlp"),
+                      "median_abs_log10_vs_discrepancy": med("err_disc_log")},
+              "train": {"first_epoch_loss": losses[0], "last_epoch_loss": losses[-1], "seconds": t_train,
+                        "data_seconds": t_data},
+              "ms_per_lambda": {"mlp": 1e3 * t_inf / len(rows), "gcv": 1e3 * t_gcv / len(rows)}}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local, dist = dist_init(args)
@@ -587,6 +697,8 @@ def main():
             return run_reference(args, ws, rank, dist)
         if args.workload == "batched64":
             return run_batched(args, ws, rank, local, dist)
+        if args.workload == "learned_lambda":
+            return run_learned(args, ws, rank, local, dist)
         return run_ours(args, ws, rank, local, dist)
     finally:
         if dist is not None:

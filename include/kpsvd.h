@@ -293,6 +293,38 @@ typedef struct {
  * (host, nullable): wall time of the whole batch in milliseconds. */
 kp_status kp_solve_batch(int device, kp_problem* probs, int nprob, const kp_batch_opts* opts, double* ms_total);
 
+/* ---- Learned lambda (not in the paper; Section 5 asks for a systematic
+ * parameter choice) ----------------------------------------------------------
+ * Spectral features of b for the context's problem: with s2 = Sigma^2 and
+ * s2max = max s2, component i falls in bin j = floor(-log10(s2_i / s2max)
+ * 127 / 16) when s2_i > s2max 1e-16; features[j] = log10((sum over bin j of
+ * b_hat^2 + 1e-30 s2max) / (count_j + 1)), features[127 + j] =
+ * log10((count_j + 1) / N) (j < 127), features[254] = log10 of the mean
+ * b_hat^2 over the deepest bins that together hold >= N / 8 components (a
+ * noise estimate), features[255] = log10(s2max); b_hat = vec(U_c^T B U_r).
+ *   b         device, vec type;  features  device, 256 floats (written) */
+kp_status kp_lambda_features(kp_ctx* ctx, const void* b, float* features);
+
+/* Multilayer perceptron features -> log10(lambda): x -> (x - mean) inv_std
+ * -> [Linear(256, width) -> GELU] x depth -> Linear(width, 1); FP32 master
+ * weights with bf16 copies used in the products, FP32 biases, activations
+ * and accumulation; GELU(z) = z Phi(z); loss = mean squared error; Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  The parameter vector
+ * (host, kp_mlp_param_count floats) is mean (256), inv_std (256), then per
+ * layer W (out x in, row-major) and the bias (out).  X: device, batch x 256
+ * row-major; y, labels: device, batch floats.  Work runs on cuda_stream
+ * (NULL: a private stream); set/get_params and the loss output synchronise. */
+typedef struct kp_mlp kp_mlp;
+kp_status kp_mlp_create(kp_mlp** out, int device, void* cuda_stream, int width, int depth, int max_batch);
+void kp_mlp_destroy(kp_mlp* mlp);
+long long kp_mlp_param_count(const kp_mlp* mlp);
+kp_status kp_mlp_set_params(kp_mlp* mlp, const float* params); /* also resets the Adam state */
+kp_status kp_mlp_get_params(kp_mlp* mlp, float* params);
+kp_status kp_mlp_forward(kp_mlp* mlp, const float* X, int batch, float* y);
+/* gradients (host, param_count floats; zero for mean / inv_std) and loss (host, nullable) */
+kp_status kp_mlp_gradients(kp_mlp* mlp, const float* X, const float* labels, int batch, float* grads, double* loss);
+kp_status kp_mlp_train_step(kp_mlp* mlp, const float* X, const float* labels, int batch, float lr, double* loss);
+
 /* Number of this library's kernel launches issued on the context since the
  * last reset (reset = 1 clears it after reading). */
 long long kp_launch_count(kp_ctx* ctx, int reset);

@@ -13,7 +13,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libkpsvd.so")
 SOURCES = ["kp_api.cu", "kp_setup.cu", "kp_ops.cu", "kp_solver.cu", "kp_lambda.cu", "kp_jacobi.cu",
-           "kp_gemm_simt.cu", "kp_gemm_tc.cu", "kp_vec.cu", "kp_noalloc.cu", "kp_batch.cu"]
+           "kp_gemm_simt.cu", "kp_gemm_tc.cu", "kp_vec.cu", "kp_noalloc.cu", "kp_batch.cu", "kp_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

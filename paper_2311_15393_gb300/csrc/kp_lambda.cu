@@ -393,8 +393,11 @@ static kp_status f64_at(LamCtx& L, int method, double lam, double N, double eps,
   return KP_OK;
 }
 
+// With coeffs_only non-null: stop after b_hat = vec(U_c^T B U_r) and the
+// spectrum's bounds, returning the device pointer to b_hat (FP64, N values,
+// valid until the next call on the context) instead of choosing lambda.
 static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method method, double param,
-                                    const void* x_true, double* lambda_out) {
+                                    const void* x_true, double* lambda_out, const double** coeffs_only = nullptr) {
   const int n_r = ctx->n_r, n_c = ctx->n_c;
   const long long N = (long long)n_r * n_c;
   cudaStream_t st = ctx->stream;
@@ -519,6 +522,10 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
   if (!ctx->lam_sigma_ready) {
     KP_CUDA(cudaStreamSynchronize(st));
     ctx->lam_sigma_ready = true;
+  }
+  if (coeffs_only) {
+    *coeffs_only = bh;
+    return KP_OK;
   }
   const double* he = ctx->lam_sigma_ext;
   const double smax = he[0];
@@ -776,3 +783,100 @@ extern "C" kp_status choose_lambda(kp_ctx* ctx, const void* b, kp_lambda_method 
   kp_status l = kp_leave(ctx);
   return s != KP_OK ? s : l;
 }
+
+// ---------------------------------------------------------------- spectral features
+// Features of a problem for the learned lambda (not in the paper; its
+// Section 5 asks for a systematic parameter choice): with s2 = Sigma^2 and
+// s2max = max s2, component i goes to bin j = floor(-log10(s2_i / s2max)
+// NB / DEC) when s2_i > s2max 10^-DEC (NB = 127 bins over DEC = 16 decades);
+// f[j] = log10((sum_bin b_hat^2 + TINY s2max) / (count_j + 1)),
+// f[NB + j] = log10((count_j + 1) / N), f[254] = log10 of the mean b_hat^2
+// over the deepest bins that together hold >= N / 8 components (a noise
+// estimate), f[255] = log10(s2max).
+namespace {
+constexpr int FT_NB = 127;
+constexpr double FT_DEC = 16.0, FT_TINY = 1e-30;
+
+__global__ void k_feat_bins(const double* __restrict__ sig, const double* __restrict__ bh, long long n, double s2max,
+                            unsigned long long* __restrict__ cnt, double* __restrict__ sb) {
+  __shared__ unsigned int c_sh[FT_NB];
+  __shared__ double b_sh[FT_NB];
+  for (int j = threadIdx.x; j < FT_NB; j += blockDim.x) {
+    c_sh[j] = 0u;
+    b_sh[j] = 0.0;
+  }
+  __syncthreads();
+  const double floor_ = s2max * pow(10.0, -FT_DEC);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double s2 = sig[i] * sig[i];
+    if (s2 > floor_) {
+      int j = (int)floor(-log10(s2 / s2max) * FT_NB / FT_DEC);
+      j = min(max(j, 0), FT_NB - 1);
+      atomicAdd(&c_sh[j], 1u);
+      atomicAdd(&b_sh[j], bh[i] * bh[i]);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < FT_NB; j += blockDim.x) {
+    if (c_sh[j]) {
+      atomicAdd(&cnt[j], (unsigned long long)c_sh[j]);
+      atomicAdd(&sb[j], b_sh[j]);
+    }
+  }
+}
+
+__global__ void k_feat_finish(const unsigned long long* __restrict__ cnt, const double* __restrict__ sb, long long n,
+                              double s2max, float* __restrict__ f) {
+  const int j = threadIdx.x;
+  if (j < FT_NB) {
+    f[j] = (float)log10((sb[j] + FT_TINY * s2max) / ((double)cnt[j] + 1.0));
+    f[FT_NB + j] = (float)log10(((double)cnt[j] + 1.0) / (double)n);
+  }
+  if (j == 0) {
+    double ac = 0.0, ab = 0.0;
+    for (int q = FT_NB - 1; q >= 0; --q) {
+      ac += (double)cnt[q];
+      ab += sb[q];
+      if (ac >= (double)n / 8.0) break;
+    }
+    f[2 * FT_NB] = (float)log10((ab + FT_TINY * s2max) / fmax(ac, 1.0));
+    f[2 * FT_NB + 1] = (float)log10(s2max);
+  }
+}
+}  // namespace
+
+extern "C" kp_status kp_lambda_features(kp_ctx* ctx, const void* b, float* features) {
+  KP_TRY(kp_check_ready(ctx));
+  if (!b || !features) {
+    kp_set_error("kp_lambda_features: NULL argument");
+    return KP_EINVAL;
+  }
+  KP_TRY(kp_enter(ctx));
+  const double* bh = nullptr;
+  double dummy = 0.0;
+  kp_status s = choose_lambda_impl(ctx, b, KP_LAMBDA_GCV, 0.0, nullptr, &dummy, &bh);
+  if (s == KP_OK) {
+    cudaStream_t st = ctx->stream;
+    const long long N = (long long)ctx->n_r * ctx->n_c;
+    const double smax = ctx->lam_sigma_ext[0];
+    const double s2max = smax * smax;
+    void* w = nullptr;
+    s = kp_alloc(ctx, &w, FT_NB * (sizeof(unsigned long long) + sizeof(double)));
+    if (s == KP_OK) {
+      unsigned long long* cnt = (unsigned long long*)w;
+      double* sb = (double*)(cnt + FT_NB);
+      cudaMemsetAsync(w, 0, FT_NB * (sizeof(unsigned long long) + sizeof(double)), st);
+      const int g = std::max(1, std::min((int)((N + 255) / 256), ctx->sm_count * 4));
+      k_feat_bins<<<g, 256, 0, st>>>(ctx->Sigma64, bh, N, s2max, cnt, sb);
+      k_feat_finish<<<1, 128, 0, st>>>(cnt, sb, N, s2max, features);
+      ctx->launches += 2;
+      if (cudaGetLastError() != cudaSuccess) {
+        kp_set_error("kp_lambda_features: launch failed");
+        s = KP_ECUDA;
+      }
+    }
+  }
+  kp_status l = kp_leave(ctx);
+  return s != KP_OK ? s : l;
+}
+

@@ -28,7 +28,8 @@ LAMBDA = {"gcv": 0, "wgcv": 1, "discrepancy": 2, "opt": 3}
 EXPORTS = ["kp_create", "kp_destroy", "kp_setup", "kp_forward", "tik_pcg", "choose_lambda", "kp_apply_A",
            "kp_apply_K", "kp_apply_Minv", "kp_get_spectrum", "kp_get_terms", "kp_get_kpsvd", "kp_get_rank",
            "kp_set_option", "kp_launch_count", "kp_status_str", "kp_last_error", "kp_apply_Minv_noalloc",
-           "kp_solve_batch"]
+           "kp_solve_batch", "kp_lambda_features", "kp_mlp_create", "kp_mlp_destroy", "kp_mlp_param_count",
+           "kp_mlp_set_params", "kp_mlp_get_params", "kp_mlp_forward", "kp_mlp_gradients", "kp_mlp_train_step"]
 
 
 class KpError(RuntimeError):
@@ -84,6 +85,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "kp_last_error": ([], ctypes.c_char_p),
         "kp_apply_Minv_noalloc": ([vp, vp, vp, i, i, d, vp, vp, vp], i),
         "kp_solve_batch": ([i, ctypes.POINTER(Problem), i, ctypes.POINTER(BatchOpts), dp], i),
+        "kp_lambda_features": ([vp, vp, vp], i),
+        "kp_mlp_create": ([ctypes.POINTER(vp), i, vp, i, i, i], i),
+        "kp_mlp_destroy": ([vp], None),
+        "kp_mlp_param_count": ([vp], ctypes.c_longlong),
+        "kp_mlp_set_params": ([vp, vp], i),
+        "kp_mlp_get_params": ([vp, vp], i),
+        "kp_mlp_forward": ([vp, vp, i, vp], i),
+        "kp_mlp_gradients": ([vp, vp, vp, i, vp, dp], i),
+        "kp_mlp_train_step": ([vp, vp, vp, i, ctypes.c_float, dp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -208,6 +218,10 @@ class KpContext:
         return lam.value
 
     # -- hooks ---------------------------------------------------------------------
+    def kp_lambda_features(self, b, out):
+        """256 spectral features of b (device float32 tensor ``out``)."""
+        _check(_lib.kp_lambda_features(self._h, _ptr(b), _ptr(out)))
+
     def kp_apply_A(self, x, y, transpose: bool = False):
         _check(_lib.kp_apply_A(self._h, _ptr(x), _ptr(y), 1 if transpose else 0))
 
@@ -273,3 +287,60 @@ def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_pr
     out = [(q.lambda_, Info(q.info.iters, q.info.replacements, q.info.rel_res, q.info.status, q.info.ms_solve,
                             np.zeros(0))) for q in arr]
     return st, ms.value, out
+
+
+class Mlp:
+    """Owns one kp_mlp (learned lambda); methods mirror the C ABI.  Parameter
+    vectors are float32 numpy arrays of param_count entries."""
+
+    def __init__(self, width: int = 256, depth: int = 3, max_batch: int = 1024, device: int = 0,
+                 stream: int | None = None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = ctypes.c_void_p()
+        _check(_lib.kp_mlp_create(ctypes.byref(h), device, stream, width, depth, max_batch))
+        self._h = h
+        self.param_count = int(_lib.kp_mlp_param_count(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.kp_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self, params: np.ndarray):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.param_count
+        _check(_lib.kp_mlp_set_params(self._h, a.ctypes.data))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.param_count, dtype=np.float32)
+        _check(_lib.kp_mlp_get_params(self._h, a.ctypes.data))
+        return a
+
+    def forward(self, X, y):
+        _check(_lib.kp_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(y)))
+
+    def gradients(self, X, labels):
+        g = np.empty(self.param_count, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(_lib.kp_mlp_gradients(self._h, _ptr(X), _ptr(labels), X.shape[0], g.ctypes.data, ctypes.byref(loss)))
+        return g, loss.value
+
+    def train_step(self, X, labels, lr: float) -> float:
+        loss = ctypes.c_double(0.0)
+        _check(_lib.kp_mlp_train_step(self._h, _ptr(X), _ptr(labels), X.shape[0], lr, ctypes.byref(loss)))
+        return loss.value
+
