@@ -29,6 +29,7 @@ namespace {
 constexpr int NGRID = 400;
 constexpr int GPB = 16;  // grid values per block
 constexpr int LT = 256;
+constexpr size_t LAM_FEAT_BYTES = 127 * (sizeof(unsigned long long) + sizeof(double));  // feature bins
 
 enum LMethod { LM_GCV = 0, LM_WGCV = 1, LM_DISC = 2, LM_OPT = 3, LM_TRACE = 4 };
 
@@ -397,7 +398,8 @@ static kp_status f64_at(LamCtx& L, int method, double lam, double N, double eps,
 // spectrum's bounds, returning the device pointer to b_hat (FP64, N values,
 // valid until the next call on the context) instead of choosing lambda.
 static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method method, double param,
-                                    const void* x_true, double* lambda_out, const double** coeffs_only = nullptr) {
+                                    const void* x_true, double* lambda_out, const double** coeffs_only = nullptr,
+                                    void** feat_ws_out = nullptr) {
   const int n_r = ctx->n_r, n_c = ctx->n_c;
   const long long N = (long long)n_r * n_c;
   cudaStream_t st = ctx->stream;
@@ -406,8 +408,10 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
   // scratch: allocated at the first call after a kp_setup, kept with the problem
   if (!ctx->lam_ws) {
     const int chunks_max = std::max(1, std::min((int)((N + LT - 1) / LT), ctx->sm_count * 2));
-    const size_t bytes = sizeof(double) * (size_t)N * 6 + sizeof(float) * (size_t)N * 4 +
-                         sizeof(double) * (NGRID + 2 * (size_t)chunks_max * NGRID + 2 * NGRID + 2) + 1024;
+    auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };  // as `take` below rounds
+    const size_t bytes = 5 * r256(sizeof(double) * (size_t)N) + 4 * r256(sizeof(float) * (size_t)N) +
+                         r256(sizeof(double) * NGRID) + r256(sizeof(double) * 2 * (size_t)chunks_max * NGRID) +
+                         r256(sizeof(double) * 2 * NGRID) + r256(sizeof(double) * 2) + r256(LAM_FEAT_BYTES);
     KP_TRY(kp_alloc(ctx, &ctx->lam_ws, bytes));
   }
   char* wp = (char*)ctx->lam_ws;
@@ -430,6 +434,7 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
   double* part = (double*)take(sizeof(double) * 2 * (size_t)chunks * NGRID);
   double* sums = (double*)take(sizeof(double) * 2 * NGRID);
   double* ext = (double*)take(sizeof(double) * 2);
+  void* feat_ws = take(LAM_FEAT_BYTES);  // bins of kp_lambda_features
   if (method != KP_LAMBDA_OPT) {
     xh = nullptr;
     xhf = nullptr;
@@ -525,6 +530,7 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
   }
   if (coeffs_only) {
     *coeffs_only = bh;
+    if (feat_ws_out) *feat_ws_out = feat_ws;
     return KP_OK;
   }
   const double* he = ctx->lam_sigma_ext;
@@ -853,16 +859,15 @@ extern "C" kp_status kp_lambda_features(kp_ctx* ctx, const void* b, float* featu
   }
   KP_TRY(kp_enter(ctx));
   const double* bh = nullptr;
+  void* w = nullptr;
   double dummy = 0.0;
-  kp_status s = choose_lambda_impl(ctx, b, KP_LAMBDA_GCV, 0.0, nullptr, &dummy, &bh);
+  kp_status s = choose_lambda_impl(ctx, b, KP_LAMBDA_GCV, 0.0, nullptr, &dummy, &bh, &w);
   if (s == KP_OK) {
     cudaStream_t st = ctx->stream;
     const long long N = (long long)ctx->n_r * ctx->n_c;
     const double smax = ctx->lam_sigma_ext[0];
     const double s2max = smax * smax;
-    void* w = nullptr;
-    s = kp_alloc(ctx, &w, FT_NB * (sizeof(unsigned long long) + sizeof(double)));
-    if (s == KP_OK) {
+    {
       unsigned long long* cnt = (unsigned long long*)w;
       double* sb = (double*)(cnt + FT_NB);
       cudaMemsetAsync(w, 0, FT_NB * (sizeof(unsigned long long) + sizeof(double)), st);
