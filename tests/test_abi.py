@@ -86,3 +86,20 @@ def test_batch_structs_match_the_header(tmp_path):
 def test_batch_rejects_bad_arguments_without_gpu(lib):
     assert lib.kp_solve_batch(0, None, 1, None, None) != 0
     assert lib.kp_solve_batch(0, None, -1, None, None) != 0
+
+
+def test_learned_lambda_entry_points_reject_bad_arguments_without_gpu(lib):
+    """Argument checks run before any device call."""
+    h = ctypes.c_void_p()
+    assert lib.kp_mlp_create(None, 0, None, 256, 3, 64) != 0
+    assert lib.kp_mlp_create(ctypes.byref(h), 0, None, 0, 3, 64) != 0      # width
+    assert lib.kp_mlp_create(ctypes.byref(h), 0, None, 256, 0, 64) != 0    # depth
+    assert lib.kp_mlp_create(ctypes.byref(h), 0, None, 256, 3, 0) != 0     # max_batch
+    lib.kp_mlp_param_count.restype = ctypes.c_longlong
+    assert lib.kp_mlp_param_count(None) == -1
+    assert lib.kp_mlp_set_params(None, None) != 0
+    assert lib.kp_mlp_get_params(None, None) != 0
+    assert lib.kp_mlp_forward(None, None, 1, None) != 0
+    assert lib.kp_mlp_train_step(None, None, None, 1, ctypes.c_float(1e-3), None) != 0
+    assert lib.kp_lambda_features(None, None, None) != 0
+    lib.kp_mlp_destroy(None)  # NULL is allowed
