@@ -59,7 +59,7 @@ def test_preconditioner_solve_matches_dense_solve():
 
 
 def test_separable_zero_bc_pcg_converges_in_one_iteration():
-    """spec pin (b): separable PSF + zero BC => M = K exactly, alpha = 1, x_1 = x_lam."""
+    """Separable PSF + zero BC => M = K exactly, alpha = 1, x_1 = x_lam (closed form)."""
     n = 16
     P = synth.separable_psf(n, n, 8, 8, 2.5, 1.5)
     rng = np.random.default_rng(2)
@@ -81,7 +81,7 @@ def test_separable_zero_bc_pcg_converges_in_one_iteration():
 @pytest.mark.parametrize("bc", ["zero", "reflexive"])
 @pytest.mark.parametrize("flexible", [False, True])
 def test_pcg_converges_to_dense_cholesky(bc, flexible):
-    """spec pin (c): converged (F)PCG equals a dense Cholesky solve at 16 x 16."""
+    """Converged (F)PCG equals a dense Cholesky solve at 16 x 16."""
     op, _, B = _problem(n=16, bc=bc, rank=3)
     kp = kpsvd.kp_svd(op, "projected")
     lam = 0.05
