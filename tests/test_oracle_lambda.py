@@ -108,3 +108,23 @@ def test_wgcv_spurious_minimum_is_excluded(separable):
     l0 = lam.wgcv_lower_limit(kp.Sigma, 3.0, lo, hi)
     assert lam.wgcv_trace(kp.Sigma, l0 * 1.0001, 3.0) > 0
     assert lam.choose_lambda(kp, B, "wgcv", 3.0) > l0
+
+
+def test_discrepancy_lambda_increases_with_eta(separable):
+    """eq. DSCTikSVD's residual norm increases with lambda, so the root for
+    eps = eta ||e|| increases with the safety factor eta (the eta sweeps of
+    Section 5.1), and at each root the residual norm equals eps."""
+    op, kp, A, B, X, enorm = separable
+    b = kron.vec(B)
+    lams = [lam.choose_lambda(kp, B, "discrepancy", eta * enorm) for eta in (0.9, 1.0, 1.01, 1.1, 1.5)]
+    assert all(a < c for a, c in zip(lams, lams[1:]))
+    for eta, l in zip((0.9, 1.0, 1.01, 1.1, 1.5), lams):
+        x = np.linalg.solve(A.T @ A + l * l * np.eye(A.shape[1]), A.T @ b)
+        assert np.linalg.norm(A @ x - b) == pytest.approx(eta * enorm, rel=1e-8)
+
+
+def test_wgcv_with_omega_one_is_gcv(separable):
+    """wGCV's denominator N - omega tr(A A_lam^+) is GCV's at omega = 1 (eqs.
+    wGCVTik, GCVTik), so both choose the same lambda."""
+    op, kp, A, B, X, _ = separable
+    assert lam.choose_lambda(kp, B, "wgcv", 1.0) == pytest.approx(lam.choose_lambda(kp, B, "gcv"), rel=1e-8)
