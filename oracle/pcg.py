@@ -104,3 +104,31 @@ def tik_exact(op: kron.KronOperator, kp: kpsvd.KPSVD, B: np.ndarray, lam: float,
     if not info.converged:
         raise RuntimeError("oracle PCG did not reach the reference tolerance")
     return x
+
+
+def multiterm_minv(op: kron.KronOperator, kp: kpsvd.KPSVD, lam: float, k: int, inner_iters: int,
+                   inner_tol: float = 0.0):
+    """Preconditioner from the first k Kronecker terms of A (scope-table NEXT 3;
+    Section 5.3 finds the one-term preconditioner of no use for some blurs with
+    many terms): z ~ (M_k^T M_k + lam^2 I)^-1 r with M_k = sum_{j<k} A_r^(j) (x)
+    A_c^(j).  For k > 1 no single KP-SVD diagonalises M_k^T M_k, so z comes from
+    `inner_iters` PCG steps on it, preconditioned by the one-term KP-SVD solve
+    (eq. PreconSolve), from z = 0.  The result varies with r (an inexact inner
+    solve), hence flexible PCG outside."""
+    opk = kron.KronOperator(Ac=op.Ac[:k], Ar=op.Ar[:k], s=op.s[:k], u=op.u[:, :k], v=op.v[:, :k], bc=op.bc)
+    S = kpsvd.precond_scale(kp.Sigma, lam)
+
+    def minv(R):
+        z, _ = pcg(lambda X: kron.apply_K(opk, X, lam), lambda Q: kpsvd.precond_apply(kp, S, Q), R,
+                   inner_tol, inner_iters, flexible=False)
+        return z
+
+    return minv
+
+
+def tik_fpcg_multiterm(op: kron.KronOperator, kp: kpsvd.KPSVD, B: np.ndarray, lam: float, k: int,
+                       inner_iters: int, tol: float, maxit: int, inner_tol: float = 0.0):
+    """Flexible PCG on the Tikhonov normal equations with multiterm_minv."""
+    rhs = kron.apply_AT(op, B)
+    return pcg(lambda X: kron.apply_K(op, X, lam), multiterm_minv(op, kp, lam, k, inner_iters, inner_tol), rhs, tol,
+               maxit, flexible=True)

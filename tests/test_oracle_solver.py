@@ -188,3 +188,42 @@ def test_preconditioner_lambda_changes_the_path_not_the_solution():
         xc, _ = pcg.tik_pcg(op, kp, B, lam, 0.0, 3, flexible, lam_pc=3 * lam)
         assert np.array_equal(xa, xb)
         assert np.linalg.norm(xc - xa) > 1e-6 * np.linalg.norm(xa)
+
+
+def test_multiterm_preconditioner_with_all_terms_is_exact():
+    """With k = all terms and the inner solve run to convergence the
+    preconditioner is K^-1 itself: flexible PCG stops after one iteration at
+    x_lambda (alpha = 1, x_1 = K^-1 A^T b)."""
+    op, _, B = _problem(n=16, bc="reflexive", rank=3)
+    kp = kpsvd.kp_svd(op, "projected")
+    lam = 0.05
+    x_chol = pcg.tik_exact_dense(op, B, lam)
+    x, info = pcg.tik_fpcg_multiterm(op, kp, B, lam, k=3, inner_iters=300, tol=1e-10, maxit=5, inner_tol=1e-15)
+    assert info.iters == 1
+    assert np.linalg.norm(x - x_chol) <= 1e-10 * np.linalg.norm(x_chol)
+
+
+def test_multiterm_preconditioner_with_one_term_is_the_kp_svd_solve():
+    """k = 1 with the PRODUCT spectrum: M_1^T M_1 + lam^2 I is diagonalised
+    exactly by V_r (x) V_c with eigenvalues sigma_c^2 sigma_r^2 + lam^2 (eq.
+    AKronSVD), so one inner step already returns eq. PreconSolve's z."""
+    op, _, B = _problem(n=16, bc="reflexive", rank=3)
+    kp = kpsvd.kp_svd(op, "product")
+    lam = 0.05
+    R = np.random.default_rng(7).standard_normal((16, 16))
+    z1 = pcg.multiterm_minv(op, kp, lam, k=1, inner_iters=1)(R)
+    z_kp = kpsvd.precond_apply(kp, kpsvd.precond_scale(kp.Sigma, lam), R)
+    np.testing.assert_allclose(z1, z_kp, rtol=0, atol=1e-12 * np.abs(z_kp).max())
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_multiterm_fpcg_converges_to_the_tikhonov_solution(k):
+    """Two inner steps with k terms: the preconditioner varies with r, and
+    flexible PCG still converges to the dense Cholesky x_lambda."""
+    op, _, B = _problem(n=16, bc="zero", rank=3)
+    kp = kpsvd.kp_svd(op, "projected")
+    lam = 0.05
+    x_chol = pcg.tik_exact_dense(op, B, lam)
+    x, info = pcg.tik_fpcg_multiterm(op, kp, B, lam, k=k, inner_iters=2, tol=1e-13, maxit=300)
+    assert info.converged
+    assert np.linalg.norm(x - x_chol) <= 1e-10 * np.linalg.norm(x_chol)
