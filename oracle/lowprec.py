@@ -46,5 +46,25 @@ def to_e4m3(x):
     return np.sign(f) * y
 
 
+def to_mxfp8(x, axis: int = -1, block: int = 32):
+    """Block-scaled FP8 (the MX format: E4M3 elements with one power-of-two
+    scale per `block` consecutive elements along `axis`, the contraction
+    axis of a product).  The scale is 2^(floor(log2 amax) - 8), 8 being
+    E4M3's largest normal exponent, so each block's largest element lands in
+    [256, 512) before the (saturating) E4M3 rounding; an all-zero block stays
+    zero.  Returns the represented values (scale x element) as float64."""
+    a = np.moveaxis(np.asarray(x, dtype=np.float64), axis, -1)
+    n = a.shape[-1]
+    pad = (-n) % block
+    b = np.concatenate([a, np.zeros(a.shape[:-1] + (pad,))], axis=-1) if pad else a
+    b = b.reshape(b.shape[:-1] + (-1, block))
+    amax = np.abs(b).max(axis=-1, keepdims=True)
+    _, e = np.frexp(np.where(amax > 0, amax, 1.0))  # amax = m 2^e, m in [0.5, 1)
+    scale = np.ldexp(1.0, (e - 1) - 8)
+    y = to_e4m3(b / scale) * scale
+    y = np.where(amax > 0, y, 0.0).reshape(b.shape[:-2] + (-1,))[..., :n]
+    return np.moveaxis(y, -1, axis)
+
+
 ROUND = {"f64": lambda x: np.asarray(x, dtype=np.float64), "f32": to_fp32,
          "bf16": to_bf16, "f16": to_fp16, "e4m3": to_e4m3}
