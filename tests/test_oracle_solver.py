@@ -227,3 +227,15 @@ def test_multiterm_fpcg_converges_to_the_tikhonov_solution(k):
     x, info = pcg.tik_fpcg_multiterm(op, kp, B, lam, k=k, inner_iters=2, tol=1e-13, maxit=300)
     assert info.converged
     assert np.linalg.norm(x - x_chol) <= 1e-10 * np.linalg.norm(x_chol)
+
+
+@pytest.mark.parametrize("bc", ["zero", "reflexive"])
+def test_projected_and_product_spectra_coincide_for_one_term(bc):
+    """With one Kronecker term A = A_r (x) A_c, diag((U_r (x) U_c)^T A (V_r (x) V_c))
+    is sigma_c,i sigma_r,j, eq. AKronSVD's product spectrum; with more terms
+    they differ."""
+    op1, _, _ = _problem(n=12, bc=bc, rank=1)
+    np.testing.assert_allclose(kpsvd.kp_svd(op1, "projected").Sigma, kpsvd.kp_svd(op1, "product").Sigma,
+                               rtol=0, atol=1e-13)
+    op3, _, _ = _problem(n=12, bc=bc, rank=3)
+    assert np.abs(kpsvd.kp_svd(op3, "projected").Sigma - kpsvd.kp_svd(op3, "product").Sigma).max() > 1e-6
