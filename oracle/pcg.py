@@ -127,8 +127,8 @@ def multiterm_minv(op: kron.KronOperator, kp: kpsvd.KPSVD, lam: float, k: int, i
 
 
 def tik_fpcg_multiterm(op: kron.KronOperator, kp: kpsvd.KPSVD, B: np.ndarray, lam: float, k: int,
-                       inner_iters: int, tol: float, maxit: int, inner_tol: float = 0.0):
+                       inner_iters: int, tol: float, maxit: int, inner_tol: float = 0.0, callback=None):
     """Flexible PCG on the Tikhonov normal equations with multiterm_minv."""
     rhs = kron.apply_AT(op, B)
     return pcg(lambda X: kron.apply_K(op, X, lam), multiterm_minv(op, kp, lam, k, inner_iters, inner_tol), rhs, tol,
-               maxit, flexible=True)
+               maxit, flexible=True, callback=callback)

@@ -13,8 +13,8 @@ from oracle import forward, kpsvd, kron, lam
 from paper_2311_15393_gb300 import synth
 
 
-@pytest.fixture(scope="module")
-def separable():
+def separable_problem():
+    """12 x 12 separable blur (reflexive BC), 2% noise: the KP-SVD is the exact SVD of A."""
     n = 12
     P = synth.separable_psf(n, n, 6, 6, 1.6, 1.1)
     rng = np.random.default_rng(11)
@@ -24,6 +24,11 @@ def separable():
     B, enorm = forward.observe(op, X, synth.noise_direction(n, n, rng), 0.02)
     A = kron.dense_A(op)
     return op, kp, A, B, X, enorm
+
+
+@pytest.fixture(scope="module")
+def separable():
+    return separable_problem()
 
 
 def _influence(A, l):
@@ -87,6 +92,14 @@ def test_minimisers_match_exhaustive_grid(separable, method):
     vals = np.array([f(g) for g in grid])
     assert f(l_star) <= vals.min() * (1 + 1e-12)
     assert abs(np.log(l_star) - np.log(grid[np.argmin(vals)])) <= 2 * np.log(hi / lo) / 10_000
+
+
+def test_lambda_search_bounds_by_hand():
+    """The search runs between the smallest nonzero |sigma| and the largest
+    (Section 2.2), the lower end floored at 1e-10 sigma_max; PROJECTED
+    spectra may hold negative entries, which count by magnitude."""
+    assert lam.lambda_bounds(np.array([[0.5, 0.01], [-1.0, 0.0]])) == (0.01, 1.0)
+    assert lam.lambda_bounds(np.array([1e-12, 0.0, 1e-3, 2.0])) == (2e-10, 2.0)
 
 
 def test_discrepancy_root_and_no_root(separable):

@@ -16,6 +16,10 @@ def test_bf16_hand_values():
     assert lp.to_bf16(1.0 + 2.0 ** -8) == 1.0                      # tie -> even (1.0)
     assert lp.to_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2 * 2.0 ** -7  # tie -> even (1 + 2^-6)
     assert lp.to_bf16(1.0 + 2.0 ** -8 + 2.0 ** -12) == 1.0 + 2.0 ** -7
+    # rounded from the float32 value, as the GPU's conversion is: 2^-30 is
+    # lost in float32, leaving the tie 1 + 2^-8, which goes to even (1.0)
+    assert lp.to_bf16(1.0 + 2.0 ** -8 + 2.0 ** -30) == 1.0
+    assert lp.to_fp16(1.0 + 2.0 ** -11 + 2.0 ** -30) == 1.0       # same for fp16 (tie 1 + 2^-11)
     assert lp.to_bf16(-3.0) == -3.0
     assert lp.to_bf16(2.0 ** -130) > 0                              # subnormal range kept
     x = np.random.default_rng(1).standard_normal(1000)
@@ -40,9 +44,13 @@ def test_mxfp8_hand_values():
     """Block of 4 with amax 3.0 = 1.5 * 2^1: scale 2^(1 - 8) = 2^-7, elements
     x * 128 rounded to E4M3 (spacing 32 in [256, 512), 16 in [128, 256)), so
     3.0 -> 384 exactly, 1.3 -> 166.4 -> 160 (x 2^-7 = 1.25), 0.01 -> 1.28 ->
-    1.25 (spacing 2^-3 in [1, 2)), -2.9 -> -371.2 -> -384 (-3.0)."""
-    x = np.array([3.0, 1.3, 0.01, -2.9])
-    np.testing.assert_array_equal(lp.to_mxfp8(x, block=4), [3.0, 1.25, 1.25 / 128, -3.0])
+    1.25 (spacing 2^-3 in [1, 2)), -2.9 -> -371.2 -> -384 (-3.0).  Second
+    block, amax 3.75 = 1.875 * 2^1, same scale: 3.75 -> 480 saturates to 448
+    (3.5), which only the block maximum's binade [256, 512) produces (a
+    scale one binade larger would give 240, exact); 0.5 -> 64, -1 -> -128,
+    0 -> 0."""
+    x = np.array([3.0, 1.3, 0.01, -2.9, 3.75, 0.5, -1.0, 0.0])
+    np.testing.assert_array_equal(lp.to_mxfp8(x, block=4), [3.0, 1.25, 1.25 / 128, -3.0, 3.5, 0.5, -1.0, 0.0])
 
 
 def test_mxfp8_blocks_are_independent_and_zero_blocks_stay_zero():

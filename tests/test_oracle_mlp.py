@@ -16,6 +16,28 @@ def test_gelu_is_x_times_normal_cdf():
     np.testing.assert_allclose(mlp.gelu_grad(x), (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h), rtol=1e-7, atol=1e-9)
 
 
+def test_forward_pass_by_hand():
+    """One hidden unit, fed by feature 0 alone: x_0 = 3, mean 1, inv_std 0.5
+    normalise to 1; the unit's pre-activation is 1 (weight 1, bias 0), GELU(1)
+    = Phi(1) = 0.8413447461 (standard normal table); the output layer gives
+    2 Phi(1) + 0.5.  Every other feature equals its mean.  The output weight
+    is stored as 2 + 2^-7, a tie between the bf16 neighbours 2 and 2 + 2^-6
+    that rounds to even (2): the forward pass uses bf16-rounded weights."""
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(mlp.N_FEAT)
+    mean = x.copy()
+    inv_std = rng.uniform(0.5, 2.0, mlp.N_FEAT)
+    x[0], mean[0], inv_std[0] = 3.0, 1.0, 0.5
+    net = mlp.init(1, 1, rng, mean=mean, inv_std=inv_std)
+    net.W[0][:] = 0.0
+    net.W[0][0, 0] = 1.0
+    net.W[1][:] = 2.0 + 2.0 ** -7
+    net.c[1][:] = 0.5
+    pred, _, _ = mlp.forward(net, x[None, :])
+    assert pred[0] == pytest.approx(2.0 * 0.8413447461 + 0.5, abs=2e-10)
+    assert mlp.loss(net, x[None, :], [pred[0] + 0.25]) == pytest.approx(0.0625, rel=1e-14)
+
+
 def test_gradients_match_finite_differences():
     rng = np.random.default_rng(3)
     net = mlp.init(8, 2, rng, mean=rng.standard_normal(mlp.N_FEAT), inv_std=rng.uniform(0.5, 2, mlp.N_FEAT))
@@ -87,3 +109,9 @@ def test_features_are_permutation_invariant_and_shift_with_scale():
     occupied = f[mlp.NB:2 * mlp.NB] > np.log10(1.0 / 400) + 1e-9
     np.testing.assert_allclose(g[:mlp.NB][occupied], f[:mlp.NB][occupied] + 2.0, atol=1e-12)
     assert g[254] == pytest.approx(f[254] + 2.0, abs=1e-12)
+    # scaling Sigma by 10 scales s2 by 100: bins and counts (relative to
+    # s2max) stay, f[255] = log10(s2max) moves by 2
+    h = mlp.features(10.0 * sig, bh)
+    np.testing.assert_array_equal(h[mlp.NB:2 * mlp.NB], f[mlp.NB:2 * mlp.NB])
+    np.testing.assert_allclose(h[:mlp.NB][occupied], f[:mlp.NB][occupied], atol=1e-12)
+    assert h[255] == pytest.approx(f[255] + 2.0, abs=1e-12)

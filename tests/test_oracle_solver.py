@@ -56,6 +56,8 @@ def test_preconditioner_solve_matches_dense_solve():
     Z = kpsvd.precond_apply(kp, kpsvd.precond_scale(kp.Sigma, lam), R)
     z_ref = np.linalg.solve(M, kron.vec(R))
     assert np.linalg.norm(kron.vec(Z) - z_ref) <= 1e-10 * np.linalg.norm(z_ref)
+    # eq. PreconSystem's explicit M is the same matrix for the PRODUCT spectrum
+    np.testing.assert_allclose(kpsvd.dense_M(kp, lam), M, rtol=0, atol=1e-12 * np.abs(M).max())
 
 
 def test_separable_zero_bc_pcg_converges_in_one_iteration():
@@ -137,6 +139,48 @@ def test_fpcg_equals_pcg_with_constant_preconditioner():
     x1, i1 = pcg.tik_pcg(op, kp, B, lam, 0.0, 12, flexible=False)
     x2, i2 = pcg.tik_pcg(op, kp, B, lam, 0.0, 12, flexible=True)
     assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x1)
+
+
+def _directions_and_residuals(op, B, lam, minv, flexible, iters):
+    rhs = kron.apply_AT(op, B)
+    K = lambda X: kron.apply_K(op, X, lam)  # noqa: E731
+    xs = [np.zeros_like(rhs)]
+    pcg.pcg(K, minv, rhs, 0.0, iters, flexible, callback=lambda it, xk: xs.append(xk.copy()))
+    ps = [xs[k + 1] - xs[k] for k in range(len(xs) - 1)]       # alpha_k p_k
+    rs = [rhs - K(xk) for xk in xs]
+    return ps, rs, K
+
+
+def test_fpcg_local_conjugacy_with_a_varying_preconditioner():
+    """Flexible PCG (Polak-Ribiere beta, Section 3's last paragraph) keeps
+    p_{k+1}^T K p_k = 0 and p_k^T r_{k+1} = 0 for ANY sequence of
+    preconditioners: with alpha_k = z_k^T r_k / p_k^T K p_k and r_{k+1} - r_k
+    = -alpha_k K p_k, beta_k = -z_{k+1}^T K p_k / p_k^T K p_k.  Here every
+    application uses another lambda_M; the Fletcher-Reeves beta loses the
+    property under the same preconditioners."""
+    op, _, B = _problem(n=16, bc="reflexive", rank=3)
+    kp = kpsvd.kp_svd(op, "projected")
+    lam = 0.05
+    calls = []
+
+    def minv(R):
+        calls.append(None)
+        lam_m = lam * (1.0 + 0.8 * np.sin(1.7 * len(calls)))
+        return kpsvd.precond_apply(kp, kpsvd.precond_scale(kp.Sigma, lam_m), R)
+
+    def worst(flexible):
+        calls.clear()
+        ps, rs, K = _directions_and_residuals(op, B, lam, minv, flexible, 8)
+        conj = max(abs(np.vdot(ps[k + 1], K(ps[k]))) / (np.linalg.norm(ps[k + 1]) * np.linalg.norm(K(ps[k])))
+                   for k in range(len(ps) - 1))
+        orth = max(abs(np.vdot(ps[k], rs[k + 1])) / (np.linalg.norm(ps[k]) * np.linalg.norm(rs[k + 1]))
+                   for k in range(len(ps)))
+        return conj, orth
+
+    conj, orth = worst(True)
+    assert conj <= 1e-9 and orth <= 1e-9
+    conj_fr, _ = worst(False)
+    assert conj_fr > 1e-4
 
 
 def test_unpreconditioned_cg_is_slower():
@@ -227,6 +271,50 @@ def test_multiterm_fpcg_converges_to_the_tikhonov_solution(k):
     x, info = pcg.tik_fpcg_multiterm(op, kp, B, lam, k=k, inner_iters=2, tol=1e-13, maxit=300)
     assert info.converged
     assert np.linalg.norm(x - x_chol) <= 1e-10 * np.linalg.norm(x_chol)
+
+
+def test_multiterm_outer_iteration_is_flexible():
+    """The inner solve makes the preconditioner vary with r, and the outer
+    iteration keeps flexible PCG's local conjugacy p_{k+1}^T K p_k = 0 (which
+    the Fletcher-Reeves beta loses under a varying preconditioner)."""
+    op, _, B = _problem(n=16, bc="reflexive", rank=3)
+    kp = kpsvd.kp_svd(op, "projected")
+    lam = 0.05
+    K = lambda X: kron.apply_K(op, X, lam)  # noqa: E731
+    xs = [np.zeros_like(B)]
+    pcg.tik_fpcg_multiterm(op, kp, B, lam, k=2, inner_iters=2, tol=0.0, maxit=6,
+                           callback=lambda it, xk: xs.append(xk.copy()))
+    ps = [xs[j + 1] - xs[j] for j in range(len(xs) - 1)]
+    for j in range(len(ps) - 1):
+        c = abs(np.vdot(ps[j + 1], K(ps[j]))) / (np.linalg.norm(ps[j + 1]) * np.linalg.norm(K(ps[j])))
+        assert c <= 1e-9, j
+
+
+def test_exact_solution_above_the_dense_size_uses_pcg_to_the_filter_factor_solution():
+    """N = 72^2 > 4096 takes the FP64 PCG branch; a separable blur makes the
+    KP-SVD the exact SVD of A, so x_lam = V_c ((Sigma .* B_hat) ./ (Sigma^2 +
+    lam^2)) V_r^T with B_hat = U_c^T B U_r (eq. TikSV, filter factors)."""
+    n = 72
+    P = synth.separable_psf(n, n, n // 2, n // 2, 2.5, 1.5)
+    rng = np.random.default_rng(8)
+    X = synth.phantom(n, n, 8, rng)
+    op = kron.kron_operator(P, (n // 2, n // 2), "reflexive", rank=1)
+    kp = kpsvd.kp_svd(op, "product")
+    B, _ = forward.observe(op, X, synth.noise_direction(n, n, rng), 0.01)
+    lam = 0.02
+    Ur, sr, Vrt = np.linalg.svd(op.Ar[0])
+    Uc, sc, Vct = np.linalg.svd(op.Ac[0])
+    Sig = np.outer(sc, sr)
+    x_ff = Vct.T @ (Sig * (Uc.T @ B @ Ur) / (Sig ** 2 + lam ** 2)) @ Vrt
+    x = pcg.tik_exact(op, kp, B, lam)
+    assert np.linalg.norm(x - x_ff) <= 1e-11 * np.linalg.norm(x_ff)
+    # a non-separable blur (the preconditioner no longer exact): the normal
+    # equations hold to the branch's tolerance
+    P2 = synth.gaussian_psf(n, n, n // 2, n // 2, 2.5, 1.5, 0.6)
+    op2 = kron.kron_operator(P2, (n // 2, n // 2), "reflexive", rank=2)
+    x2 = pcg.tik_exact(op2, kpsvd.kp_svd(op2, "projected"), B, lam)
+    rhs = kron.apply_AT(op2, B)
+    assert np.linalg.norm(kron.apply_K(op2, x2, lam) - rhs) <= 1e-12 * np.linalg.norm(rhs)
 
 
 @pytest.mark.parametrize("bc", ["zero", "reflexive"])
