@@ -46,7 +46,8 @@ typedef enum {
   KP_ENOMEM = 2,      /* device or host allocation failed */
   KP_ECUDA = 3,       /* CUDA runtime / driver error */
   KP_ENOTSUP = 4,     /* valid but unsupported combination or device */
-  KP_ENOCONV = 5,     /* maxit reached before tol; x holds the last iterate */
+  KP_ENOCONV = 5,     /* maxit reached before tol, or the true residual stagnated
+                         above tol; x holds the last iterate */
   KP_EBREAKDOWN = 6,  /* p^T K p <= 0 or z^T r <= 0 in (F)PCG */
   KP_ENUMERIC = 7,    /* NaN / Inf met in a reduction */
   KP_ENOROOT = 8,     /* discrepancy equation has no root */
@@ -115,9 +116,20 @@ void kp_destroy(kp_ctx* ctx);
  *   sigma    KP spectrum definition
  * Supported combinations: (F64, F64, F64); (F32, F32|BF16|F16|E4M3, F32);
  * (BF16|BF16X3, F32|BF16|F16|E4M3, F32).  Tensor-core precisions need
- * n_r and n_c multiples of 16.  Factor SVDs (one-sided Jacobi), Sigma and the
- * spectral quantities are computed in FP64 on the device.  May be called
- * again on the same context to replace the problem.  Synchronises. */
+ * n_r and n_c multiples of 16.  The factor SVDs (one-sided Jacobi), the PSF
+ * terms, Sigma and the spectral quantities are computed on the device: in
+ * FP64 for FP64 vectors; for FP32 vectors the O(n^3) products, the Jacobi
+ * rotations and the PSF subspace iteration run in FP32 (norms, sorting and
+ * the stored Sigma stay FP64; option "setup_fp64" restores FP64).  May be
+ * called again on the same context to replace the problem.  Errors:
+ * KP_EINVAL for a NULL or unaligned psf, n_r or n_c < 2, a centre outside the
+ * grid, op_rank outside [0, min(n_r, n_c)], an unknown bc or sigma, or an
+ * unsupported precision combination; KP_ENOTSUP when tensor-core precisions
+ * meet a device other than sm_103 or sizes not multiples of 16.  These
+ * checks run first and leave the context's previous problem in place; a
+ * failure after them (KP_ENOMEM, KP_ECUDA) leaves the context without a
+ * problem, and later calls other than kp_setup return KP_ESTATE.
+ * Synchronises. */
 kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, int center_r, int center_c,
                    kp_bc bc, int op_rank, kp_prec op_prec, kp_prec pc_prec, kp_prec vec_prec,
                    kp_sigma sigma);
@@ -131,28 +143,43 @@ kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, int center_
 kp_status kp_forward(kp_ctx* ctx, const void* x, const void* g, double noise_level, void* b,
                      double* noise_norm);
 
-/* Solve (A^T A + lambda^2 I) x = A^T b by PCG (flexible = 0, Fletcher-Reeves
- * beta) or flexible PCG (flexible = 1, Polak-Ribiere beta), preconditioned by
- * the KP-SVD with the same lambda.  Stops when ||r|| <= tol ||A^T b|| or after
- * maxit iterations (returns KP_ENOCONV, x = last iterate).
+/* Solve (A^T A + lambda^2 I) x = A^T b (eq. tik:normal2) by PCG (flexible =
+ * 0, Fletcher-Reeves beta) or flexible PCG (flexible = 1, Polak-Ribiere beta,
+ * Section 3 last paragraph), preconditioned by the KP-SVD (eq. PreconSolve)
+ * with the same lambda (times option "pc_lambda_ratio", default 1).  Stops
+ * when ||r|| <= tol ||A^T b||; after maxit iterations it returns KP_ENOCONV
+ * with x = last iterate, and likewise when three residual replacements in a
+ * row fail to halve the true residual (the attainable accuracy of the
+ * reduced-precision operator and FP32 vectors lies above tol).  Other
+ * errors: KP_EBREAKDOWN (p^T K p <= 0 or z^T r <= 0), KP_ENUMERIC (NaN / Inf),
+ * KP_ETIMEOUT (a bounded device wait gave up), KP_ESTATE before kp_setup,
+ * KP_EINVAL for lambda <= 0 or not finite, tol < 0, maxit < 1, or b, x NULL
+ * or not 16-byte aligned.
  *   b        device, vec type, n_r x n_c
  *   x        device, vec type, n_r x n_c; input when warm_start != 0, output
  *   info     host, nullable
  * With an operator below FP64 the residual is replaced by the true residual
  * A^T (b - A x) - lambda^2 x, computed with an FP32-accurate operator,
  * whenever ||r|| has fallen by the reliable-update factor since the last
- * replacement, and always before convergence is declared. */
+ * replacement, after 50 iterations without one, and always before
+ * convergence is declared. */
 kp_status tik_pcg(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible,
                   void* x, int warm_start, kp_solve_info* info);
 
-/* Choose lambda in closed form over the KP spectrum (Section 2.2):
- * b_hat = vec(U_c^T B U_r), x_hat = vec(V_c^T X_true V_r) in FP64.
+/* Choose lambda in closed form over the KP spectrum (Section 2.2; eqs.
+ * GCVTikSVD, wGCVTikSVD, DSCTikSVD, OptTikSVD):
+ * b_hat = vec(U_c^T B U_r), x_hat = vec(V_c^T X_true V_r).
  * GCV / wGCV / OPT: minimum on lambda in [max(min|Sigma|>0, 1e-10 max|Sigma|),
- * max|Sigma|] by a 400-point grid in log lambda and a golden-section /
- * parabolic refinement in the best cell (ties -> larger lambda; for wGCV with
- * omega > 1 the range starts at the root of trace(I - omega A A^+)).
- * DISCREPANCY: root of D(lambda) (increasing) by bracketing in log lambda and
- * safeguarded bisection / secant; KP_ENOROOT when no root exists.
+ * max|Sigma|] by a 400-point grid in log lambda (one launch), the best point
+ * re-checked in FP64, then refined in the two adjacent cells in FP64: GCV and
+ * wGCV by safeguarded Newton on log G in log lambda from the vertex of the
+ * parabola through the best point and its neighbours, OPT by golden-section
+ * search (ties -> larger lambda; for wGCV with omega > 1 the range starts at
+ * the root of trace(I - omega A A^+)).  DISCREPANCY: root of D(lambda)
+ * (increasing) bracketed by decades in log lambda (down to 1e-16 max|Sigma|)
+ * and refined by safeguarded Newton; KP_ENOROOT when no root exists (eps >=
+ * ||b||, or D > 0 down to 1e-16 max|Sigma|).  KP_EINVAL for NULL b or lambda_out, an unknown method, omega <= 0,
+ * eps <= 0, or a missing x_true for OPT; KP_ESTATE before kp_setup.
  *   b        device, vec type
  *   x_true   device, vec type, only for KP_LAMBDA_OPT (else NULL)
  *   lambda_out host */
@@ -243,12 +270,13 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     dependent launch (default 1: each kernel's launch and
  *                     prologue overlap the tail of the previous one)
  *   "setup_fp64"      nonzero: keep the O(n^3) products of kp_setup and of
- *                     choose_lambda's spectral coefficients in FP64 also for
- *                     FP32 vectors.  By default they run in FP32 when
- *                     vec_prec is KP_F32 (factor SVD products and Gram test
- *                     at FP32 tolerance, rotations in FP64), which moves the
- *                     chosen lambda by ~1e-6 relative; FP64 vectors always
- *                     use FP64.  Takes effect at the next kp_setup. */
+ *                     choose_lambda's spectral coefficients, the Jacobi
+ *                     rotations and the PSF subspace iteration in FP64 also
+ *                     for FP32 vectors.  By default they run in FP32 when
+ *                     vec_prec is KP_F32 (Gram convergence test at FP32
+ *                     tolerance), which moves the chosen lambda by ~2.5e-7
+ *                     relative at 1024^2; FP64 vectors always use FP64.
+ *                     Takes effect at the next kp_setup. */
 kp_status kp_set_option(kp_ctx* ctx, const char* name, double value);
 
 /* ---- Batched independent problems of uneven sizes ------------------------
