@@ -23,6 +23,7 @@ BC = {"zero": 0, "reflexive": 1}
 PREC = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "f16": 4, "e4m3": 5}
 SIGMA = {"product": 0, "projected": 1}
 LAMBDA = {"gcv": 0, "wgcv": 1, "discrepancy": 2, "opt": 3}
+N_FEAT = 256  # spectral features per problem (kp_lambda_features, the MLP's input width)
 
 # every function declared in include/kpsvd.h
 EXPORTS = ["kp_create", "kp_destroy", "kp_setup", "kp_forward", "tik_pcg", "choose_lambda", "kp_apply_A",
@@ -105,11 +106,26 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
 _lib = load_library()
 
 
-def _ptr(t) -> int | None:
-    if t is None:
-        return None
-    if isinstance(t, int):
+_VEC_DTYPE = {"f64": "float64", "f32": "float32"}
+
+
+def _dev(t, dtype: str | None, numel: int, device: int, what: str) -> int | None:
+    """Device address of tensor ``t`` after the checks the C library cannot
+    make on a raw pointer: ``t`` must be a contiguous CUDA tensor of
+    ``dtype`` ("float64" / "float32"; None: any) on cuda:``device`` with at
+    least ``numel`` elements.  None stays None (the C call decides whether it
+    is allowed); an int is taken as a device address the caller vouches for."""
+    if t is None or isinstance(t, int):
         return t
+    dev = getattr(t, "device", None)
+    if dev is None or getattr(dev, "type", None) != "cuda" or dev.index != device:
+        raise KpError(KP_EINVAL, f"{what}: needs a CUDA tensor on cuda:{device}, got one on {dev}")
+    if dtype is not None and str(t.dtype) != "torch." + dtype:
+        raise KpError(KP_EINVAL, f"{what}: needs {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise KpError(KP_EINVAL, f"{what}: needs a contiguous tensor")
+    if t.numel() < numel:
+        raise KpError(KP_EINVAL, f"{what}: needs at least {numel} elements, got {t.numel()}")
     return t.data_ptr()
 
 
@@ -140,10 +156,15 @@ def from_device(t, n_r: int, n_c: int) -> np.ndarray:
 def kp_apply_Minv_noalloc(Vc, Vr, sigma, n_r: int, n_c: int, lam: float, r, z, stream: int | None = None):
     """Preconditioner solve without any device allocation (see include/kpsvd.h):
     Vc, Vr float32 column-major factors, sigma float64 spectrum, r, z float32."""
+    import torch
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream().cuda_stream
-    _check(_lib.kp_apply_Minv_noalloc(_ptr(Vc), _ptr(Vr), _ptr(sigma), n_r, n_c, lam, _ptr(r), _ptr(z), stream))
+    d = torch.cuda.current_device()
+    N = max(n_r, 0) * max(n_c, 0)
+    _check(_lib.kp_apply_Minv_noalloc(
+        _dev(Vc, "float32", max(n_r, 0) ** 2, d, "Vc"), _dev(Vr, "float32", max(n_c, 0) ** 2, d, "Vr"),
+        _dev(sigma, "float64", N, d, "sigma"), n_r, n_c, lam, _dev(r, "float32", N, d, "r"),
+        _dev(z, "float32", N, d, "z"), stream))
 
 
 @dataclass
@@ -157,7 +178,10 @@ class Info:
 
 
 class KpContext:
-    """Owns one kp_ctx.  All methods mirror the C ABI."""
+    """Owns one kp_ctx.  All methods mirror the C ABI.  Image arguments are
+    checked to be contiguous CUDA tensors on the context's device with the
+    element type and size of the problem set up (before kp_setup only the
+    device is checked; the C call then returns KP_ESTATE)."""
 
     def __init__(self, device: int = 0, stream: int | None = None):
         if stream is None:
@@ -166,8 +190,14 @@ class KpContext:
         h = ctypes.c_void_p()
         _check(_lib.kp_create(ctypes.byref(h), device, stream))
         self._h = h
+        self.device = device
         self.n_r = self.n_c = 0
         self.vec = "f64"
+
+    def _img(self, t, what: str):
+        if self.n_r == 0:
+            return _dev(t, None, 0, self.device, what)
+        return _dev(t, _VEC_DTYPE[self.vec], self.n_r * self.n_c, self.device, what)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -189,13 +219,15 @@ class KpContext:
     # -- setup / solve -------------------------------------------------------------
     def kp_setup(self, psf_dev, n_r: int, n_c: int, center, bc: str = "reflexive", op_rank: int = 0,
                  op_prec: str = "f64", pc_prec: str = "f64", vec_prec: str = "f64", sigma: str = "projected"):
-        _check(_lib.kp_setup(self._h, _ptr(psf_dev), n_r, n_c, int(center[0]), int(center[1]), BC[bc], op_rank,
+        psf = _dev(psf_dev, "float64", max(n_r, 0) * max(n_c, 0), self.device, "psf")
+        _check(_lib.kp_setup(self._h, psf, n_r, n_c, int(center[0]), int(center[1]), BC[bc], op_rank,
                              PREC[op_prec], PREC[pc_prec], PREC[vec_prec], SIGMA[sigma]))
         self.n_r, self.n_c, self.vec = n_r, n_c, vec_prec
 
     def kp_forward(self, x, g, noise_level: float, b) -> float:
         nn = ctypes.c_double(0.0)
-        _check(_lib.kp_forward(self._h, _ptr(x), _ptr(g), noise_level, _ptr(b), ctypes.byref(nn)))
+        _check(_lib.kp_forward(self._h, self._img(x, "x"), self._img(g, "g"), noise_level, self._img(b, "b"),
+                               ctypes.byref(nn)))
         return nn.value
 
     def tik_pcg(self, b, lam: float, tol: float, maxit: int, flexible: bool, x, warm_start: bool = False,
@@ -205,8 +237,8 @@ class KpContext:
         if hist_len > 0:
             info.res_hist = _dptr(hist)
             info.res_hist_len = hist_len
-        st = _lib.tik_pcg(self._h, _ptr(b), lam, tol, maxit, 1 if flexible else 0, _ptr(x), 1 if warm_start else 0,
-                          ctypes.byref(info))
+        st = _lib.tik_pcg(self._h, self._img(b, "b"), lam, tol, maxit, 1 if flexible else 0, self._img(x, "x"),
+                          1 if warm_start else 0, ctypes.byref(info))
         if check and st not in (KP_OK,):
             _check(st)
         n = min(hist_len, info.iters + 1) if hist_len > 0 else 0
@@ -214,22 +246,23 @@ class KpContext:
 
     def choose_lambda(self, b, method: str, param: float = 0.0, x_true=None) -> float:
         lam = ctypes.c_double(0.0)
-        _check(_lib.choose_lambda(self._h, _ptr(b), LAMBDA[method], param, _ptr(x_true), ctypes.byref(lam)))
+        _check(_lib.choose_lambda(self._h, self._img(b, "b"), LAMBDA[method], param, self._img(x_true, "x_true"),
+                                  ctypes.byref(lam)))
         return lam.value
 
     # -- hooks ---------------------------------------------------------------------
     def kp_lambda_features(self, b, out):
         """256 spectral features of b (device float32 tensor ``out``)."""
-        _check(_lib.kp_lambda_features(self._h, _ptr(b), _ptr(out)))
+        _check(_lib.kp_lambda_features(self._h, self._img(b, "b"), _dev(out, "float32", N_FEAT, self.device, "out")))
 
     def kp_apply_A(self, x, y, transpose: bool = False):
-        _check(_lib.kp_apply_A(self._h, _ptr(x), _ptr(y), 1 if transpose else 0))
+        _check(_lib.kp_apply_A(self._h, self._img(x, "x"), self._img(y, "y"), 1 if transpose else 0))
 
     def kp_apply_K(self, x, y, lam: float):
-        _check(_lib.kp_apply_K(self._h, _ptr(x), _ptr(y), lam))
+        _check(_lib.kp_apply_K(self._h, self._img(x, "x"), self._img(y, "y"), lam))
 
     def kp_apply_Minv(self, r, z, lam: float):
-        _check(_lib.kp_apply_Minv(self._h, _ptr(r), _ptr(z), lam))
+        _check(_lib.kp_apply_Minv(self._h, self._img(r, "r"), self._img(z, "z"), lam))
 
     def kp_get_rank(self) -> int:
         r = ctypes.c_int(0)
@@ -270,9 +303,13 @@ def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_pr
     optionally lam (> 0: fixed) and lambda_param.  Returns (status, ms_total,
     [(lambda, Info), ...]) in the order given."""
     arr = (Problem * len(problems))()
+    vt = _VEC_DTYPE.get(vec_prec, "float32")
     for k, p in enumerate(problems):
         q = arr[k]
-        q.psf, q.b, q.x = _ptr(p["psf"]), _ptr(p["b"]), _ptr(p["x"])
+        N = max(p["n_r"], 0) * max(p["n_c"], 0)
+        q.psf = _dev(p["psf"], "float64", N, device, f"problem {k} psf")
+        q.b = _dev(p["b"], vt, N, device, f"problem {k} b")
+        q.x = _dev(p["x"], vt, N, device, f"problem {k} x")
         q.n_r, q.n_c = p["n_r"], p["n_c"]
         q.center_r, q.center_c = int(p["center"][0]), int(p["center"][1])
         q.bc, q.op_rank = BC[p["bc"]], p["op_rank"]
@@ -301,7 +338,14 @@ class Mlp:
         h = ctypes.c_void_p()
         _check(_lib.kp_mlp_create(ctypes.byref(h), device, stream, width, depth, max_batch))
         self._h = h
+        self.device = device
         self.param_count = int(_lib.kp_mlp_param_count(h))
+
+    def _batch(self, X, what: str = "X"):
+        """(batch, device address) of a contiguous float32 batch x 256 CUDA tensor."""
+        if getattr(X, "dim", None) is None or X.dim() != 2 or X.shape[1] != N_FEAT:
+            raise KpError(KP_EINVAL, f"{what}: needs a batch x {N_FEAT} tensor")
+        return X.shape[0], _dev(X, "float32", X.shape[0] * N_FEAT, self.device, what)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -331,16 +375,21 @@ class Mlp:
         return a
 
     def forward(self, X, y):
-        _check(_lib.kp_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(y)))
+        n, xp = self._batch(X)
+        _check(_lib.kp_mlp_forward(self._h, xp, n, _dev(y, "float32", n, self.device, "y")))
 
     def gradients(self, X, labels):
+        n, xp = self._batch(X)
         g = np.empty(self.param_count, dtype=np.float32)
         loss = ctypes.c_double(0.0)
-        _check(_lib.kp_mlp_gradients(self._h, _ptr(X), _ptr(labels), X.shape[0], g.ctypes.data, ctypes.byref(loss)))
+        _check(_lib.kp_mlp_gradients(self._h, xp, _dev(labels, "float32", n, self.device, "labels"), n,
+                                     g.ctypes.data, ctypes.byref(loss)))
         return g, loss.value
 
     def train_step(self, X, labels, lr: float) -> float:
+        n, xp = self._batch(X)
         loss = ctypes.c_double(0.0)
-        _check(_lib.kp_mlp_train_step(self._h, _ptr(X), _ptr(labels), X.shape[0], lr, ctypes.byref(loss)))
+        _check(_lib.kp_mlp_train_step(self._h, xp, _dev(labels, "float32", n, self.device, "labels"), n, lr,
+                                      ctypes.byref(loss)))
         return loss.value
 
