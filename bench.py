@@ -428,10 +428,12 @@ def run_ours(args, ws, rank, local, dist):
             ctx64.close()
 
     # roofline of the dominant kernel family, the operator's tcgen05 GEMMs, per
-    # K application (4 GEMMs of 2 (r n_r) n_c n_r flops each, with the two term
-    # sums and the bf16 split of p that belong to one application)
+    # K application (A and A^T: per term one n_r x n_r by n_r x n_c product and
+    # one n_r x n_c by n_c x n_c product each, 4 r n_r n_c (n_r + n_c) flops in
+    # all, with the two term sums and the bf16 split of p that belong to one
+    # application)
     r = P.op_rank
-    flops_kapply = 4 * 2.0 * r * n_r * n_r * n_c
+    flops_kapply = 4.0 * r * n_r * n_c * (n_r + n_c)
     pk_, how = peaks()
     peak_tf = pk_.get("bf16_tflops")   # burst figure: the K application is timed alone
     achieved = flops_kapply / (kapply_ms * 1e-3) / 1e12
