@@ -17,12 +17,18 @@ Modules
   lam       closed-form parameter choice over the KP spectrum
             (eqs. OptTikSVD, GCVTikSVD, wGCVTikSVD, DSCTikSVD)
   forward   observed data b = A x_true + e at a given noise level (Section 5)
-  lowprec   rounding to bf16 / fp16 / e4m3 / fp32 for reduced-precision checks
-            (Section 4 uses the same rounding-simulation idea)
+  lowprec   rounding to bf16 / fp16 / e4m3 / fp32 and block-scaled FP8 for
+            reduced-precision checks (Section 4 uses the same
+            rounding-simulation idea)
+  mlp       spectral features and the GELU MLP of the learned lambda, with
+            its backward pass and Adam (not in the paper, which asks for a
+            systematic parameter choice, Section 5)
 
 Parity status: every function is pinned by a `-m "not gpu"` test against
-closed forms, brute force or identities (tests/test_oracle_*.py), except the
-reduced-precision emulation helpers in ``lowprec`` whose rounding is pinned
+closed forms, brute force, identities or hand-worked values
+(tests/test_oracle_*.py); the rounding helpers in ``lowprec`` are pinned
 against numpy's own float16/float32 casts and hand-worked values.
+tests/test_oracle_planted_mistakes.py plants plausible mistakes in copies of
+these modules and checks that a pin fails for each.
 """
-from . import kron, kpsvd, pcg, lam, forward, lowprec  # noqa: F401
+from . import kron, kpsvd, pcg, lam, forward, lowprec, mlp  # noqa: F401
