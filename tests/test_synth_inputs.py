@@ -57,3 +57,21 @@ def test_batch_is_reproducible_and_seeded():
         assert np.array_equal(p.x_true, q.x_true) and np.array_equal(p.psf, q.psf)
         assert p.noise_levels == q.noise_levels and p.bc == q.bc
     assert any(not np.array_equal(p.psf, q.psf) for p, q in zip(a, c))
+
+
+def test_gaussian_psf_moments_fix_the_axes():
+    """The PSF is the bivariate normal with sigma_x along the columns (x),
+    sigma_y along the rows (y) and correlation rho, normalised to sum 1: on a
+    grid reaching 20 sigma from the centre the sampled second moments about
+    the centre equal the covariance [[sx^2, rho sx sy], [rho sx sy, sy^2]] (the
+    grid sums of a Gaussian match its integrals to far below rounding), and
+    the peak sits at the centre."""
+    sx, sy, rho, n, c = 3.0, 1.5, 0.5, 128, (64, 60)
+    P = synth.gaussian_psf(n, n, c[0], c[1], sx, sy, rho)
+    assert abs(P.sum() - 1.0) < 1e-14
+    assert np.unravel_index(np.argmax(P), P.shape) == c
+    dy = np.arange(n)[:, None] - c[0]
+    dx = np.arange(n)[None, :] - c[1]
+    np.testing.assert_allclose([np.sum(P * dx * dx), np.sum(P * dy * dy), np.sum(P * dx * dy)],
+                               [sx * sx, sy * sy, rho * sx * sy], rtol=1e-12)
+    np.testing.assert_allclose([np.sum(P * dx), np.sum(P * dy)], [0.0, 0.0], atol=1e-12)
