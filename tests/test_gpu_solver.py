@@ -294,3 +294,23 @@ def test_discrepancy_without_root(kpsvd):
         with pytest.raises(kpsvd.KpError) as e:
             ctx.choose_lambda(b, "discrepancy", 2.0 * np.linalg.norm(pr.B))
         assert e.value.status == kpsvd.KP_ENOROOT
+
+
+@pytest.mark.parametrize("op,pc,flexible", [("f32", "f32", False), ("f32", "f32", True), ("bf16", "f16", True)])
+def test_discrepancy_lambda_solve_reaches_oracle_solution(kpsvd, op, pc, flexible):
+    """256 x 256 with lambda by the discrepancy principle (eps = 1.01 times the
+    generator's noise norm, the workload's second parameter choice): the
+    GPU's lambda equals the oracle's root, and PCG / FPCG reach the oracle's
+    x_lambda to 1e-4 within +3 iterations of the oracle's FP64 run."""
+    pr = OracleProblem("deblur256_fp32")
+    eps = 1.01 * pr.enorm
+    lam = olam.choose_lambda(pr.kp, pr.B, "discrepancy", eps)
+    x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam)
+    _, io = opcg.tik_pcg(pr.op, pr.kp, pr.B, lam, 1e-7, 500, flexible)
+    with setup_ctx(kpsvd, pr, op, pc, "f32") as ctx:
+        lg = ctx.choose_lambda(kpsvd.to_device(pr.B, torch.float32), "discrepancy", eps)
+        x, info = run(kpsvd, ctx, pr, lam, 1e-7, 500, flexible, "f32")
+    assert abs(np.log(lg / lam)) < 1e-4
+    assert info.status == kpsvd.KP_OK
+    assert rel(x, x_star) < 1e-4
+    assert info.iters <= io.iters + 3
