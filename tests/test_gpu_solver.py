@@ -314,3 +314,20 @@ def test_discrepancy_lambda_solve_reaches_oracle_solution(kpsvd, op, pc, flexibl
     assert info.status == kpsvd.KP_OK
     assert rel(x, x_star) < 1e-4
     assert info.iters <= io.iters + 3
+
+
+@pytest.mark.parametrize("pc", ["f16", "bf16"])
+def test_fp32_operator_with_half_precision_preconditioner(kpsvd, pc):
+    """The 256 x 256 configuration as stated: rank-3 operator in FP32 (SIMT),
+    KP-SVD preconditioner in FP16 or BF16 on the tensor cores with FP32
+    accumulation; FPCG with the GCV lambda reaches the oracle's x_lambda to
+    1e-4 within +3 iterations of the oracle's FP64 FPCG."""
+    pr = OracleProblem("deblur256_fp32")
+    lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
+    x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam)
+    _, io = opcg.tik_pcg(pr.op, pr.kp, pr.B, lam, 1e-7, 500, True)
+    with setup_ctx(kpsvd, pr, "f32", pc, "f32") as ctx:
+        x, info = run(kpsvd, ctx, pr, lam, 1e-7, 500, True, "f32")
+    assert info.status == kpsvd.KP_OK
+    assert rel(x, x_star) < 1e-4
+    assert info.iters <= io.iters + 3
