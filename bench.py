@@ -53,7 +53,7 @@ def parse():
                          "learned_lambda: train the lambda regressor on generated 256^2 problems and compare it "
                          "with GCV on new ones (each its own JSON line; the default workload is the headline "
                          "metric)")
-    ap.add_argument("--train", type=int, default=4096, help="learned_lambda: training problems")
+    ap.add_argument("--train", type=int, default=20000, help="learned_lambda: training problems")
     ap.add_argument("--eval", type=int, default=512, help="learned_lambda: evaluation problems")
     ap.add_argument("--workers", type=int, default=8, help="batched64: concurrent problems")
     ap.add_argument("--kernel-only", choices=["kapply", "minv"], default=None,
