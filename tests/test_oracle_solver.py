@@ -327,3 +327,23 @@ def test_projected_and_product_spectra_coincide_for_one_term(bc):
                                rtol=0, atol=1e-13)
     op3, _, _ = _problem(n=12, bc=bc, rank=3)
     assert np.abs(kpsvd.kp_svd(op3, "projected").Sigma - kpsvd.kp_svd(op3, "product").Sigma).max() > 1e-6
+
+
+@pytest.mark.parametrize("bc", ["zero", "reflexive"])
+def test_delta_psf_is_the_identity(bc):
+    """Degenerate blur: a PSF that is 1 at its centre and 0 elsewhere gives
+    A = I for either boundary condition (one Kronecker term), a KP spectrum
+    of ones, and x_lambda = b / (1 + lambda^2) (eq. TikSV with every singular
+    value 1), which PCG reaches in one iteration."""
+    n_r, n_c, c = 12, 10, (5, 4)
+    P = np.zeros((n_r, n_c))
+    P[c] = 1.0
+    op = kron.kron_operator(P, c, bc, rank=0)
+    np.testing.assert_allclose(kron.dense_A(op), np.eye(n_r * n_c), rtol=0, atol=1e-14)
+    kp = kpsvd.kp_svd(op, "projected")
+    np.testing.assert_allclose(np.abs(kp.Sigma), 1.0, rtol=0, atol=1e-14)
+    B = np.random.default_rng(3).standard_normal((n_r, n_c))
+    lam = 0.3
+    x, info = pcg.tik_pcg(op, kp, B, lam, 1e-14, 5)
+    assert info.iters == 1
+    np.testing.assert_allclose(x, B / (1.0 + lam * lam), rtol=0, atol=1e-14)
