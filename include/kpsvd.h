@@ -178,8 +178,10 @@ kp_status tik_pcg(kp_ctx* ctx, const void* b, double lambda, double tol, int max
  * the root of trace(I - omega A A^+)).  DISCREPANCY: root of D(lambda)
  * (increasing) bracketed by decades in log lambda (down to 1e-16 max|Sigma|)
  * and refined by safeguarded Newton; KP_ENOROOT when no root exists (eps >=
- * ||b||, or D > 0 down to 1e-16 max|Sigma|).  KP_EINVAL for NULL b or lambda_out, an unknown method, omega <= 0,
- * eps <= 0, or a missing x_true for OPT; KP_ESTATE before kp_setup.
+ * ||b||, or D > 0 down to 1e-16 max|Sigma|).  KP_ENUMERIC when b (or x_true
+ * for OPT) holds a NaN or Inf.  KP_EINVAL for NULL b or lambda_out, an unknown
+ * method, omega <= 0, eps <= 0, or a missing x_true for OPT; KP_ESTATE before
+ * kp_setup.
  *   b        device, vec type
  *   x_true   device, vec type, only for KP_LAMBDA_OPT (else NULL)
  *   lambda_out host */

@@ -578,6 +578,10 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
       KP_TRY(eval64(L, &big, 1, &s1, &s2v));
       bb = s1;
     }
+    if (!std::isfinite(bb)) {
+      kp_set_error("choose_lambda: the KP coefficients of b are not finite");
+      return KP_ENUMERIC;
+    }
     if (!(bb > eps * eps)) {
       kp_set_error("choose_lambda: discrepancy has no root (eps >= ||b_hat||)");
       return KP_ENOROOT;
@@ -667,6 +671,14 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
   std::vector<double> hsum(2 * NGRID);
   KP_CUDA(cudaMemcpyAsync(hsum.data(), sums, sizeof(double) * 2 * NGRID, cudaMemcpyDeviceToHost, st));
   KP_CUDA(cudaStreamSynchronize(st));
+  // every grid sum is bounded for finite data (phi in [0, 1], d >= lam^2 > 0):
+  // a NaN or Inf comes from b (or x_true) and would leave no minimum to find
+  for (int g = 0; g < 2 * NGRID; ++g) {
+    if (!std::isfinite(hsum[g])) {
+      kp_set_error("choose_lambda: the KP coefficients of %s are not finite", lm == LM_OPT ? "b or x_true" : "b");
+      return KP_ENUMERIC;
+    }
+  }
   int best = 0;
   double bv = INFINITY;
   for (int g = 0; g < NGRID; ++g) {

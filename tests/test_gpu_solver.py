@@ -331,3 +331,28 @@ def test_fp32_operator_with_half_precision_preconditioner(kpsvd, pc):
     assert info.status == kpsvd.KP_OK
     assert rel(x, x_star) < 1e-4
     assert info.iters <= io.iters + 3
+
+
+@pytest.mark.parametrize("vec", ["f64", "f32"])
+def test_non_finite_data_is_reported(kpsvd, vec):
+    """A NaN in b is a status, not a result: tik_pcg returns KP_ENUMERIC
+    (A^T b is not finite) and choose_lambda returns KP_ENUMERIC for GCV and
+    the discrepancy principle instead of a lambda; the context then solves
+    finite data as before."""
+    pr = OracleProblem("deblur256_fp32", n=64, rank=2)
+    op = "f64" if vec == "f64" else "bf16"
+    pc = "f64" if vec == "f64" else "f16"
+    with setup_ctx(kpsvd, pr, op, pc, vec) as ctx:
+        Bn = pr.B.copy()
+        Bn[3, 5] = np.nan
+        b = kpsvd.to_device(Bn, vt(vec))
+        x = torch.zeros_like(b)
+        info = ctx.tik_pcg(b, 0.05, 1e-6, 50, True, x, check=False)
+        assert info.status == kpsvd.KP_ENUMERIC
+        for method, param in (("gcv", 0.0), ("discrepancy", 1.01 * pr.enorm)):
+            with pytest.raises(kpsvd.KpError) as e:
+                ctx.choose_lambda(b, method, param)
+            assert e.value.status == kpsvd.KP_ENUMERIC
+        x, info = run(kpsvd, ctx, pr, 0.05, 1e-7, 300, True, vec)
+        assert info.status == kpsvd.KP_OK
+        assert rel(x, opcg.tik_exact(pr.op, pr.kp, pr.B, 0.05)) < 1e-4
