@@ -126,9 +126,10 @@ void kp_destroy(kp_ctx* ctx);
  * grid, op_rank outside [0, min(n_r, n_c)], an unknown bc or sigma, or an
  * unsupported precision combination; KP_ENOTSUP when tensor-core precisions
  * meet a device other than sm_103 or sizes not multiples of 16.  These
- * checks run first and leave the context's previous problem in place; a
- * failure after them (KP_ENOMEM, KP_ECUDA) leaves the context without a
- * problem, and later calls other than kp_setup return KP_ESTATE.
+ * checks run first and leave the context's previous problem in place.  A
+ * failure after them leaves the context without a problem, and later calls
+ * other than kp_setup return KP_ESTATE: KP_ENUMERIC for a PSF holding a NaN
+ * or Inf, KP_EINVAL for an all-zero PSF, KP_ENOMEM, KP_ECUDA.
  * Synchronises. */
 kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, int center_r, int center_c,
                    kp_bc bc, int op_rank, kp_prec op_prec, kp_prec pc_prec, kp_prec vec_prec,

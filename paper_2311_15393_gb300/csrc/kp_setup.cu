@@ -336,6 +336,20 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
   KP_TRY(kp_alloc(ctx, (void**)&Vw, sizeof(double) * (size_t)nn * nn));
   k_weight_psf<<<grid_for(ctx, N), 256, 0, st>>>(psf, n_r, n_c, center_r, center_c, W);
   KP_LAUNCHED(ctx);
+  {  // the weighted PSF is finite and nonzero exactly when the PSF is
+    double h[2];
+    KP_TRY(norm_amax_dev(ctx, W, N, true, ctx->dscal + S_RR));
+    KP_CUDA(cudaMemcpyAsync(h, ctx->dscal + S_RR, sizeof(h), cudaMemcpyDeviceToHost, st));
+    KP_CUDA(cudaStreamSynchronize(st));
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) {
+      kp_set_error("kp_setup: the PSF holds a NaN or Inf");
+      return KP_ENUMERIC;
+    }
+    if (!(h[1] > 0.0)) {
+      kp_set_error("kp_setup: the PSF is zero");
+      return KP_EINVAL;
+    }
+  }
   double *Uc_w, *Vc_w;  // left (n_r) and right (n_c) singular vectors of W
   const double* Wsrc = W;
   if (n_r < n_c) {  // work on W^T (m >= n)

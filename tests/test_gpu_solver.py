@@ -356,3 +356,28 @@ def test_non_finite_data_is_reported(kpsvd, vec):
         x, info = run(kpsvd, ctx, pr, 0.05, 1e-7, 300, True, vec)
         assert info.status == kpsvd.KP_OK
         assert rel(x, opcg.tik_exact(pr.op, pr.kp, pr.B, 0.05)) < 1e-4
+
+
+def test_non_finite_or_zero_psf_is_rejected(kpsvd):
+    """kp_setup checks the PSF before factoring it: a NaN gives KP_ENUMERIC,
+    an all-zero PSF KP_EINVAL, and a solve on the context then reports that
+    no problem is set up (KP_ESTATE); the same context then takes a valid
+    PSF, whose KP spectrum matches the oracle to FP32 level."""
+    pr = OracleProblem("deblur256_fp32", n=64, rank=2)
+    P = pr.P
+    args = (P.n_r, P.n_c, P.center, P.bc, P.op_rank, "f32", "f32", "f32")
+    with kpsvd.KpContext(0) as ctx:
+        bad = P.psf.copy()
+        bad[10, 20] = np.nan
+        with pytest.raises(kpsvd.KpError) as e:
+            ctx.kp_setup(kpsvd.to_device(bad), *args)
+        assert e.value.status == kpsvd.KP_ENUMERIC
+        with pytest.raises(kpsvd.KpError) as e:
+            ctx.kp_setup(kpsvd.to_device(np.zeros_like(P.psf)), *args)
+        assert e.value.status == kpsvd.KP_EINVAL
+        b = kpsvd.to_device(pr.B, torch.float32)
+        info = ctx.tik_pcg(b, 0.05, 1e-6, 10, True, torch.zeros_like(b), check=False)
+        assert info.status == kpsvd.KP_ESTATE
+        ctx.kp_setup(kpsvd.to_device(P.psf), *args)
+        smax = np.abs(pr.kp.Sigma).max()
+        np.testing.assert_allclose(ctx.kp_get_spectrum(), pr.kp.Sigma, rtol=0, atol=8 * 64 * 2.0 ** -23 * smax)
