@@ -334,8 +334,9 @@ kp_status kp_solve_batch(int device, kp_problem* probs, int nprob, const kp_batc
  * b_hat^2 over the deepest bins that together hold >= N / 8 components (a
  * noise estimate), features[255] = log10(s2max); b_hat = vec(U_c^T B U_r).
  *   b         device, vec type;  features  device, 256 floats (written)
- * Asynchronous, except that the first call after kp_setup (or choose_lambda)
- * synchronises once to read the spectrum's extremes; b is not checked (a NaN
+ * Asynchronous, except when it is the first of kp_lambda_features and
+ * choose_lambda after a kp_setup: that call synchronises once to read the
+ * spectrum's extremes; b is not checked (a NaN
  * or Inf in b gives non-finite features, where choose_lambda would return
  * KP_ENUMERIC). */
 kp_status kp_lambda_features(kp_ctx* ctx, const void* b, float* features);
