@@ -45,3 +45,17 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
     p = _bench("--n", "64", "--steps", "1", "--warmup", "0", "--no-cpu-baseline")
     assert p.returncode != 0
     assert not [l for l in p.stdout.splitlines() if l.startswith("{")]
+
+
+def test_traffic_figure_is_used_only_for_the_kernels_it_was_taken_on(monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu capture; it is
+    reported only for the workload it was taken on (n = 1024, rank 4) and
+    only while the K application's CUDA sources hash to the recorded digest."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "kapply_deblur1024_traffic.json")))
+    assert bench.kapply_traffic(1024, 4) == rec["dram_bytes_per_k_application"]
+    assert bench.kapply_traffic(512, 4) is None
+    assert bench.kapply_traffic(1024, 3) is None
+    monkeypatch.setattr(bench, "sources_digest", lambda: "0" * 64)
+    assert bench.kapply_traffic(1024, 4) is None
