@@ -54,8 +54,11 @@ def test_traffic_figure_is_used_only_for_the_kernels_it_was_taken_on(monkeypatch
     sys.path.insert(0, ROOT)
     import bench
     rec = json.load(open(os.path.join(ROOT, "profiles", "kapply_deblur1024_traffic.json")))
+    current = bench.sources_digest() == rec["sources_sha256"]
+    assert bench.kapply_traffic(1024, 4) == (rec["dram_bytes_per_k_application"] if current else None)
+    monkeypatch.setattr(bench, "sources_digest", lambda: rec["sources_sha256"])  # sources as captured
     assert bench.kapply_traffic(1024, 4) == rec["dram_bytes_per_k_application"]
     assert bench.kapply_traffic(512, 4) is None
     assert bench.kapply_traffic(1024, 3) is None
-    monkeypatch.setattr(bench, "sources_digest", lambda: "0" * 64)
+    monkeypatch.setattr(bench, "sources_digest", lambda: "0" * 64)          # sources changed since
     assert bench.kapply_traffic(1024, 4) is None
