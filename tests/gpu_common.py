@@ -63,6 +63,31 @@ def setup_ctx(kpsvd, prob: OracleProblem, op_prec, pc_prec, vec_prec, sigma="pro
     return ctx
 
 
+def gpu_operator(ctx, prob: OracleProblem):
+    """Operator built from the context's own Kronecker terms (kp_get_terms)
+    by the oracle's factor construction (eq. KronSumDecomp).  A
+    reduced-precision emulation fed with it rounds exactly the factor values
+    the GPU rounds, so comparing against it checks the GEMMs alone; how the
+    GPU's setup arrived at its terms is checked against the oracle apart."""
+    s, U, V = ctx.kp_get_terms()
+    P = prob.P
+    c_r, c_c = P.center
+    Ac = [kron.blur_factor(U[:, m], c_r, P.bc) for m in range(U.shape[1])]
+    Ar = [kron.blur_factor(V[:, m], c_c, P.bc) for m in range(V.shape[1])]
+    return kron.KronOperator(Ac=Ac, Ar=Ar, s=s, u=U, v=V, bc=P.bc)
+
+
+class GpuKpsvd:
+    """The context's own KP-SVD factors and spectrum (getters), in the shape
+    the emulations read (Vc, Vr, Sigma)."""
+
+    def __init__(self, ctx):
+        f = ctx.kp_get_kpsvd()
+        self.Vc, self.Vr, self.sc, self.sr = f["Vc"], f["Vr"], f["sc"], f["sr"]
+        self.Uc, self.Ur = f["Uc"], f["Ur"]
+        self.Sigma = ctx.kp_get_spectrum()
+
+
 def vt(vec_prec):
     return torch.float64 if vec_prec == "f64" else torch.float32
 
@@ -79,6 +104,68 @@ def emulate_apply_A_bf16(op, X):
     Xb = bf(lp.to_fp32(X))
     W = [bf(lp.to_fp32(bf(Ac) @ Xb)) for Ac in op.Ac]
     return lp.to_fp32(sum(Wk @ bf(Ar).T for Wk, Ar in zip(W, op.Ar)))
+
+
+def emulate_apply_AT_bf16(op, Y):
+    """A^T Y on the tensor-core inner operator, with the rounding points of
+    emulate_apply_A_bf16 (G3 output rounded to bf16, G4 accumulated)."""
+    Yb = bf(lp.to_fp32(Y))
+    W = [bf(lp.to_fp32(bf(Ac).T @ Yb)) for Ac in op.Ac]
+    return lp.to_fp32(sum(Wk @ bf(Ar) for Wk, Ar in zip(W, op.Ar)))
+
+
+U32 = 2.0 ** -24
+
+
+def bf16_operator_bound(op, X, transpose=False):
+    """Bound on |GPU - emulation| / |emulation| for the inner BF16 operator
+    applied to X, derived from the arithmetic.  The two sides round the same
+    bf16 operands and products of bf16 values are exact in FP32; they differ
+    only by FP32 accumulation.  A sum of m nonzero products accumulated in
+    FP32 in any order (rounded or truncated) is within 2 (m - 1) u32 sum |.|
+    of the exact sum.  (1) Where that interval around an exact first-GEMM
+    output straddles a bf16 rounding boundary, the GPU's bf16 intermediate W
+    may be one bf16 step off the emulation's (D); (2) the second GEMM's FP32
+    sum adds its own accumulation error.  Returns
+    (|| sum_k D_k |B_k| || + || 2 (m - 1) u32 sum_k |W_k| |B_k| ||) / ||Y||,
+    with B_k the second factor as the second GEMM reads it."""
+    Xb = bf(lp.to_fp32(X))
+    first = [bf(Ac).T if transpose else bf(Ac) for Ac in op.Ac]
+    second = [bf(Ar) if transpose else bf(Ar).T for Ar in op.Ar]
+    nz = lambda A: (A != 0).astype(np.float64)  # noqa: E731
+    Y = 0.0
+    flips = 0.0
+    acc = 0.0
+    cnt2 = 0.0
+    for F, G in zip(first, second):
+        S = F @ Xb
+        m1 = nz(F) @ nz(Xb)
+        E = 2.0 * np.maximum(m1 - 1.0, 0.0) * U32 * (np.abs(F) @ np.abs(Xb))
+        W = bf(lp.to_fp32(S))
+        D = np.maximum(np.abs(bf(lp.to_fp32(S + E)) - W), np.abs(bf(lp.to_fp32(S - E)) - W))
+        Y = Y + W @ G
+        flips = flips + D @ np.abs(G)
+        acc = acc + np.abs(W) @ np.abs(G)
+        cnt2 = cnt2 + nz(W) @ nz(G)
+    acc_err = 2.0 * np.maximum(cnt2 - 1.0, 0.0) * U32 * acc
+    return (np.linalg.norm(flips) + np.linalg.norm(acc_err)) / np.linalg.norm(Y)
+
+
+def spike_image(n_r, n_c, seed=0):
+    """Sparse test image for the tensor-core operator: one entry per used
+    column (so every element of the first GEMM's output is a single product,
+    exact in FP32 and in bf16), at rows and columns that reach the first,
+    the interior and the ragged last tiles of both dimensions (128-row and
+    64-element blocks), with values +-2^e, e in {-1, 0, 1}."""
+    rng = np.random.default_rng(seed)
+    cols = sorted({c for c in (0, 1, 31, 63, 64, 100, 127, 128, 191, 192, 255, n_c - 17, n_c - 2, n_c - 1)
+                   if 0 <= c < n_c})
+    rows = [0, 15, 63, 64, 127, 128, 150, n_r - 33, n_r - 16, n_r - 1]
+    X = np.zeros((n_r, n_c))
+    for m, c in enumerate(cols):
+        r = rows[m % len(rows)] % n_r
+        X[r, c] = rng.choice([-1.0, 1.0]) * 2.0 ** int(rng.integers(-1, 2))
+    return X
 
 
 def pow2_scale(amax, target):
@@ -145,3 +232,32 @@ def emulate_minv(kp, Sigma, R, lam, fmt):
     T3 = rd(lp.to_fp32(Vc @ W))
     inv = lp.to_fp32(1.0 / (lam * lam * s))
     return lp.to_fp32(lp.to_fp32(T3 @ Vr.T) * inv)
+
+
+def check_bf16_operator(kpsvd, ctx, pr, n_r, n_c):
+    """Inner BF16 operator A and A^T against their emulation on the GPU's own
+    terms (both sides round the same factor values):
+    - on a spike image every product of the first GEMM stands alone, so both
+      sides form the same bf16 intermediate and differ only by the second
+      GEMM's FP32 sum of a few dozen exact products: agreement to the
+      derived bound (~1e-5, typically ~1e-7 measured), which any misplaced,
+      dropped or stale row, column or k-block of a ragged tile would exceed
+      by orders of magnitude;
+    - on a dense random image, within the bound derived from the FP32
+      accumulation (bf16_operator_bound), and within bf16 rounding of FP64."""
+    gop = gpu_operator(ctx, pr)
+    for name, X in (("spike", spike_image(n_r, n_c, 3)), ("random", synth.random_matrix(n_r, n_c, 11))):
+        x = kpsvd.to_device(X, torch.float32)
+        y = torch.empty_like(x)
+        for tr in (False, True):
+            ctx.kp_apply_A(x, y, tr)
+            Y = kpsvd.from_device(y, n_r, n_c)
+            emu = emulate_apply_AT_bf16(gop, X) if tr else emulate_apply_A_bf16(gop, X)
+            e_emu = rel(Y, emu)
+            bound = bf16_operator_bound(gop, X, tr)
+            print(f"{(n_r, n_c)} {name} {'A^T' if tr else 'A'}: vs emulation {e_emu:.3e} (bound {bound:.2e})")
+            assert e_emu <= bound
+            if name == "spike":   # exact intermediates: only the second sum's rounding remains
+                assert bound < 1e-4
+            ref = kron.apply_AT(pr.op, X) if tr else kron.apply_A(pr.op, X)
+            assert rel(Y, ref) < 2e-2

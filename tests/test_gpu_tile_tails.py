@@ -11,7 +11,7 @@ the oracle exactly as at the tile-aligned sizes."""
 import numpy as np
 import pytest
 
-from gpu_common import OracleProblem, emulate_apply_A_bf16, emulate_minv, lib, rel, setup_ctx, torch
+from gpu_common import GpuKpsvd, OracleProblem, check_bf16_operator, emulate_minv, lib, rel, setup_ctx, torch
 from oracle import kpsvd as okp, kron, lam as olam, pcg as opcg
 from paper_2311_15393_gb300 import synth
 
@@ -31,20 +31,13 @@ def _problem(shape, psf=None):
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
 def test_operator_with_tile_tails(kpsvd, shape):
-    """Inner BF16 operator: A against its bf16 emulation and FP64, A^T against
-    FP64; the accurate operator (kp_forward) against the oracle's b."""
+    """Inner BF16 operator A and A^T against the emulation (check_bf16_operator);
+    the accurate operator (kp_forward) against the oracle's b, which also
+    checks the GPU's terms against the oracle's."""
     n_r, n_c = shape
     pr = _problem(shape)
     with setup_ctx(kpsvd, pr, "bf16", "f16", "f32") as ctx:
-        X = synth.random_matrix(n_r, n_c, 11)
-        x = kpsvd.to_device(X, torch.float32)
-        y = torch.empty_like(x)
-        ctx.kp_apply_A(x, y, False)
-        Y = kpsvd.from_device(y, n_r, n_c)
-        assert rel(Y, emulate_apply_A_bf16(pr.op, X)) < 1e-5
-        assert rel(Y, kron.apply_A(pr.op, X)) < 2e-2
-        ctx.kp_apply_A(x, y, True)
-        assert rel(kpsvd.from_device(y, n_r, n_c), kron.apply_AT(pr.op, X)) < 2e-2
+        check_bf16_operator(kpsvd, ctx, pr, n_r, n_c)
         xt = kpsvd.to_device(pr.P.x_true, torch.float32)
         g = kpsvd.to_device(pr.P.noise_dirs[0], torch.float32)
         b = torch.empty_like(xt)
@@ -54,9 +47,9 @@ def test_operator_with_tile_tails(kpsvd, shape):
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
 def test_fp16_preconditioner_with_tile_tails(kpsvd, shape):
-    """FP16 KP-SVD solve against its emulation (a narrow PSF keeps the factor
-    singular values far above rounding level, so both sides round the same V)
-    and against FP64."""
+    """FP16 KP-SVD solve against its emulation on the GPU's own factors and
+    spectrum (so both sides round the same V) and against FP64 (a narrow PSF
+    keeps the factor singular values far above rounding level)."""
     n_r, n_c = shape
     psf = synth.gaussian_psf(n_r, n_c, n_r // 2, n_c // 2, 0.8, 0.6, 0.3)
     pr = _problem(shape, psf=psf)
@@ -68,7 +61,8 @@ def test_fp16_preconditioner_with_tile_tails(kpsvd, shape):
         z = torch.empty_like(r)
         ctx.kp_apply_Minv(r, z, lam)
         Z = kpsvd.from_device(z, n_r, n_c)
-        assert rel(Z, emulate_minv(pr.kp, pr.kp.Sigma, R, lam, "f16")) < 0.5 * 2.0 ** -11
+        gk = GpuKpsvd(ctx)
+        assert rel(Z, emulate_minv(gk, gk.Sigma, R, lam, "f16")) < 0.5 * 2.0 ** -11
         assert rel(Z, okp.precond_apply(pr.kp, okp.precond_scale(pr.kp.Sigma, lam), R)) < 5e-3
 
 
