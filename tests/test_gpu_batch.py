@@ -22,13 +22,11 @@ def kpsvd():
 
 @pytest.fixture(scope="module")
 def problems():
-    """Six problems drawn by the batched workload's generator at small sizes
-    (noise levels raised to >= 1%, which keeps cond(A^T A + lambda^2 I) at
-    the GCV lambda where a 1e-7 residual means a 1e-4 solution error), with
-    the oracle's observed data b (its own FP64 operator)."""
+    """Six problems drawn by the batched workload's generator at small sizes,
+    at the generator's own noise levels (0.1% to 5%), with the oracle's
+    observed data b (its own FP64 operator)."""
     out = []
     for P in synth.make_batch(6, sizes=SIZES, seed=77):
-        P.noise_levels = [max(P.noise_levels[0], 0.01)]
         op = kron.kron_operator(P.psf, P.center, P.bc, P.op_rank)
         kp = okp.kp_svd(op, "projected")
         B, _ = forward.observe(op, P.x_true, P.noise_dirs[0], P.noise_levels[0])
@@ -53,10 +51,11 @@ def test_batch_matches_oracle(kpsvd, problems):
     put), and x is within 1e-4 of the oracle's x_lambda at that lambda (the
     metric's bar) where cond(K) = (sigma_max^2 + lambda^2) / lambda^2 <= 1e4,
     else within the forward-error bound cond(K) tol of the residual stopping
-    rule."""
+    rule.  A problem may stop as stagnated (KP_ENOCONV: the true residual no
+    longer halves at FP32 accuracy) only where cond(K) > 1e4; such a problem
+    is not a solve at the metric's bar and is reported, not counted."""
     dev = device_problems(kpsvd, problems)
-    st, ms, res = kpsvd.kp_solve_batch(dev, tol=TOL, workers=3)
-    assert st == kpsvd.KP_OK
+    st, ms, res = kpsvd.kp_solve_batch(dev, tol=TOL, workers=3, check=False)
     for pr, d, (lam, info) in zip(problems, dev, res):
         P = pr["P"]
         lam_o = olam.choose_lambda(pr["kp"], pr["B"], "gcv")
@@ -65,12 +64,12 @@ def test_batch_matches_oracle(kpsvd, problems):
         print(f"{P.n_r}x{P.n_c} {P.bc} nl {P.noise_levels[0]:.4f}: lambda {lam:.6g} (oracle {lam_o:.6g}), "
               f"{info.iters} iterations, rel. error {rel(X, x_star):.2e}, cond(K) "
               f"{(np.max(np.abs(pr['kp'].Sigma)) ** 2 + lam ** 2) / lam ** 2:.1e}")
-        assert info.status == kpsvd.KP_OK
+        cond = (np.max(np.abs(pr["kp"].Sigma)) ** 2 + lam ** 2) / lam ** 2
+        assert info.status == kpsvd.KP_OK or (info.status == kpsvd.KP_ENOCONV and cond > 1e4)
         bh = olam.spectral_coeffs(pr["kp"], pr["B"])
         g_gpu, g_o = olam.gcv(pr["kp"].Sigma, bh, lam), olam.gcv(pr["kp"].Sigma, bh, lam_o)
         assert g_gpu <= g_o * (1.0 + 1e-5)
         assert abs(np.log(lam / lam_o)) < 0.1
-        cond = (np.max(np.abs(pr["kp"].Sigma)) ** 2 + lam ** 2) / lam ** 2
         assert rel(X, x_star) < (1e-4 if cond <= 1e4 else cond * TOL)
 
 
@@ -79,8 +78,7 @@ def test_batch_equals_single_solves(kpsvd, problems):
     tik_pcg compute for it alone on one context (concurrency changes no
     result)."""
     dev = device_problems(kpsvd, problems)
-    st, _, res = kpsvd.kp_solve_batch(dev, tol=TOL, workers=4)
-    assert st == kpsvd.KP_OK
+    st, _, res = kpsvd.kp_solve_batch(dev, tol=TOL, workers=4, check=False)
     for pr, d, (lam, info) in zip(problems, dev, res):
         P = pr["P"]
         with kpsvd.KpContext(0) as ctx:
@@ -88,8 +86,14 @@ def test_batch_equals_single_solves(kpsvd, problems):
             ctx.kp_setup(d["psf"], P.n_r, P.n_c, P.center, P.bc, P.op_rank, "bf16", "f16", "f32", "projected")
             lam1 = ctx.choose_lambda(d["b"], "gcv")
             x1 = torch.zeros_like(d["b"])
-            info1 = ctx.tik_pcg(d["b"], lam1, TOL, 500, True, x1)
+            info1 = ctx.tik_pcg(d["b"], lam1, TOL, 500, True, x1, check=False)
+            if info1.status in (kpsvd.KP_ENOCONV, kpsvd.KP_EBREAKDOWN, kpsvd.KP_ENUMERIC):
+                # the batch's rule: a stalled BF16 inner operator is solved again with BF16X3
+                ctx.kp_set_option("op_auto_cond", 1.0)
+                x1.zero_()
+                info1 = ctx.tik_pcg(d["b"], lam1, TOL, 500, True, x1, check=False)
         assert lam1 == lam
+        assert info1.status == info.status
         assert info1.iters == info.iters
         assert rel(kpsvd.from_device(d["x"], P.n_r, P.n_c), kpsvd.from_device(x1, P.n_r, P.n_c)) < 1e-12
 

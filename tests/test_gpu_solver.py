@@ -93,22 +93,28 @@ def test_separable_zero_bc_converges_in_one_iteration(kpsvd):
 U32 = 2.0 ** -24
 
 
-@pytest.mark.parametrize("lam", [0.15, 0.03])
+@pytest.mark.parametrize("lam", [0.3, 0.15, 0.03])
 def test_fp32_path_fixed_iterations(kpsvd, lam):
     """256 x 256 workload, all-FP32 path (FP32 operator, preconditioner and
     vectors; reliable updates off): x after 10 iterations vs the FP64
     oracle's.  Two FP32 effects bound the difference: GEMM accumulation over
     K = r n terms (~ sqrt(K) u) and the rounding of r, whose white part M^-1
     amplifies by up to 1 / lam^2; bound 8 u (sqrt(r n) + 1 / lam^2)
-    (3.4e-5 at lam = 0.15, 5.5e-4 at lam = 0.03; numpy's FP32 BLAS shows the
-    same size of difference)."""
+    (1.9e-5 at lam = 0.3, 3.4e-5 at 0.15, 5.5e-4 at 0.03).  Where the
+    1 / lam^2 amplification is moderate (lam >= 0.15) the difference also
+    meets the stated 1e-5 of the all-FP32 path at a fixed iteration count
+    (numpy's FP32 BLAS gives 1.5e-6 / 5.7e-6 / 1.3e-4 at the three lambdas)."""
     pr = OracleProblem("deblur256_fp32")
     with setup_ctx(kpsvd, pr, "f32", "f32", "f32") as ctx:
         ctx.kp_set_option("reliable_delta", 0.0)
         x, info = run(kpsvd, ctx, pr, lam, 0.0, 10, True, "f32")
         xo, _ = opcg.tik_pcg(pr.op, pr.kp, pr.B, lam, 0.0, 10, True)
+        err = rel(x, xo)
         bound = 8 * U32 * (np.sqrt(pr.op.rank * pr.P.n_c) + 1.0 / lam ** 2)
-        assert rel(x, xo) < bound
+        print(f"lambda {lam}: all-FP32 x_10 vs FP64 oracle {err:.3e} (bound {bound:.2e})")
+        assert err < bound
+        if lam >= 0.15:
+            assert err < 1e-5
 
 
 @pytest.mark.parametrize("flexible", [False, True])
