@@ -214,7 +214,9 @@ kp_status kp_apply_Minv(kp_ctx* ctx, const void* r, void* z, double lambda);
  *   Vr       device, float, column-major n_c x n_c (right singular vectors of A_r^(1))
  *   sigma    device, double, column-major n_r x n_c KP spectrum
  *   r, z     device, float, column-major n_r x n_c, distinct
- *   cuda_stream  cudaStream_t the work is issued on (asynchronous)
+ *   cuda_stream  cudaStream_t the work is issued on (asynchronous); it must
+ *            belong to the current device (KP_EINVAL otherwise), since the
+ *            scratch address is looked up for the current device
  * Limits: n_r, n_c <= 512 (KP_EINVAL beyond).  The first call on a device
  * looks up the scratch address on that device (make it before any stream
  * capture).  All calls share the scratch array and it keeps the last call's
@@ -360,6 +362,22 @@ kp_status kp_mlp_forward(kp_mlp* mlp, const float* X, int batch, float* y);
 /* gradients (host, param_count floats; zero for mean / inv_std) and loss (host, nullable) */
 kp_status kp_mlp_gradients(kp_mlp* mlp, const float* X, const float* labels, int batch, float* grads, double* loss);
 kp_status kp_mlp_train_step(kp_mlp* mlp, const float* X, const float* labels, int batch, float lr, double* loss);
+
+/* Timing of the parts of one (F)PCG iteration (a benchmark hook): each part
+ * is launched `reps` times on the context's stream between CUDA events, on
+ * the context's own solver vectors (r = p = the last A^T b; the caller's
+ * data is not touched), and its average device time per launch goes to
+ * ms[k] (host, 4 doubles); launches (host, nullable, 4 long longs) receives
+ * the kernels per part:
+ *   [0] the K application q = (A^T A + lambda^2 I) p as the iteration runs it
+ *   [1] the preconditioner solve z = M^-1 r (eq. PreconSolve)
+ *   [2] the vector phase: x / r update with ||r||^2, z^T r (and z^T r_old),
+ *       beta, p = z + beta p
+ *   [3] one residual replacement A^T (b - A x) - lambda^2 x with the
+ *       accurate operator, and its norm
+ * Synchronises.  KP_ESTATE before kp_setup; KP_EINVAL for reps < 1, lambda
+ * <= 0 or ms NULL.  Meaningful after a tik_pcg on the context. */
+kp_status kp_time_parts(kp_ctx* ctx, double lambda, int reps, double* ms, long long* launches);
 
 /* Number of this library's kernel launches issued on the context since the
  * last reset (reset = 1 clears it after reading). */

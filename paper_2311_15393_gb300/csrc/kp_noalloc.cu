@@ -75,6 +75,15 @@ extern "C" kp_status kp_apply_Minv_noalloc(const float* Vc, const float* Vr, con
                  KP_NOALLOC_MAX_SIDE, KP_NOALLOC_MAX_SIDE);
     return KP_EINVAL;
   }
+  {  // the scratch address is per device: the stream must run on the current one
+    int cur = 0, sdev = 0;
+    KP_CUDA(cudaGetDevice(&cur));
+    KP_CUDA(cudaStreamGetDevice(static_cast<cudaStream_t>(cuda_stream), &sdev));
+    if (sdev != cur) {
+      kp_set_error("kp_apply_Minv_noalloc: the stream belongs to device %d, the current device is %d", sdev, cur);
+      return KP_EINVAL;
+    }
+  }
   float* scratch = nullptr;
   KP_TRY(scratch_address(&scratch));
   const long long N = (long long)n_r * n_c;
