@@ -59,6 +59,15 @@ __global__ void __launch_bounds__(THREADS) simt_gemm_kernel(SimtParams<T> p) {
           }
         }
         __syncthreads();
+        // blocked summation: each k-tile of BK products is summed on its own
+        // and then added to the running sum, so rounding errors grow with
+        // BK + K / BK additions instead of K (the blocked / pairwise
+        // summation argument of Section 4)
+        T part[TM][TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) part[i][j] = T(0);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
           T a[TM], b[TN];
@@ -69,8 +78,12 @@ __global__ void __launch_bounds__(THREADS) simt_gemm_kernel(SimtParams<T> p) {
 #pragma unroll
           for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < TN; ++j) part[i][j] = fma(a[i], b[j], part[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] += part[i][j];
         __syncthreads();
       }
     }
