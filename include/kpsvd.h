@@ -270,7 +270,11 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *   "tc_kblocks_per_stage" 1, 2 or 4 (4: 64-wide tiles only): k-blocks per
  *                     shared-memory ring stage (default 0 = 4 for 64-wide
  *                     tiles, 1 with two CTAs per SM, else 2)
- *                     The three tile options take effect at the next kp_setup.
+ *   "tc_pair"         0 (default): BF16 GEMMs whose 256 x 256 tiles fill most
+ *                     SM pairs run on CTA pairs (tcgen05 cta_group::2, one
+ *                     256 x 256 tile per pair of SMs); 1: never; 2: wherever
+ *                     the shape allows (N >= 256, per-term blocks of 256 rows)
+ *                     The tile options take effect at the next kp_setup.
  *   "pdl"             0: launch the iteration's kernels without programmatic
  *                     dependent launch (default 1: each kernel's launch and
  *                     prologue overlap the tail of the previous one)

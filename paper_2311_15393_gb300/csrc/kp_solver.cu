@@ -477,3 +477,95 @@ extern "C" kp_status kp_forward(kp_ctx* ctx, const void* x, const void* g, doubl
   if (noise_norm) *noise_norm = scale * std::sqrt(h[1]);
   return kp_leave(ctx);
 }
+
+// ---------------------------------------------------------------- per-part timing
+// The parts of one (F)PCG iteration launched `reps` times each on the
+// context's stream between CUDA events, on the context's own solver vectors
+// (the caller's data is not touched): [0] the K application as the iteration
+// runs it (bf16 slices of p ready, p^T q and alpha fused where the iteration
+// fuses them), [1] the preconditioner solve (narrow input made by the x / r
+// update where the iteration folds it), [2] the vector phase (x / r update,
+// z^T r / beta, p update), [3] one residual replacement (true residual with
+// the accurate operator, its norm).  No pause flag is passed, so every kernel
+// does its full work whatever the scalars hold.
+extern "C" kp_status kp_time_parts(kp_ctx* ctx, double lambda, int reps, double* ms, long long* launches) {
+  KP_TRY(kp_check_ready(ctx));
+  if (!ms || reps < 1 || !(lambda > 0.0)) {
+    kp_set_error("kp_time_parts: need ms (4 doubles), reps >= 1 and lambda > 0");
+    return KP_EINVAL;
+  }
+  KP_TRY(kp_enter(ctx));
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  const bool f64 = ctx->vec_prec == KP_F64;
+  const size_t vs = f64 ? 8 : 4;
+  const double lam2 = lambda * lambda;
+  const SolveBufs B = bufs(ctx);
+  void* x = ctx->tmp_img;
+  cudaStream_t st = ctx->stream;
+  // contents: r = p = the last right-hand side A^T b, the other vectors zero
+  for (void* v : {B.r_old, B.q, B.z, x}) KP_CUDA(cudaMemsetAsync(v, 0, vs * N, st));
+  KP_TRY(copy_vec(ctx, B.rhs, B.r, N, f64));
+  KP_TRY(copy_vec(ctx, B.rhs, B.p, N, f64));
+  if (op_inner_slices(ctx) > 0)
+    KP_TRY(split_bf16(ctx, B.p, false, N, ctx->w_img2, op_inner_slices(ctx), N));
+  KP_TRY(norm_amax_dev(ctx, B.r, N, f64, ctx->dscal + S_RR));
+  const bool folded = cg_fusable(ctx);
+  double* s = ctx->dscal;
+  PostOp pa;
+  pa.kind = POST_ALPHA;
+  pa.s = s;
+  pa.f = ctx->dflags;
+  PostOp pc = pa;
+  pc.kind = POST_CHECK;
+  pc.hist = ctx->hist;
+  pc.hist_cap = ctx->hist_cap;
+  PostOp pb = pa;
+  pb.kind = POST_BETA;
+  const int sl = op_inner_slices(ctx);
+  const int nt = ctx->pc_prec == KP_BF16 ? NT_BF16 : NT_F16;
+  auto part = [&](int k) -> kp_status {
+    if (k == 0) {
+      bool fused = false;
+      return op_apply_K(ctx, B.p, B.q, lam2, sl > 0, nullptr, s + (folded ? S_QPQ : S_PQ), &pa, &fused, folded);
+    }
+    if (k == 1) return pc_apply(ctx, B.r, B.z, lam2, s + S_RR, nullptr, folded);
+    if (k == 2) {
+      if (folded)
+        KP_TRY(update_xr_q_dev(ctx, x, B.r, B.r_old, B.p, B.q, N, s + S_ALPHA, s + S_RR, s + S_QMAX, nt, lam2,
+                               ctx->pc_in, cg_inv_slot(ctx), nullptr, pc));
+      else
+        KP_TRY(update_xr_dev(ctx, x, B.r, B.r_old, B.p, B.q, N, f64, s + S_ALPHA, s + S_RR, nullptr, pc));
+      KP_TRY(dot2_dev(ctx, B.z, B.r, B.r_old, N, f64, s + S_ZRNEW, nullptr, pb));
+      return p_update_dev(ctx, B.p, B.z, N, f64, s + S_BETA, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N,
+                          nullptr);
+    }
+    KP_TRY(op_true_residual(ctx, B.rhs, x, B.r, lam2, nullptr));
+    return norm_amax_dev(ctx, B.r, N, f64, s + S_RR);
+  };
+  cudaEvent_t e0, e1;
+  KP_CUDA(cudaEventCreate(&e0));
+  KP_CUDA(cudaEventCreate(&e1));
+  kp_status res = KP_OK;
+  for (int k = 0; k < 4 && res == KP_OK; ++k) {
+    for (int w = 0; w < 2 && res == KP_OK; ++w) res = part(k);
+    if (res != KP_OK) break;
+    const long long l0 = ctx->launches;
+    cudaEventRecord(e0, st);
+    for (int i = 0; i < reps && res == KP_OK; ++i) res = part(k);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      kp_set_error("kp_time_parts: %s", cudaGetErrorString(cudaGetLastError()));
+      res = KP_ECUDA;
+      break;
+    }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    ms[k] = t / reps;
+    if (launches) launches[k] = (ctx->launches - l0) / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  KP_TRY(res);
+  KP_TRY(read_status(ctx));
+  return kp_leave(ctx);
+}

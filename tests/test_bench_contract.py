@@ -1,5 +1,6 @@
 """bench.py on the CPU: the reference arm (the FP64 oracle timed on the host
-cores) prints one JSON line with the keys and units of the GPU arm's line,
+cores, a measured bounded sample per step and its extrapolation to the
+whole step) prints one JSON line with the keys and units of the GPU arm's line,
 and the GPU arm fails loudly, printing no number, where no GPU exists."""
 import json
 import os
@@ -27,7 +28,12 @@ def test_reference_arm_prints_one_contract_line():
     import bench
     assert d["metric"] == bench.METRIC and d["unit"] == "solves/s"
     assert d["value"] > 0 and d["ms_per_step"] > 0
-    assert d["value"] == pytest.approx(2000.0 / d["ms_per_step"])      # two solves per step
+    # ms_per_step is the measured bounded sample; the solves/s value is its
+    # extrapolation to the whole step (two solves), reported apart
+    ex = d["extrapolation"]
+    assert ex["measured_ms_per_sample"] == pytest.approx(d["ms_per_step"])
+    assert d["value"] == pytest.approx(2000.0 / ex["est_ms_per_full_step"])
+    assert len(ex["oracle_iterations"]) == 2 and min(ex["oracle_iterations"]) >= 1
     assert (d["n_gpus"], d["steps"], d["warmup"]) == (1, 2, 1)
     assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
     assert d["dtype"] == "f64" and d["data"] == "synthetic"
