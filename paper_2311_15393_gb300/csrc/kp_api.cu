@@ -181,6 +181,8 @@ extern "C" void kp_destroy(kp_ctx* ctx) {
   kp_free_all(ctx);
   kp_pool_release(ctx);
   if (ctx->hmirror) cudaFreeHost(ctx->hmirror);
+  for (auto& e : ctx->ev_setup)
+    if (e) cudaEventDestroy(e);
   for (auto& e : ctx->ev_blk)
     if (e) cudaEventDestroy(e);
   if (ctx->ctx_block) cudaFree(ctx->ctx_block);
@@ -247,6 +249,14 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
     ctx->tc_kps_override = (int)value;
   } else if (!strcmp(name, "tc_ctas_per_sm")) {
     ctx->tc_cps_override = (int)value;
+  } else if (!strcmp(name, "pc_inner_iters")) {
+    if (!(value >= 1.0 && value <= 64.0)) {
+      kp_set_error("pc_inner_iters must be in [1, 64]");
+      return KP_EINVAL;
+    }
+    ctx->pc_inner_iters = (int)value;
+  } else if (!strcmp(name, "tc_pair")) {
+    ctx->tc_pair_override = (int)value;
   } else if (!strcmp(name, "setup_fp64")) {
     ctx->force_setup_fp64 = value != 0.0;
   } else {

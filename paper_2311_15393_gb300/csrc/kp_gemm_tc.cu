@@ -617,6 +617,322 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
   }
 }
 
+// ------------------------------------------------------------- CTA-pair kernel
+// The same GEMM on 256 x 256 output tiles computed by a pair of CTAs on two
+// SMs (a cluster of 2) with tcgen05.mma.cta_group::2: the MMA of M = 256,
+// N = 256 reads 128 rows of A and 128 rows of B from each CTA's shared
+// memory and leaves 128 rows x 256 columns of the accumulator in each CTA's
+// TMEM.  Each SM then stages 32 KB per 64-wide k-block for 256 x 128 x 64
+// MACs of its own accumulator rows, two thirds of the 48 KB a one-CTA
+// 128 x 256 tile needs for the same work; the L2 -> shared-memory stream
+// is what limits the one-CTA tiles here.
+//   rank 0 (leader): lane 0 of warp 0 arms the stage's full barrier with the
+//     bytes of both CTAs' loads; lane 0 of warp 1 issues the MMAs and commits
+//     them to both CTAs' empty / accumulator-full barriers (multicast)
+//   both ranks: warp 0 loads this CTA's halves of A and B (TMA, completion
+//     counted on the leader's full barrier); warps 2..5 read this CTA's TMEM
+//     rows and arrive on the leader's accumulator-empty barrier
+// Every wait is bounded by a time limit; all paths end at a cluster barrier
+// before TMEM is freed, so neither CTA leaves while the other may still
+// signal its barriers.
+constexpr int PAIR_M = 256, PAIR_N = 256;
+constexpr unsigned long long KP_WAIT_NS = 500000000ull;  // 0.5 s per wait
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local_shared, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_shared), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait bounded by a time limit; false (and the status word flagged) on give-up
+__device__ __forceinline__ bool mbar_wait_t(uint32_t bar, uint32_t parity, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned int i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 0u && global_ns() - t0 > KP_WAIT_NS) {
+      atomicOr(status, DEV_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                                 uint32_t leader_bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(leader_bar)
+      : "memory");
+}
+template <int KIND>
+__device__ __forceinline__ void mma_issue_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accum) {
+  if constexpr (KIND == TC_E4M3) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+// arrive (once) on the barrier at this address in both CTAs of the pair when
+// the MMAs issued so far have completed
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"((unsigned short)3)
+      : "memory");
+}
+
+template <int KPS>
+struct PairCfg {
+  static constexpr int A_BYTES = 128 * 128;  // this CTA's 128 rows of A, one 128-byte k-block row each
+  static constexpr int B_BYTES = 128 * 128;  // this CTA's 128 rows (of 256) of B
+  static constexpr int KB_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGE = KPS * KB_BYTES;
+  static constexpr int STAGES = 196608 / STAGE;
+  // + 16 KB of slack past the last B tile: shared-memory reads of the MMA
+  // stay inside the allocation even if they extend past a 128-row B tile
+  static constexpr int SLACK = 16384;
+  static constexpr int SMEM = STAGES * STAGE + SLACK + 1024 + 512;
+  static constexpr int TMEM_COLS = 2 * PAIR_N;
+  static_assert(STAGES >= 2, "ring too shallow");
+};
+
+struct PairUnit {
+  int m0, n0;
+};
+__device__ __forceinline__ PairUnit decode_pair(const TcParams& p, int u) {
+  PairUnit r;
+  r.m0 = (u / p.tiles_n) * PAIR_M;
+  r.n0 = (u % p.tiles_n) * PAIR_N;
+  return r;
+}
+
+template <int KIND, int KPS>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+  using C = PairCfg<KPS>;
+  if (threadIdx.x == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE + C::SLACK);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + C::STAGES;
+  uint64_t* tfull = bars + 2 * C::STAGES;  // [2]
+  uint64_t* tempty = tfull + 2;            // [2]
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 8);  // 4 epilogue warps in each CTA (the leader's is used)
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // barriers of both CTAs initialised before any remote signal
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ksh = KIND == TC_E4M3 ? 0 : 1;
+  const int nk = p.batch_rows ? 1 : p.nkron;
+  bool skip = false;
+  if (warp == 0 && lane < 2 * KPS) {
+    // ---------------- TMA producer of this CTA's halves
+    const bool isB = lane & 1;
+    const int q = lane >> 1;
+    const CUtensorMap* map = isB ? &tmB : &tmA;
+    const unsigned mask = (1u << (2 * KPS)) - 1u;
+    auto load = [&](const PairUnit& w, int j, int s, bool a_side) {
+      const int nkb = min(KPS, p.steps_total - j * KPS);
+      if (q >= nkb || isB == a_side) return;
+      const int tb = p.batch_rows ? w.m0 / p.batch_rows : 0;
+      const int row0 = isB ? w.n0 + 128 * (int)rank : w.m0 + 128 * (int)rank - tb * p.batch_rows;
+      const int stp = j * KPS + q;
+      const int kb = stp % p.kblocks;
+      const int rest = stp / p.kblocks;
+      const int k = rest % nk, pr = rest / nk;
+      const int term = (isB ? p.sb[pr] * p.b_terms : p.sa[pr] * p.a_terms) + (p.batch_rows ? tb : k);
+      const uint32_t dst = smem_u32(smem + s * C::STAGE + q * C::KB_BYTES) + (isB ? (uint32_t)C::A_BYTES : 0u);
+      tma_load_3d_pair(dst, map, (kb * 128) >> ksh, row0, term, peer_addr(smem_u32(&full[s]), 0));
+    };
+    auto arm = [&](int j, int s) {  // leader: both CTAs' bytes of stage j
+      const int nkb = min(KPS, p.steps_total - j * KPS);
+      mbar_expect_tx(smem_u32(&full[s]), (uint32_t)(2 * nkb * C::KB_BYTES));
+    };
+    int npre = 0;
+    PairUnit w0;
+    const int nstages = (p.steps_total + KPS - 1) / KPS;
+    if (cl < p.units) {
+      w0 = decode_pair(p, cl);
+      npre = min(C::STAGES, nstages);
+      for (int j = 0; j < npre; ++j) {
+        if (leader && lane == 0) arm(j, j);
+        __syncwarp(mask);
+        load(w0, j, j, true);
+      }
+    }
+    KP_PDL_WAIT();
+    KP_PDL_TRIGGER();
+    skip = p.flags && *(volatile const int*)p.flags;
+    for (int j = 0; j < npre; ++j) load(w0, j, j, false);
+    if (skip) {
+      if (leader && lane == 0)  // every prefetched stage lands before the pair leaves
+        for (int j = 0; j < npre; ++j) mbar_wait_t(smem_u32(&full[j]), 0, p.status);
+    } else {
+      int it = npre;
+      bool run = true;
+      for (int u = cl; run && u < p.units && !*(volatile int*)&s_abort; u += ncl) {
+        const PairUnit w = decode_pair(p, u);
+        for (int j = u == cl ? npre : 0; j < nstages; ++j, ++it) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (it / C::STAGES) & 1;
+          int okw = 1;
+          if (lane == 0) {
+            okw = mbar_wait_t(smem_u32(&empty[s]), ph ^ 1, p.status) ? 1 : 0;
+            if (okw && leader) arm(j, s);
+          }
+          okw = __shfl_sync(mask, okw, 0);
+          if (!okw) {
+            if (lane == 0) s_abort = 1;
+            run = false;
+            break;
+          }
+          load(w, j, s, true);
+          load(w, j, s, false);
+        }
+      }
+    }
+  } else {
+    KP_PDL_WAIT();
+    KP_PDL_TRIGGER();
+    skip = p.flags && *(volatile const int*)p.flags;
+  }
+
+  if (skip || warp == 0) {
+  } else if (warp == 1) {
+    if (leader && lane == 0) {
+      // ---------------- MMA issuer (leader CTA only)
+      const int nstages = (p.steps_total + KPS - 1) / KPS;
+      int it = 0, i = 0;
+      for (int u = cl; u < p.units; u += ncl, ++i) {
+        const int buf = i & 1;
+        if (*(volatile int*)&s_abort || !mbar_wait_t(smem_u32(&tempty[buf]), ((i >> 1) & 1) ^ 1, p.status)) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * PAIR_N);
+        bool ok = true;
+        for (int j = 0; j < nstages; ++j, ++it) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (it / C::STAGES) & 1;
+          if (*(volatile int*)&s_abort || !mbar_wait_t(smem_u32(&full[s]), ph, p.status)) {
+            s_abort = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int nkb = min(KPS, p.steps_total - j * KPS);
+#pragma unroll
+          for (int q = 0; q < KPS; ++q) {
+            if (q < nkb) {
+              const uint32_t a0 = smem_u32(smem + s * C::STAGE + q * C::KB_BYTES);
+              const uint32_t b0 = a0 + C::A_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                mma_issue_pair<KIND>(d, make_sdesc(a0 + kk * 32), make_sdesc(b0 + kk * 32), p.idesc,
+                                     (j > 0 || q > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit_pair(smem_u32(&empty[s]));
+        }
+        mma_commit_pair(smem_u32(&tfull[buf]));
+        if (!ok) break;
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 2..5: this CTA's 128 accumulator rows
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const float sdev = p.alpha_dev ? *p.alpha_dev : 1.f;
+    int i = 0;
+    for (int u = cl; u < p.units; u += ncl, ++i) {
+      const PairUnit w = decode_pair(p, u);
+      const int buf = i & 1;
+      if (!mbar_wait_t(smem_u32(&tfull[buf]), (i >> 1) & 1, p.status)) break;
+      tc_fence_after();
+      const int gm = w.m0 + 128 * (int)rank + row;
+      const bool row_ok = gm < p.M;
+      float tmax = 0.f;
+#pragma unroll 1
+      for (int chunk = 0; chunk < PAIR_N / 32; ++chunk) {
+        float acc[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * PAIR_N + chunk * 32), acc);
+        const int gn0 = w.n0 + chunk * 32;
+        if (row_ok && gn0 < p.N) epi_store32(p.epi, sdev, gm, gn0, p.N, acc, tmax);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_remote(peer_addr(smem_u32(&tempty[buf]), 0));
+      if (p.epi.amax_bits) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        if (lane == 0 && tmax > 0.f) atomicMax(p.epi.amax_bits, __float_as_uint(tmax));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // both CTAs are done with TMEM and with each other's barriers
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- host side
@@ -627,6 +943,7 @@ struct TcGemmPlan {
   int bn;
   int cps;
   int kps;
+  bool pair;  // 256 x 256 tiles on CTA pairs (tc_gemm_pair_kernel)
   dim3 grid;
 };
 
@@ -678,7 +995,7 @@ static kp_status make_map(CUtensorMap* map, const GemmOp& op, int kind, int box_
   return KP_OK;
 }
 
-static uint32_t make_idesc(int kind, int bn) {
+static uint32_t make_idesc(int kind, int bn, int bm) {
   uint32_t d = 0;
   d |= 1u << 4;  // D format F32
   if (kind == TC_BF16) {
@@ -687,7 +1004,7 @@ static uint32_t make_idesc(int kind, int bn) {
   }                 // F16 / E4M3: format code 0
   // K-major A and B (bits 15, 16 = 0)
   d |= (uint32_t)(bn >> 3) << 17;
-  d |= (uint32_t)(TBM >> 4) << 24;
+  d |= (uint32_t)(bm >> 4) << 24;
   return d;
 }
 
@@ -735,9 +1052,22 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
     splits = 1;
     if (2 * tiles_bn < sms) splits = std::max(1, std::min({4, sms / tiles_bn, steps_all / 16}));
   }
+  // CTA pairs (256 x 256 tiles, cta_group::2) for BF16 GEMMs without a K
+  // split whose pair tiles fill most SM pairs; option tc_pair: 1 = never,
+  // 2 = whenever the shape allows
+  const int pair_tiles = ((g.M + PAIR_M - 1) / PAIR_M) * ((g.N + PAIR_N - 1) / PAIR_N);
+  const bool pair_ok = kind == TC_BF16 && splits == 1 && g.N >= PAIR_N &&
+                       (g.batch_rows == 0 || g.batch_rows % PAIR_M == 0) && g.M >= PAIR_M;
+  const bool pair = pair_ok && ctx->tc_pair_override != 1 &&
+                    (ctx->tc_pair_override == 2 || (ctx->tc_bn_override == 0 && 4 * pair_tiles >= 3 * (sms / 2)));
   TcGemmPlan* pl = new TcGemmPlan();
+  pl->pair = pair;
+  if (pair) {
+    splits = 1;
+    bn = PAIR_N;
+  }
   kp_status st = make_map(&pl->mapA, g.A, kind, TBM);
-  if (st == KP_OK) st = make_map(&pl->mapB, g.B, kind, bn);
+  if (st == KP_OK) st = make_map(&pl->mapB, g.B, kind, pair ? PAIR_N / 2 : bn);
   if (st != KP_OK) {
     delete pl;
     return st;
@@ -758,13 +1088,13 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
   p.kblocks = (g.K + bk - 1) / bk;
   p.batch_rows = g.batch_rows;
   p.steps_total = g.npairs * (g.batch_rows > 0 ? 1 : g.nkron) * p.kblocks;
-  p.tiles_m = (g.M + TBM - 1) / TBM;
+  p.tiles_m = pair ? (g.M + PAIR_M - 1) / PAIR_M : (g.M + TBM - 1) / TBM;
   p.tiles_n = (g.N + bn - 1) / bn;
   const int tiles = p.tiles_m * p.tiles_n;
   splits = std::min(splits, p.steps_total);
   p.splits = splits;
   p.units = tiles * splits;
-  p.idesc = make_idesc(kind, bn);
+  p.idesc = make_idesc(kind, bn, pair ? PAIR_M : TBM);
   p.epi = g.epi;
   if (p.epi.ld_aux == 0) p.epi.ld_aux = p.epi.ldd;
   p.ws = ctx->w_split;
@@ -796,6 +1126,10 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
       (ctx->tc_kps_override == 4 && bn == 64))
     pl->kps = ctx->tc_kps_override;
   pl->grid = dim3(std::min(p.units, ctx->sm_count * cps), 1, 1);
+  if (pair) {
+    pl->kps = (ctx->tc_kps_override == 1) ? 1 : 2;
+    pl->grid = dim3(2 * std::min(p.units, ctx->sm_count / 2), 1, 1);
+  }
   ctx->tc_plans.push_back(pl);
   *out = pl;
   return KP_OK;
@@ -826,8 +1160,29 @@ static kp_status launch_kind(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
   return KP_OK;
 }
 
+template <int KIND, int KPS>
+static kp_status launch_pair(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
+  using C = PairCfg<KPS>;
+  static std::atomic<bool> attr_set{false};
+  if (!attr_set.load()) {
+    KP_CUDA(cudaFuncSetAttribute(tc_gemm_pair_kernel<KIND, KPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    attr_set = true;
+  }
+  KP_CUDA(kp_launch(ctx, tc_gemm_pair_kernel<KIND, KPS>, pl->grid, dim3(TC_THREADS), C::SMEM, pl->mapA, pl->mapB, p));
+  KP_LAUNCHED(ctx);
+  return KP_OK;
+}
+
 template <int KIND>
 static kp_status launch_cfg(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
+  if (pl->pair) {
+    if constexpr (KIND == TC_BF16) {
+      return pl->kps == 1 ? launch_pair<KIND, 1>(ctx, pl, p) : launch_pair<KIND, 2>(ctx, pl, p);
+    } else {
+      kp_set_error("tensor-core GEMM: CTA-pair tiles are built for BF16 only");
+      return KP_ENOTSUP;
+    }
+  }
   if (pl->bn == 256) return pl->kps == 2 ? launch_kind<KIND, 256, 1, 2>(ctx, pl, p) : launch_kind<KIND, 256, 1, 1>(ctx, pl, p);
   if (pl->bn == 64) {
     if (pl->kps == 4) return launch_kind<KIND, 64, 1, 4>(ctx, pl, p);

@@ -123,6 +123,8 @@ struct kp_ctx {
   // problem
   bool ready = false;
   int n_r = 0, n_c = 0, c_r = 0, c_c = 0, rank = 0;
+  int pc_rank = 1;          // Kronecker terms behind the preconditioner (1: the KP-SVD solve)
+  int pc_inner_iters = 2;   // inner PCG steps of a multi-term preconditioner
   kp_bc bc = KP_BC_ZERO;
   kp_prec op_prec = KP_F64, pc_prec = KP_F64, vec_prec = KP_F64;
   kp_prec op_prec_setup = KP_F64;  // op_prec given to kp_setup (op_prec may be raised per solve)
@@ -140,10 +142,13 @@ struct kp_ctx {
   bool pdl = true;           // programmatic dependent launch in the iteration
   void* hmirror = nullptr;   // pinned host copies of the solver flags / scalars (2 slots)
   cudaEvent_t ev_blk[2] = {nullptr, nullptr};
+  cudaEvent_t ev_setup[2] = {nullptr, nullptr};  // timing of kp_setup
+  double last_setup_ms = 0.0;                     // device time of the last kp_setup
   int splitk_override = 0;  // > 0: fixed split-K factor for the square GEMMs
   int tc_bn_override = 0;   // 128 / 256: fixed tensor-core tile width
   int tc_cps_override = 0;  // 1 / 2: fixed CTAs per SM for 128-wide tiles
   int tc_kps_override = 0;  // 1 / 2: fixed k-blocks per ring stage
+  int tc_pair_override = 0;  // 1: no CTA-pair tiles; 2: CTA-pair tiles wherever the shape allows
 
   // device allocations: ctx_block lives with the context, allocs with the
   // problem; a new kp_setup returns the previous problem's blocks to `pool`,
@@ -205,6 +210,7 @@ struct kp_ctx {
   void* pc_t3 = nullptr;     // P3 out
   float* pc_f32 = nullptr;   // FP32 staging for E4M3 dynamic scaling
   void* vbuf[10] = {nullptr};  // solver vectors (vec type)
+  void* pc_inner[5] = {nullptr};  // multi-term preconditioner's inner r, r_old, p, q, z
   void* tmp_img = nullptr;   // vec-type scratch image
   void* tmp_img2 = nullptr;
 
