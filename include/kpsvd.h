@@ -90,6 +90,7 @@ typedef struct {
   double rel_res;        /* ||r|| / ||A^T b|| of the residual the solver ended with */
   kp_status status;      /* same as the return value of tik_pcg */
   double ms_solve;       /* device time of the solve (CUDA events) */
+  double ms_setup;       /* device time of the context's last kp_setup (CUDA events) */
   double* res_hist;      /* optional caller-owned host buffer of res_hist_len doubles: */
   int res_hist_len;      /*   ||r_k|| / ||A^T b|| for k = 0 .. min(iters, len - 1) */
 } kp_solve_info;
@@ -110,6 +111,14 @@ void kp_destroy(kp_ctx* ctx);
  *   op_rank  number of Kronecker terms of A (eq. KronSumDecomp), from the
  *            SVD of the weighted PSF D_c P D_r (Frobenius-optimal first term);
  *            0 = full rank min(n_r, n_c)
+ *   pc_rank  Kronecker terms behind the preconditioner, 1 .. op_rank.  1: the
+ *            KP-SVD preconditioner M = V (Sigma^2 + lambda^2 I) V^T of the
+ *            first term (eqs. PreconSystem, PreconSolve).  k > 1 (Section
+ *            5.3 finds the one-term M weak for blurs with many terms):
+ *            z ~ (M_k^T M_k + lambda^2 I)^-1 r, M_k the first k terms of A,
+ *            by "pc_inner_iters" (default 2) PCG steps on that system from
+ *            z = 0, preconditioned by the one-term KP-SVD solve; it varies
+ *            with r, so use it with flexible = 1 in tik_pcg
  *   op_prec  KP_F64 | KP_F32 | KP_BF16 | KP_BF16X3
  *   pc_prec  KP_F64 | KP_F32 | KP_BF16 | KP_F16 | KP_E4M3 (rank-1 KP-SVD preconditioner)
  *   vec_prec KP_F64 | KP_F32: element type of images and of the PCG vectors
@@ -123,7 +132,8 @@ void kp_destroy(kp_ctx* ctx);
  * the stored Sigma stay FP64; option "setup_fp64" restores FP64).  May be
  * called again on the same context to replace the problem.  Errors:
  * KP_EINVAL for a NULL or unaligned psf, n_r or n_c < 2, a centre outside the
- * grid, op_rank outside [0, min(n_r, n_c)], an unknown bc or sigma, or an
+ * grid, op_rank outside [0, min(n_r, n_c)], pc_rank outside [1, op_rank], an
+ * unknown bc or sigma, or an
  * unsupported precision combination; KP_ENOTSUP when tensor-core precisions
  * meet a device other than sm_103 or sizes not multiples of 16.  These
  * checks run first and leave the context's previous problem in place.  A
@@ -132,7 +142,7 @@ void kp_destroy(kp_ctx* ctx);
  * or Inf, KP_EINVAL for an all-zero PSF, KP_ENOMEM, KP_ECUDA.
  * Synchronises. */
 kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, int center_r, int center_c,
-                   kp_bc bc, int op_rank, kp_prec op_prec, kp_prec pc_prec, kp_prec vec_prec,
+                   kp_bc bc, int op_rank, int pc_rank, kp_prec op_prec, kp_prec pc_prec, kp_prec vec_prec,
                    kp_sigma sigma);
 
 /* Observed data (eq. invp, Section 5 noise level): b = A x + e with
@@ -278,6 +288,8 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *   "pdl"             0: launch the iteration's kernels without programmatic
  *                     dependent launch (default 1: each kernel's launch and
  *                     prologue overlap the tail of the previous one)
+ *   "pc_inner_iters"  1 .. 64 (default 2): inner PCG steps of a preconditioner
+ *                     with pc_rank > 1
  *   "setup_fp64"      nonzero: keep the O(n^3) products of kp_setup and of
  *                     choose_lambda's spectral coefficients, the Jacobi
  *                     rotations and the PSF subspace iteration in FP64 also

@@ -59,7 +59,7 @@ void run_worker(int device, kp_problem* probs, const std::vector<int>& order, st
     kp_problem& p = probs[i];
     kp_status s = cs;
     if (s == KP_OK)
-      s = kp_setup(ctx, p.psf, p.n_r, p.n_c, p.center_r, p.center_c, p.bc, p.op_rank, o.op_prec, o.pc_prec,
+      s = kp_setup(ctx, p.psf, p.n_r, p.n_c, p.center_r, p.center_c, p.bc, p.op_rank, 1, o.op_prec, o.pc_prec,
                    o.vec_prec, o.sigma);
     double lam = p.lambda;
     if (s == KP_OK && !(lam > 0.0)) s = choose_lambda(ctx, p.b, o.method, p.lambda_param, nullptr, &lam);

@@ -28,6 +28,7 @@ namespace {
 struct OpsState {
   TcGemmPlan* G[2][4] = {{nullptr}};  // [mode][gemm]
   TcGemmPlan* Gin[2][4] = {{nullptr}};  // inner-operator plans per variant: [0] BF16 pair, [1] BF16X3 pairs
+  TcGemmPlan* Gk[4] = {nullptr};      // inner operator of the first pc_rank terms (multi-term preconditioner)
   bool batched = false;               // G2 / G4 write per-term outputs, summed by k_term_reduce
   TcGemmPlan* P[4] = {nullptr};
   float* inv_slot = nullptr;          // device scale for P4
@@ -80,20 +81,23 @@ static void pairs_for(kp_ctx* ctx, int mode, GemmDesc& g) {
 // (tile, split) units to fill the GPU
 static int square_splits(kp_ctx* ctx) { return ctx->splitk_override > 0 ? ctx->splitk_override : 0; }
 
-// GEMM descriptors of the operator: which = 0..3 (G1..G4)
-static GemmDesc op_desc(kp_ctx* ctx, int which, int mode, const void* bptr) {
+// GEMM descriptors of the operator: which = 0..3 (G1..G4), over the first
+// `terms` Kronecker terms (the full operator: terms = rank; the factor
+// blocks stay laid out for all rank terms)
+static GemmDesc op_desc(kp_ctx* ctx, int which, int mode, const void* bptr, int terms = 0) {
   const int n_r = ctx->n_r, n_c = ctx->n_c, r = ctx->rank;
+  const int t = terms > 0 ? terms : r;
   const long long N = (long long)n_r * n_c;
   GemmDesc g;
   pairs_for(ctx, mode, g);
   const int slices = op_is_tc(ctx) ? 3 : 1;
   if (which == 0 || which == 2) {  // G1 / G3: stacked factors x image
-    g.M = r * n_r;
+    g.M = t * n_r;
     g.N = n_c;
     g.K = n_r;
     g.nkron = 1;
     g.A.ptr = which == 0 ? ctx->opAc : ctx->opAcT;
-    g.A.rows = r * n_r;
+    g.A.rows = t * n_r;
     g.A.K = n_r;
     g.A.ld = n_r;
     g.A.tstride = (long long)r * n_r * n_r;
@@ -110,7 +114,7 @@ static GemmDesc op_desc(kp_ctx* ctx, int which, int mode, const void* bptr) {
     g.M = n_c;
     g.N = n_r;
     g.K = n_c;
-    g.nkron = r;
+    g.nkron = t;
     g.A.ptr = which == 1 ? ctx->opAr : ctx->opArT;
     g.A.rows = n_c;
     g.A.K = n_c;
@@ -278,13 +282,14 @@ __global__ void __launch_bounds__(VEC_THREADS)
 }
 
 // tensor-core plan of GEMM w of the operator in `mode` for the current pairs
-static kp_status op_plan(kp_ctx* ctx, OpsState* os, int mode, int w, TcGemmPlan** out) {
+static kp_status op_plan(kp_ctx* ctx, OpsState* os, int mode, int w, TcGemmPlan** out, int terms = 0) {
   const void* bptr = w == 0 ? (mode == OP_INNER ? ctx->w_img2 : ctx->w_img3) : (w == 2 ? ctx->w_img : nullptr);
-  GemmDesc g = op_desc(ctx, w, mode, bptr);
+  const int t = terms > 0 ? terms : ctx->rank;
+  GemmDesc g = op_desc(ctx, w, mode, bptr, t);
   int splits = (w == 1 || w == 3) ? square_splits(ctx) : 1;
   if ((w == 1 || w == 3) && os->batched) {
     g.batch_rows = ctx->n_c;
-    g.M = ctx->rank * ctx->n_c;
+    g.M = t * ctx->n_c;
     splits = 1;
   }
   return tc_plan_create(ctx, g, TC_BF16, splits, out);
@@ -365,7 +370,11 @@ kp_status ops_prepare(kp_ctx* ctx) {
     for (int mode = 0; mode < 2; ++mode)
       for (int w = 0; w < 4; ++w) KP_TRY(op_plan(ctx, os, mode, w, &os->G[mode][w]));
     for (int w = 0; w < 4; ++w) os->Gin[ctx->op_prec == KP_BF16X3 ? 1 : 0][w] = os->G[OP_INNER][w];
+    if (ctx->pc_rank > 1 && ctx->pc_rank < r)
+      for (int w = 0; w < 4; ++w) KP_TRY(op_plan(ctx, os, OP_INNER, w, &os->Gk[w], ctx->pc_rank));
   }
+  if (ctx->pc_rank > 1)  // inner solve of the multi-term preconditioner: r, r_old, p, q, z
+    for (int i = 0; i < 5; ++i) KP_TRY(kp_alloc(ctx, &ctx->pc_inner[i], vs * N));
   if (pc_is_tc(ctx)) {
     const int kind = ctx->pc_prec == KP_BF16 ? TC_BF16 : (ctx->pc_prec == KP_F16 ? TC_F16 : TC_E4M3);
     for (int w = 0; w < 4; ++w) {
@@ -378,8 +387,8 @@ kp_status ops_prepare(kp_ctx* ctx) {
 
 // ------------------------------------------------------------- operator
 template <typename T>
-static kp_status simt_op(kp_ctx* ctx, int which, const void* bptr, EpiParams e, const int* flags) {
-  GemmDesc g = op_desc(ctx, which, OP_INNER, bptr);
+static kp_status simt_op(kp_ctx* ctx, int which, const void* bptr, EpiParams e, const int* flags, int terms) {
+  GemmDesc g = op_desc(ctx, which, OP_INNER, bptr, terms);
   g.npairs = 1;
   g.sa[0] = g.sb[0] = 0;
   e.mode = EPI_T;
@@ -389,11 +398,16 @@ static kp_status simt_op(kp_ctx* ctx, int which, const void* bptr, EpiParams e, 
 }
 
 static kp_status run_op(kp_ctx* ctx, int which, int mode, const void* bptr, const EpiParams& e, const int* flags,
-                        const TermDot* td = nullptr, bool* dot_done = nullptr) {
+                        const TermDot* td = nullptr, bool* dot_done = nullptr, int terms = 0) {
   if (dot_done) *dot_done = false;
+  const int nterm = terms > 0 ? terms : ctx->rank;
   if (op_is_tc(ctx)) {
     OpsState* os = ops(ctx);
-    TcGemmPlan* pl = os->G[mode][which];
+    TcGemmPlan* pl = (nterm < ctx->rank && mode == OP_INNER) ? os->Gk[which] : os->G[mode][which];
+    if (!pl) {
+      kp_set_error("operator: no plan for %d terms", nterm);
+      return KP_ESTATE;
+    }
     tc_plan_set_runtime(pl, nullptr, flags);
     if (!(os->batched && (which == 1 || which == 3))) return tc_plan_run(ctx, pl, &e);
     // per-term FP32 outputs into the split workspace, then the term sum
@@ -410,14 +424,14 @@ static kp_status run_op(kp_ctx* ctx, int which, int mode, const void* bptr, cons
       t = *td;
       if (dot_done) *dot_done = true;
     }
-    KP_CUDA(kp_launch(ctx, k_term_reduce, dim3(g), dim3(VEC_THREADS), 0, (const float*)ctx->w_split, ctx->rank, nel,
+    KP_CUDA(kp_launch(ctx, k_term_reduce, dim3(g), dim3(VEC_THREADS), 0, (const float*)ctx->w_split, nterm, nel,
                       (float)e.alpha, (float)e.beta, (const float*)e.aux, e.mode == EPI_SLICES ? 1 : 0, e.out,
                       e.slices, e.slice_stride, vec, t, flags));
     KP_LAUNCHED(ctx);
     return KP_OK;
   }
-  if (vec64(ctx)) return simt_op<double>(ctx, which, bptr, e, flags);
-  return simt_op<float>(ctx, which, bptr, e, flags);
+  if (vec64(ctx)) return simt_op<double>(ctx, which, bptr, e, flags, nterm);
+  return simt_op<float>(ctx, which, bptr, e, flags, nterm);
 }
 
 // epilogue writing the stacked intermediate (G1 / G3 output)
@@ -488,7 +502,7 @@ kp_status op_apply(kp_ctx* ctx, const void* x, void* y, int transpose, int mode)
 }
 
 kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_slices_ready, const int* flags,
-                     double* pq_out, const PostOp* pq_post, bool* pq_done, bool qmax) {
+                     double* pq_out, const PostOp* pq_post, bool* pq_done, bool qmax, int terms) {
   if (pq_done) *pq_done = false;
   const void* bx = p;
   if (op_is_tc(ctx)) {
@@ -496,9 +510,10 @@ kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_sl
     bx = ctx->w_img2;
   }
   const bool tc = op_is_tc(ctx);
-  KP_TRY(run_op(ctx, 0, OP_INNER, bx, epi_stack(ctx, OP_INNER), flags));
-  KP_TRY(run_op(ctx, 1, OP_INNER, nullptr, epi_img(ctx, OP_INNER, ctx->w_img, tc, 1.0, 0.0, nullptr), flags));
-  KP_TRY(run_op(ctx, 2, OP_INNER, ctx->w_img, epi_stack(ctx, OP_INNER), flags));
+  KP_TRY(run_op(ctx, 0, OP_INNER, bx, epi_stack(ctx, OP_INNER), flags, nullptr, nullptr, terms));
+  KP_TRY(run_op(ctx, 1, OP_INNER, nullptr, epi_img(ctx, OP_INNER, ctx->w_img, tc, 1.0, 0.0, nullptr), flags, nullptr,
+                nullptr, terms));
+  KP_TRY(run_op(ctx, 2, OP_INNER, ctx->w_img, epi_stack(ctx, OP_INNER), flags, nullptr, nullptr, terms));
   if (pq_out) {  // p^T q (and the alpha step) fused into the term sum when G4 is batched
     TermDot td;
     td.out = pq_out;
@@ -506,10 +521,12 @@ kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_sl
     td.counter = ctx->red_count;
     if (pq_post) td.po = *pq_post;
     td.qmax = qmax ? 1 : 0;
-    KP_TRY(run_op(ctx, 3, OP_INNER, nullptr, epi_img(ctx, OP_INNER, q, false, 1.0, lam2, p), flags, &td, pq_done));
+    KP_TRY(run_op(ctx, 3, OP_INNER, nullptr, epi_img(ctx, OP_INNER, q, false, 1.0, lam2, p), flags, &td, pq_done,
+                  terms));
     return KP_OK;
   }
-  KP_TRY(run_op(ctx, 3, OP_INNER, nullptr, epi_img(ctx, OP_INNER, q, false, 1.0, lam2, p), flags));
+  KP_TRY(run_op(ctx, 3, OP_INNER, nullptr, epi_img(ctx, OP_INNER, q, false, 1.0, lam2, p), flags, nullptr, nullptr,
+                terms));
   return KP_OK;
 }
 
@@ -551,8 +568,60 @@ static kp_status simt_pc(kp_ctx* ctx, const void* r, void* z, double lam2, const
   return KP_OK;
 }
 
+static kp_status pc_apply_kp(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat, const int* flags,
+                             bool narrow_ready);
+
+// Multi-term preconditioner (pc_rank = k > 1): z ~ (M_k^T M_k + lam2 I)^-1 r,
+// M_k the first k Kronecker terms of A, from `pc_inner_iters` PCG steps on
+// that system from z = 0, each preconditioned by the one-term KP-SVD solve
+// (eq. PreconSolve) and with the Fletcher-Reeves beta.  All scalars live in a
+// block of device slots of their own; the kernels follow the outer pause
+// flag.  The result changes with r, so the outer iteration is flexible PCG.
+static kp_status pc_apply_multiterm(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat,
+                                    const int* flags) {
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  const bool f64 = vec64(ctx);
+  const size_t vs = f64 ? 8 : 4;
+  void *ir = ctx->pc_inner[0], *ir_old = ctx->pc_inner[1], *ip = ctx->pc_inner[2], *iq = ctx->pc_inner[3],
+       *iz = ctx->pc_inner[4];
+  double* s = ctx->dscal + S_INNER;
+  int* f = ctx->dflags + F_INNER;
+  const int k = ctx->pc_rank;
+  const int m = std::max(1, ctx->pc_inner_iters);
+  const int sl = op_inner_slices(ctx);
+  PostOp pa;  // alpha of the inner iteration
+  pa.kind = POST_ALPHA;
+  pa.s = s;
+  pa.f = f;
+  PostOp pb = pa;  // Fletcher-Reeves beta (the inner flags keep F_FLEX = 0)
+  pb.kind = POST_BETA;
+  KP_CUDA(cudaMemsetAsync(z, 0, vs * N, ctx->stream));
+  KP_CUDA(cudaMemsetAsync(f, 0, 8 * sizeof(int), ctx->stream));
+  KP_TRY(copy_vec(ctx, r, ir, N, f64));
+  KP_TRY(pc_apply_kp(ctx, ir, iz, lam2, stat, flags, false));
+  KP_TRY(dot2_dev(ctx, iz, ir, nullptr, N, f64, s + S_ZR, flags));
+  KP_TRY(p_update_dev(ctx, ip, iz, N, f64, nullptr, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N, flags));
+  for (int it = 1; it <= m; ++it) {
+    bool fused = false;
+    KP_TRY(op_apply_K(ctx, ip, iq, lam2, sl > 0, flags, s + S_PQ, &pa, &fused, false, k));
+    if (!fused) KP_TRY(dot2_dev(ctx, ip, iq, nullptr, N, f64, s + S_PQ, flags, pa));
+    KP_TRY(update_xr_dev(ctx, z, ir, ir_old, ip, iq, N, f64, s + S_ALPHA, s + S_RR, flags));
+    if (it == m) break;
+    KP_TRY(pc_apply_kp(ctx, ir, iz, lam2, s + S_RR, flags, false));
+    KP_TRY(dot2_dev(ctx, iz, ir, ir_old, N, f64, s + S_ZRNEW, flags, pb));
+    KP_TRY(p_update_dev(ctx, ip, iz, N, f64, s + S_BETA, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N, flags));
+  }
+  return KP_OK;
+}
+
 kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat, const int* flags,
                    bool narrow_ready) {
+  if (ctx->pc_rank > 1) return pc_apply_multiterm(ctx, r, z, lam2, stat, flags);
+  return pc_apply_kp(ctx, r, z, lam2, stat, flags, narrow_ready);
+}
+
+static kp_status pc_apply_kp(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat, const int* flags,
+                             bool narrow_ready) {
   if (!pc_is_tc(ctx)) {
     if (vec64(ctx)) return simt_pc<double>(ctx, r, z, lam2, flags);
     return simt_pc<float>(ctx, r, z, lam2, flags);
@@ -620,7 +689,7 @@ kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const doubl
 
 // ------------------------------------------------------------- folded quantisation
 bool cg_fusable(kp_ctx* ctx) {
-  if (!ctx->cg_fuse || !op_is_tc(ctx) || !pc_is_tc(ctx) || ctx->vec_prec != KP_F32) return false;
+  if (!ctx->cg_fuse || !op_is_tc(ctx) || !pc_is_tc(ctx) || ctx->vec_prec != KP_F32 || ctx->pc_rank > 1) return false;
   if (ctx->pc_prec != KP_F16 && ctx->pc_prec != KP_BF16) return false;
   return ops(ctx)->batched;
 }

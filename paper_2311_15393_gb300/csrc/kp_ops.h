@@ -17,14 +17,18 @@ kp_status op_apply(kp_ctx* ctx, const void* x, void* y, int transpose, int mode)
 // *pq_done says whether it was (else the caller computes it).  With qmax,
 // max |q| goes to pq_out[1] as well (only when *pq_done).
 struct PostOp;
+// `terms` > 0: the operator of the first `terms` Kronecker terms only (the
+// multi-term preconditioner's inner system); 0: all of them.
 kp_status op_apply_K(kp_ctx* ctx, const void* p, void* q, double lam2, bool p_slices_ready, const int* flags,
                      double* pq_out = nullptr, const PostOp* pq_post = nullptr, bool* pq_done = nullptr,
-                     bool qmax = false);
+                     bool qmax = false, int terms = 0);
 
 // r = A^T (b - A x) - lam2 x with the accurate operator
 kp_status op_true_residual(kp_ctx* ctx, const void* b, const void* x, void* r, double lam2, const int* flags);
 
-// z = M^-1 r.  `stat` points to device [||r||^2, amax(r)] when known (else
+// z = M^-1 r (pc_rank 1: the KP-SVD solve of eq. PreconSolve; pc_rank > 1:
+// pc_inner_iters PCG steps on the first pc_rank terms, see kp_ops.cu).
+// `stat` points to device [||r||^2, amax(r)] when known (else
 // computed here); `inv_slot` is a device float used for the output scale.
 // narrow_ready (F16 / BF16 preconditioners): ctx->pc_in and the inverse
 // scale slot already hold the narrow copy of r (written by the x / r update).

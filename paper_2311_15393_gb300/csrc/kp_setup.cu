@@ -254,7 +254,8 @@ static kp_status projected_diag(kp_ctx* ctx, const double* F, const double* U, c
 }
 
 extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, int center_r, int center_c, kp_bc bc,
-                              int op_rank, kp_prec op_prec, kp_prec pc_prec, kp_prec vec_prec, kp_sigma sigma) {
+                              int op_rank, int pc_rank, kp_prec op_prec, kp_prec pc_prec, kp_prec vec_prec,
+                              kp_sigma sigma) {
   if (!ctx) {
     kp_set_error("kp_setup: NULL context");
     return KP_EINVAL;
@@ -281,6 +282,10 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
     return KP_EINVAL;
   }
   const int rank = op_rank == 0 ? rmax : op_rank;
+  if (pc_rank < 1 || pc_rank > rank) {
+    kp_set_error("kp_setup: pc_rank %d outside [1, %d] (the operator's terms)", pc_rank, rank);
+    return KP_EINVAL;
+  }
   // supported precision combinations
   bool okc = false;
   if (op_prec == KP_F64 && pc_prec == KP_F64 && vec_prec == KP_F64) okc = true;
@@ -307,12 +312,16 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
   }
   KP_CUDA(cudaSetDevice(ctx->device));
   KP_TRY(kp_enter(ctx));
+  for (auto& e : ctx->ev_setup)
+    if (!e) KP_CUDA(cudaEventCreate(&e));
+  KP_CUDA(cudaEventRecord(ctx->ev_setup[0], ctx->stream));
   kp_free_all(ctx);
   ctx->n_r = n_r;
   ctx->n_c = n_c;
   ctx->c_r = center_r;
   ctx->c_c = center_c;
   ctx->rank = rank;
+  ctx->pc_rank = pc_rank;
   ctx->bc = bc;
   ctx->op_prec = op_prec;
   ctx->op_prec_setup = op_prec;
@@ -545,8 +554,14 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
 
   // ---- workspaces and GEMM plans
   KP_TRY(ops_prepare(ctx));
+  KP_CUDA(cudaEventRecord(ctx->ev_setup[1], st));
   KP_CUDA(cudaStreamSynchronize(st));
   KP_TRY(read_status(ctx));
+  {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev_setup[0], ctx->ev_setup[1]);
+    ctx->last_setup_ms = ms;
+  }
   ctx->ready = true;
   return kp_leave(ctx);
 }

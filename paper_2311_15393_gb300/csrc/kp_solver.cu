@@ -396,6 +396,7 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
     info->rel_res = rr0 > 0 ? std::sqrt(final_rr / rr0) : 0.0;
     info->status = result;
     info->ms_solve = ms;
+    info->ms_setup = ctx->last_setup_ms;
     if (info->res_hist && info->res_hist_len > 0) {
       int n = std::min(info->res_hist_len, std::min(iters + 1, ctx->hist_cap));
       KP_CUDA(cudaMemcpy(info->res_hist, ctx->hist, sizeof(double) * n, cudaMemcpyDeviceToHost));

@@ -21,6 +21,9 @@ enum {
   S_RTPREV = 14             // ||r||^2 of the previous true residual (stagnation test)
 };
 enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4, F_STAG = 5, F_SINCE = 6 };
+// the multi-term preconditioner's inner PCG keeps its scalars and flags in
+// blocks of their own, at these offsets into ctx->dscal / ctx->dflags
+constexpr int S_INNER = 64, F_INNER = 16;
 // a reliable update is also due after this many iterations without one (so a
 // recurred residual that stops falling is checked against the true one)
 constexpr int REPLACE_EVERY = 50;

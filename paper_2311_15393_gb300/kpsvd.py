@@ -41,7 +41,7 @@ class KpError(RuntimeError):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("replacements", ctypes.c_int), ("rel_res", ctypes.c_double),
-                ("status", ctypes.c_int), ("ms_solve", ctypes.c_double),
+                ("status", ctypes.c_int), ("ms_solve", ctypes.c_double), ("ms_setup", ctypes.c_double),
                 ("res_hist", ctypes.POINTER(ctypes.c_double)), ("res_hist_len", ctypes.c_int)]
 
 
@@ -69,7 +69,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     sig = {
         "kp_create": ([ctypes.POINTER(vp), i, vp], i),
         "kp_destroy": ([vp], None),
-        "kp_setup": ([vp, vp, i, i, i, i, i, i, i, i, i, i], i),
+        "kp_setup": ([vp, vp, i, i, i, i, i, i, i, i, i, i, i], i),
         "kp_forward": ([vp, vp, vp, d, vp, dp], i),
         "tik_pcg": ([vp, vp, d, d, i, i, vp, i, ctypes.POINTER(SolveInfo)], i),
         "choose_lambda": ([vp, vp, i, d, vp, dp], i),
@@ -176,6 +176,7 @@ class Info:
     status: int
     ms_solve: float
     res_hist: np.ndarray
+    ms_setup: float = 0.0
 
 
 class KpContext:
@@ -219,9 +220,10 @@ class KpContext:
 
     # -- setup / solve -------------------------------------------------------------
     def kp_setup(self, psf_dev, n_r: int, n_c: int, center, bc: str = "reflexive", op_rank: int = 0,
-                 op_prec: str = "f64", pc_prec: str = "f64", vec_prec: str = "f64", sigma: str = "projected"):
+                 op_prec: str = "f64", pc_prec: str = "f64", vec_prec: str = "f64", sigma: str = "projected",
+                 pc_rank: int = 1):
         psf = _dev(psf_dev, "float64", max(n_r, 0) * max(n_c, 0), self.device, "psf")
-        _check(_lib.kp_setup(self._h, psf, n_r, n_c, int(center[0]), int(center[1]), BC[bc], op_rank,
+        _check(_lib.kp_setup(self._h, psf, n_r, n_c, int(center[0]), int(center[1]), BC[bc], op_rank, pc_rank,
                              PREC[op_prec], PREC[pc_prec], PREC[vec_prec], SIGMA[sigma]))
         self.n_r, self.n_c, self.vec = n_r, n_c, vec_prec
 
@@ -243,7 +245,7 @@ class KpContext:
         if check and st not in (KP_OK,):
             _check(st)
         n = min(hist_len, info.iters + 1) if hist_len > 0 else 0
-        return Info(info.iters, info.replacements, info.rel_res, st, info.ms_solve, hist[:n])
+        return Info(info.iters, info.replacements, info.rel_res, st, info.ms_solve, hist[:n], info.ms_setup)
 
     def choose_lambda(self, b, method: str, param: float = 0.0, x_true=None) -> float:
         lam = ctypes.c_double(0.0)

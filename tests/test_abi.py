@@ -50,7 +50,7 @@ def test_status_strings(lib):
 def test_null_context_is_rejected_without_gpu(lib):
     # argument validation runs before any device call
     assert lib.tik_pcg(None, None, ctypes.c_double(0.1), ctypes.c_double(1e-6), 10, 0, None, 0, None) != 0
-    assert lib.kp_setup(None, None, 8, 8, 4, 4, 0, 0, 0, 0, 0, 1) != 0
+    assert lib.kp_setup(None, None, 8, 8, 4, 4, 0, 0, 1, 0, 0, 0, 1) != 0
     assert lib.kp_create(None, 0, None) != 0
 
 

@@ -1,0 +1,102 @@
+"""GPU parity of the multi-term preconditioner (kp_setup pc_rank > 1) against
+the oracle's pcg.multiterm_minv / tik_fpcg_multiterm.
+
+With pc_rank = k the preconditioner solves (M_k^T M_k + lambda^2 I) z = r,
+M_k the first k Kronecker terms of A, by pc_inner_iters PCG steps from
+z = 0 preconditioned by the one-term KP-SVD solve (eq. PreconSolve);
+Section 5.3 finds the one-term preconditioner weak for blurs with many
+Kronecker terms."""
+import numpy as np
+import pytest
+
+from gpu_common import OracleProblem, lib, rel, torch, vt
+from oracle import kpsvd as okp, lam as olam, pcg as opcg
+from paper_2311_15393_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kpsvd():
+    return lib()
+
+
+def _ctx(kpsvd, pr, op, pc, vec, k, inner):
+    ctx = kpsvd.KpContext(0)
+    ctx.kp_set_option("pc_inner_iters", inner)
+    P = pr.P
+    ctx.kp_setup(kpsvd.to_device(P.psf), P.n_r, P.n_c, P.center, P.bc, P.op_rank, op, pc, vec, "projected",
+                 pc_rank=k)
+    torch.cuda.synchronize()
+    return ctx
+
+
+def _problem(n=64, rank=8, rho=0.6):
+    psf = synth.gaussian_psf(n, n, n // 2, n // 2, 4.0, 2.0, rho)
+    return OracleProblem("deblur64_fp64", n=n, psf=psf, center=(n // 2, n // 2), bc="reflexive", rank=rank)
+
+
+@pytest.mark.parametrize("k,inner", [(2, 2), (4, 3), (8, 1)])
+def test_multiterm_apply_matches_oracle(kpsvd, k, inner):
+    """FP64: z = M_k^-1 r (kp_apply_Minv) equals the oracle's multiterm_minv."""
+    pr = _problem()
+    lam = 0.02
+    R = synth.random_matrix(64, 64, 9)
+    with _ctx(kpsvd, pr, "f64", "f64", "f64", k, inner) as ctx:
+        r = kpsvd.to_device(R)
+        z = torch.empty_like(r)
+        ctx.kp_apply_Minv(r, z, lam)
+        Z = kpsvd.from_device(z, 64, 64)
+    Zo = opcg.multiterm_minv(pr.op, pr.kp, lam, k, inner)(R)
+    assert rel(Z, Zo) < 1e-11
+
+
+@pytest.mark.parametrize("k,inner", [(2, 2), (4, 2)])
+def test_multiterm_fpcg_iterates_match_oracle(kpsvd, k, inner):
+    """FP64: the flexible-PCG iterates with the multi-term preconditioner after
+    1, 5 and 15 iterations equal the oracle's tik_fpcg_multiterm."""
+    pr = _problem()
+    lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
+    with _ctx(kpsvd, pr, "f64", "f64", "f64", k, inner) as ctx:
+        b = kpsvd.to_device(pr.B)
+        for j in (1, 5, 15):
+            x = torch.zeros_like(b)
+            info = ctx.tik_pcg(b, lam, 0.0, j, True, x, check=False)
+            xo, io = opcg.tik_fpcg_multiterm(pr.op, pr.kp, pr.B, lam, k, inner, 0.0, j)
+            assert info.iters == j
+            assert rel(kpsvd.from_device(x, 64, 64), xo) < 1e-9, j
+
+
+def test_multiterm_reduced_precision_solve(kpsvd):
+    """256 x 256, rank-4 operator with a strongly non-separable PSF (rho 0.85),
+    BF16 operator, FP16 preconditioner: FPCG with the two-term preconditioner
+    (2 inner steps) reaches the oracle's x_lambda to 1e-4, within +3
+    iterations of the oracle's FP64 multi-term FPCG."""
+    psf = synth.gaussian_psf(256, 256, 128, 128, 4.0, 2.0, 0.85)
+    pr = OracleProblem("deblur256_fp32", n=256, psf=psf, rank=4)
+    lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
+    x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam, tol=1e-10)
+    _, io = opcg.tik_fpcg_multiterm(pr.op, pr.kp, pr.B, lam, 2, 2, 1e-7, 500)
+    _, i1 = opcg.tik_pcg(pr.op, pr.kp, pr.B, lam, 1e-7, 500, True)
+    with _ctx(kpsvd, pr, "bf16", "f16", "f32", 2, 2) as ctx:
+        b = kpsvd.to_device(pr.B, torch.float32)
+        x = torch.zeros_like(b)
+        info = ctx.tik_pcg(b, lam, 1e-7, 500, True, x)
+        err = rel(kpsvd.from_device(x, 256, 256), x_star)
+    print(f"two-term preconditioner: {info.iters} iterations (oracle {io.iters}; one term {i1.iters}), "
+          f"rel. error {err:.2e}")
+    assert info.status == kpsvd.KP_OK
+    assert err < 1e-4
+    assert info.iters <= io.iters + 3
+
+
+def test_pc_rank_is_validated(kpsvd):
+    pr = _problem(n=32, rank=3)
+    with kpsvd.KpContext(0) as ctx:
+        with pytest.raises(kpsvd.KpError) as e:
+            ctx.kp_setup(kpsvd.to_device(pr.P.psf), 32, 32, (16, 16), "reflexive", 3, "f64", "f64", "f64",
+                         "projected", pc_rank=4)
+        assert e.value.status == kpsvd.KP_EINVAL
+        with pytest.raises(kpsvd.KpError):
+            ctx.kp_setup(kpsvd.to_device(pr.P.psf), 32, 32, (16, 16), "reflexive", 3, "f64", "f64", "f64",
+                         "projected", pc_rank=0)
