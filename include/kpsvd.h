@@ -285,6 +285,12 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     256 x 256 tile per pair of SMs); 1: never; 2: wherever
  *                     the shape allows (N >= 256, per-term blocks of 256 rows)
  *                     The tile options take effect at the next kp_setup.
+ *   "device_loop"     1 (default): tik_pcg runs its whole iteration as one CUDA
+ *                     graph with a device-side while loop (the residual
+ *                     replacement in a nested conditional), no host round
+ *                     trip until the solve stops; 0: blocks of check_every
+ *                     iterations launched and checked by the host (also the
+ *                     fallback when the device loop cannot be built)
  *   "pdl"             0: launch the iteration's kernels without programmatic
  *                     dependent launch (default 1: each kernel's launch and
  *                     prologue overlap the tail of the previous one)

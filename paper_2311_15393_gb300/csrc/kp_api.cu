@@ -188,6 +188,7 @@ extern "C" void kp_destroy(kp_ctx* ctx) {
   if (ctx->ctx_block) cudaFree(ctx->ctx_block);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   if (ctx->stream && ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -243,6 +244,8 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
     ctx->splitk_override = (int)value;
   } else if (!strcmp(name, "pdl")) {
     ctx->pdl = value != 0.0;
+  } else if (!strcmp(name, "device_loop")) {
+    ctx->device_loop = value != 0.0;
   } else if (!strcmp(name, "tc_bn")) {
     ctx->tc_bn_override = (int)value;
   } else if (!strcmp(name, "tc_kblocks_per_stage")) {

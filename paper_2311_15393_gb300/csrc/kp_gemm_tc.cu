@@ -712,10 +712,7 @@ struct PairCfg {
   static constexpr int KB_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGE = KPS * KB_BYTES;
   static constexpr int STAGES = 196608 / STAGE;
-  // + 16 KB of slack past the last B tile: shared-memory reads of the MMA
-  // stay inside the allocation even if they extend past a 128-row B tile
-  static constexpr int SLACK = 16384;
-  static constexpr int SMEM = STAGES * STAGE + SLACK + 1024 + 512;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
   static constexpr int TMEM_COLS = 2 * PAIR_N;
   static_assert(STAGES >= 2, "ring too shallow");
 };
@@ -740,7 +737,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
   }
   extern __shared__ unsigned char smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE + C::SLACK);
+  uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE);
   uint64_t* full = bars;
   uint64_t* empty = bars + C::STAGES;
   uint64_t* tfull = bars + 2 * C::STAGES;  // [2]

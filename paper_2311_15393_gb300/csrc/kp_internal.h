@@ -140,6 +140,8 @@ struct kp_ctx {
   double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD
   int jacobi_max_sweeps = 40;
   bool pdl = true;           // programmatic dependent launch in the iteration
+  bool device_loop = true;   // (F)PCG loop as a device-side graph while loop (host loop: false)
+  cudaStream_t aux_stream = nullptr;  // second capture stream (nested graph bodies)
   void* hmirror = nullptr;   // pinned host copies of the solver flags / scalars (2 slots)
   cudaEvent_t ev_blk[2] = {nullptr, nullptr};
   cudaEvent_t ev_setup[2] = {nullptr, nullptr};  // timing of kp_setup

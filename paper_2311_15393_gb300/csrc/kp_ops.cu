@@ -687,6 +687,16 @@ static kp_status pc_apply_kp(kp_ctx* ctx, const void* r, void* z, double lam2, c
   return KP_OK;
 }
 
+// the preconditioner's narrow input made from r (F16 / BF16 tensor-core
+// preconditioners; nothing to do otherwise), as pc_apply makes it when the
+// x / r update has not: after a residual replacement inside the device loop
+kp_status pc_prepare_input(kp_ctx* ctx, const void* r, double lam2, const double* stat, const int* flags) {
+  if (!pc_is_tc(ctx) || ctx->pc_prec == KP_E4M3 || ctx->pc_rank > 1) return KP_OK;
+  const int nt = ctx->pc_prec == KP_BF16 ? NT_BF16 : NT_F16;
+  return quantize_dev(ctx, r, (long long)ctx->n_r * ctx->n_c, false, stat, nt, lam2, ctx->pc_in, ops(ctx)->inv_slot,
+                      flags);
+}
+
 // ------------------------------------------------------------- folded quantisation
 bool cg_fusable(kp_ctx* ctx) {
   if (!ctx->cg_fuse || !op_is_tc(ctx) || !pc_is_tc(ctx) || ctx->vec_prec != KP_F32 || ctx->pc_rank > 1) return false;

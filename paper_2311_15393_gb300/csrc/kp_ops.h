@@ -35,6 +35,10 @@ kp_status op_true_residual(kp_ctx* ctx, const void* b, const void* x, void* r, d
 kp_status pc_apply(kp_ctx* ctx, const void* r, void* z, double lam2, const double* stat, const int* flags,
                    bool narrow_ready = false);
 
+// the preconditioner's narrow input made from r, as pc_apply makes it when
+// it is not made by the x / r update (F16 / BF16 one-term preconditioners)
+kp_status pc_prepare_input(kp_ctx* ctx, const void* r, double lam2, const double* stat, const int* flags);
+
 // number of bf16 slices the inner operator wants for p (0 for SIMT operators)
 int op_inner_slices(kp_ctx* ctx);
 

@@ -57,6 +57,55 @@ __global__ void k_after_replace(double* s, int* f, double* hist, int hist_cap) {
 }
 }  // namespace
 
+// ---------------------------------------------------------------- device-side loop
+// The iteration as a CUDA graph while loop, with the residual replacement in
+// a nested if: per iteration half_a, then k_loop_decide_a (is a replacement
+// due: the reliable-update rule or a convergence / maxit stop with a reduced-
+// precision operator), then if so the replacement and k_loop_after_replace,
+// then k_loop_decide_b (continue while no stop is flagged), then half_b
+// (whose kernels skip when a stop is flagged).  The host launches the graph
+// once and reads the flags after it.
+__global__ void k_loop_decide_a(int* f, int reliable, cudaGraphConditionalHandle h_replace) {
+  const int reason = f[F_REASON];
+  int repl = 0;
+  if (f[F_PAUSE] && !(reason & (R_NUMERIC | R_BREAKDOWN)) && reliable && (reason & (R_CONV | R_REPLACE | R_MAXIT))) {
+    repl = 1;
+    f[F_SAVED] = reason;
+  }
+  cudaGraphSetConditional(h_replace, repl);
+}
+// after a replacement: k_after_replace's rule, a maxit stop stays a stop
+__global__ void k_loop_after_replace(double* s, int* f, double* hist, int hist_cap) {
+  const double rr = s[S_RR];
+  const int it = f[F_ITER];
+  if (it < hist_cap) hist[it] = sqrt(rr / s[S_RR0]);
+  const double prev = s[S_RTPREV];
+  f[F_STAG] = (prev > 0.0 && rr > 0.25 * prev) ? f[F_STAG] + 1 : 0;
+  f[F_SINCE] = 0;
+  f[F_REPL] += 1;
+  s[S_RTPREV] = rr;
+  if (rr <= s[S_TOL2]) {
+    f[F_REASON] = R_CONV | R_TRUE;
+    f[F_PAUSE] = 1;
+  } else if (f[F_STAG] >= STAG_REPLACEMENTS && !(f[F_SAVED] & R_MAXIT)) {
+    f[F_REASON] = R_STAGNATE;
+    f[F_PAUSE] = 1;
+  } else if (f[F_SAVED] & R_MAXIT) {
+    f[F_REASON] = R_MAXIT;
+    f[F_PAUSE] = 1;
+  } else {
+    f[F_REASON] = 0;
+    f[F_PAUSE] = 0;
+  }
+}
+// continue while no stop is flagged; F_GUARD counts body runs and ends the
+// loop in any case a few runs past maxit
+constexpr int F_GUARD = 15;
+__global__ void k_loop_decide_b(int* f, cudaGraphConditionalHandle h_loop) {
+  const int runs = ++f[F_GUARD];
+  cudaGraphSetConditional(h_loop, (f[F_PAUSE] || runs > f[F_MAXIT] + 8) ? 0u : 1u);
+}
+
 struct SolveBufs {
   void *r, *r_old, *p, *q, *z, *rhs;
 };
@@ -96,7 +145,7 @@ static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
 
 // second half: z = M^-1 r, beta, p = z + beta p (+ bf16 slices of p)
 // (narrow_ready: the narrow copy of r for the preconditioner is already made)
-static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2_pc, bool narrow_ready = false) {
+static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2_pc, bool narrow_ready) {
   const long long N = (long long)ctx->n_r * ctx->n_c;
   const bool f64 = ctx->vec_prec == KP_F64;
   const int* fl = ctx->dflags;
@@ -164,6 +213,112 @@ static kp_status replace_residual(kp_ctx* ctx, const SolveBufs& B, const void* b
   KP_TRY(norm_amax_dev(ctx, B.r, N, ctx->vec_prec == KP_F64, ctx->dscal + S_RR));
   KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RMAX, ctx->dscal + S_RR, sizeof(double), cudaMemcpyDeviceToDevice,
                           ctx->stream));
+  return KP_OK;
+}
+
+// ---- the device-side loop graph (see k_loop_decide_a)
+struct LoopGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches_body = 0, launches_replace = 0;
+  ~LoopGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+  }
+};
+
+static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2);
+static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2_pc, bool narrow_ready);
+static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2, double lam2_pc);
+
+static kp_status build_loop_graph(kp_ctx* ctx, const SolveBufs& B, const void* b, void* x, double lam2, double lam2_pc,
+                                  bool reliable, bool folded, LoopGraph* L) {
+  cudaStream_t st = ctx->stream;
+  if (!ctx->aux_stream) KP_CUDA(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+  KP_CUDA(cudaGraphCreate(&L->g, 0));
+  cudaGraphConditionalHandle h_loop, h_rep;
+  KP_CUDA(cudaGraphConditionalHandleCreate(&h_loop, L->g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = h_loop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  KP_CUDA(cudaGraphAddNode(&wnode, L->g, nullptr, nullptr, 0, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  KP_CUDA(cudaGraphConditionalHandleCreate(&h_rep, body, 0, 0));
+  const long long l0 = ctx->launches;
+  KP_CUDA(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  kp_status cs = folded ? half_a_folded(ctx, B, x, lam2, lam2_pc) : half_a(ctx, B, x, lam2);
+  cudaGraph_t ibody = nullptr;
+  bool aux_capturing = false;
+  if (cs == KP_OK) {
+    k_loop_decide_a<<<1, 1, 0, st>>>(ctx->dflags, reliable ? 1 : 0, h_rep);
+    KP_LAUNCHED(ctx);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_rep;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cst, nullptr, &cg, &deps, &ed, &nd);
+    if (e == cudaSuccess) e = cudaGraphAddNode(&inode, cg, deps, ed, nd, &ip);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+      ibody = ip.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(ctx->aux_stream, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    }
+    if (e != cudaSuccess) {
+      kp_set_error("tik_pcg: loop graph: %s", cudaGetErrorString(e));
+      cs = KP_ECUDA;
+    } else {
+      aux_capturing = true;
+      // the replacement (and the preconditioner input from the new r) in the if body
+      const long long l1 = ctx->launches;
+      ctx->stream = ctx->aux_stream;
+      cs = replace_residual(ctx, B, b, x, lam2);
+      if (cs == KP_OK) {
+        k_loop_after_replace<<<1, 1, 0, ctx->stream>>>(ctx->dscal, ctx->dflags, ctx->hist, ctx->hist_cap);
+        KP_LAUNCHED(ctx);
+        if (folded) cs = pc_prepare_input(ctx, B.r, lam2_pc, ctx->dscal + S_RR, nullptr);
+      }
+      ctx->stream = st;
+      L->launches_replace = ctx->launches - l1;
+      cudaGraph_t tmp = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(ctx->aux_stream, &tmp);
+      aux_capturing = false;
+      if (cs == KP_OK && e2 != cudaSuccess) {
+        kp_set_error("tik_pcg: loop graph (replacement): %s", cudaGetErrorString(e2));
+        cs = KP_ECUDA;
+      }
+    }
+  }
+  if (cs == KP_OK) {
+    const long long l2 = ctx->launches;
+    k_loop_decide_b<<<1, 1, 0, st>>>(ctx->dflags, h_loop);
+    KP_LAUNCHED(ctx);
+    cs = half_b(ctx, B, lam2_pc, folded);
+    (void)l2;
+  }
+  if (aux_capturing) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(ctx->aux_stream, &tmp);
+  }
+  cudaGraph_t tmp = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(st, &tmp);
+  L->launches_body = ctx->launches - l0 - L->launches_replace;
+  ctx->launches = l0;
+  if (cs != KP_OK) return cs;
+  if (ee != cudaSuccess) {
+    kp_set_error("tik_pcg: loop graph capture: %s", cudaGetErrorString(ee));
+    return KP_ECUDA;
+  }
+  KP_CUDA(cudaGraphInstantiate(&L->exec, L->g, 0));
   return KP_OK;
 }
 
@@ -253,6 +408,50 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
       const int sl = op_inner_slices(ctx);
       KP_TRY(p_update_dev(ctx, B.p, B.z, N, f64, nullptr, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N,
                           nullptr));
+      bool done_device = false;
+      if (ctx->device_loop) {
+        // the whole loop on the device (one graph launch); on any failure
+        // to build it, the host-driven loop below
+        LoopGraph L;
+        const kp_status bs = build_loop_graph(ctx, B, b, x, lam2, lam2_pc, reliable, folded, &L);
+        if (bs == KP_OK) {
+          KP_CUDA(cudaGraphLaunch(L.exec, st));
+          int fl[16];
+          KP_CUDA(cudaMemcpyAsync(fl, ctx->dflags, sizeof(fl), cudaMemcpyDeviceToHost, st));
+          KP_CUDA(cudaMemcpyAsync(hs, ctx->dscal, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
+          KP_CUDA(cudaStreamSynchronize(st));
+          iters = fl[F_ITER];
+          repl = fl[F_REPL];
+          final_rr = hs[S_RR];
+          ctx->launches += (long long)fl[F_GUARD] * L.launches_body + (long long)repl * L.launches_replace;
+          const int reason = fl[F_REASON];
+          if (reason & R_NUMERIC) {
+            kp_set_error("tik_pcg: NaN / Inf at iteration %d", iters);
+            result = KP_ENUMERIC;
+          } else if (reason & R_BREAKDOWN) {
+            kp_set_error("tik_pcg: breakdown (p^T K p <= 0 or z^T r <= 0) at iteration %d", iters);
+            result = KP_EBREAKDOWN;
+          } else if (reason & R_TRUE) {
+            result = KP_OK;
+          } else if (reason & R_STAGNATE) {
+            result = KP_ENOCONV;
+            kp_set_error("tik_pcg: stagnated at ||r||/||A^T b|| = %.3e (iteration %d): the tolerance is below the "
+                         "attainable accuracy of this precision", std::sqrt(final_rr / rr0), iters);
+          } else if (reason & R_MAXIT) {
+            result = KP_ENOCONV;
+            kp_set_error("tik_pcg: maxit %d reached, ||r||/||A^T b|| = %.3e", maxit, std::sqrt(final_rr / rr0));
+          } else if (reason & R_CONV) {
+            result = KP_OK;
+          } else {
+            result = KP_ENOCONV;
+            kp_set_error("tik_pcg: the device loop ended without a stop reason (iteration %d)", iters);
+          }
+          done_device = true;
+        } else {
+          cudaGetLastError();  // a capture error is not sticky; use the host loop
+        }
+      }
+      if (!done_device) {
       // capture one block of iterations
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
@@ -336,7 +535,7 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
           ++repl;
           k_after_replace<<<1, 1, 0, st>>>(ctx->dscal, ctx->dflags, ctx->hist, ctx->hist_cap);
           KP_LAUNCHED(ctx);
-          KP_TRY(half_b(ctx, B, lam2_pc));
+          KP_TRY(half_b(ctx, B, lam2_pc, false));
           cur = 0;
           KP_TRY(launch_block(cur));
           continue;
@@ -373,13 +572,14 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
         // resume: clear the pause, finish the interrupted iteration, continue
         int zero2[2] = {0, 0};
         KP_CUDA(cudaMemcpyAsync(ctx->dflags, zero2, sizeof(zero2), cudaMemcpyHostToDevice, st));
-        KP_TRY(half_b(ctx, B, lam2_pc));
+        KP_TRY(half_b(ctx, B, lam2_pc, false));
         KP_CUDA(cudaStreamSynchronize(st));
         cur = 0;
         KP_TRY(launch_block(cur));
       }
       cudaGraphExecDestroy(exec);
       cudaGraphDestroy(graph);
+      }  // host loop
     }
   }
   KP_CUDA(cudaEventRecord(e1, st));

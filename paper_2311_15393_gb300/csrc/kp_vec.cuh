@@ -20,7 +20,9 @@ enum {
   S_QPQ = 12, S_QMAX = 13,  // fused iteration: p^T q and max |q| (K application's term sum)
   S_RTPREV = 14             // ||r||^2 of the previous true residual (stagnation test)
 };
-enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4, F_STAG = 5, F_SINCE = 6 };
+enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4, F_STAG = 5, F_SINCE = 6,
+       F_SAVED = 7,   // device loop: the reason that triggered a residual replacement
+       F_REPL = 8 };  // device loop: residual replacements done
 // the multi-term preconditioner's inner PCG keeps its scalars and flags in
 // blocks of their own, at these offsets into ctx->dscal / ctx->dflags
 constexpr int S_INNER = 64, F_INNER = 16;
