@@ -237,6 +237,20 @@ __device__ __forceinline__ void epi_store32(const EpiParams& e, float scale_dev,
     }
   }
   if (e.mode == EPI_F32) {
+    if (e.bias || e.act) {  // the learned-lambda MLP's bias and activation
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < cnt) {
+          if (e.bias) v[c] += e.bias[gn0 + c];
+          if (e.act == 1) {
+            e.pre[base + c] = v[c];
+            v[c] = kp_gelu(v[c]);
+          } else if (e.act == 2) {
+            v[c] *= kp_gelu_grad(e.pre[base + c]);
+          }
+        }
+      }
+    }
     if (e.amax_bits) {
 #pragma unroll
       for (int c = 0; c < 32; ++c)
@@ -1130,6 +1144,51 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
   ctx->tc_plans.push_back(pl);
   *out = pl;
   return KP_OK;
+}
+
+namespace {
+__global__ void k_f64_to_bf16(const double* __restrict__ in, long long n, __nv_bfloat16* __restrict__ out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = __float2bfloat16_rn((float)in[t]);
+}
+}  // namespace
+
+// D = A B^T with bf16 inputs and FP32 accumulation on the tensor cores: A is
+// rows_a x K and B rows_b x K (FP64, K-major, leading dimension K), D is
+// row-major rows_a x rows_b FP32.  The half-precision products of the
+// setup (option setup_half); K a multiple of 8.
+kp_status half_product(kp_ctx* ctx, const double* A, int rows_a, const double* B, int rows_b, int K, float* D) {
+  __nv_bfloat16 *a16 = nullptr, *b16 = nullptr;
+  const long long na = (long long)rows_a * K, nb = (long long)rows_b * K;
+  KP_TRY(kp_alloc(ctx, (void**)&a16, sizeof(__nv_bfloat16) * na));
+  KP_TRY(kp_alloc(ctx, (void**)&b16, sizeof(__nv_bfloat16) * nb));
+  const int ga = (int)std::max(1LL, std::min((na + 255) / 256, (long long)ctx->sm_count * 16));
+  const int gb = (int)std::max(1LL, std::min((nb + 255) / 256, (long long)ctx->sm_count * 16));
+  k_f64_to_bf16<<<ga, 256, 0, ctx->stream>>>(A, na, a16);
+  k_f64_to_bf16<<<gb, 256, 0, ctx->stream>>>(B, nb, b16);
+  ctx->launches += 2;
+  GemmDesc g;
+  g.M = rows_a;
+  g.N = rows_b;
+  g.K = K;
+  g.A.ptr = a16;
+  g.A.rows = rows_a;
+  g.A.K = K;
+  g.A.ld = K;
+  g.A.tstride = na;
+  g.A.nterm_idx = 1;
+  g.B.ptr = b16;
+  g.B.rows = rows_b;
+  g.B.K = K;
+  g.B.ld = K;
+  g.B.tstride = nb;
+  g.B.nterm_idx = 1;
+  g.epi.mode = EPI_F32;
+  g.epi.out = D;
+  g.epi.ldd = rows_b;
+  TcGemmPlan* pl = nullptr;
+  KP_TRY(tc_plan_create(ctx, g, TC_BF16, 1, &pl));
+  return tc_plan_run(ctx, pl, nullptr);
 }
 
 void tc_plan_set_epi(TcGemmPlan* plan, const EpiParams& e) {

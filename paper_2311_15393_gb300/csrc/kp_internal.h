@@ -89,7 +89,20 @@ struct EpiParams {
   double lam2 = 0.0;
   int narrow = NT_BF16;
   unsigned int* amax_bits = nullptr;  // EPI_F32: atomicMax of max |out| (bits of a non-negative float)
+  // EPI_F32 only (the learned-lambda MLP): + bias[n]; act 1: pre[m][n] =
+  // the value, out = GELU(value); act 2: out = value * GELU'(pre[m][n]);
+  // pre has the indexing of out
+  const float* bias = nullptr;
+  float* pre = nullptr;
+  int act = 0;
 };
+
+// GELU(z) = z Phi(z) with the normal CDF Phi, and its derivative
+__device__ __forceinline__ float kp_phi(float z) { return 0.5f * erfcf(-z * 0.70710678118654752f); }
+__device__ __forceinline__ float kp_gelu(float z) { return z * kp_phi(z); }
+__device__ __forceinline__ float kp_gelu_grad(float z) {
+  return kp_phi(z) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
 
 struct GemmDesc {
   int M = 0, N = 0, K = 0;
@@ -163,6 +176,11 @@ struct kp_ctx {
   // FP32 vectors unless the "setup_fp64" option is set
   bool setup_fp32 = false;
   bool force_setup_fp64 = false;
+  // half-precision setup (the paper's future work, Section 3 after eq.
+  // PreconSolve): the products that form V_c, V_r and the spectrum take bf16
+  // inputs with FP32 accumulation on the tensor cores (FP32 vectors only)
+  bool setup_half = false;
+  bool force_setup_half = false;
   int* dev_status = nullptr;     // device status word
   double* dscal = nullptr;       // device scalars (see kp_solver.cu)
   double* red_part = nullptr;    // reduction partials
@@ -254,6 +272,9 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
 kp_status tc_plan_run(kp_ctx* ctx, TcGemmPlan* plan, const EpiParams* epi_override);
 void tc_plan_set_epi(TcGemmPlan* plan, const EpiParams& e);
 bool tc_device_supported(kp_ctx* ctx);
+// D (rows_a x rows_b row-major FP32) = A B^T, A rows_a x K and B rows_b x K
+// FP64 K-major, with bf16 inputs and FP32 accumulation on the tensor cores
+kp_status half_product(kp_ctx* ctx, const double* A, int rows_a, const double* B, int rows_b, int K, float* D);
 
 // one-sided Jacobi SVD (FP64): A (m x n col-major, m >= n) -> U (m x n), s (n), V (n x n)
 kp_status jacobi_svd(kp_ctx* ctx, const double* A, int m, int n, double* U, double* s, double* V,

@@ -8,11 +8,17 @@
 // Weights: FP32 masters (for Adam) and bf16 copies used by the products;
 // biases and every activation and accumulation in FP32.  GELU(z) = z Phi(z).
 // Loss: mean squared error of log10(lambda).  Adam with bias correction.
-// All products are small (batch x 256 x 256), so one tiled SIMT kernel with
-// strided operand access serves the forward pass and both backward products.
+// The width x width products of the hidden layers (forward, weight
+// gradients, input gradients) run on the tcgen05 tensor cores: FP32
+// activations and gradients enter as three bf16 slices each (an exact split
+// of the FP32 value), weights as their bf16 copy, with FP32 accumulation in
+// TMEM, so the products keep FP32 accuracy; bias, GELU and GELU' are fused
+// into the GEMM epilogue.  The scalar output layer (width -> 1) and the
+// column sums of the bias gradients are small SIMT kernels.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "kp_internal.h"
@@ -31,6 +37,16 @@ struct kp_mlp {
   double* loss_dev = nullptr;
   int t = 0;
   std::vector<void*> allocs;
+  // tensor-core products of the hidden layers
+  kp_ctx* tc = nullptr;                          // context that owns the GEMM plans (its stream is ours)
+  int bpad = 0;                                  // max_batch rounded up to 8 (16-byte rows of bf16 over the batch)
+  std::vector<__nv_bfloat16*> actS, actT;        // per hidden layer l: act[l] as 3 bf16 slices, and transposed
+  __nv_bfloat16 *gS = nullptr, *gT = nullptr;    // the backward gradient as 3 bf16 slices, and transposed
+  std::vector<__nv_bfloat16*> WbT;               // per layer: bf16 W^T (in x out)
+  struct Plans {
+    std::vector<TcGemmPlan*> fwd, dW, dX;
+  };
+  std::map<int, Plans> plans;                    // per batch size
 };
 
 namespace {
@@ -40,11 +56,6 @@ constexpr int MT = 32, NT = 32, KT = 16, MLP_THREADS = 256;
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-__device__ __forceinline__ float phi(float z) { return 0.5f * erfcf(-z * 0.70710678118654752f); }
-__device__ __forceinline__ float gelu(float z) { return z * phi(z); }
-__device__ __forceinline__ float gelu_grad(float z) {
-  return phi(z) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
-}
 
 enum { MEPI_STORE = 0, MEPI_BIAS = 1, MEPI_BIAS_GELU = 2, MEPI_GELU_GRAD = 3 };
 
@@ -95,9 +106,9 @@ __global__ void __launch_bounds__(MLP_THREADS)
       if (epi == MEPI_BIAS || epi == MEPI_BIAS_GELU) v += bias[n];
       if (epi == MEPI_BIAS_GELU) {
         pre[o] = v;
-        v = gelu(v);
+        v = kp_gelu(v);
       } else if (epi == MEPI_GELU_GRAD) {
-        v *= gelu_grad(aux[o]);
+        v *= kp_gelu_grad(aux[o]);
       }
       C[o] = v;
     }
@@ -142,10 +153,12 @@ __global__ void k_mlp_colsum(const float* __restrict__ g, int batch, int n, floa
   out[o] = a;
 }
 
-// Adam on one parameter array; wb (nullable) receives the bf16 copy
+// Adam on one parameter array; wb (nullable) receives the bf16 copy and wbt
+// (nullable) its transpose (w is rows x cols, row-major)
 __global__ void k_mlp_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                            const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
-                           float c1, float c2, __nv_bfloat16* __restrict__ wb) {
+                           float c1, float c2, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wbt,
+                           int rows, int cols) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -154,13 +167,40 @@ __global__ void k_mlp_adam(float* __restrict__ w, float* __restrict__ m, float* 
     v[i] = vi;
     const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     w[i] = wi;
-    if (wb) wb[i] = __float2bfloat16_rn(wi);
+    const __nv_bfloat16 h = __float2bfloat16_rn(wi);
+    if (wb) wb[i] = h;
+    if (wbt) wbt[(i % cols) * rows + i / cols] = h;
   }
 }
 
-__global__ void k_mlp_to_bf16(const float* __restrict__ w, long long n, __nv_bfloat16* __restrict__ wb) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    wb[i] = __float2bfloat16_rn(w[i]);
+// X (rows x cols FP32, row-major) as three bf16 slices x = s0 + s1 + s2 (an
+// exact split of the FP32 value): S[s][r][c] for r < rows (row stride cols,
+// slice stride s_stride) and T[s][c][r] for r < rows_pad (zero for r >=
+// rows; row stride t_ld, slice stride t_stride)
+__global__ void k_mlp_slices(const float* __restrict__ X, int rows, int cols, int rows_pad,
+                             __nv_bfloat16* __restrict__ S, long long s_stride, __nv_bfloat16* __restrict__ T,
+                             int t_ld, long long t_stride) {
+  const long long tot = (long long)rows_pad * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / cols), c = (int)(t % cols);
+    float v = r < rows ? X[t] : 0.f;
+    for (int sl = 0; sl < 3; ++sl) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      v -= __bfloat162float(h);
+      if (S && r < rows) S[sl * s_stride + t] = h;
+      if (T) T[sl * t_stride + (long long)c * t_ld + r] = h;
+    }
+  }
+}
+
+// bf16 copy of w (rows x cols, row-major) and of its transpose
+__global__ void k_mlp_to_bf16(const float* __restrict__ w, long long n, __nv_bfloat16* __restrict__ wb,
+                              __nv_bfloat16* __restrict__ wbt, int rows, int cols) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(w[i]);
+    wb[i] = h;
+    wbt[(i % cols) * rows + i / cols] = h;
+  }
 }
 
 template <typename TB>
@@ -172,34 +212,160 @@ kp_status gemm(kp_mlp* p, int M, int N, int K, const float* A, long long sam, lo
   return KP_OK;
 }
 
+// operand of a tensor-core product: rows x K bf16, `slices` blocks of
+// `tstride` elements
+GemmOp op_of(const void* ptr, int rows, int K, long long ld, long long tstride, int slices) {
+  GemmOp o;
+  o.ptr = ptr;
+  o.rows = rows;
+  o.K = K;
+  o.ld = ld;
+  o.tstride = tstride;
+  o.nterm_idx = slices;
+  return o;
+}
+
+// the tensor-core plans of one batch size (built at its first use)
+kp_status plans_for(kp_mlp* p, int batch, kp_mlp::Plans** out) {
+  auto it = p->plans.find(batch);
+  if (it != p->plans.end()) {
+    *out = &it->second;
+    return KP_OK;
+  }
+  kp_mlp::Plans P;
+  const int bp = (batch + 7) / 8 * 8;
+  const int w = p->width;
+  static const int acc_a[6] = {0, 0, 1, 0, 1, 2}, acc_b[6] = {0, 1, 0, 2, 1, 0};
+  for (int l = 0; l < p->L - 1; ++l) {
+    const int in = p->in[l];
+    // forward: act[l + 1] = GELU(sum_s S_s(act[l]) W_l^T + c_l), pre[l] keeps the sum
+    GemmDesc f;
+    f.M = batch;
+    f.N = w;
+    f.K = in;
+    f.npairs = 3;
+    for (int q = 0; q < 3; ++q) {
+      f.sa[q] = q;
+      f.sb[q] = 0;
+    }
+    f.A = op_of(p->actS[l], batch, in, in, (long long)p->bpad * in, 3);
+    f.B = op_of(p->Wb[l], w, in, in, (long long)w * in, 1);
+    f.epi.mode = EPI_F32;
+    f.epi.out = p->act[l + 1];
+    f.epi.ldd = w;
+    f.epi.bias = p->c[l];
+    f.epi.pre = p->pre[l];
+    f.epi.act = 1;
+    TcGemmPlan* pf = nullptr;
+    KP_TRY(tc_plan_create(p->tc, f, TC_BF16, 1, &pf));
+    P.fwd.push_back(pf);
+    // weight gradient: gW_l[o][i] = sum_b g[b][o] act_l[b][i] over the padded batch (six slice pairs)
+    GemmDesc d;
+    d.M = w;
+    d.N = in;
+    d.K = bp;
+    d.npairs = 6;
+    for (int q = 0; q < 6; ++q) {
+      d.sa[q] = acc_a[q];
+      d.sb[q] = acc_b[q];
+    }
+    d.A = op_of(p->gT, w, bp, p->bpad, (long long)w * p->bpad, 3);
+    d.B = op_of(p->actT[l], in, bp, p->bpad, (long long)in * p->bpad, 3);
+    d.epi.mode = EPI_F32;
+    d.epi.out = p->gW[l];
+    d.epi.ldd = in;
+    TcGemmPlan* pd = nullptr;
+    KP_TRY(tc_plan_create(p->tc, d, TC_BF16, 1, &pd));
+    P.dW.push_back(pd);
+    // input gradient (l > 0): gn[b][i] = (sum_o g[b][o] W_l[o][i]) GELU'(pre_(l-1)[b][i])
+    TcGemmPlan* px = nullptr;
+    if (l > 0) {
+      GemmDesc x;
+      x.M = batch;
+      x.N = in;
+      x.K = w;
+      x.npairs = 3;
+      for (int q = 0; q < 3; ++q) {
+        x.sa[q] = q;
+        x.sb[q] = 0;
+      }
+      x.A = op_of(p->gS, batch, w, w, (long long)p->bpad * w, 3);
+      x.B = op_of(p->WbT[l], in, w, w, (long long)in * w, 1);
+      x.epi.mode = EPI_F32;
+      x.epi.out = nullptr;  // set per call (ping-pong buffer)
+      x.epi.ldd = in;
+      x.epi.pre = p->pre[l - 1];
+      x.epi.act = 2;
+      KP_TRY(tc_plan_create(p->tc, x, TC_BF16, 1, &px));
+    }
+    P.dX.push_back(px);
+  }
+  auto ins = p->plans.emplace(batch, P);
+  *out = &ins.first->second;
+  return KP_OK;
+}
+
+kp_status slices(kp_mlp* p, const float* X, int batch, int cols, __nv_bfloat16* S, __nv_bfloat16* T) {
+  const int bp = (batch + 7) / 8 * 8;
+  const long long tot = (long long)bp * cols;
+  const int g = (int)std::max(1LL, std::min((tot + 255) / 256, 2048LL));
+  k_mlp_slices<<<g, 256, 0, p->stream>>>(X, batch, cols, bp, S, (long long)p->bpad * cols, T, p->bpad,
+                                         (long long)cols * p->bpad);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
 kp_status forward(kp_mlp* p, const float* X, int batch) {
   const int g = std::max(1, std::min((batch * p->n_in + 255) / 256, 1024));
   k_mlp_normalize<<<g, 256, 0, p->stream>>>(X, batch, p->n_in, p->mean, p->inv_std, p->act[0]);
-  for (int l = 0; l < p->L; ++l) {
-    const bool last = l == p->L - 1;
-    // act[l + 1] = GELU(act[l] W_l^T + c_l) (pre[l] keeps the sum); the last layer has no GELU
-    KP_TRY(gemm<__nv_bfloat16>(p, batch, p->out[l], p->in[l], p->act[l], p->in[l], 1, p->Wb[l], 1, p->in[l],
-                               p->act[l + 1], p->out[l], last ? MEPI_BIAS : MEPI_BIAS_GELU, p->c[l], p->pre[l],
-                               nullptr));
+  kp_mlp::Plans* P = nullptr;
+  KP_TRY(plans_for(p, batch, &P));
+  for (int l = 0; l < p->L - 1; ++l) {
+    // act[l + 1] = GELU(act[l] W_l^T + c_l) on the tensor cores (pre[l] keeps the sum)
+    KP_TRY(slices(p, p->act[l], batch, p->in[l], p->actS[l], p->actT[l]));
+    KP_TRY(tc_plan_run(p->tc, P->fwd[l], nullptr));
   }
+  // the scalar output layer: act[L] = act[L - 1] W^T + c (no GELU)
+  const int l = p->L - 1;
+  KP_TRY(gemm<__nv_bfloat16>(p, batch, p->out[l], p->in[l], p->act[l], p->in[l], 1, p->Wb[l], 1, p->in[l],
+                             p->act[l + 1], p->out[l], MEPI_BIAS, p->c[l], p->pre[l], nullptr));
   return KP_OK;
 }
 
 // loss and the gradients of every weight and bias into gW / gc
 kp_status backward(kp_mlp* p, const float* X, const float* y, int batch) {
   KP_TRY(forward(p, X, batch));
+  kp_mlp::Plans* P = nullptr;
+  KP_TRY(plans_for(p, batch, &P));
   float* g = p->g0;
   float* gn = p->g1;
   k_mlp_loss<<<1, MLP_THREADS, 0, p->stream>>>(p->act[p->L], y, batch, g, p->loss_dev);
   for (int l = p->L - 1; l >= 0; --l) {
-    // gW_l[o][i] = sum_b g[b][o] act_l[b][i] ; gc_l[o] = sum_b g[b][o]
-    KP_TRY(gemm<float>(p, p->out[l], p->in[l], batch, g, 1, p->out[l], p->act[l], p->in[l], 1, p->gW[l], p->in[l],
-                       MEPI_STORE, nullptr, nullptr, nullptr));
+    if (l == p->L - 1) {
+      // the scalar output layer (SIMT): gW[0][i] = sum_b g[b] act_l[b][i]
+      KP_TRY(gemm<float>(p, p->out[l], p->in[l], batch, g, 1, p->out[l], p->act[l], p->in[l], 1, p->gW[l], p->in[l],
+                         MEPI_STORE, nullptr, nullptr, nullptr));
+    } else {
+      // gW_l[o][i] = sum_b g[b][o] act_l[b][i] on the tensor cores
+      KP_TRY(slices(p, g, batch, p->out[l], p->gS, p->gT));
+      KP_TRY(tc_plan_run(p->tc, P->dW[l], nullptr));
+    }
+    // gc_l[o] = sum_b g[b][o]
     k_mlp_colsum<<<(p->out[l] + 255) / 256, 256, 0, p->stream>>>(g, batch, p->out[l], p->gc[l]);
     if (l > 0) {
       // gn[b][i] = (sum_o g[b][o] W_l[o][i]) GELU'(pre_(l-1)[b][i])
-      KP_TRY(gemm<__nv_bfloat16>(p, batch, p->in[l], p->out[l], g, p->out[l], 1, p->Wb[l], p->in[l], 1, gn,
-                                 p->in[l], MEPI_GELU_GRAD, nullptr, nullptr, p->pre[l - 1]));
+      if (l == p->L - 1) {
+        KP_TRY(gemm<__nv_bfloat16>(p, batch, p->in[l], p->out[l], g, p->out[l], 1, p->Wb[l], p->in[l], 1, gn,
+                                   p->in[l], MEPI_GELU_GRAD, nullptr, nullptr, p->pre[l - 1]));
+      } else {
+        EpiParams e;
+        e.mode = EPI_F32;
+        e.out = gn;
+        e.ldd = p->in[l];
+        e.pre = p->pre[l - 1];
+        e.act = 2;
+        KP_TRY(tc_plan_run(p->tc, P->dX[l], &e));
+      }
       std::swap(g, gn);
     }
   }
@@ -297,6 +463,28 @@ extern "C" kp_status kp_mlp_create(kp_mlp** out, int device, void* cuda_stream, 
     p->pre[l] = pr;
     p->Wb.push_back(wb);
   }
+  // tensor-core products: the context that owns their plans, the operand slices
+  p->bpad = (max_batch + 7) / 8 * 8;
+  if (s == KP_OK) s = kp_create(&p->tc, device, p->stream);
+  if (s == KP_OK && !tc_device_supported(p->tc)) {
+    kp_set_error("kp_mlp_create: the tensor-core products need an sm_103 device");
+    s = KP_ENOTSUP;
+  }
+  auto ab = [&](__nv_bfloat16** q, long long n) { return mlp_alloc(p, (void**)q, sizeof(__nv_bfloat16) * (size_t)n); };
+  for (int l = 0; l < p->L - 1 && s == KP_OK; ++l) {
+    __nv_bfloat16 *aS = nullptr, *aT = nullptr;
+    s = ab(&aS, 3LL * p->bpad * p->in[l]);
+    if (s == KP_OK) s = ab(&aT, 3LL * p->bpad * p->in[l]);
+    p->actS.push_back(aS);
+    p->actT.push_back(aT);
+  }
+  if (s == KP_OK) s = ab(&p->gS, 3LL * p->bpad * width);
+  if (s == KP_OK) s = ab(&p->gT, 3LL * p->bpad * width);
+  for (int l = 0; l < p->L && s == KP_OK; ++l) {
+    __nv_bfloat16* t = nullptr;
+    s = ab(&t, (long long)p->out[l] * p->in[l]);
+    p->WbT.push_back(t);
+  }
   if (s != KP_OK) return fail(s);
   *out = p;
   return KP_OK;
@@ -306,6 +494,7 @@ extern "C" void kp_mlp_destroy(kp_mlp* p) {
   if (!p) return;
   cudaSetDevice(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->tc) kp_destroy(p->tc);
   for (void* a : p->allocs) cudaFree(a);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -332,7 +521,9 @@ extern "C" kp_status kp_mlp_set_params(kp_mlp* p, const float* params) {
     q += nw;
     KP_CUDA(cudaMemcpyAsync(p->c[l], q, sizeof(float) * p->out[l], cudaMemcpyHostToDevice, p->stream));
     q += p->out[l];
-    k_mlp_to_bf16<<<std::max(1LL, std::min((nw + 255) / 256, 1024LL)), 256, 0, p->stream>>>(p->Wm[l], nw, p->Wb[l]);
+    k_mlp_to_bf16<<<std::max(1LL, std::min((nw + 255) / 256, 1024LL)), 256, 0, p->stream>>>(p->Wm[l], nw, p->Wb[l],
+                                                                                              p->WbT[l], p->out[l],
+                                                                                              p->in[l]);
     KP_CUDA(cudaMemsetAsync(p->mW[l], 0, sizeof(float) * nw, p->stream));
     KP_CUDA(cudaMemsetAsync(p->vW[l], 0, sizeof(float) * nw, p->stream));
     KP_CUDA(cudaMemsetAsync(p->mc[l], 0, sizeof(float) * p->out[l], p->stream));
@@ -425,9 +616,10 @@ extern "C" kp_status kp_mlp_train_step(kp_mlp* p, const float* X, const float* y
   for (int l = 0; l < p->L; ++l) {
     const long long nw = (long long)p->out[l] * p->in[l];
     k_mlp_adam<<<std::max(1LL, std::min((nw + 255) / 256, 1024LL)), 256, 0, p->stream>>>(
-        p->Wm[l], p->mW[l], p->vW[l], p->gW[l], nw, lr, b1, b2, eps, c1, c2, p->Wb[l]);
+        p->Wm[l], p->mW[l], p->vW[l], p->gW[l], nw, lr, b1, b2, eps, c1, c2, p->Wb[l], p->WbT[l], p->out[l],
+        p->in[l]);
     k_mlp_adam<<<1, 256, 0, p->stream>>>(p->c[l], p->mc[l], p->vc[l], p->gc[l], p->out[l], lr, b1, b2, eps, c1, c2,
-                                         nullptr);
+                                         nullptr, nullptr, 1, p->out[l]);
   }
   KP_CUDA(cudaGetLastError());
   if (loss) {
