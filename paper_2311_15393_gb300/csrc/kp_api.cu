@@ -99,6 +99,9 @@ void kp_free_all(kp_ctx* ctx) {
   for (auto& b : ctx->allocs) ctx->pool.emplace(b.second, b.first);
   ctx->allocs.clear();
   tc_plans_free(ctx);
+  for (auto& t : ctx->lam_tc) t = kp_ctx::LamTc();
+  ctx->lam_img16 = ctx->lam_t16 = nullptr;
+  ctx->lam_t32 = ctx->lam_o32 = nullptr;
   ctx->lam_ws = nullptr;
   ctx->lam_sigma_ready = false;
   ctx->Uc32 = ctx->Ur32 = ctx->Vc32 = ctx->Vr32 = nullptr;
@@ -262,6 +265,8 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
     ctx->tc_pair_override = (int)value;
   } else if (!strcmp(name, "setup_fp64")) {
     ctx->force_setup_fp64 = value != 0.0;
+  } else if (!strcmp(name, "setup_half")) {
+    ctx->force_setup_half = value != 0.0;
   } else {
     kp_set_error("kp_set_option: unknown option '%s'", name);
     return KP_EINVAL;

@@ -1147,48 +1147,82 @@ kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, T
 }
 
 namespace {
-__global__ void k_f64_to_bf16(const double* __restrict__ in, long long n, __nv_bfloat16* __restrict__ out) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    out[t] = __float2bfloat16_rn((float)in[t]);
+// bf16 slices of FP64 or FP32 data (the FP32-rounded value, split exactly
+// into `slices` parts): out[s * n + t]
+template <typename T>
+__global__ void k_to_bf16_slices(const T* __restrict__ in, long long n, int slices, __nv_bfloat16* __restrict__ out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    float v = (float)in[t];
+    for (int sl = 0; sl < slices; ++sl) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      out[sl * n + t] = h;
+      v -= __bfloat162float(h);
+    }
+  }
 }
 }  // namespace
 
-// D = A B^T with bf16 inputs and FP32 accumulation on the tensor cores: A is
-// rows_a x K and B rows_b x K (FP64, K-major, leading dimension K), D is
-// row-major rows_a x rows_b FP32.  The half-precision products of the
-// setup (option setup_half); K a multiple of 8.
-kp_status half_product(kp_ctx* ctx, const double* A, int rows_a, const double* B, int rows_b, int K, float* D) {
-  __nv_bfloat16 *a16 = nullptr, *b16 = nullptr;
-  const long long na = (long long)rows_a * K, nb = (long long)rows_b * K;
-  KP_TRY(kp_alloc(ctx, (void**)&a16, sizeof(__nv_bfloat16) * na));
-  KP_TRY(kp_alloc(ctx, (void**)&b16, sizeof(__nv_bfloat16) * nb));
-  const int ga = (int)std::max(1LL, std::min((na + 255) / 256, (long long)ctx->sm_count * 16));
-  const int gb = (int)std::max(1LL, std::min((nb + 255) / 256, (long long)ctx->sm_count * 16));
-  k_f64_to_bf16<<<ga, 256, 0, ctx->stream>>>(A, na, a16);
-  k_f64_to_bf16<<<gb, 256, 0, ctx->stream>>>(B, nb, b16);
-  ctx->launches += 2;
+kp_status tc_operand_slices(kp_ctx* ctx, const void* in, bool f64, long long n, int slices, void* out) {
+  const int g = (int)std::max(1LL, std::min((n + 255) / 256, (long long)ctx->sm_count * 16));
+  if (f64)
+    k_to_bf16_slices<double><<<g, 256, 0, ctx->stream>>>((const double*)in, n, slices, (__nv_bfloat16*)out);
+  else
+    k_to_bf16_slices<float><<<g, 256, 0, ctx->stream>>>((const float*)in, n, slices, (__nv_bfloat16*)out);
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+kp_status tc_product_plan(kp_ctx* ctx, const void* a16, int rows_a, const void* b16, int rows_b, int K, int slices,
+                          float* D, TcGemmPlan** out) {
+  static const int acc_a[6] = {0, 0, 1, 0, 1, 2}, acc_b[6] = {0, 1, 0, 2, 1, 0};
   GemmDesc g;
   g.M = rows_a;
   g.N = rows_b;
   g.K = K;
+  g.npairs = slices == 3 ? 6 : 1;
+  for (int q = 0; q < g.npairs; ++q) {
+    g.sa[q] = acc_a[q];
+    g.sb[q] = acc_b[q];
+  }
   g.A.ptr = a16;
   g.A.rows = rows_a;
   g.A.K = K;
   g.A.ld = K;
-  g.A.tstride = na;
-  g.A.nterm_idx = 1;
+  g.A.tstride = (long long)rows_a * K;
+  g.A.nterm_idx = slices;
   g.B.ptr = b16;
   g.B.rows = rows_b;
   g.B.K = K;
   g.B.ld = K;
-  g.B.tstride = nb;
-  g.B.nterm_idx = 1;
+  g.B.tstride = (long long)rows_b * K;
+  g.B.nterm_idx = slices;
   g.epi.mode = EPI_F32;
   g.epi.out = D;
   g.epi.ldd = rows_b;
+  return tc_plan_create(ctx, g, TC_BF16, 1, out);
+}
+
+// D = A B^T on the tensor cores: A rows_a x K and B rows_b x K (FP64 or FP32,
+// K-major, leading dimension K), D row-major rows_a x rows_b FP32; the
+// inputs as `slices` bf16 slices (1: half-precision inputs; 3: an exact
+// split of the FP32 values, six slice products, FP32-level result), FP32
+// accumulation.  K a multiple of 8.
+kp_status tc_product(kp_ctx* ctx, const void* A, bool a64, int rows_a, const void* B, bool b64, int rows_b, int K,
+                     float* D, int slices) {
+  __nv_bfloat16 *a16 = nullptr, *b16 = nullptr;
+  const long long na = (long long)rows_a * K, nb = (long long)rows_b * K;
+  KP_TRY(kp_alloc(ctx, (void**)&a16, sizeof(__nv_bfloat16) * na * slices));
+  KP_TRY(kp_alloc(ctx, (void**)&b16, sizeof(__nv_bfloat16) * nb * slices));
+  KP_TRY(tc_operand_slices(ctx, A, a64, na, slices, a16));
+  KP_TRY(tc_operand_slices(ctx, B, b64, nb, slices, b16));
   TcGemmPlan* pl = nullptr;
-  KP_TRY(tc_plan_create(ctx, g, TC_BF16, 1, &pl));
+  KP_TRY(tc_product_plan(ctx, a16, rows_a, b16, rows_b, K, slices, D, &pl));
   return tc_plan_run(ctx, pl, nullptr);
+}
+
+kp_status half_product(kp_ctx* ctx, const double* A, int rows_a, const double* B, int rows_b, int K, float* D) {
+  return tc_product(ctx, A, true, rows_a, B, true, rows_b, K, D, 1);
 }
 
 void tc_plan_set_epi(TcGemmPlan* plan, const EpiParams& e) {

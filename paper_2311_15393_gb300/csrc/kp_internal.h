@@ -181,6 +181,22 @@ struct kp_ctx {
   // inputs with FP32 accumulation on the tensor cores (FP32 vectors only)
   bool setup_half = false;
   bool force_setup_half = false;
+  // the setup's FP32 products on the tensor cores (inputs as three bf16
+  // slices, six slice products): FP32 vectors, a tcgen05 device, sizes
+  // multiples of 16
+  bool setup_tc = false;
+  // choose_lambda's spectral coefficients on the tensor cores (built once
+  // per setup): per basis (0: U, 1: V) the bases' slices and the two plans
+  struct LamTc {
+    void* L16 = nullptr;
+    void* R16 = nullptr;
+    TcGemmPlan* p1 = nullptr;
+    TcGemmPlan* p2 = nullptr;
+  } lam_tc[2];
+  void* lam_img16 = nullptr;  // slices of the image and of the intermediate
+  void* lam_t16 = nullptr;
+  float* lam_t32 = nullptr;   // FP32 intermediate and result
+  float* lam_o32 = nullptr;
   int* dev_status = nullptr;     // device status word
   double* dscal = nullptr;       // device scalars (see kp_solver.cu)
   double* red_part = nullptr;    // reduction partials
@@ -275,6 +291,15 @@ bool tc_device_supported(kp_ctx* ctx);
 // D (rows_a x rows_b row-major FP32) = A B^T, A rows_a x K and B rows_b x K
 // FP64 K-major, with bf16 inputs and FP32 accumulation on the tensor cores
 kp_status half_product(kp_ctx* ctx, const double* A, int rows_a, const double* B, int rows_b, int K, float* D);
+// the same with FP64 or FP32 inputs as 1 (half precision) or 3 (exact FP32
+// split, six slice products) bf16 slices
+kp_status tc_product(kp_ctx* ctx, const void* A, bool a64, int rows_a, const void* B, bool b64, int rows_b, int K,
+                     float* D, int slices);
+// pieces of tc_product for reuse: bf16 slices of an operand (out: slices x n)
+// and the plan of D = A B^T from sliced operands
+kp_status tc_operand_slices(kp_ctx* ctx, const void* in, bool f64, long long n, int slices, void* out);
+kp_status tc_product_plan(kp_ctx* ctx, const void* a16, int rows_a, const void* b16, int rows_b, int K, int slices,
+                          float* D, TcGemmPlan** out);
 
 // one-sided Jacobi SVD (FP64): A (m x n col-major, m >= n) -> U (m x n), s (n), V (n x n)
 kp_status jacobi_svd(kp_ctx* ctx, const double* A, int m, int n, double* U, double* s, double* V,

@@ -663,10 +663,14 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
       const int gb = std::max(1, std::min((int)(((long long)n * n + 255) / 256), ctx->sm_count * 8));
       KP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st));
       if (fast) {
-        gd.A.ptr = W32;
-        gd.B.ptr = W32;
-        gd.epi.out = G32;
-        KP_TRY(simt_gemm<float>(ctx, gd));
+        if (ctx->setup_tc && m % 8 == 0) {  // FP32-level product on the tensor cores
+          KP_TRY(tc_product(ctx, W32, false, n, W32, false, n, m, G32, 3));
+        } else {
+          gd.A.ptr = W32;
+          gd.B.ptr = W32;
+          gd.epi.out = G32;
+          KP_TRY(simt_gemm<float>(ctx, gd));
+        }
         k_gram_violations<float><<<gb, 256, 0, st>>>(G32, n, tol, floor, cnt);
       } else {
         gd.A.ptr = W;
@@ -820,6 +824,10 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
     gd.B.ld = n;
     gd.epi.mode = EPI_T;
     gd.epi.ldd = n;
+    if (ctx->setup_tc) {  // tensor cores: FP32-level (3 slices) or half precision (1)
+      KP_TRY(tc_product(ctx, C, true, n, X_rm, true, n, n, W32, ctx->setup_half ? 1 : 3));
+      return convert_f32_to_f64(ctx, W32, out, nn);
+    }
     if (fast) {
       KP_TRY(convert_f64_to_f32(ctx, X_rm, F32, nn));
       gd.A.ptr = C32;

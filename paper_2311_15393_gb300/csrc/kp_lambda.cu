@@ -445,6 +445,33 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
   auto kp_coeffs32 = [&](const float* img, const float* Lc, const float* Rr, double* out) -> kp_status {
     float* T32 = (float*)T;  // T holds N doubles: room for two FP32 images
     float* O32 = T32 + N;
+    if (ctx->setup_tc) {
+      // tensor cores, inputs as three bf16 slices (FP32-level products); the
+      // bases' slices and the plans are made once per setup
+      kp_ctx::LamTc& lt = ctx->lam_tc[Lc == ctx->Uc32 ? 0 : 1];
+      if (!ctx->lam_img16) {
+        KP_TRY(kp_alloc(ctx, &ctx->lam_img16, sizeof(__nv_bfloat16) * 3 * N));
+        KP_TRY(kp_alloc(ctx, &ctx->lam_t16, sizeof(__nv_bfloat16) * 3 * N));
+        KP_TRY(kp_alloc(ctx, (void**)&ctx->lam_t32, sizeof(float) * N));
+        KP_TRY(kp_alloc(ctx, (void**)&ctx->lam_o32, sizeof(float) * N));
+      }
+      if (!lt.p1) {
+        KP_TRY(kp_alloc(ctx, &lt.L16, sizeof(__nv_bfloat16) * 3 * (size_t)n_r * n_r));
+        KP_TRY(kp_alloc(ctx, &lt.R16, sizeof(__nv_bfloat16) * 3 * (size_t)n_c * n_c));
+        KP_TRY(tc_operand_slices(ctx, Lc, false, (long long)n_r * n_r, 3, lt.L16));
+        KP_TRY(tc_operand_slices(ctx, Rr, false, (long long)n_c * n_c, 3, lt.R16));
+        // T[i'][j] = sum_i Lc[i, i'] Y[i, j]; out[l][i'] = sum_j Rr[j, l] T[i'][j]
+        KP_TRY(tc_product_plan(ctx, lt.L16, n_r, ctx->lam_img16, n_c, n_r, 3, ctx->lam_t32, &lt.p1));
+        KP_TRY(tc_product_plan(ctx, lt.R16, n_c, ctx->lam_t16, n_r, n_c, 3, ctx->lam_o32, &lt.p2));
+      }
+      KP_TRY(tc_operand_slices(ctx, img, false, N, 3, ctx->lam_img16));
+      KP_TRY(tc_plan_run(ctx, lt.p1, nullptr));
+      KP_TRY(tc_operand_slices(ctx, ctx->lam_t32, false, N, 3, ctx->lam_t16));
+      KP_TRY(tc_plan_run(ctx, lt.p2, nullptr));
+      k_to_f64<float><<<gr, 256, 0, st>>>(ctx->lam_o32, N, out);
+      KP_LAUNCHED(ctx);
+      return KP_OK;
+    }
     GemmDesc g1;
     g1.M = n_r;
     g1.N = n_c;

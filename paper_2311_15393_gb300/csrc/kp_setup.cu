@@ -232,7 +232,9 @@ static kp_status projected_diag(kp_ctx* ctx, const double* F, const double* U, c
   g.epi.mode = EPI_T;
   g.epi.out = tmp;
   g.epi.ldd = n;
-  if (U32) {
+  if (U32 && ctx->setup_tc) {  // tensor cores: FP32-level (3 slices) or half precision (1)
+    KP_TRY(tc_product(ctx, F + blk, true, (rank - 1) * n, V, true, n, n, (float*)tmp, ctx->setup_half ? 1 : 3));
+  } else if (U32) {
     KP_TRY(convert_f64_to_f32(ctx, F + blk, F32, (rank - 1) * blk));
     g.A.ptr = F32;
     g.B.ptr = V32;
@@ -330,6 +332,8 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
   ctx->vec_prec = vec_prec;
   ctx->sigma_mode = sigma;
   ctx->setup_fp32 = vec_prec == KP_F32 && !ctx->force_setup_fp64;
+  ctx->setup_tc = ctx->setup_fp32 && n_r % 16 == 0 && n_c % 16 == 0 && tc_device_supported(ctx);
+  ctx->setup_half = ctx->setup_tc && ctx->force_setup_half;
   KP_CUDA(cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), ctx->stream));
 
   cudaStream_t st = ctx->stream;
