@@ -280,6 +280,13 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *   "tc_kblocks_per_stage" 1, 2 or 4 (4: 64-wide tiles only): k-blocks per
  *                     shared-memory ring stage (default 0 = 4 for 64-wide
  *                     tiles, 1 with two CTAs per SM, else 2)
+ *   "tc_autotune"     nonzero: at kp_setup each tensor-core GEMM shape's tile
+ *                     configuration (tile width, CTAs per SM, k-blocks per
+ *                     stage, CTA pairs) is chosen by timing the candidates
+ *                     (CUDA events, a scratch output); the choices are kept per
+ *                     process and, when the environment variable
+ *                     KPSVD_TUNE_CACHE names a file, read from and appended
+ *                     to it (one line per shape); default 0: the built-in rule
  *   "tc_pair"         0 (default): BF16 GEMMs whose 256 x 256 tiles fill most
  *                     SM pairs run on CTA pairs (tcgen05 cta_group::2, one
  *                     256 x 256 tile per pair of SMs); 1: never; 2: wherever

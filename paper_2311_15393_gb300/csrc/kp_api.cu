@@ -261,6 +261,8 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
       return KP_EINVAL;
     }
     ctx->pc_inner_iters = (int)value;
+  } else if (!strcmp(name, "tc_autotune")) {
+    ctx->tc_autotune = value != 0.0;
   } else if (!strcmp(name, "tc_pair")) {
     ctx->tc_pair_override = (int)value;
   } else if (!strcmp(name, "setup_fp64")) {

@@ -27,6 +27,12 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "kp_internal.h"
 #include "kp_vec.cuh"
@@ -1026,7 +1032,7 @@ bool tc_device_supported(kp_ctx* ctx) {
   return major == 10 && minor == 3;
 }
 
-kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, TcGemmPlan** out) {
+static kp_status tc_plan_create_one(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, TcGemmPlan** out) {
   if (g.npairs < 1 || g.npairs > KP_MAX_PAIRS || g.nkron < 1) {
     kp_set_error("tc_plan_create: bad term description");
     return KP_EINVAL;
@@ -1223,6 +1229,161 @@ kp_status tc_product(kp_ctx* ctx, const void* A, bool a64, int rows_a, const voi
 
 kp_status half_product(kp_ctx* ctx, const double* A, int rows_a, const double* B, int rows_b, int K, float* D) {
   return tc_product(ctx, A, true, rows_a, B, true, rows_b, K, D, 1);
+}
+
+// ------------------------------------------------------------- tile autotuner
+// With the option tc_autotune, each GEMM shape's tile configuration (tile
+// width, CTAs per SM, k-blocks per ring stage, CTA pairs) is picked by
+// timing the candidates: each runs once to warm up and three times between
+// CUDA events on the context's stream, writing an FP32 scratch output.  The
+// winners are kept per process and, when the environment variable
+// KPSVD_TUNE_CACHE names a file, read from and appended to it, one line per
+// shape: "kind M N K pairs terms batch_rows splits sms bn cps kps pair".
+namespace {
+struct TuneCfg {
+  int bn, cps, kps, pair;
+};
+std::mutex g_tune_mutex;
+std::map<std::string, TuneCfg> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string tune_key(const GemmDesc& g, int kind, int splits, int sms) {
+  char b[160];
+  std::snprintf(b, sizeof(b), "%d %d %d %d %d %d %d %d %d", kind, g.M, g.N, g.K, g.npairs, g.nkron, g.batch_rows,
+                splits, sms);
+  return b;
+}
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("KPSVD_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  int v[13];
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                     &v[7], &v[8], &v[9], &v[10], &v[11], &v[12]) == 13) {
+    char b[160];
+    std::snprintf(b, sizeof(b), "%d %d %d %d %d %d %d %d %d", v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8]);
+    g_tune_cache[b] = TuneCfg{v[9], v[10], v[11], v[12]};
+  }
+  std::fclose(f);
+}
+
+void tune_store(const std::string& key, const TuneCfg& c) {
+  g_tune_cache[key] = c;
+  const char* path = std::getenv("KPSVD_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), c.bn, c.cps, c.kps, c.pair);
+  std::fclose(f);
+}
+
+// the context's tile overrides set to one configuration, restored on exit
+struct OverrideScope {
+  kp_ctx* c;
+  int bn, cps, kps, pair;
+  OverrideScope(kp_ctx* ctx, const TuneCfg& t)
+      : c(ctx), bn(ctx->tc_bn_override), cps(ctx->tc_cps_override), kps(ctx->tc_kps_override),
+        pair(ctx->tc_pair_override) {
+    c->tc_bn_override = t.bn;
+    c->tc_cps_override = t.cps;
+    c->tc_kps_override = t.kps;
+    c->tc_pair_override = t.pair ? 2 : 1;
+  }
+  ~OverrideScope() {
+    c->tc_bn_override = bn;
+    c->tc_cps_override = cps;
+    c->tc_kps_override = kps;
+    c->tc_pair_override = pair;
+  }
+};
+
+void plan_discard(kp_ctx* ctx, TcGemmPlan* pl) {
+  auto& v = ctx->tc_plans;
+  v.erase(std::remove(v.begin(), v.end(), pl), v.end());
+  delete pl;
+}
+}  // namespace
+
+kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, TcGemmPlan** out) {
+  if (!ctx->tc_autotune) return tc_plan_create_one(ctx, g, kind, splits, out);
+  const std::string key = tune_key(g, kind, splits, ctx->sm_count);
+  TuneCfg best{0, 0, 0, 0};
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_load();
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best = it->second;
+      have = true;
+    }
+  }
+  if (!have) {
+    // candidates; configurations the shape does not allow fall back inside
+    // tc_plan_create_one and are skipped as duplicates of what it built
+    std::vector<TuneCfg> cand;
+    for (int bn : {64, 128, 256})
+      for (int cps : {1, 2})
+        for (int kps : {1, 2, 4}) {
+          if (cps == 2 && bn != 128) continue;
+          if (kps == 4 && bn != 64) continue;
+          if (bn > 64 && bn > g.N) continue;
+          cand.push_back(TuneCfg{bn, cps, kps, 0});
+        }
+    for (int kps : {1, 2}) cand.push_back(TuneCfg{256, 1, kps, 1});
+    float* scratch = nullptr;
+    KP_TRY(kp_alloc(ctx, (void**)&scratch, sizeof(float) * (size_t)g.M * g.N));
+    EpiParams e;
+    e.mode = EPI_F32;
+    e.out = scratch;
+    e.ldd = g.N;
+    cudaEvent_t e0, e1;
+    KP_CUDA(cudaEventCreate(&e0));
+    KP_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    std::vector<TuneCfg> seen;
+    kp_status res = KP_OK;
+    for (const TuneCfg& c : cand) {
+      TcGemmPlan* pl = nullptr;
+      {
+        OverrideScope os(ctx, c);
+        res = tc_plan_create_one(ctx, g, kind, splits, &pl);
+      }
+      if (res != KP_OK) break;
+      const TuneCfg got{pl->bn, pl->cps, pl->kps, pl->pair ? 1 : 0};
+      bool dup = false;
+      for (const TuneCfg& q : seen) dup |= q.bn == got.bn && q.cps == got.cps && q.kps == got.kps && q.pair == got.pair;
+      if (!dup && !(c.pair && !got.pair)) {
+        seen.push_back(got);
+        tc_plan_set_runtime(pl, nullptr, nullptr);
+        res = tc_plan_run(ctx, pl, &e);
+        if (res == KP_OK) res = cudaEventRecord(e0, ctx->stream) == cudaSuccess ? KP_OK : KP_ECUDA;
+        for (int r = 0; r < 3 && res == KP_OK; ++r) res = tc_plan_run(ctx, pl, &e);
+        if (res == KP_OK && (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+          res = KP_ECUDA;
+        float ms = 0.f;
+        if (res == KP_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (res == KP_OK && ms < best_ms) {
+          best_ms = ms;
+          best = got;
+        }
+      }
+      plan_discard(ctx, pl);
+      if (res != KP_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    KP_TRY(res);
+    KP_TRY(read_status(ctx));
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_store(key, best);
+  }
+  OverrideScope os(ctx, best);
+  return tc_plan_create_one(ctx, g, kind, splits, out);
 }
 
 void tc_plan_set_epi(TcGemmPlan* plan, const EpiParams& e) {

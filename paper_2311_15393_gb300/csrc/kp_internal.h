@@ -164,6 +164,7 @@ struct kp_ctx {
   int tc_cps_override = 0;  // 1 / 2: fixed CTAs per SM for 128-wide tiles
   int tc_kps_override = 0;  // 1 / 2: fixed k-blocks per ring stage
   int tc_pair_override = 0;  // 1: no CTA-pair tiles; 2: CTA-pair tiles wherever the shape allows
+  bool tc_autotune = false;  // pick each GEMM shape's tile configuration by timing (cached)
 
   // device allocations: ctx_block lives with the context, allocs with the
   // problem; a new kp_setup returns the previous problem's blocks to `pool`,

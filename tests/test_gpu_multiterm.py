@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from gpu_common import OracleProblem, lib, rel, torch, vt
-from oracle import kpsvd as okp, lam as olam, pcg as opcg
+from oracle import forward, kpsvd as okp, lam as olam, pcg as opcg
 from paper_2311_15393_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -69,14 +69,15 @@ def test_multiterm_fpcg_iterates_match_oracle(kpsvd, k, inner):
 
 def test_multiterm_reduced_precision_solve(kpsvd):
     """256 x 256, rank-4 operator with a strongly non-separable PSF (rho 0.85),
-    BF16 operator, FP16 preconditioner: FPCG with the two-term preconditioner
-    (2 inner steps) reaches the oracle's x_lambda to 1e-4, within +3
-    iterations of the oracle's FP64 multi-term FPCG.  This problem's
-    attainable accuracy with FP32 vectors lies at the 1e-7 tolerance: the
-    solve may also stop as stagnated (the true residual no longer halves)
-    within twice the tolerance, which the error check then covers."""
+    5% noise, BF16 operator, FP16 preconditioner: FPCG with the two-term
+    preconditioner (2 inner steps) reaches the oracle's x_lambda to 1e-4,
+    within +3 iterations of the oracle's FP64 multi-term FPCG.  (At 1% noise
+    the GCV lambda puts FP32 vectors' attainable accuracy right at the 1e-7
+    tolerance, where the solve ends converged or stagnated by rounding
+    details; 5% noise keeps the comparison about the preconditioner.)"""
     psf = synth.gaussian_psf(256, 256, 128, 128, 4.0, 2.0, 0.85)
     pr = OracleProblem("deblur256_fp32", n=256, psf=psf, rank=4)
+    pr.B, _ = forward.observe(pr.op, pr.P.x_true, pr.P.noise_dirs[0], 0.05)
     lam = olam.choose_lambda(pr.kp, pr.B, "gcv")
     x_star = opcg.tik_exact(pr.op, pr.kp, pr.B, lam, tol=1e-10)
     _, io = opcg.tik_fpcg_multiterm(pr.op, pr.kp, pr.B, lam, 2, 2, 1e-7, 500)
@@ -88,7 +89,7 @@ def test_multiterm_reduced_precision_solve(kpsvd):
         err = rel(kpsvd.from_device(x, 256, 256), x_star)
     print(f"two-term preconditioner: status {info.status}, {info.iters} iterations (oracle {io.iters}; one term "
           f"{i1.iters}), rel_res {info.rel_res:.3e}, rel. error {err:.2e}")
-    assert info.status == kpsvd.KP_OK or (info.status == kpsvd.KP_ENOCONV and info.rel_res < 2e-7)
+    assert info.status == kpsvd.KP_OK
     assert err < 1e-4
     assert info.iters <= io.iters + 3
 
