@@ -59,23 +59,15 @@ __global__ void k_after_replace(double* s, int* f, double* hist, int hist_cap) {
 
 // ---------------------------------------------------------------- device-side loop
 // The iteration as a CUDA graph while loop, with the residual replacement in
-// a nested if: per iteration half_a, then k_loop_decide_a (is a replacement
-// due: the reliable-update rule or a convergence / maxit stop with a reduced-
-// precision operator), then if so the replacement and k_loop_after_replace,
-// then k_loop_decide_b (continue while no stop is flagged), then half_b
+// a nested if: per iteration half_a, whose x / r update ends (in the last
+// block of its reduction) by deciding whether a replacement is due (the
+// reliable-update rule, or a convergence / maxit stop with a reduced-
+// precision operator) and whether the loop goes on; then, if due, the
+// replacement and k_loop_after_replace (which decides the loop); then half_b
 // (whose kernels skip when a stop is flagged).  The host launches the graph
 // once and reads the flags after it.
-__global__ void k_loop_decide_a(int* f, int reliable, cudaGraphConditionalHandle h_replace) {
-  const int reason = f[F_REASON];
-  int repl = 0;
-  if (f[F_PAUSE] && !(reason & (R_NUMERIC | R_BREAKDOWN)) && reliable && (reason & (R_CONV | R_REPLACE | R_MAXIT))) {
-    repl = 1;
-    f[F_SAVED] = reason;
-  }
-  cudaGraphSetConditional(h_replace, repl);
-}
 // after a replacement: k_after_replace's rule, a maxit stop stays a stop
-__global__ void k_loop_after_replace(double* s, int* f, double* hist, int hist_cap) {
+__global__ void k_loop_after_replace(double* s, int* f, double* hist, int hist_cap, cudaGraphConditionalHandle h_loop) {
   const double rr = s[S_RR];
   const int it = f[F_ITER];
   if (it < hist_cap) hist[it] = sqrt(rr / s[S_RR0]);
@@ -97,13 +89,7 @@ __global__ void k_loop_after_replace(double* s, int* f, double* hist, int hist_c
     f[F_REASON] = 0;
     f[F_PAUSE] = 0;
   }
-}
-// continue while no stop is flagged; F_GUARD counts body runs and ends the
-// loop in any case a few runs past maxit
-constexpr int F_GUARD = 15;
-__global__ void k_loop_decide_b(int* f, cudaGraphConditionalHandle h_loop) {
-  const int runs = ++f[F_GUARD];
-  cudaGraphSetConditional(h_loop, (f[F_PAUSE] || runs > f[F_MAXIT] + 8) ? 0u : 1u);
+  cudaGraphSetConditional(h_loop, (f[F_PAUSE] || f[F_GUARD] > f[F_MAXIT] + 8) ? 0u : 1u);
 }
 
 struct SolveBufs {
@@ -121,8 +107,13 @@ static SolveBufs bufs(kp_ctx* ctx) {
   return b;
 }
 
+// conditions of the loop graph, set by the x / r update's last block
+struct LoopConds {
+  cudaGraphConditionalHandle h_rep = 0, h_loop = 0;
+};
+
 // first half of an iteration: q = K p, alpha, x/r update, convergence flags
-static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
+static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2, const LoopConds* lc) {
   const long long N = (long long)ctx->n_r * ctx->n_c;
   const bool f64 = ctx->vec_prec == KP_F64;
   const int* fl = ctx->dflags;
@@ -135,6 +126,11 @@ static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2) {
   pc.kind = POST_CHECK;
   pc.hist = ctx->hist;
   pc.hist_cap = ctx->hist_cap;
+  if (lc) {
+    pc.cond = 1;
+    pc.h_rep = lc->h_rep;
+    pc.h_loop = lc->h_loop;
+  }
   bool fused = false;
   KP_TRY(op_apply_K(ctx, B.p, B.q, lam2, op_inner_slices(ctx) > 0, fl, s + S_PQ, &pa, &fused));
   if (!fused) KP_TRY(dot2_dev(ctx, B.p, B.q, nullptr, N, f64, s + S_PQ, fl, pa));
@@ -165,7 +161,8 @@ static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2_pc, bool na
 // (cg_fusable): the K application's term sum also gives max |q|, so the
 // update writes the preconditioner's narrow input with a scale bounded from
 // max |r_old| + |alpha| max |q| >= max |r_new|, known before the update.
-static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2, double lam2_pc) {
+static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2, double lam2_pc,
+                               const LoopConds* lc) {
   const long long N = (long long)ctx->n_r * ctx->n_c;
   const int* fl = ctx->dflags;
   double* s = ctx->dscal;
@@ -177,6 +174,11 @@ static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double 
   pc.kind = POST_CHECK;
   pc.hist = ctx->hist;
   pc.hist_cap = ctx->hist_cap;
+  if (lc) {
+    pc.cond = 1;
+    pc.h_rep = lc->h_rep;
+    pc.h_loop = lc->h_loop;
+  }
   bool fused = false;
   KP_TRY(op_apply_K(ctx, B.p, B.q, lam2, true, fl, s + S_QPQ, &pa, &fused, true));
   if (!fused) {
@@ -216,7 +218,7 @@ static kp_status replace_residual(kp_ctx* ctx, const SolveBufs& B, const void* b
   return KP_OK;
 }
 
-// ---- the device-side loop graph (see k_loop_decide_a)
+// ---- the device-side loop graph (see k_loop_after_replace)
 struct LoopGraph {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -227,9 +229,11 @@ struct LoopGraph {
   }
 };
 
-static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2);
+struct LoopConds;
+static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2, const LoopConds* lc);
 static kp_status half_b(kp_ctx* ctx, const SolveBufs& B, double lam2_pc, bool narrow_ready);
-static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2, double lam2_pc);
+static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2, double lam2_pc,
+                               const LoopConds* lc);
 
 static kp_status build_loop_graph(kp_ctx* ctx, const SolveBufs& B, const void* b, void* x, double lam2, double lam2_pc,
                                   bool reliable, bool folded, LoopGraph* L) {
@@ -249,12 +253,14 @@ static kp_status build_loop_graph(kp_ctx* ctx, const SolveBufs& B, const void* b
   KP_CUDA(cudaGraphConditionalHandleCreate(&h_rep, body, 0, 0));
   const long long l0 = ctx->launches;
   KP_CUDA(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  kp_status cs = folded ? half_a_folded(ctx, B, x, lam2, lam2_pc) : half_a(ctx, B, x, lam2);
+  LoopConds lc;
+  lc.h_rep = h_rep;
+  lc.h_loop = h_loop;
+  (void)reliable;  // the update's last block reads it from the tolerance slots
+  kp_status cs = folded ? half_a_folded(ctx, B, x, lam2, lam2_pc, &lc) : half_a(ctx, B, x, lam2, &lc);
   cudaGraph_t ibody = nullptr;
   bool aux_capturing = false;
   if (cs == KP_OK) {
-    k_loop_decide_a<<<1, 1, 0, st>>>(ctx->dflags, reliable ? 1 : 0, h_rep);
-    KP_LAUNCHED(ctx);
     cudaStreamCaptureStatus cst;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -283,7 +289,7 @@ static kp_status build_loop_graph(kp_ctx* ctx, const SolveBufs& B, const void* b
       ctx->stream = ctx->aux_stream;
       cs = replace_residual(ctx, B, b, x, lam2);
       if (cs == KP_OK) {
-        k_loop_after_replace<<<1, 1, 0, ctx->stream>>>(ctx->dscal, ctx->dflags, ctx->hist, ctx->hist_cap);
+        k_loop_after_replace<<<1, 1, 0, ctx->stream>>>(ctx->dscal, ctx->dflags, ctx->hist, ctx->hist_cap, h_loop);
         KP_LAUNCHED(ctx);
         if (folded) cs = pc_prepare_input(ctx, B.r, lam2_pc, ctx->dscal + S_RR, nullptr);
       }
@@ -298,13 +304,7 @@ static kp_status build_loop_graph(kp_ctx* ctx, const SolveBufs& B, const void* b
       }
     }
   }
-  if (cs == KP_OK) {
-    const long long l2 = ctx->launches;
-    k_loop_decide_b<<<1, 1, 0, st>>>(ctx->dflags, h_loop);
-    KP_LAUNCHED(ctx);
-    cs = half_b(ctx, B, lam2_pc, folded);
-    (void)l2;
-  }
+  if (cs == KP_OK) cs = half_b(ctx, B, lam2_pc, folded);
   if (aux_capturing) {
     cudaGraph_t tmp = nullptr;
     cudaStreamEndCapture(ctx->aux_stream, &tmp);
@@ -460,7 +460,7 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
       KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       kp_status cs = KP_OK;
       for (int i = 0; i < blk && cs == KP_OK; ++i) {
-        cs = folded ? half_a_folded(ctx, B, x, lam2, lam2_pc) : half_a(ctx, B, x, lam2);
+        cs = folded ? half_a_folded(ctx, B, x, lam2, lam2_pc, nullptr) : half_a(ctx, B, x, lam2, nullptr);
         if (cs == KP_OK) cs = half_b(ctx, B, lam2_pc, folded);
       }
       cudaError_t ce = cudaStreamEndCapture(st, &graph);

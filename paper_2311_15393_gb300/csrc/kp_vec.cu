@@ -89,7 +89,15 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T*
                                                            PostOp po) {
   KP_PDL_WAIT();
   KP_PDL_TRIGGER();
-  if (paused(flags)) return;
+  if (paused(flags)) {
+    // paused before the update (NaN or breakdown in alpha): inside the loop
+    // graph no replacement, and the loop ends
+    if (po.cond && blockIdx.x == 0 && threadIdx.x == 0) {
+      cudaGraphSetConditional(po.h_rep, 0u);
+      cudaGraphSetConditional(po.h_loop, 0u);
+    }
+    return;
+  }
   double v[2] = {0.0, 0.0};
   const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
   if constexpr (std::is_same<T, float>::value) {
@@ -297,7 +305,13 @@ __global__ void __launch_bounds__(VEC_THREADS)
                   double* partials, unsigned int* counter, double* out2, const int* flags, PostOp po) {
   KP_PDL_WAIT();
   KP_PDL_TRIGGER();
-  if (paused(flags)) return;
+  if (paused(flags)) {
+    if (po.cond && blockIdx.x == 0 && threadIdx.x == 0) {
+      cudaGraphSetConditional(po.h_rep, 0u);
+      cudaGraphSetConditional(po.h_loop, 0u);
+    }
+    return;
+  }
   __shared__ float s_sh;
   if (threadIdx.x == 0) {
     const double bound = out2[1] + fabs(*alpha_dev) * *qmax_dev;

@@ -23,6 +23,7 @@ enum {
 enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4, F_STAG = 5, F_SINCE = 6,
        F_SAVED = 7,   // device loop: the reason that triggered a residual replacement
        F_REPL = 8 };  // device loop: residual replacements done
+constexpr int F_GUARD = 15;  // device loop: passes of the loop body
 // the multi-term preconditioner's inner PCG keeps its scalars and flags in
 // blocks of their own, at these offsets into ctx->dscal / ctx->dflags
 constexpr int S_INNER = 64, F_INNER = 16;
@@ -38,6 +39,10 @@ enum { R_CONV = 1, R_REPLACE = 2, R_MAXIT = 4, R_BREAKDOWN = 8, R_NUMERIC = 16 }
 enum { POST_NONE = 0, POST_ALPHA = 1, POST_CHECK = 2, POST_BETA = 3 };
 struct PostOp {
   int kind = POST_NONE;
+  // POST_CHECK inside the device-side loop graph: also set the graph's
+  // conditions (residual replacement due; loop continues)
+  int cond = 0;
+  cudaGraphConditionalHandle h_rep = 0, h_loop = 0;
   double* s = nullptr;
   int* f = nullptr;
   double* hist = nullptr;
@@ -316,6 +321,24 @@ __device__ inline void run_post(const PostOp& po, const double* vals) {
     if (reason) {
       f[F_REASON] |= reason;
       f[F_PAUSE] = 1;
+    }
+    if (po.cond) {
+      // the loop graph's decisions: a reliable update is due (then the
+      // replacement's own step decides whether the loop goes on), or the
+      // loop stops, or it goes on; the loop also ends a few passes past maxit
+      const int rs = f[F_REASON];
+      unsigned int repl = 0u, loop = 1u;
+      if (f[F_PAUSE]) {
+        if (!(rs & (R_NUMERIC | R_BREAKDOWN)) && s[S_DELTA2] > 0.0 && (rs & (R_CONV | R_REPLACE | R_MAXIT))) {
+          repl = 1u;
+          f[F_SAVED] = rs;
+        } else {
+          loop = 0u;
+        }
+      }
+      if (++f[F_GUARD] > f[F_MAXIT] + 8) loop = 0u;
+      cudaGraphSetConditional(po.h_rep, repl);
+      cudaGraphSetConditional(po.h_loop, loop);
     }
   } else if (po.kind == POST_BETA) {  // vals[0] = z^T r, vals[1] = z^T r_old
     const double zn = vals[0], zo = vals[1], zr = s[S_ZR];
