@@ -408,6 +408,18 @@ kp_status kp_mlp_train_step(kp_mlp* mlp, const float* X, const float* labels, in
  * <= 0 or ms NULL.  Meaningful after a tik_pcg on the context. */
 kp_status kp_time_parts(kp_ctx* ctx, double lambda, int reps, double* ms, long long* launches);
 
+/* Test hook for the bounded device-side waits: one kernel waits on a barrier
+ * that nothing releases, bounded by limit_ms (0 < limit_ms <= 10000) of
+ * device time, and gives up as every bounded wait of the library does: it
+ * sets the timeout bit of the status word, and the call returns KP_ETIMEOUT.
+ * The status word is cleared again, and the context stays usable.
+ * Synchronises.  KP_EINVAL for a NULL context or a limit out of range.
+ *
+ * Fault injection (environment): KPSVD_FAULT=alloc:N makes the N-th device
+ * allocation of the library after the variable was set (or changed) fail
+ * with KP_ENOMEM, as a failing cudaMalloc would. */
+kp_status kp_test_bounded_wait(kp_ctx* ctx, double limit_ms);
+
 /* Number of this library's kernel launches issued on the context since the
  * last reset (reset = 1 clears it after reading). */
 long long kp_launch_count(kp_ctx* ctx, int reset);

@@ -3,6 +3,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <mutex>
 #include <string>
 
 #include <algorithm>
@@ -41,8 +43,31 @@ extern "C" const char* kp_status_str(kp_status s) {
   return "unknown status";
 }
 
+// Host-side fault injection: with KPSVD_FAULT=alloc:N in the environment the
+// N-th device allocation after the variable was set (or changed) fails as if
+// cudaMalloc had, so the error paths can be tested without touching the GPU.
+static bool injected_alloc_failure() {
+  static std::mutex mu;
+  static std::string last;
+  static long count = 0;
+  const char* v = std::getenv("KPSVD_FAULT");
+  std::lock_guard<std::mutex> lock(mu);
+  const std::string cur = v ? v : "";
+  if (cur != last) {
+    last = cur;
+    count = 0;
+  }
+  if (cur.compare(0, 6, "alloc:") != 0) return false;
+  const long n = std::atol(cur.c_str() + 6);
+  return n > 0 && ++count == n;
+}
+
 kp_status kp_alloc(kp_ctx* ctx, void** p, size_t bytes) {
   *p = nullptr;
+  if (injected_alloc_failure()) {
+    kp_set_error("device allocation of %zu bytes failed (injected by KPSVD_FAULT)", bytes);
+    return KP_ENOMEM;
+  }
   bytes = (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
   // smallest pooled block that fits and wastes at most half of itself
   auto it = ctx->pool.lower_bound(bytes);
@@ -106,6 +131,54 @@ void kp_free_all(kp_ctx* ctx) {
   ctx->lam_sigma_ready = false;
   ctx->Uc32 = ctx->Ur32 = ctx->Vc32 = ctx->Vr32 = nullptr;
   ctx->ready = false;
+}
+
+namespace {
+// a wait on an mbarrier that nothing arrives on, bounded by limit_ns (the
+// global timer): on give-up the status word's timeout bit is set
+__global__ void k_bounded_wait(int* status, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(1u) : "memory");
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(0u)
+        : "memory");
+    if (ok) return;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > limit_ns) {
+      atomicOr(status, DEV_ERR_TIMEOUT);
+      return;
+    }
+  }
+}
+}  // namespace
+
+// Test hook: one bounded device wait that nothing releases, so that the
+// timeout path (status word -> KP_ETIMEOUT, context still usable) can be
+// exercised without a GPU fault.
+extern "C" kp_status kp_test_bounded_wait(kp_ctx* ctx, double limit_ms) {
+  if (!ctx || !(limit_ms > 0.0) || limit_ms > 10000.0) {
+    kp_set_error("kp_test_bounded_wait: need a context and 0 < limit_ms <= 10000");
+    return KP_EINVAL;
+  }
+  KP_CUDA(cudaSetDevice(ctx->device));
+  KP_TRY(kp_enter(ctx));
+  KP_CUDA(cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), ctx->stream));
+  k_bounded_wait<<<1, 1, 0, ctx->stream>>>(ctx->dev_status, (unsigned long long)(limit_ms * 1e6));
+  KP_LAUNCHED(ctx);
+  KP_CUDA(cudaGetLastError());
+  const kp_status st = read_status(ctx);
+  KP_CUDA(cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  const kp_status l = kp_leave(ctx);
+  return st != KP_OK ? st : l;
 }
 
 kp_status read_status(kp_ctx* ctx) {

@@ -28,7 +28,7 @@ N_FEAT = 256  # spectral features per problem (kp_lambda_features, the MLP's inp
 # every function declared in include/kpsvd.h
 EXPORTS = ["kp_create", "kp_destroy", "kp_setup", "kp_forward", "tik_pcg", "choose_lambda", "kp_apply_A",
            "kp_apply_K", "kp_apply_Minv", "kp_get_spectrum", "kp_get_terms", "kp_get_kpsvd", "kp_get_rank",
-           "kp_set_option", "kp_launch_count", "kp_time_parts", "kp_status_str", "kp_last_error", "kp_apply_Minv_noalloc",
+           "kp_set_option", "kp_launch_count", "kp_time_parts", "kp_test_bounded_wait", "kp_status_str", "kp_last_error", "kp_apply_Minv_noalloc",
            "kp_solve_batch", "kp_lambda_features", "kp_mlp_create", "kp_mlp_destroy", "kp_mlp_param_count",
            "kp_mlp_set_params", "kp_mlp_get_params", "kp_mlp_forward", "kp_mlp_gradients", "kp_mlp_train_step"]
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "kp_set_option": ([vp, ctypes.c_char_p, d], i),
         "kp_launch_count": ([vp, i], ctypes.c_longlong),
         "kp_time_parts": ([vp, d, i, dp, ctypes.POINTER(ctypes.c_longlong)], i),
+        "kp_test_bounded_wait": ([vp, d], i),
         "kp_status_str": ([i], ctypes.c_char_p),
         "kp_last_error": ([], ctypes.c_char_p),
         "kp_apply_Minv_noalloc": ([vp, vp, vp, i, i, d, vp, vp, vp], i),
@@ -296,6 +297,10 @@ class KpContext:
 
     def kp_launch_count(self, reset: bool = False) -> int:
         return int(_lib.kp_launch_count(self._h, 1 if reset else 0))
+
+    def kp_test_bounded_wait(self, limit_ms: float) -> int:
+        """Status of one bounded device wait that nothing releases (KP_ETIMEOUT)."""
+        return int(_lib.kp_test_bounded_wait(self._h, limit_ms))
 
     def kp_time_parts(self, lam: float, reps: int = 20):
         """Device ms per launch and kernels per launch of the iteration's parts:
