@@ -56,7 +56,11 @@ def parse():
                          "metric)")
     ap.add_argument("--train", type=int, default=20000, help="learned_lambda: training problems")
     ap.add_argument("--eval", type=int, default=512, help="learned_lambda: evaluation problems")
-    ap.add_argument("--workers", type=int, default=8, help="batched64: concurrent problems")
+    ap.add_argument("--workers", type=int, default=0,
+                    help="batched64: 0 = grouped form (one launch per iteration step over all problems, one host "
+                         "thread); > 0 = that many host threads, one context each")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batched64 (grouped): tile shapes of the grouped GEMMs chosen by timing")
     ap.add_argument("--kernel-only", choices=["kapply", "minv"], default=None,
                     help="set up once, then run only the operator application (or preconditioner solve) "
                          "--steps times: for kernel profiles")
@@ -659,7 +663,8 @@ def run_batched(args, ws, rank, local, dist):
         for d in dp:
             d["x"].zero_()
         st, ms_, res_ = kpsvd.kp_solve_batch(dp, op_prec=args.op, pc_prec=args.pc, tol=1e-7, maxit=500,
-                                             workers=args.workers, device=dev, check=False)
+                                             workers=args.workers, device=dev, check=False,
+                                             autotune=args.autotune)
         bad = [i.status for _, i in res_ if i.status not in (kpsvd.KP_OK, kpsvd.KP_ENOCONV)]
         if bad:  # anything but convergence or stagnation at FP32 accuracy is a failure
             raise RuntimeError(f"kp_solve_batch failed: statuses {bad}: {kpsvd._lib.kp_last_error().decode()}")
@@ -719,7 +724,10 @@ def run_batched(args, ws, rank, local, dist):
               "data": "synthetic",
               "config": {"workload": "batched64", "sizes": [f"{a}x{b}" for a, b in synth.BATCH_SIZES],
                          "op_prec": args.op, "pc_prec": args.pc, "vec_prec": "f32", "lambda": "gcv", "tol": 1e-7,
-                         "workers": args.workers, "parallelism": f"replicas x{ws}",
+                         "workers": args.workers,
+                         "form": ("grouped: one launch per iteration step over all problems, one CUDA graph with "
+                                  "a device-side loop" if args.workers <= 0 else f"{args.workers} host threads"),
+                         "autotune": bool(args.autotune), "parallelism": f"replicas x{ws}",
                          "l2": "256 MiB buffer written before every step",
                          "step": "kp_solve_batch over 64 problems"},
               "e2e": {"value": sum_over_ranks(dist, float(n_ok)) / (e2e_ms / 1e3), "unit": "solves/s",

@@ -317,11 +317,24 @@ kp_status kp_set_option(kp_ctx* ctx, const char* name, double value);
  * Many deblurring problems, each with its own PSF, size, boundary condition,
  * b and lambda (given, or chosen per problem), solved with one set of
  * precisions and solver settings.  Not part of the paper; the batched
- * configuration of the project's workloads.  The problems run concurrently:
- * `workers` host threads each own one context (and stream) and take the
- * problems largest first, so the GPU overlaps the kernels of different
- * problems; each problem computes exactly what kp_setup, choose_lambda and
- * tik_pcg compute for it alone.
+ * configuration of the project's workloads.  Each problem computes what
+ * kp_setup, choose_lambda and tik_pcg compute for it alone.
+ * Grouped form (workers <= 0, the default): one host thread; setup and
+ * lambda problem by problem, then the (F)PCG iterations of all problems
+ * together: every launch of the iteration (a tensor-core GEMM, a vector
+ * update, a reduction) is ONE launch over all problems (GEMMs: a persistent
+ * kernel over the (problem, tile) units of all problems, each problem's
+ * tensor maps in a device table; vector kernels: one grid row per problem),
+ * inside one CUDA graph whose device-side while loop runs until every
+ * problem has stopped; a stopped problem's part of each launch does no
+ * work.  Reductions may then sum their partials in another order than
+ * alone (rounding-level differences).  The library keeps one context per
+ * problem slot for the next call on the device (kp_batch_release frees
+ * them); concurrent calls on one device are serialised.  Problems whose
+ * iteration cannot run grouped (an operator or preconditioner without the
+ * fused iteration) run alone after the group.
+ * workers > 0: `workers` host threads each own one context (and stream) and
+ * take the problems largest first.
  *   psf, b, x   device pointers as for kp_setup / tik_pcg (x: written)
  *   lambda      in: > 0 a fixed lambda; <= 0 chosen by `method` with
  *               lambda_param (choose_lambda's param); out: the lambda used
@@ -346,7 +359,9 @@ typedef struct {
   double tol;
   int maxit;
   int flexible;
-  int workers; /* concurrent problems; <= 0: 8 */
+  int workers;  /* <= 0: grouped form (one host thread); > 0: that many host threads */
+  int autotune; /* grouped form: nonzero = tile shapes of the grouped GEMMs chosen by timing
+                   (the tc_autotune option; cache file KPSVD_TUNE_CACHE) */
 } kp_batch_opts;
 
 /* Solve probs[0..nprob) (device `device`).  Returns KP_OK when every problem
@@ -354,6 +369,13 @@ typedef struct {
  * in kp_last_error); KP_EINVAL for NULL arguments or nprob < 0.  ms_total
  * (host, nullable): wall time of the whole batch in milliseconds. */
 kp_status kp_solve_batch(int device, kp_problem* probs, int nprob, const kp_batch_opts* opts, double* ms_total);
+
+/* Free the contexts and device table that the grouped form keeps for `device`. */
+void kp_batch_release(int device);
+
+/* How many problems the last grouped kp_solve_batch call on `device` ran in
+ * its grouped loop (0 when none did), and that loop's passes (nullable). */
+int kp_batch_grouped(int device, int* passes);
 
 /* ---- Learned lambda (not in the paper; Section 5 asks for a systematic
  * parameter choice) ----------------------------------------------------------

@@ -2,20 +2,38 @@
 //
 // Each problem is what kp_setup + choose_lambda + tik_pcg compute for it
 // alone (Sections 3-5: KP-SVD preconditioned (F)PCG on the Tikhonov normal
-// equations, lambda by GCV / discrepancy / ...).  Concurrency: `workers` host
-// threads, each with its own context on its own non-blocking stream, take
-// the problems largest first from a shared counter, so the GPU overlaps the
-// kernels (and the host round trips) of different problems; results do not
-// depend on which worker ran a problem.
+// equations, lambda by GCV / discrepancy / ...).
+//
+// Default (grouped): one host thread and one context per problem.  Setup,
+// lambda and the steps before the iterations run problem by problem; then
+// one iteration of every problem is recorded (kp_group.cuh: launches kept as
+// argument records), and the records at each position of the iteration
+// become ONE launch over all problems: a persistent tensor-core GEMM over
+// the (problem, tile) units of all problems' plans (tc_gemm_group_kernel,
+// per-problem tensor maps in a device table), or a vector kernel with one
+// blockIdx.y per problem.  The whole iteration of all problems is one CUDA
+// graph with a device-side while loop; each problem's flags say whether it
+// still runs (a stopped problem's launches do no work), whether its residual
+// replacement is due (the replacement runs inside an if node, skipped by the
+// problems for which none is due), and the loop ends when no problem runs.
+// Tile shapes are each plan's (the per-shape choice, or the timed one with
+// the tc_autotune option and its cache file).
+//
+// workers > 0: the former form, `workers` host threads, each with its own
+// context on its own stream, taking the problems largest first.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
 #include <vector>
 
 #include "kp_internal.h"
+#include "kp_vec.cuh"
 
 namespace {
 
@@ -85,6 +103,8 @@ void run_worker(int device, kp_problem* probs, const std::vector<int>& order, st
 
 }  // namespace
 
+static kp_status solve_grouped(int device, kp_problem* probs, int nprob, const kp_batch_opts* opts);
+
 extern "C" kp_status kp_solve_batch(int device, kp_problem* probs, int nprob, const kp_batch_opts* opts,
                                     double* ms_total) {
   if (!opts || nprob < 0 || (nprob > 0 && !probs)) {
@@ -101,13 +121,19 @@ extern "C" kp_status kp_solve_batch(int device, kp_problem* probs, int nprob, co
     probs[i].info.replacements = 0;
   }
   const auto t0 = std::chrono::steady_clock::now();
+  if (opts->workers <= 0) {
+    const kp_status gs = solve_grouped(device, probs, nprob, opts);
+    if (ms_total)
+      *ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return gs;
+  }
   // largest problems first (the longest run in the tail is then a small one)
   std::vector<int> order(nprob);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (long long)probs[a].n_r * probs[a].n_c > (long long)probs[b].n_r * probs[b].n_c;
   });
-  const int nw = std::max(1, std::min(opts->workers > 0 ? opts->workers : 8, std::max(nprob, 1)));
+  const int nw = std::max(1, std::min(opts->workers, std::max(nprob, 1)));
   std::atomic<int> next{0};
   std::vector<WorkerResult> res(nw);
   std::vector<std::thread> threads;
@@ -124,5 +150,355 @@ extern "C" kp_status kp_solve_batch(int device, kp_problem* probs, int nprob, co
     kp_set_error("kp_solve_batch: problem %d: %s", first->first_idx, first->msg.c_str());
     return first->first;
   }
+  return KP_OK;
+}
+
+// ---------------------------------------------------------------- grouped form
+namespace {
+
+// The loop condition of the grouped graph: h = whether any problem's flag
+// `slot` is nonzero (want_zero: is zero).  With `passes` (the while loop's
+// condition), also a bound on the passes, so that the loop ends even if a
+// problem's flags never stop it (each problem also stops itself a few
+// passes past maxit).
+__global__ void k_batch_any(int* const* __restrict__ flags, int n, int slot, int want_zero, int* passes,
+                            int max_passes, cudaGraphConditionalHandle h) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int v = *(volatile const int*)(flags[i] + slot);
+    if (want_zero ? v == 0 : v != 0) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int go = any ? 1u : 0u;
+    if (passes && ++*passes > max_passes) go = 0u;
+    cudaGraphSetConditional(h, go);
+  }
+}
+
+// Contexts and buffers kept from one call to the next on a device (the
+// problems' buffers are reused when the sizes repeat); kp_batch_release
+// frees them.
+struct GroupPool {
+  std::mutex mu;
+  std::vector<kp_ctx*> ctxs;
+  unsigned char* dev = nullptr;
+  size_t dev_bytes = 0;
+  int last_grouped = 0;  // problems the last call's grouped loop ran
+  int last_passes = 0;   // passes of that loop
+};
+std::mutex g_pools_mu;
+std::map<int, GroupPool*> g_pools;
+
+GroupPool* group_pool(int device) {
+  std::lock_guard<std::mutex> lock(g_pools_mu);
+  auto it = g_pools.find(device);
+  if (it != g_pools.end()) return it->second;
+  GroupPool* p = new GroupPool();
+  g_pools[device] = p;
+  return p;
+}
+
+// one grouped launch: the records of one kernel at one position
+struct Group {
+  std::vector<const KpRec*> recs;
+  size_t off = 0;  // its table in the device buffer
+};
+
+// Positions of one segment across the problems: the records at position k
+// of every problem, split by kernel.
+kp_status plan_segment(const std::vector<KpRecorder*>& segs, std::vector<Group>* out, size_t* bytes) {
+  const size_t len = segs[0]->recs.size();
+  for (size_t k = 0; k < len; ++k) {
+    std::vector<const void*> keys;
+    std::vector<Group> gs;
+    for (KpRecorder* r : segs) {
+      const KpRec* rec = &r->recs[k];
+      size_t g = 0;
+      while (g < keys.size() && keys[g] != rec->key) ++g;
+      if (g == keys.size()) {
+        keys.push_back(rec->key);
+        gs.emplace_back();
+      }
+      gs[g].recs.push_back(rec);
+    }
+    for (Group& g : gs) {
+      g.off = *bytes;
+      *bytes += (g.recs[0]->table_bytes((int)g.recs.size()) + 255) & ~(size_t)255;
+      out->push_back(std::move(g));
+    }
+  }
+  return KP_OK;
+}
+
+kp_status launch_groups(kp_ctx* dctx, const std::vector<Group>& gs, const unsigned char* dev) {
+  for (const Group& g : gs) KP_TRY(g.recs[0]->launch(dctx, g.recs.data(), (int)g.recs.size(), dev + g.off));
+  return KP_OK;
+}
+
+}  // namespace
+
+extern "C" int kp_batch_grouped(int device, int* passes) {
+  GroupPool* p = group_pool(device);
+  std::lock_guard<std::mutex> lock(p->mu);
+  if (passes) *passes = p->last_passes;
+  return p->last_grouped;
+}
+
+extern "C" void kp_batch_release(int device) {
+  GroupPool* p = group_pool(device);
+  std::lock_guard<std::mutex> lock(p->mu);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(device);
+  for (kp_ctx* c : p->ctxs) kp_destroy(c);
+  p->ctxs.clear();
+  if (p->dev) cudaFree(p->dev);
+  p->dev = nullptr;
+  p->dev_bytes = 0;
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+static kp_status solve_grouped(int device, kp_problem* probs, int nprob, const kp_batch_opts* o) {
+  GroupPool* pool = group_pool(device);
+  std::lock_guard<std::mutex> lock(pool->mu);
+  pool->last_grouped = 0;
+  pool->last_passes = 0;
+  KP_CUDA(cudaSetDevice(device));
+  const bool bf16 = o->op_prec == KP_BF16;
+  const double auto_cond = 1e4;  // ill-conditioned problems of a BF16 batch: BF16X3 inner operator
+  while ((int)pool->ctxs.size() < nprob) {
+    kp_ctx* c = nullptr;
+    KP_TRY(kp_create(&c, device, nullptr));
+    pool->ctxs.push_back(c);
+  }
+  std::vector<BatchRun*> runs(nprob, nullptr);
+  std::vector<kp_status> st(nprob, KP_OK);
+  std::vector<std::string> msg(nprob);
+  std::vector<char> entered(nprob, 0);
+  auto fail = [&](int i, kp_status s) {
+    st[i] = s;
+    msg[i] = kp_last_error();
+    probs[i].info.status = s;
+  };
+  // setup, lambda and the steps before the iterations, problem by problem
+  for (int i = 0; i < nprob; ++i) {
+    kp_problem& p = probs[i];
+    kp_ctx* ctx = pool->ctxs[i];
+    kp_status s = kp_set_option(ctx, "op_auto_cond", bf16 ? auto_cond : 0.0);
+    ctx->tc_group = true;  // grouped GEMMs: one-CTA tiles, no K split
+    if (s == KP_OK) s = kp_set_option(ctx, "tc_autotune", o->autotune ? 1 : 0);
+    entered[i] = 0;
+    if (s == KP_OK)
+      s = kp_setup(ctx, p.psf, p.n_r, p.n_c, p.center_r, p.center_c, p.bc, p.op_rank, 1, o->op_prec, o->pc_prec,
+                   o->vec_prec, o->sigma);
+    double lam = p.lambda;
+    if (s == KP_OK && !(lam > 0.0)) s = choose_lambda(ctx, p.b, o->method, p.lambda_param, nullptr, &lam);
+    if (s == KP_OK) {
+      p.lambda = lam;
+      if (!p.b || !p.x || ((uintptr_t)p.b & 15) || ((uintptr_t)p.x & 15)) {
+        kp_set_error("kp_solve_batch: problem %d: b and x must be 16-byte aligned device pointers", i);
+        s = KP_EINVAL;
+      }
+    }
+    if (s == KP_OK && !(o->tol >= 0.0 && o->maxit >= 1)) {
+      kp_set_error("kp_solve_batch: need tol >= 0 and maxit >= 1");
+      s = KP_EINVAL;
+    }
+    if (s == KP_OK) {
+      s = kp_enter(ctx);
+      entered[i] = 1;
+    }
+    if (s == KP_OK) s = batch_begin(ctx, p.b, lam, o->tol, o->maxit, o->flexible, p.x, &runs[i]);
+    if (s != KP_OK) fail(i, s);
+  }
+  // record one iteration of every problem whose loop can run grouped
+  std::vector<int> grp;
+  std::string record_msg;
+  std::vector<KpRecorder> ra(nprob), rr(nprob), rb(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    if (!runs[i] || !batch_groupable(runs[i])) continue;
+    const kp_status s = batch_record(pool->ctxs[i], runs[i], &ra[i], &rr[i], &rb[i]);
+    if (s == KP_OK) {
+      grp.push_back(i);
+    } else {
+      cudaGetLastError();
+      if (record_msg.empty()) record_msg = kp_last_error();
+    }
+  }
+  // the grouped problems' iterations must line up launch by launch; the
+  // largest set of equal lengths runs grouped, the rest alone
+  {
+    std::map<std::vector<size_t>, std::vector<int>> by_len;
+    for (int i : grp) by_len[{ra[i].recs.size(), rr[i].recs.size(), rb[i].recs.size()}].push_back(i);
+    std::vector<int> best;
+    for (auto& kv : by_len)
+      if (kv.second.size() > best.size()) best = kv.second;
+    grp = best;
+  }
+  std::vector<char> in_grp(nprob, 0);
+  for (int i : grp) in_grp[i] = 1;
+  kp_status gst = KP_OK;
+  if (!grp.empty()) {
+    std::vector<KpRecorder*> sa, sr, sb;
+    for (int i : grp) {
+      sa.push_back(&ra[i]);
+      sr.push_back(&rr[i]);
+      sb.push_back(&rb[i]);
+    }
+    std::vector<Group> ga, gr, gb;
+    size_t bytes = 0;
+    plan_segment(sa, &ga, &bytes);
+    plan_segment(sr, &gr, &bytes);
+    plan_segment(sb, &gb, &bytes);
+    const size_t off_flags = bytes;
+    bytes += sizeof(int*) * grp.size() + sizeof(int) * 64;
+    const size_t off_passes = off_flags + sizeof(int*) * grp.size();
+    if (bytes > pool->dev_bytes) {
+      if (pool->dev) cudaFree(pool->dev);
+      pool->dev = nullptr;
+      pool->dev_bytes = 0;
+      KP_CUDA(cudaMalloc((void**)&pool->dev, bytes));
+      pool->dev_bytes = bytes;
+    }
+    std::vector<unsigned char> host(bytes, 0);
+    for (auto* gs : {&ga, &gr, &gb})
+      for (const Group& g : *gs) g.recs[0]->table(g.recs.data(), (int)g.recs.size(), host.data() + g.off);
+    for (size_t j = 0; j < grp.size(); ++j) {
+      int* fp = pool->ctxs[grp[j]]->dflags;
+      std::memcpy(host.data() + off_flags + sizeof(int*) * j, &fp, sizeof(fp));
+    }
+    KP_CUDA(cudaMemcpy(pool->dev, host.data(), bytes, cudaMemcpyHostToDevice));
+    int* const* dflags = reinterpret_cast<int* const*>(pool->dev + off_flags);
+    int* passes = reinterpret_cast<int*>(pool->dev + off_passes);
+    // the graph: while (any problem runs) { first halves; if (any replacement
+    // due) { replacements }; second halves }
+    kp_ctx* dctx = pool->ctxs[grp[0]];
+    cudaStream_t s0 = dctx->stream;
+    if (!dctx->aux_stream) KP_CUDA(cudaStreamCreateWithFlags(&dctx->aux_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    KP_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h_loop, h_rep;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
+    cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_rep, body, 0, 0);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(s0, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      kp_set_error("kp_solve_batch: loop graph: %s", cudaGetErrorString(e));
+      return KP_ECUDA;
+    }
+    const int n = (int)grp.size();
+    kp_status cs = launch_groups(dctx, ga, pool->dev);
+    if (cs == KP_OK) {
+      k_batch_any<<<1, 256, 0, s0>>>(dflags, n, F_NOTDUE, 1, nullptr, 0, h_rep);
+      cudaStreamCaptureStatus cst;
+      cudaGraph_t cg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      const cudaGraphEdgeData* ed = nullptr;
+      size_t nd = 0;
+      cudaGraphNodeParams ip = {};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = h_rep;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t inode;
+      e = cudaStreamGetCaptureInfo(s0, &cst, nullptr, &cg, &deps, &ed, &nd);
+      if (e == cudaSuccess) e = cudaGraphAddNode(&inode, cg, deps, ed, nd, &ip);
+      if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(s0, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+      if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(dctx->aux_stream, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        kp_set_error("kp_solve_batch: loop graph (replacement): %s", cudaGetErrorString(e));
+        cs = KP_ECUDA;
+      } else {
+        dctx->stream = dctx->aux_stream;
+        cs = launch_groups(dctx, gr, pool->dev);
+        dctx->stream = s0;
+        cudaGraph_t tmp = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(dctx->aux_stream, &tmp);
+        if (cs == KP_OK && e2 != cudaSuccess) {
+          kp_set_error("kp_solve_batch: loop graph (replacement): %s", cudaGetErrorString(e2));
+          cs = KP_ECUDA;
+        }
+      }
+    }
+    if (cs == KP_OK) cs = launch_groups(dctx, gb, pool->dev);
+    if (cs == KP_OK) k_batch_any<<<1, 256, 0, s0>>>(dflags, n, F_BLOOP, 0, passes, o->maxit + 16, h_loop);
+    {
+      cudaGraph_t tmp = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(s0, &tmp);
+      if (cs == KP_OK && ee != cudaSuccess) {
+        kp_set_error("kp_solve_batch: loop graph capture: %s", cudaGetErrorString(ee));
+        cs = KP_ECUDA;
+      }
+    }
+    if (cs == KP_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+      kp_set_error("kp_solve_batch: loop graph instantiation failed");
+      cs = KP_ECUDA;
+    }
+    for (int i : grp)
+      if (cs == KP_OK) cs = batch_arm(pool->ctxs[i], runs[i]);
+    if (cs == KP_OK) {
+      KP_CUDA(cudaMemsetAsync(passes, 0, sizeof(int), s0));
+      KP_CUDA(cudaGraphLaunch(ge, s0));
+      KP_CUDA(cudaMemcpyAsync(&pool->last_passes, passes, sizeof(int), cudaMemcpyDeviceToHost, s0));
+      KP_CUDA(cudaStreamSynchronize(s0));
+      pool->last_grouped = n;
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    gst = cs;
+  }
+  // results; problems outside the grouped loop run it alone; a BF16 inner
+  // operator that stalled or broke down is retried with BF16X3 (as alone)
+  for (int i = 0; i < nprob; ++i) {
+    if (!runs[i]) continue;
+    kp_problem& p = probs[i];
+    kp_ctx* ctx = pool->ctxs[i];
+    kp_status s;
+    if (in_grp[i] && gst == KP_OK) {
+      s = batch_finish(ctx, runs[i], &p.info);
+    } else if (!batch_needs_loop(runs[i])) {
+      s = batch_finish(ctx, runs[i], &p.info);
+    } else {
+      batch_discard(runs[i]);
+      s = tik_pcg(ctx, p.b, p.lambda, o->tol, o->maxit, o->flexible, p.x, 0, &p.info);
+    }
+    runs[i] = nullptr;
+    if (bf16 && ctx->op_prec == KP_BF16 && (s == KP_ENOCONV || s == KP_EBREAKDOWN || s == KP_ENUMERIC)) {
+      kp_status so = kp_set_option(ctx, "op_auto_cond", 1.0);
+      if (so == KP_OK) s = tik_pcg(ctx, p.b, p.lambda, o->tol, o->maxit, o->flexible, p.x, 0, &p.info);
+      kp_set_option(ctx, "op_auto_cond", auto_cond);
+    }
+    p.info.status = s;
+    if (s != KP_OK) fail(i, s);
+  }
+  for (int i = 0; i < nprob; ++i)
+    if (entered[i]) kp_leave(pool->ctxs[i]);
+  if (gst != KP_OK) {
+    kp_set_error("kp_solve_batch: grouped loop: %s", kp_last_error());
+    return gst;
+  }
+  for (int i = 0; i < nprob; ++i)
+    if (st[i] != KP_OK) {
+      kp_set_error("kp_solve_batch: problem %d: %s", i, msg[i].c_str());
+      return st[i];
+    }
+  // (a problem that could not be recorded ran alone; say why, without failing)
+  if (!record_msg.empty()) kp_set_error("kp_solve_batch: ran alone: %s", record_msg.c_str());
   return KP_OK;
 }

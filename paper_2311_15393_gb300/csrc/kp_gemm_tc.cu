@@ -29,6 +29,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
@@ -637,6 +638,216 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
   }
 }
 
+// ------------------------------------------------------------- grouped kernel
+// The GEMMs of several independent problems (one plan each: its own tensor
+// maps, sizes and epilogue, all in global memory) as one persistent launch:
+// the units of all plans are numbered consecutively (ustart[e] is the first
+// unit of plan e) and the CTAs take them in turn, so small problems share the
+// GPU instead of each filling it with a launch of its own.  A plan whose
+// pause flag is set (its problem has stopped) contributes no work: every
+// role reads the same flag, written before this launch, and skips its units.
+// No split-K; the ring and accumulator phases run on across plans.
+struct alignas(64) TcGroupEntry {
+  CUtensorMap mapA, mapB;
+  TcParams p;
+};
+
+__device__ __forceinline__ int group_find(const int* __restrict__ ustart, int nent, int u) {
+  int lo = 0, hi = nent - 1;  // largest e with ustart[e] <= u
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ustart[mid] <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int KIND, int BN, int CPS, int KPS>
+__global__ void __launch_bounds__(TC_THREADS, CPS)
+    tc_gemm_group_kernel(const TcGroupEntry* __restrict__ ents, const int* __restrict__ ustart, int nent,
+                         int* status) {
+  using C = TcCfg<BN, CPS, KPS>;
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + C::STAGES;
+  uint64_t* tfull = bars + 2 * C::STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ksh = KIND == TC_E4M3 ? 0 : 1;
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
+  const int units = ustart[nent];
+  // plan of unit u and the unit's index within it; false: the plan is paused
+  auto unit_of = [&](int u, const TcGroupEntry*& e, Unit& w) -> bool {
+    const int k = group_find(ustart, nent, u);
+    e = ents + k;
+    if (e->p.flags && *(volatile const int*)e->p.flags) return false;
+    w = decode_unit(e->p, u - ustart[k], BN);
+    return true;
+  };
+  if (warp == 0 && lane < 2 * KPS) {
+    // ---------------- TMA producer (lanes as in tc_gemm_kernel)
+    const bool isB = lane & 1;
+    const int q = lane >> 1;
+    const unsigned mask = (1u << (2 * KPS)) - 1u;
+    int it = 0;
+    bool run = true;
+    for (int u = blockIdx.x; run && u < units && !*(volatile int*)&s_abort; u += gridDim.x) {
+      const TcGroupEntry* e;
+      Unit w;
+      if (!unit_of(u, e, w)) continue;
+      const TcParams& p = e->p;
+      const CUtensorMap* map = isB ? &e->mapB : &e->mapA;
+      const int nk = p.batch_rows ? 1 : p.nkron;
+      for (int j = 0; j * KPS < w.nsteps; ++j, ++it) {
+        const int s = it % C::STAGES;
+        const uint32_t ph = (it / C::STAGES) & 1;
+        const int nkb = min(KPS, w.nsteps - j * KPS);
+        int okw = 1;
+        if (lane == 0) {
+          okw = mbar_wait(smem_u32(&empty[s]), ph ^ 1, status) ? 1 : 0;
+          if (okw) mbar_expect_tx(smem_u32(&full[s]), (uint32_t)(nkb * C::KB_BYTES));
+        }
+        okw = __shfl_sync(mask, okw, 0);
+        if (!okw) {
+          if (lane == 0) s_abort = 1;
+          run = false;
+          break;
+        }
+        if (q < nkb) {
+          const int tb = p.batch_rows ? w.m0 / p.batch_rows : 0;
+          const int row0 = isB ? w.n0 : w.m0 - tb * p.batch_rows;
+          const int stp = w.step0 + j * KPS + q;
+          const int kb = stp % p.kblocks;
+          const int rest = stp / p.kblocks;
+          const int k = rest % nk, pr = rest / nk;
+          const int term = (isB ? p.sb[pr] * p.b_terms : p.sa[pr] * p.a_terms) + (p.batch_rows ? tb : k);
+          const uint32_t dst =
+              smem_u32(smem + s * C::STAGE + q * C::KB_BYTES) + (isB ? (uint32_t)C::A_BYTES : 0u);
+          tma_load_3d(dst, map, (kb * 128) >> ksh, row0, term, smem_u32(&full[s]));
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int it = 0, i = 0;
+      for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const TcGroupEntry* e;
+        Unit w;
+        if (!unit_of(u, e, w)) continue;
+        const uint32_t idesc = e->p.idesc;
+        const int buf = i & 1;
+        if (*(volatile int*)&s_abort || !mbar_wait(smem_u32(&tempty[buf]), ((i >> 1) & 1) ^ 1, status)) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        bool ok = true;
+        for (int j = 0; j * KPS < w.nsteps; ++j, ++it) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (it / C::STAGES) & 1;
+          if (*(volatile int*)&s_abort || !mbar_wait(smem_u32(&full[s]), ph, status)) {
+            s_abort = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int nkb = min(KPS, w.nsteps - j * KPS);
+#pragma unroll
+          for (int q = 0; q < KPS; ++q) {
+            if (q < nkb) {
+              const uint32_t a0 = smem_u32(smem + s * C::STAGE + q * C::KB_BYTES);
+              const uint32_t b0 = a0 + C::A_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                mma_issue<KIND>(d, make_sdesc(a0 + kk * 32), make_sdesc(b0 + kk * 32), idesc,
+                                (j > 0 || q > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(smem_u32(&empty[s]));
+        }
+        mma_commit(smem_u32(&tfull[buf]));
+        ++i;
+        if (!ok) break;
+      }
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps 2..5 -> TMEM lanes 32 * (warp % 4)
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    int i = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+      const TcGroupEntry* e;
+      Unit w;
+      if (!unit_of(u, e, w)) continue;
+      const TcParams& p = e->p;
+      const int buf = i & 1;
+      if (!mbar_wait(smem_u32(&tfull[buf]), (i >> 1) & 1, status)) break;
+      ++i;
+      tc_fence_after();
+      const float sdev = p.alpha_dev ? *p.alpha_dev : 1.f;
+      const int gm = w.m0 + row;
+      const bool row_ok = gm < p.M;
+      float tmax = 0.f;
+#pragma unroll 1
+      for (int chunk = 0; chunk < BN / 32; ++chunk) {
+        float acc[32];
+        if (w.nsteps > 0) {
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + chunk * 32), acc);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+        }
+        const int gn0 = w.n0 + chunk * 32;
+        if (row_ok && gn0 < p.N) epi_store32(p.epi, sdev, gm, gn0, p.N, acc, tmax);
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&tempty[buf]));
+      if (p.epi.amax_bits) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        if (lane == 0 && tmax > 0.f) atomicMax(p.epi.amax_bits, __float_as_uint(tmax));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+  }
+}
+
 // ------------------------------------------------------------- CTA-pair kernel
 // The same GEMM on 256 x 256 output tiles computed by a pair of CTAs on two
 // SMs (a cluster of 2) with tcgen05.mma.cta_group::2: the MMA of M = 256,
@@ -1067,7 +1278,8 @@ static kp_status tc_plan_create_one(kp_ctx* ctx, const GemmDesc& g, int kind, in
   if (bn == 128 && (ctx->tc_cps_override == 1 || ctx->tc_cps_override == 2)) cps = ctx->tc_cps_override;
   if (splits < 1) {  // K split only when even 64-wide tiles leave most SMs idle
     splits = 1;
-    if (2 * tiles_bn < sms) splits = std::max(1, std::min({4, sms / tiles_bn, steps_all / 16}));
+    if (2 * tiles_bn < sms && !ctx->tc_grouping)
+      splits = std::max(1, std::min({4, sms / tiles_bn, steps_all / 16}));
   }
   // CTA pairs (256 x 256 tiles, cta_group::2) for BF16 GEMMs without a K
   // split whose pair tiles fill most SM pairs; option tc_pair: 1 = never,
@@ -1075,7 +1287,8 @@ static kp_status tc_plan_create_one(kp_ctx* ctx, const GemmDesc& g, int kind, in
   const int pair_tiles = ((g.M + PAIR_M - 1) / PAIR_M) * ((g.N + PAIR_N - 1) / PAIR_N);
   const bool pair_ok = kind == TC_BF16 && splits == 1 && g.N >= PAIR_N &&
                        (g.batch_rows == 0 || g.batch_rows % PAIR_M == 0) && g.M >= PAIR_M;
-  const bool pair = pair_ok && ctx->tc_pair_override != 1 &&
+  // (plans of a batched solve run in grouped launches: one-CTA tiles, no K split)
+  const bool pair = pair_ok && !ctx->tc_grouping && ctx->tc_pair_override != 1 &&
                     (ctx->tc_pair_override == 2 || (ctx->tc_bn_override == 0 && 4 * pair_tiles >= 3 * (sms / 2)));
   TcGemmPlan* pl = new TcGemmPlan();
   pl->pair = pair;
@@ -1424,8 +1637,93 @@ static kp_status launch_pair(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
   return KP_OK;
 }
 
+// recorded launches of a batched solve (see KpRec): the records of one
+// kernel configuration at one position become one tc_gemm_group_kernel launch
+template <int KIND, int BN, int CPS, int KPS>
+struct GemmGroup {
+  static size_t bytes(int n) { return sizeof(TcGroupEntry) * (size_t)n + sizeof(int) * (size_t)(n + 1); }
+  static int units_of(const KpRec* r) {
+    TcGroupEntry e;
+    std::memcpy(&e, r->blob.data(), sizeof(e));
+    return e.p.units;
+  }
+  static void table(const KpRec* const* r, int n, unsigned char* dst) {
+    // (before the graph capture that launches it)
+    static std::atomic<bool> attr_set{false};
+    if (!attr_set.load()) {
+      cudaFuncSetAttribute(tc_gemm_group_kernel<KIND, BN, CPS, KPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           TcCfg<BN, CPS, KPS>::SMEM);
+      attr_set = true;
+    }
+    int* us = reinterpret_cast<int*>(dst + sizeof(TcGroupEntry) * (size_t)n);
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+      std::memcpy(dst + sizeof(TcGroupEntry) * (size_t)i, r[i]->blob.data(), sizeof(TcGroupEntry));
+      us[i] = acc;
+      acc += units_of(r[i]);
+    }
+    us[n] = acc;
+  }
+  static kp_status launch(kp_ctx* ctx, const KpRec* const* r, int n, const void* dev) {
+    using C = TcCfg<BN, CPS, KPS>;
+    long long total = 0;
+    for (int i = 0; i < n; ++i) total += units_of(r[i]);
+    TcGroupEntry e0;
+    std::memcpy(&e0, r[0]->blob.data(), sizeof(e0));
+    const int grid = (int)std::max(1LL, std::min(total, (long long)ctx->sm_count * CPS));
+    const TcGroupEntry* ents = reinterpret_cast<const TcGroupEntry*>(dev);
+    const int* us = reinterpret_cast<const int*>(reinterpret_cast<const unsigned char*>(dev) +
+                                                 sizeof(TcGroupEntry) * (size_t)n);
+    KP_CUDA(kp_launch(ctx, tc_gemm_group_kernel<KIND, BN, CPS, KPS>, dim3(grid), dim3(TC_THREADS), C::SMEM, ents, us,
+                      n, e0.p.status));
+    KP_LAUNCHED(ctx);
+    return KP_OK;
+  }
+  static void record(kp_ctx* ctx, const TcGemmPlan* pl, const TcParams& p) {
+    TcGroupEntry e;
+    e.mapA = pl->mapA;
+    e.mapB = pl->mapB;
+    e.p = p;
+    KpRec rec;
+    rec.key = reinterpret_cast<const void*>(tc_gemm_group_kernel<KIND, BN, CPS, KPS>);
+    rec.table_bytes = &bytes;
+    rec.table = &table;
+    rec.launch = &launch;
+    rec.grid = pl->grid;
+    rec.block = dim3(TC_THREADS);
+    rec.smem = TcCfg<BN, CPS, KPS>::SMEM;
+    rec.blob.resize(sizeof(e));
+    std::memcpy(rec.blob.data(), &e, sizeof(e));
+    ctx->rec->recs.push_back(std::move(rec));
+  }
+};
+
+template <int KIND>
+static kp_status record_cfg(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
+  if (pl->pair || p.splits != 1) {
+    kp_set_error("batched solve: a CTA-pair or split-K GEMM plan cannot be grouped");
+    return KP_ENOTSUP;
+  }
+  if (pl->bn == 256) {
+    if (pl->kps == 2) GemmGroup<KIND, 256, 1, 2>::record(ctx, pl, p);
+    else GemmGroup<KIND, 256, 1, 1>::record(ctx, pl, p);
+  } else if (pl->bn == 64) {
+    if (pl->kps == 4) GemmGroup<KIND, 64, 1, 4>::record(ctx, pl, p);
+    else if (pl->kps == 2) GemmGroup<KIND, 64, 1, 2>::record(ctx, pl, p);
+    else GemmGroup<KIND, 64, 1, 1>::record(ctx, pl, p);
+  } else if (pl->cps == 2) {
+    GemmGroup<KIND, 128, 2, 1>::record(ctx, pl, p);
+  } else if (pl->kps == 2) {
+    GemmGroup<KIND, 128, 1, 2>::record(ctx, pl, p);
+  } else {
+    GemmGroup<KIND, 128, 1, 1>::record(ctx, pl, p);
+  }
+  return KP_OK;
+}
+
 template <int KIND>
 static kp_status launch_cfg(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
+  if (ctx->rec) return record_cfg<KIND>(ctx, pl, p);
   if (pl->pair) {
     if constexpr (KIND == TC_BF16) {
       return pl->kps == 1 ? launch_pair<KIND, 1>(ctx, pl, p) : launch_pair<KIND, 2>(ctx, pl, p);

@@ -253,7 +253,43 @@ struct kp_ctx {
 
   // prepared tensor-core GEMM plans
   std::vector<TcGemmPlan*> tc_plans;
+
+  // batched solves: while set, launches are recorded here instead of run
+  struct KpRecorder* rec = nullptr;
+  bool tc_group = false;     // batched solve: the operator's and preconditioner's plans run in grouped launches
+  bool tc_grouping = false;  // set while those plans are made: no K split, no CTA pairs
 };
+
+// ---------------------------------------------------------------- recorded launches
+// A batched solve runs one iteration of each problem in recording mode: each
+// launch becomes a KpRec (its arguments as bytes) instead of running.  The
+// records at the same position of the problems' sequences that share a
+// kernel (`key`) then become one grouped launch: `table` writes their
+// arguments into a device table (before graph capture), `launch` runs the
+// grouped kernel over them.
+struct KpRec {
+  const void* key = nullptr;
+  size_t (*table_bytes)(int n) = nullptr;
+  void (*table)(const KpRec* const* recs, int n, unsigned char* host_dst) = nullptr;
+  kp_status (*launch)(kp_ctx* ctx, const KpRec* const* recs, int n, const void* dev_table) = nullptr;
+  dim3 grid, block;
+  size_t smem = 0;
+  std::vector<unsigned char> blob;
+};
+struct KpRecorder {
+  std::vector<KpRec> recs;
+};
+
+// one problem's solve around a grouped loop (kp_solver.cu; driven by kp_batch.cu)
+struct BatchRun;
+kp_status batch_begin(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible, void* x,
+                      BatchRun** out);
+bool batch_groupable(const BatchRun* br);
+bool batch_needs_loop(const BatchRun* br);
+kp_status batch_record(kp_ctx* ctx, BatchRun* br, KpRecorder* seg_a, KpRecorder* seg_r, KpRecorder* seg_b);
+kp_status batch_arm(kp_ctx* ctx, BatchRun* br);
+kp_status batch_finish(kp_ctx* ctx, BatchRun* br, kp_solve_info* info);
+void batch_discard(BatchRun* br);
 
 // launch with programmatic stream serialization (when ctx->pdl); the kernel
 // must begin with KP_PDL_WAIT()
@@ -317,7 +353,7 @@ kp_status topr_svd(kp_ctx* ctx, const double* W, int m, int n, int r, double* U,
 kp_status dot_dev(kp_ctx* ctx, const void* x, const void* y, long long n, bool f64, double* out_dev);
 kp_status norm2_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out_dev);
 kp_status split_bf16(kp_ctx* ctx, const void* x, bool f64, long long n, void* out, int slices,
-                     long long slice_stride);
+                     long long slice_stride, const int* flags = nullptr);
 kp_status copy_vec(kp_ctx* ctx, const void* x, void* y, long long n, bool f64);
 kp_status read_status(kp_ctx* ctx);
 kp_status kp_check_ready(kp_ctx* ctx);

@@ -21,6 +21,7 @@
 // below 2^-24 relative (FP32 level).
 #include <algorithm>
 
+#include "kp_group.cuh"
 #include "kp_ops.h"
 #include "kp_vec.cuh"
 
@@ -39,6 +40,15 @@ struct OpsState {
 }  // namespace
 
 static OpsState* ops(kp_ctx* ctx) { return reinterpret_cast<OpsState*>(ctx->ops_state); }
+
+// plans made in this scope are for grouped launches when the context is a
+// batched solve's (tc_group)
+struct GroupedPlans {
+  kp_ctx* c;
+  bool old;
+  explicit GroupedPlans(kp_ctx* ctx) : c(ctx), old(ctx->tc_grouping) { c->tc_grouping = c->tc_group; }
+  ~GroupedPlans() { c->tc_grouping = old; }
+};
 
 void ops_state_free(kp_ctx* ctx) {
   delete ops(ctx);
@@ -202,10 +212,10 @@ __device__ __forceinline__ void term_dot_finish(float (&dh)[2], float (&dl)[2], 
   }
 }
 
-__global__ void __launch_bounds__(VEC_THREADS)
-    k_term_reduce(const float* __restrict__ Z, int terms, long long nel, float alpha, float beta,
-                  const float* __restrict__ aux, int slices_mode, void* __restrict__ out, int slices, long long sstride,
-                  int vec, TermDot td, const int* flags) {
+__device__ __forceinline__ void k_term_reduce_body(const float* __restrict__ Z, int terms, long long nel, float alpha,
+                                                   float beta, const float* __restrict__ aux, int slices_mode,
+                                                   void* __restrict__ out, int slices, long long sstride, int vec,
+                                                   TermDot td, const int* flags) {
   KP_PDL_WAIT();
   KP_PDL_TRIGGER();
   if (flags && *(volatile const int*)flags) return;
@@ -280,6 +290,13 @@ __global__ void __launch_bounds__(VEC_THREADS)
   }
   if (td.out) term_dot_finish(dh, dl, td);
 }
+__global__ void __launch_bounds__(VEC_THREADS)
+    k_term_reduce(const float* __restrict__ Z, int terms, long long nel, float alpha, float beta,
+                  const float* __restrict__ aux, int slices_mode, void* __restrict__ out, int slices, long long sstride,
+                  int vec, TermDot td, const int* flags) {
+  k_term_reduce_body(Z, terms, nel, alpha, beta, aux, slices_mode, out, slices, sstride, vec, td, flags);
+}
+KP_BODY(TermReduce, k_term_reduce_body);
 
 // tensor-core plan of GEMM w of the operator in `mode` for the current pairs
 static kp_status op_plan(kp_ctx* ctx, OpsState* os, int mode, int w, TcGemmPlan** out, int terms = 0) {
@@ -301,6 +318,7 @@ kp_status ops_set_inner(kp_ctx* ctx, kp_prec p) {
     return KP_ENOTSUP;
   }
   if (ctx->op_prec == p) return KP_OK;
+  GroupedPlans gp(ctx);
   OpsState* os = ops(ctx);
   const int v = p == KP_BF16X3 ? 1 : 0;
   const kp_prec old = ctx->op_prec;
@@ -323,6 +341,7 @@ kp_status ops_prepare(kp_ctx* ctx) {
   const long long N = (long long)n_r * n_c;
   const size_t vs = vec64(ctx) ? 8 : 4;
   ops_state_free(ctx);
+  GroupedPlans gp(ctx);
   OpsState* os = new OpsState();
   ctx->ops_state = os;
   KP_TRY(kp_alloc(ctx, (void**)&os->inv_slot, 16));
@@ -424,7 +443,7 @@ static kp_status run_op(kp_ctx* ctx, int which, int mode, const void* bptr, cons
       t = *td;
       if (dot_done) *dot_done = true;
     }
-    KP_CUDA(kp_launch(ctx, k_term_reduce, dim3(g), dim3(VEC_THREADS), 0, (const float*)ctx->w_split, nterm, nel,
+    KP_CUDA(kp_launch_g<TermReduce>(ctx, k_term_reduce, dim3(g), dim3(VEC_THREADS), 0, (const float*)ctx->w_split, nterm, nel,
                       (float)e.alpha, (float)e.beta, (const float*)e.aux, e.mode == EPI_SLICES ? 1 : 0, e.out,
                       e.slices, e.slice_stride, vec, t, flags));
     KP_LAUNCHED(ctx);
@@ -473,14 +492,14 @@ static EpiParams epi_img(kp_ctx* ctx, int mode, void* out, bool as_slices, doubl
 }
 
 // B operand of G1 for image x: tensor cores need bf16 slices in w_img2 / w_img3
-static kp_status stage_input(kp_ctx* ctx, const void* x, int mode, const void** bptr) {
+static kp_status stage_input(kp_ctx* ctx, const void* x, int mode, const void** bptr, const int* flags = nullptr) {
   if (!op_is_tc(ctx)) {
     *bptr = x;
     return KP_OK;
   }
   void* dst = mode == OP_INNER ? ctx->w_img2 : ctx->w_img3;
   const int slices = mode == OP_ACCURATE ? 3 : op_inner_slices(ctx);
-  KP_TRY(split_bf16(ctx, x, false, (long long)ctx->n_r * ctx->n_c, dst, slices, (long long)ctx->n_r * ctx->n_c));
+  KP_TRY(split_bf16(ctx, x, false, (long long)ctx->n_r * ctx->n_c, dst, slices, (long long)ctx->n_r * ctx->n_c, flags));
   *bptr = dst;
   return KP_OK;
 }
@@ -534,7 +553,7 @@ kp_status op_true_residual(kp_ctx* ctx, const void* b, const void* x, void* r, d
   const void* bx;
   const int mode = OP_ACCURATE;
   if (op_is_tc(ctx)) {
-    KP_TRY(stage_input(ctx, x, mode, &bx));
+    KP_TRY(stage_input(ctx, x, mode, &bx, flags));
   } else {
     bx = x;
   }

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <vector>
 
+#include "kp_group.cuh"
 #include "kp_internal.h"
 #include "kp_ops.h"
 #include "kp_vec.cuh"
@@ -67,7 +68,14 @@ __global__ void k_after_replace(double* s, int* f, double* hist, int hist_cap) {
 // (whose kernels skip when a stop is flagged).  The host launches the graph
 // once and reads the flags after it.
 // after a replacement: k_after_replace's rule, a maxit stop stays a stop
-__global__ void k_loop_after_replace(double* s, int* f, double* hist, int hist_cap, cudaGraphConditionalHandle h_loop) {
+// (batched loop: `flags` is the problem's skip word, F_NOTDUE, and the
+// decision goes to F_BLOOP for the loop's own condition kernel)
+__device__ __forceinline__ void k_loop_after_replace_body(double* s, int* f, double* hist, int hist_cap,
+                                                          cudaGraphConditionalHandle h_loop, const int* flags,
+                                                          int batch) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
+  if (flags && *(volatile const int*)flags) return;
   const double rr = s[S_RR];
   const int it = f[F_ITER];
   if (it < hist_cap) hist[it] = sqrt(rr / s[S_RR0]);
@@ -89,8 +97,29 @@ __global__ void k_loop_after_replace(double* s, int* f, double* hist, int hist_c
     f[F_REASON] = 0;
     f[F_PAUSE] = 0;
   }
-  cudaGraphSetConditional(h_loop, (f[F_PAUSE] || f[F_GUARD] > f[F_MAXIT] + 8) ? 0u : 1u);
+  const unsigned int go = (f[F_PAUSE] || f[F_GUARD] > f[F_MAXIT] + 8) ? 0u : 1u;
+  if (batch) {
+    f[F_BLOOP] = (int)go;
+    if (!go) f[F_PAUSE] = 1;
+  } else {
+    cudaGraphSetConditional(h_loop, go);
+  }
 }
+__global__ void k_loop_after_replace(double* s, int* f, double* hist, int hist_cap, cudaGraphConditionalHandle h_loop,
+                                     const int* flags, int batch) {
+  k_loop_after_replace_body(s, f, hist, hist_cap, h_loop, flags, batch);
+}
+KP_BODY(AfterReplace, k_loop_after_replace_body);
+
+// dst = src (one scalar), unless flagged
+__device__ __forceinline__ void k_copy_scalar_body(double* dst, const double* src, const int* flags) {
+  KP_PDL_WAIT();
+  KP_PDL_TRIGGER();
+  if (flags && *(volatile const int*)flags) return;
+  if (threadIdx.x == 0) *dst = *src;
+}
+__global__ void k_copy_scalar(double* dst, const double* src, const int* flags) { k_copy_scalar_body(dst, src, flags); }
+KP_BODY(CopyScalar, k_copy_scalar_body);
 
 struct SolveBufs {
   void *r, *r_old, *p, *q, *z, *rhs;
@@ -110,6 +139,7 @@ static SolveBufs bufs(kp_ctx* ctx) {
 // conditions of the loop graph, set by the x / r update's last block
 struct LoopConds {
   cudaGraphConditionalHandle h_rep = 0, h_loop = 0;
+  int mode = 1;  // PostOp::cond: 1 device loop, 2 batched loop
 };
 
 // first half of an iteration: q = K p, alpha, x/r update, convergence flags
@@ -127,7 +157,7 @@ static kp_status half_a(kp_ctx* ctx, const SolveBufs& B, void* x, double lam2, c
   pc.hist = ctx->hist;
   pc.hist_cap = ctx->hist_cap;
   if (lc) {
-    pc.cond = 1;
+    pc.cond = lc->mode;
     pc.h_rep = lc->h_rep;
     pc.h_loop = lc->h_loop;
   }
@@ -175,7 +205,7 @@ static kp_status half_a_folded(kp_ctx* ctx, const SolveBufs& B, void* x, double 
   pc.hist = ctx->hist;
   pc.hist_cap = ctx->hist_cap;
   if (lc) {
-    pc.cond = 1;
+    pc.cond = lc->mode;
     pc.h_rep = lc->h_rep;
     pc.h_loop = lc->h_loop;
   }
@@ -209,12 +239,20 @@ static kp_status set_scalar(kp_ctx* ctx, int slot, double v) {
 }
 
 // replace r by the true residual; returns its ||r||^2 via the RR / RMAX slots
-static kp_status replace_residual(kp_ctx* ctx, const SolveBufs& B, const void* b, const void* x, double lam2) {
+// (`flags`: skip word of a batched loop's replacement, else null)
+static kp_status replace_residual(kp_ctx* ctx, const SolveBufs& B, const void* b, const void* x, double lam2,
+                                  const int* flags = nullptr) {
   const long long N = (long long)ctx->n_r * ctx->n_c;
-  KP_TRY(op_true_residual(ctx, b, x, B.r, lam2, nullptr));
-  KP_TRY(norm_amax_dev(ctx, B.r, N, ctx->vec_prec == KP_F64, ctx->dscal + S_RR));
-  KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RMAX, ctx->dscal + S_RR, sizeof(double), cudaMemcpyDeviceToDevice,
-                          ctx->stream));
+  KP_TRY(op_true_residual(ctx, b, x, B.r, lam2, flags));
+  KP_TRY(norm_amax_dev(ctx, B.r, N, ctx->vec_prec == KP_F64, ctx->dscal + S_RR, flags));
+  if (flags) {
+    KP_CUDA(kp_launch_g<CopyScalar>(ctx, k_copy_scalar, dim3(1), dim3(32), 0, ctx->dscal + S_RMAX,
+                                    (const double*)ctx->dscal + S_RR, flags));
+    KP_LAUNCHED(ctx);
+  } else {
+    KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RMAX, ctx->dscal + S_RR, sizeof(double), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  }
   return KP_OK;
 }
 
@@ -289,7 +327,8 @@ static kp_status build_loop_graph(kp_ctx* ctx, const SolveBufs& B, const void* b
       ctx->stream = ctx->aux_stream;
       cs = replace_residual(ctx, B, b, x, lam2);
       if (cs == KP_OK) {
-        k_loop_after_replace<<<1, 1, 0, ctx->stream>>>(ctx->dscal, ctx->dflags, ctx->hist, ctx->hist_cap, h_loop);
+        k_loop_after_replace<<<1, 1, 0, ctx->stream>>>(ctx->dscal, ctx->dflags, ctx->hist, ctx->hist_cap, h_loop,
+                                                       nullptr, 0);
         KP_LAUNCHED(ctx);
         if (folded) cs = pc_prepare_input(ctx, B.r, lam2_pc, ctx->dscal + S_RR, nullptr);
       }
@@ -339,8 +378,26 @@ static kp_status choose_inner(kp_ctx* ctx, double lam2) {
   return ops_set_inner(ctx, cond > ctx->op_auto_cond ? KP_BF16X3 : KP_BF16);
 }
 
-static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible, void* x,
-                              int warm_start, kp_solve_info* info) {
+// One solve's state between its steps: the steps before the loop
+// (solve_begin), the loop (on the device, on the host, or as part of a
+// batched loop), and the results (solve_finish).
+struct SolveRun {
+  const void* b = nullptr;
+  void* x = nullptr;
+  SolveBufs B;
+  double lam2 = 0.0, lam2_pc = 0.0, rr0 = 0.0, final_rr = 0.0;
+  bool f64 = false, reliable = false, folded = false;
+  int maxit = 0, iters = 0, repl = 0;
+  kp_status result = KP_OK;
+  bool need_loop = false;  // the iterations are still to run
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+// Everything before the iterations: flags, A^T b and its norm, x0 / r0 (or
+// the true residual of a warm start), and z0 = M^-1 r0, p0 = z0 when the
+// start does not already meet the tolerance (then R->need_loop).
+static kp_status solve_begin(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible, void* x,
+                             int warm_start, SolveRun* R) {
   const long long N = (long long)ctx->n_r * ctx->n_c;
   KP_TRY(choose_inner(ctx, lambda * lambda));
   const bool f64 = ctx->vec_prec == KP_F64;
@@ -353,12 +410,21 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
   // default: reliable updates for every operator below FP64
   double delta = ctx->reliable_delta >= 0 ? ctx->reliable_delta : (ctx->op_prec == KP_F64 ? 0.0 : 0.1);
   const bool reliable = delta > 0.0;
-  const bool folded = cg_fusable(ctx);
+  R->b = b;
+  R->x = x;
+  R->B = B;
+  R->lam2 = lam2;
+  R->lam2_pc = lam2_pc;
+  R->f64 = f64;
+  R->reliable = reliable;
+  R->folded = cg_fusable(ctx);
+  R->maxit = maxit;
+  R->need_loop = false;
+  R->result = KP_OK;
 
-  cudaEvent_t e0, e1;
-  KP_CUDA(cudaEventCreate(&e0));
-  KP_CUDA(cudaEventCreate(&e1));
-  KP_CUDA(cudaEventRecord(e0, st));
+  KP_CUDA(cudaEventCreate(&R->e0));
+  KP_CUDA(cudaEventCreate(&R->e1));
+  KP_CUDA(cudaEventRecord(R->e0, st));
   KP_CUDA(cudaMemsetAsync(ctx->dflags, 0, 64, st));
   KP_CUDA(cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), st));
   {
@@ -373,41 +439,124 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
   double hs[12];
   KP_TRY(read_flags(ctx, &hf, hs));
   const double rr0 = hs[S_RR0];
-  kp_status result = KP_OK;
-  int iters = 0, repl = 0;
-  double final_rr = 0.0;
+  R->rr0 = rr0;
   if (!(rr0 > 0.0) || !std::isfinite(rr0)) {
     if (!std::isfinite(rr0)) {
       kp_set_error("tik_pcg: A^T b is not finite");
-      result = KP_ENUMERIC;
+      R->result = KP_ENUMERIC;
     } else {
       KP_CUDA(cudaMemsetAsync(x, 0, N * (f64 ? 8 : 4), st));
     }
+    return KP_OK;
+  }
+  KP_TRY(set_scalar(ctx, S_TOL2, tol * tol * rr0));
+  KP_TRY(set_scalar(ctx, S_DELTA2, reliable ? delta * delta : 0.0));
+  if (warm_start) {
+    KP_TRY(replace_residual(ctx, B, b, x, lam2));
   } else {
-    KP_TRY(set_scalar(ctx, S_TOL2, tol * tol * rr0));
-    KP_TRY(set_scalar(ctx, S_DELTA2, reliable ? delta * delta : 0.0));
-    if (warm_start) {
-      KP_TRY(replace_residual(ctx, B, b, x, lam2));
-    } else {
-      KP_CUDA(cudaMemsetAsync(x, 0, N * (f64 ? 8 : 4), st));
-      KP_TRY(copy_vec(ctx, B.rhs, B.r, N, f64));
-      KP_TRY(norm_amax_dev(ctx, B.r, N, f64, ctx->dscal + S_RR));
-      KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RMAX, ctx->dscal + S_RR, 8, cudaMemcpyDeviceToDevice, st));
+    KP_CUDA(cudaMemsetAsync(x, 0, N * (f64 ? 8 : 4), st));
+    KP_TRY(copy_vec(ctx, B.rhs, B.r, N, f64));
+    KP_TRY(norm_amax_dev(ctx, B.r, N, f64, ctx->dscal + S_RR));
+    KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RMAX, ctx->dscal + S_RR, 8, cudaMemcpyDeviceToDevice, st));
+  }
+  KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RTPREV, ctx->dscal + S_RR, 8, cudaMemcpyDeviceToDevice, st));
+  KP_TRY(read_flags(ctx, &hf, hs));
+  double h0 = std::sqrt(hs[S_RR] / rr0);
+  KP_CUDA(cudaMemcpyAsync(ctx->hist, &h0, sizeof(double), cudaMemcpyHostToDevice, st));
+  R->final_rr = hs[S_RR];
+  if (hs[S_RR] <= tol * tol * rr0) return KP_OK;  // converged at the start
+  // z0 = M^-1 r0, zr, p0 = z0
+  KP_TRY(pc_apply(ctx, B.r, B.z, lam2_pc, ctx->dscal + S_RR, nullptr));
+  KP_TRY(dot2_dev(ctx, B.z, B.r, nullptr, N, f64, ctx->dscal + S_ZR, nullptr));
+  const int sl = op_inner_slices(ctx);
+  KP_TRY(p_update_dev(ctx, B.p, B.z, N, f64, nullptr, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N, nullptr));
+  KP_CUDA(cudaStreamSynchronize(st));  // h0 is a host stack value
+  R->need_loop = true;
+  return KP_OK;
+}
+
+// the solve's status from the flags of a device-side (or batched) loop
+static void loop_result(SolveRun* R, const int* fl) {
+  const int reason = fl[F_REASON];
+  const int iters = R->iters;
+  const double rel = std::sqrt(R->final_rr / R->rr0);
+  if (reason & R_NUMERIC) {
+    kp_set_error("tik_pcg: NaN / Inf at iteration %d", iters);
+    R->result = KP_ENUMERIC;
+  } else if (reason & R_BREAKDOWN) {
+    kp_set_error("tik_pcg: breakdown (p^T K p <= 0 or z^T r <= 0) at iteration %d", iters);
+    R->result = KP_EBREAKDOWN;
+  } else if (reason & R_TRUE) {
+    R->result = KP_OK;
+  } else if (reason & R_STAGNATE) {
+    R->result = KP_ENOCONV;
+    kp_set_error("tik_pcg: stagnated at ||r||/||A^T b|| = %.3e (iteration %d): the tolerance is below the "
+                 "attainable accuracy of this precision", rel, iters);
+  } else if (reason & R_MAXIT) {
+    R->result = KP_ENOCONV;
+    kp_set_error("tik_pcg: maxit %d reached, ||r||/||A^T b|| = %.3e", R->maxit, rel);
+  } else if (reason & R_CONV) {
+    R->result = KP_OK;
+  } else {
+    R->result = KP_ENOCONV;
+    kp_set_error("tik_pcg: the device loop ended without a stop reason (iteration %d)", iters);
+  }
+}
+
+// after the loop: timing, the device status word, the info record
+static kp_status solve_finish(kp_ctx* ctx, SolveRun* R, kp_solve_info* info) {
+  KP_CUDA(cudaEventRecord(R->e1, ctx->stream));
+  KP_CUDA(cudaEventSynchronize(R->e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, R->e0, R->e1);
+  cudaEventDestroy(R->e0);
+  cudaEventDestroy(R->e1);
+  R->e0 = R->e1 = nullptr;
+  kp_status result = R->result;
+  kp_status dst = read_status(ctx);
+  if (dst != KP_OK) result = dst;
+  if (info) {
+    info->iters = R->iters;
+    info->replacements = R->repl;
+    info->rel_res = R->rr0 > 0 ? std::sqrt(R->final_rr / R->rr0) : 0.0;
+    info->status = result;
+    info->ms_solve = ms;
+    info->ms_setup = ctx->last_setup_ms;
+    if (info->res_hist && info->res_hist_len > 0) {
+      int n = std::min(info->res_hist_len, std::min(R->iters + 1, ctx->hist_cap));
+      KP_CUDA(cudaMemcpy(info->res_hist, ctx->hist, sizeof(double) * n, cudaMemcpyDeviceToHost));
     }
-    KP_CUDA(cudaMemcpyAsync(ctx->dscal + S_RTPREV, ctx->dscal + S_RR, 8, cudaMemcpyDeviceToDevice, st));
-    KP_TRY(read_flags(ctx, &hf, hs));
-    double h0 = std::sqrt(hs[S_RR] / rr0);
-    KP_CUDA(cudaMemcpyAsync(ctx->hist, &h0, sizeof(double), cudaMemcpyHostToDevice, st));
-    final_rr = hs[S_RR];
-    if (hs[S_RR] <= tol * tol * rr0) {
-      result = KP_OK;
-    } else {
-      // z0 = M^-1 r0, zr, p0 = z0
-      KP_TRY(pc_apply(ctx, B.r, B.z, lam2_pc, ctx->dscal + S_RR, nullptr));
-      KP_TRY(dot2_dev(ctx, B.z, B.r, nullptr, N, f64, ctx->dscal + S_ZR, nullptr));
-      const int sl = op_inner_slices(ctx);
-      KP_TRY(p_update_dev(ctx, B.p, B.z, N, f64, nullptr, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N,
-                          nullptr));
+  }
+  return result;
+}
+
+static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible, void* x,
+                              int warm_start, kp_solve_info* info) {
+  SolveRun R;
+  {
+    const kp_status bs = solve_begin(ctx, b, lambda, tol, maxit, flexible, x, warm_start, &R);
+    if (bs != KP_OK) {
+      if (R.e0) cudaEventDestroy(R.e0);
+      if (R.e1) cudaEventDestroy(R.e1);
+      return bs;
+    }
+  }
+  const long long N = (long long)ctx->n_r * ctx->n_c;
+  const bool f64 = R.f64;
+  const double lam2 = R.lam2, lam2_pc = R.lam2_pc;
+  const bool reliable = R.reliable, folded = R.folded;
+  const SolveBufs B = R.B;
+  cudaStream_t st = ctx->stream;
+  const double rr0 = R.rr0;
+  kp_status result = R.result;
+  int iters = 0, repl = 0;
+  double final_rr = R.final_rr;
+  HostFlags hf;
+  double hs[12];
+  (void)N;
+  (void)f64;
+  if (R.need_loop) {
+    {
       bool done_device = false;
       if (ctx->device_loop) {
         // the whole loop on the device (one graph launch); on any failure
@@ -424,28 +573,10 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
           repl = fl[F_REPL];
           final_rr = hs[S_RR];
           ctx->launches += (long long)fl[F_GUARD] * L.launches_body + (long long)repl * L.launches_replace;
-          const int reason = fl[F_REASON];
-          if (reason & R_NUMERIC) {
-            kp_set_error("tik_pcg: NaN / Inf at iteration %d", iters);
-            result = KP_ENUMERIC;
-          } else if (reason & R_BREAKDOWN) {
-            kp_set_error("tik_pcg: breakdown (p^T K p <= 0 or z^T r <= 0) at iteration %d", iters);
-            result = KP_EBREAKDOWN;
-          } else if (reason & R_TRUE) {
-            result = KP_OK;
-          } else if (reason & R_STAGNATE) {
-            result = KP_ENOCONV;
-            kp_set_error("tik_pcg: stagnated at ||r||/||A^T b|| = %.3e (iteration %d): the tolerance is below the "
-                         "attainable accuracy of this precision", std::sqrt(final_rr / rr0), iters);
-          } else if (reason & R_MAXIT) {
-            result = KP_ENOCONV;
-            kp_set_error("tik_pcg: maxit %d reached, ||r||/||A^T b|| = %.3e", maxit, std::sqrt(final_rr / rr0));
-          } else if (reason & R_CONV) {
-            result = KP_OK;
-          } else {
-            result = KP_ENOCONV;
-            kp_set_error("tik_pcg: the device loop ended without a stop reason (iteration %d)", iters);
-          }
+          R.iters = iters;
+          R.final_rr = final_rr;
+          loop_result(&R, fl);
+          result = R.result;
           done_device = true;
         } else {
           cudaGetLastError();  // a capture error is not sticky; use the host loop
@@ -582,27 +713,11 @@ static kp_status tik_pcg_impl(kp_ctx* ctx, const void* b, double lambda, double 
       }  // host loop
     }
   }
-  KP_CUDA(cudaEventRecord(e1, st));
-  KP_CUDA(cudaEventSynchronize(e1));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  kp_status dst = read_status(ctx);
-  if (dst != KP_OK) result = dst;
-  if (info) {
-    info->iters = iters;
-    info->replacements = repl;
-    info->rel_res = rr0 > 0 ? std::sqrt(final_rr / rr0) : 0.0;
-    info->status = result;
-    info->ms_solve = ms;
-    info->ms_setup = ctx->last_setup_ms;
-    if (info->res_hist && info->res_hist_len > 0) {
-      int n = std::min(info->res_hist_len, std::min(iters + 1, ctx->hist_cap));
-      KP_CUDA(cudaMemcpy(info->res_hist, ctx->hist, sizeof(double) * n, cudaMemcpyDeviceToHost));
-    }
-  }
-  return result;
+  R.iters = iters;
+  R.repl = repl;
+  R.final_rr = final_rr;
+  R.result = result;
+  return solve_finish(ctx, &R, info);
 }
 
 extern "C" kp_status tik_pcg(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible, void* x,
@@ -620,6 +735,99 @@ extern "C" kp_status tik_pcg(kp_ctx* ctx, const void* b, double lambda, double t
   kp_status s = tik_pcg_impl(ctx, b, lambda, tol, maxit, flexible, x, warm_start, info);
   kp_status l = kp_leave(ctx);
   return s != KP_OK ? s : l;
+}
+
+// ---------------------------------------------------------------- batched solves
+// One problem's solve around an iteration loop that runs grouped with other
+// problems' (kp_batch.cu): the steps before the loop, the loop's body
+// recorded in three segments (first half; the residual replacement, skipped
+// by the problems for which none is due; second half), the decision flags,
+// and the results after the loop.
+struct BatchRun {
+  SolveRun R;
+  bool looped = false;
+};
+
+kp_status batch_begin(kp_ctx* ctx, const void* b, double lambda, double tol, int maxit, int flexible, void* x,
+                      BatchRun** out) {
+  *out = nullptr;
+  auto* br = new BatchRun();
+  const kp_status s = solve_begin(ctx, b, lambda, tol, maxit, flexible, x, 0, &br->R);
+  if (s != KP_OK) {
+    if (br->R.e0) cudaEventDestroy(br->R.e0);
+    if (br->R.e1) cudaEventDestroy(br->R.e1);
+    delete br;
+    return s;
+  }
+  *out = br;
+  return KP_OK;
+}
+
+// the loop is still to run, and its body has the form the grouped loop runs
+// (the folded iteration of a tensor-core operator)
+bool batch_groupable(const BatchRun* br) { return br->R.need_loop && br->R.folded && br->R.reliable; }
+bool batch_needs_loop(const BatchRun* br) { return br->R.need_loop; }
+
+kp_status batch_record(kp_ctx* ctx, BatchRun* br, KpRecorder* seg_a, KpRecorder* seg_r, KpRecorder* seg_b) {
+  const SolveRun& R = br->R;
+  LoopConds lc;
+  lc.mode = 2;
+  const int* nd = ctx->dflags + F_NOTDUE;
+  kp_status s;
+  ctx->rec = seg_a;
+  s = half_a_folded(ctx, R.B, R.x, R.lam2, R.lam2_pc, &lc);
+  ctx->rec = seg_r;
+  if (s == KP_OK) s = replace_residual(ctx, R.B, R.b, R.x, R.lam2, nd);
+  if (s == KP_OK) {
+    const cudaError_t e = kp_launch_g<AfterReplace>(ctx, k_loop_after_replace, dim3(1), dim3(1), 0, ctx->dscal,
+                                                    ctx->dflags, ctx->hist, ctx->hist_cap,
+                                                    (cudaGraphConditionalHandle)0, nd, 1);
+    if (e != cudaSuccess) {
+      kp_set_error("batched solve: %s", cudaGetErrorString(e));
+      s = KP_ECUDA;
+    }
+  }
+  if (s == KP_OK) s = pc_prepare_input(ctx, R.B.r, R.lam2_pc, ctx->dscal + S_RR, nd);
+  ctx->rec = seg_b;
+  if (s == KP_OK) s = half_b(ctx, R.B, R.lam2_pc, true);
+  ctx->rec = nullptr;
+  return s;
+}
+
+// before the grouped loop: no replacement due, the loop goes on
+kp_status batch_arm(kp_ctx* ctx, BatchRun* br) {
+  const int v[2] = {1, 1};
+  static_assert(F_BLOOP == F_NOTDUE + 1, "adjacent flag slots");
+  KP_CUDA(cudaMemcpyAsync(ctx->dflags + F_NOTDUE, v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));  // v is a host stack value
+  br->looped = true;
+  return KP_OK;
+}
+
+// after the grouped loop (or without one): status and info; frees br
+kp_status batch_finish(kp_ctx* ctx, BatchRun* br, kp_solve_info* info) {
+  SolveRun& R = br->R;
+  if (br->looped) {
+    int fl[16];
+    double hs[12];
+    KP_CUDA(cudaMemcpyAsync(fl, ctx->dflags, sizeof(fl), cudaMemcpyDeviceToHost, ctx->stream));
+    KP_CUDA(cudaMemcpyAsync(hs, ctx->dscal, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+    KP_CUDA(cudaStreamSynchronize(ctx->stream));
+    R.iters = fl[F_ITER];
+    R.repl = fl[F_REPL];
+    R.final_rr = hs[S_RR];
+    loop_result(&R, fl);
+  }
+  const kp_status s = solve_finish(ctx, &R, info);
+  delete br;
+  return s;
+}
+
+void batch_discard(BatchRun* br) {
+  if (!br) return;
+  if (br->R.e0) cudaEventDestroy(br->R.e0);
+  if (br->R.e1) cudaEventDestroy(br->R.e1);
+  delete br;
 }
 
 // ---------------------------------------------------------------- operator hooks

@@ -13,6 +13,7 @@
 // convergence test, beta) on the final values, saving a launch.
 #include <type_traits>
 
+#include "kp_group.cuh"
 #include "kp_vec.cuh"
 
 namespace kpv {
@@ -26,7 +27,7 @@ constexpr int FLUSH = 16;  // float4 packets per thread between FP64 flushes
 // ------------------------------------------------------------- dot products
 // out[0] = a.b ; if c != null, out[1] = a.c
 template <typename T>
-__global__ void __launch_bounds__(VEC_THREADS) k_dot2(const T* __restrict__ a, const T* __restrict__ b,
+__device__ __forceinline__ void k_dot2_body(const T* __restrict__ a, const T* __restrict__ b,
                                                       const T* __restrict__ c, long long n, int vec4,
                                                       double* partials, unsigned int* counter, double* out,
                                                       const int* flags, PostOp po) {
@@ -70,6 +71,13 @@ __global__ void __launch_bounds__(VEC_THREADS) k_dot2(const T* __restrict__ a, c
     reduce_finish<2>(v, false, partials, counter, out, c ? 2 : 1, po);
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS) k_dot2(const T* __restrict__ a, const T* __restrict__ b,
+                                                      const T* __restrict__ c, long long n, int vec4,
+                                                      double* partials, unsigned int* counter, double* out,
+                                                      const int* flags, PostOp po) {
+  k_dot2_body<T>(a, b, c, n, vec4, partials, counter, out, flags, po);
+}
 
 // y = alpha*x + beta*y (scalars from host); used by setup / hooks
 template <typename T>
@@ -93,8 +101,13 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T*
     // paused before the update (NaN or breakdown in alpha): inside the loop
     // graph no replacement, and the loop ends
     if (po.cond && blockIdx.x == 0 && threadIdx.x == 0) {
-      cudaGraphSetConditional(po.h_rep, 0u);
-      cudaGraphSetConditional(po.h_loop, 0u);
+      if (po.cond == 1) {
+        cudaGraphSetConditional(po.h_rep, 0u);
+        cudaGraphSetConditional(po.h_loop, 0u);
+      } else {
+        po.f[F_NOTDUE] = 1;
+        po.f[F_BLOOP] = 0;
+      }
     }
     return;
   }
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(T* __restrict__ x, T*
 // p = z + beta p ; optional bf16 split copy of p (slices written at stride).
 // With beta_dev null, p = z: the old p is not read (it may be uninitialised).
 template <typename T>
-__global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long n, int vec4,
+__device__ __forceinline__ void k_p_update_body(T* __restrict__ p, const T* __restrict__ z, long long n, int vec4,
                            const double* __restrict__ beta_dev, __nv_bfloat16* __restrict__ ps, int slices,
                            long long sstride, const int* flags) {
   KP_PDL_WAIT();
@@ -217,13 +230,20 @@ __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long
     }
   }
 }
+template <typename T>
+__global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, long long n, int vec4,
+                           const double* __restrict__ beta_dev, __nv_bfloat16* __restrict__ ps, int slices,
+                           long long sstride, const int* flags) {
+  k_p_update_body<T>(p, z, n, vec4, beta_dev, ps, slices, sstride, flags);
+}
 
 // bf16 slices of a vector (x -> hi, mid, lo)
 template <typename T>
-__global__ void k_split(const T* __restrict__ x, long long n, __nv_bfloat16* __restrict__ out, int slices,
-                        long long sstride) {
+__device__ __forceinline__ void k_split_body(const T* __restrict__ x, long long n, __nv_bfloat16* __restrict__ out, int slices,
+                        long long sstride, const int* flags) {
   KP_PDL_WAIT();
   KP_PDL_TRIGGER();
+  if (paused(flags)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     float v = (float)x[i];
     for (int s = 0; s < slices; ++s) {
@@ -232,6 +252,11 @@ __global__ void k_split(const T* __restrict__ x, long long n, __nv_bfloat16* __r
       v -= __bfloat162float(h);
     }
   }
+}
+template <typename T>
+__global__ void k_split(const T* __restrict__ x, long long n, __nv_bfloat16* __restrict__ out, int slices,
+                        long long sstride, const int* flags) {
+  k_split_body<T>(x, n, out, slices, sstride, flags);
 }
 
 // Quantise r for the reduced-precision preconditioner: out = narrow(r * 2^e)
@@ -244,7 +269,7 @@ __device__ __forceinline__ float pow2_scale(double amax, double target) {
   return (float)ldexp(1.0, e - 1);
 }
 template <typename T, typename N>
-__global__ void k_quantize(const T* __restrict__ r, long long n, int vec4, const double* __restrict__ stat,
+__device__ __forceinline__ void k_quantize_body(const T* __restrict__ r, long long n, int vec4, const double* __restrict__ stat,
                            double target, double lam2, N* __restrict__ out, float* __restrict__ inv_out,
                            unsigned int* __restrict__ reset, int nreset, const int* flags) {
   KP_PDL_WAIT();
@@ -275,6 +300,12 @@ __global__ void k_quantize(const T* __restrict__ r, long long n, int vec4, const
   }
   for (long long i = i0; i < n; i += stride) out[i] = to_narrow<N>((float)r[i] * s);
 }
+template <typename T, typename N>
+__global__ void k_quantize(const T* __restrict__ r, long long n, int vec4, const double* __restrict__ stat,
+                           double target, double lam2, N* __restrict__ out, float* __restrict__ inv_out,
+                           unsigned int* __restrict__ reset, int nreset, const int* flags) {
+  k_quantize_body<T, N>(r, n, vec4, stat, target, lam2, out, inv_out, reset, nreset, flags);
+}
 
 // two narrow values packed in 32 bits (low half first)
 template <typename NQ>
@@ -298,8 +329,7 @@ __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, float b) {
 // narrow type's range.  out2[1] (max |r| of the previous update) is read by
 // every block before the last block overwrites it.
 template <typename NQ>
-__global__ void __launch_bounds__(VEC_THREADS)
-    k_update_xr_q(float* __restrict__ x, float* __restrict__ r, float* __restrict__ r_old, const float* __restrict__ p,
+__device__ __forceinline__ void k_update_xr_q_body(float* __restrict__ x, float* __restrict__ r, float* __restrict__ r_old, const float* __restrict__ p,
                   const float* __restrict__ q, long long n, int vec4, const double* __restrict__ alpha_dev,
                   const double* __restrict__ qmax_dev, double lam2, NQ* __restrict__ out, float* __restrict__ inv_out,
                   double* partials, unsigned int* counter, double* out2, const int* flags, PostOp po) {
@@ -307,8 +337,13 @@ __global__ void __launch_bounds__(VEC_THREADS)
   KP_PDL_TRIGGER();
   if (paused(flags)) {
     if (po.cond && blockIdx.x == 0 && threadIdx.x == 0) {
-      cudaGraphSetConditional(po.h_rep, 0u);
-      cudaGraphSetConditional(po.h_loop, 0u);
+      if (po.cond == 1) {
+        cudaGraphSetConditional(po.h_rep, 0u);
+        cudaGraphSetConditional(po.h_loop, 0u);
+      } else {  // batched loop: this problem takes no replacement and has stopped
+        po.f[F_NOTDUE] = 1;
+        po.f[F_BLOOP] = 0;
+      }
     }
     return;
   }
@@ -354,6 +389,14 @@ __global__ void __launch_bounds__(VEC_THREADS)
   }
   reduce_finish_df<2>(hi, lo, true, partials, counter, out2, 2, po);
 }
+template <typename NQ>
+__global__ void __launch_bounds__(VEC_THREADS)
+    k_update_xr_q(float* __restrict__ x, float* __restrict__ r, float* __restrict__ r_old, const float* __restrict__ p,
+                  const float* __restrict__ q, long long n, int vec4, const double* __restrict__ alpha_dev,
+                  const double* __restrict__ qmax_dev, double lam2, NQ* __restrict__ out, float* __restrict__ inv_out,
+                  double* partials, unsigned int* counter, double* out2, const int* flags, PostOp po) {
+  k_update_xr_q_body<NQ>(x, r, r_old, p, q, n, vec4, alpha_dev, qmax_dev, lam2, out, inv_out, partials, counter, out2, flags, po);
+}
 
 // One stage of the E4M3 preconditioner solve: the stage's FP32 GEMM output
 // (max |.| accumulated by the GEMM epilogue into *amax_bits) is scaled by a
@@ -393,10 +436,11 @@ __global__ void k_quant8(const float* __restrict__ in, long long n, int vec4, co
 
 // amax only (for one-off applies outside the loop)
 template <typename T>
-__global__ void __launch_bounds__(VEC_THREADS) k_norm_amax(const T* __restrict__ x, long long n, double* partials,
-                                                           unsigned int* counter, double* out) {
+__device__ __forceinline__ void k_norm_amax_body(const T* __restrict__ x, long long n, double* partials,
+                                                           unsigned int* counter, double* out, const int* flags) {
   KP_PDL_WAIT();
   KP_PDL_TRIGGER();
+  if (paused(flags)) return;
   double v[2] = {0.0, 0.0};
   const long long tid = blockIdx.x * (long long)VEC_THREADS + threadIdx.x, stride = (long long)gridDim.x * VEC_THREADS;
   if constexpr (std::is_same<T, float>::value) {
@@ -416,6 +460,11 @@ __global__ void __launch_bounds__(VEC_THREADS) k_norm_amax(const T* __restrict__
     reduce_finish<2>(v, true, partials, counter, out, 2);
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS) k_norm_amax(const T* __restrict__ x, long long n, double* partials,
+                                                           unsigned int* counter, double* out, const int* flags) {
+  k_norm_amax_body<T>(x, n, partials, counter, out, flags);
+}
 
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, long long n) {
@@ -427,6 +476,21 @@ __global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, long long 
 
 // ------------------------------------------------------------- host wrappers
 using namespace kpv;
+
+// bodies of the kernels that batched solves group (kp_group.cuh)
+KP_BODY(DotF, kpv::k_dot2_body<float>);
+KP_BODY(DotD, kpv::k_dot2_body<double>);
+KP_BODY(NormAmaxF, kpv::k_norm_amax_body<float>);
+KP_BODY(NormAmaxD, kpv::k_norm_amax_body<double>);
+KP_BODY(UpdXrQH, kpv::k_update_xr_q_body<__half>);
+KP_BODY(UpdXrQB, kpv::k_update_xr_q_body<__nv_bfloat16>);
+KP_BODY(PUpdF, kpv::k_p_update_body<float>);
+KP_BODY(PUpdD, kpv::k_p_update_body<double>);
+KP_BODY(SplitF, kpv::k_split_body<float>);
+KP_BODY(SplitD, kpv::k_split_body<double>);
+KP_BODY(QuantB, kpv::k_quantize_body<float, __nv_bfloat16>);
+KP_BODY(QuantH, kpv::k_quantize_body<float, __half>);
+KP_BODY(Quant8, kpv::k_quantize_body<float, __nv_fp8_e4m3>);
 
 int vec_grid(kp_ctx* ctx, long long n) {
   long long b = (n + VEC_THREADS * 4 - 1) / (VEC_THREADS * 4);
@@ -446,10 +510,10 @@ kp_status dot2_dev(kp_ctx* ctx, const void* a, const void* b, const void* c, lon
                    const int* flags, PostOp post) {
   int g = vec_grid(ctx, n);
   if (f64)
-    KP_CUDA(kp_launch(ctx, k_dot2<double>, dim3(g), dim3(VEC_THREADS), 0, (const double*)a, (const double*)b, (const double*)c, n, 0,
+    KP_CUDA(kp_launch_g<DotD>(ctx, k_dot2<double>, dim3(g), dim3(VEC_THREADS), 0, (const double*)a, (const double*)b, (const double*)c, n, 0,
                                                        ctx->red_part, ctx->red_count, out, flags, post));
   else
-    KP_CUDA(kp_launch(ctx, k_dot2<float>, dim3(g), dim3(VEC_THREADS), 0, (const float*)a, (const float*)b, (const float*)c, n,
+    KP_CUDA(kp_launch_g<DotF>(ctx, k_dot2<float>, dim3(g), dim3(VEC_THREADS), 0, (const float*)a, (const float*)b, (const float*)c, n,
                                                       aligned16(a, b, c), ctx->red_part, ctx->red_count, out, flags,
                                                       post));
   KP_LAUNCHED(ctx);
@@ -461,12 +525,12 @@ kp_status dot_dev(kp_ctx* ctx, const void* x, const void* y, long long n, bool f
   return dot2_dev(ctx, x, y, nullptr, n, f64, out_dev, nullptr);
 }
 
-kp_status norm_amax_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out2) {
+kp_status norm_amax_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out2, const int* flags) {
   int g = vec_grid(ctx, n);
   if (f64)
-    KP_CUDA(kp_launch(ctx, k_norm_amax<double>, dim3(g), dim3(VEC_THREADS), 0, (const double*)x, n, ctx->red_part, ctx->red_count, out2));
+    KP_CUDA(kp_launch_g<NormAmaxD>(ctx, k_norm_amax<double>, dim3(g), dim3(VEC_THREADS), 0, (const double*)x, n, ctx->red_part, ctx->red_count, out2, flags));
   else
-    KP_CUDA(kp_launch(ctx, k_norm_amax<float>, dim3(g), dim3(VEC_THREADS), 0, (const float*)x, n, ctx->red_part, ctx->red_count, out2));
+    KP_CUDA(kp_launch_g<NormAmaxF>(ctx, k_norm_amax<float>, dim3(g), dim3(VEC_THREADS), 0, (const float*)x, n, ctx->red_part, ctx->red_count, out2, flags));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -499,11 +563,11 @@ kp_status update_xr_q_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void
   const int g = vec_grid(ctx, n);
   const int v4 = aligned16(x, r, r_old, p, q) && (((uintptr_t)pc_out & 7) == 0);
   if (narrow == NT_F16)
-    KP_CUDA(kp_launch(ctx, k_update_xr_q<__half>, dim3(g), dim3(VEC_THREADS), 0, (float*)x, (float*)r, (float*)r_old,
+    KP_CUDA(kp_launch_g<UpdXrQH>(ctx, k_update_xr_q<__half>, dim3(g), dim3(VEC_THREADS), 0, (float*)x, (float*)r, (float*)r_old,
                       (const float*)p, (const float*)q, n, v4, alpha_dev, qmax_dev, lam2, (__half*)pc_out, inv_out,
                       ctx->red_part, ctx->red_count, out2, flags, post));
   else if (narrow == NT_BF16)
-    KP_CUDA(kp_launch(ctx, k_update_xr_q<__nv_bfloat16>, dim3(g), dim3(VEC_THREADS), 0, (float*)x, (float*)r,
+    KP_CUDA(kp_launch_g<UpdXrQB>(ctx, k_update_xr_q<__nv_bfloat16>, dim3(g), dim3(VEC_THREADS), 0, (float*)x, (float*)r,
                       (float*)r_old, (const float*)p, (const float*)q, n, v4, alpha_dev, qmax_dev, lam2,
                       (__nv_bfloat16*)pc_out, inv_out, ctx->red_part, ctx->red_count, out2, flags, post));
   else {
@@ -519,10 +583,10 @@ kp_status p_update_dev(kp_ctx* ctx, void* p, const void* z, long long n, bool f6
                        __nv_bfloat16* ps, int slices, long long sstride, const int* flags) {
   int g = vec_grid(ctx, n);
   if (f64)
-    KP_CUDA(kp_launch(ctx, k_p_update<double>, dim3(g), dim3(VEC_THREADS), 0, (double*)p, (const double*)z, n, 0, beta_dev, ps, slices,
+    KP_CUDA(kp_launch_g<PUpdD>(ctx, k_p_update<double>, dim3(g), dim3(VEC_THREADS), 0, (double*)p, (const double*)z, n, 0, beta_dev, ps, slices,
                                                            sstride, flags));
   else
-    KP_CUDA(kp_launch(ctx, k_p_update<float>, dim3(g), dim3(VEC_THREADS), 0, 
+    KP_CUDA(kp_launch_g<PUpdF>(ctx, k_p_update<float>, dim3(g), dim3(VEC_THREADS), 0, 
         (float*)p, (const float*)z, n, aligned16(p, z) && (((uintptr_t)ps & 7) == 0) && (sstride % 4 == 0), beta_dev,
         ps, slices, sstride, flags));
   KP_LAUNCHED(ctx);
@@ -530,12 +594,13 @@ kp_status p_update_dev(kp_ctx* ctx, void* p, const void* z, long long n, bool f6
   return KP_OK;
 }
 
-kp_status split_bf16(kp_ctx* ctx, const void* x, bool f64, long long n, void* out, int slices, long long sstride) {
+kp_status split_bf16(kp_ctx* ctx, const void* x, bool f64, long long n, void* out, int slices, long long sstride,
+                     const int* flags) {
   int g = vec_grid(ctx, n);
   if (f64)
-    KP_CUDA(kp_launch(ctx, k_split<double>, dim3(g), dim3(VEC_THREADS), 0, (const double*)x, n, (__nv_bfloat16*)out, slices, sstride));
+    KP_CUDA(kp_launch_g<SplitD>(ctx, k_split<double>, dim3(g), dim3(VEC_THREADS), 0, (const double*)x, n, (__nv_bfloat16*)out, slices, sstride, flags));
   else
-    KP_CUDA(kp_launch(ctx, k_split<float>, dim3(g), dim3(VEC_THREADS), 0, (const float*)x, n, (__nv_bfloat16*)out, slices, sstride));
+    KP_CUDA(kp_launch_g<SplitF>(ctx, k_split<float>, dim3(g), dim3(VEC_THREADS), 0, (const float*)x, n, (__nv_bfloat16*)out, slices, sstride, flags));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());
   return KP_OK;
@@ -562,13 +627,13 @@ kp_status quantize_dev(kp_ctx* ctx, const void* r, long long n, bool f64, const 
   const float* rf = (const float*)r;
   const int v4 = aligned16(r);
   if (narrow == NT_BF16)
-    KP_CUDA(kp_launch(ctx, k_quantize<float, __nv_bfloat16>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2,
+    KP_CUDA(kp_launch_g<QuantB>(ctx, k_quantize<float, __nv_bfloat16>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2,
                                                                           (__nv_bfloat16*)out, inv_out, reset, nreset, flags));
   else if (narrow == NT_F16)
-    KP_CUDA(kp_launch(ctx, k_quantize<float, __half>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2, (__half*)out,
+    KP_CUDA(kp_launch_g<QuantH>(ctx, k_quantize<float, __half>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2, (__half*)out,
                                                                    inv_out, reset, nreset, flags));
   else
-    KP_CUDA(kp_launch(ctx, k_quantize<float, __nv_fp8_e4m3>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2,
+    KP_CUDA(kp_launch_g<Quant8>(ctx, k_quantize<float, __nv_fp8_e4m3>, dim3(g), dim3(VEC_THREADS), 0, rf, n, v4, stat, target, lam2,
                                                                           (__nv_fp8_e4m3*)out, inv_out, reset, nreset, flags));
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaGetLastError());

@@ -22,7 +22,9 @@ enum {
 };
 enum { F_PAUSE = 0, F_REASON = 1, F_ITER = 2, F_MAXIT = 3, F_FLEX = 4, F_STAG = 5, F_SINCE = 6,
        F_SAVED = 7,   // device loop: the reason that triggered a residual replacement
-       F_REPL = 8 };  // device loop: residual replacements done
+       F_REPL = 8,    // device loop: residual replacements done
+       F_NOTDUE = 9,  // batched loop: 1 unless this problem's residual replacement is due (its skip flag)
+       F_BLOOP = 10 };  // batched loop: this problem's loop goes on
 constexpr int F_GUARD = 15;  // device loop: passes of the loop body
 // the multi-term preconditioner's inner PCG keeps its scalars and flags in
 // blocks of their own, at these offsets into ctx->dscal / ctx->dflags
@@ -39,8 +41,10 @@ enum { R_CONV = 1, R_REPLACE = 2, R_MAXIT = 4, R_BREAKDOWN = 8, R_NUMERIC = 16 }
 enum { POST_NONE = 0, POST_ALPHA = 1, POST_CHECK = 2, POST_BETA = 3 };
 struct PostOp {
   int kind = POST_NONE;
-  // POST_CHECK inside the device-side loop graph: also set the graph's
-  // conditions (residual replacement due; loop continues)
+  // POST_CHECK inside the device-side loop graph: 1 = also set the graph's
+  // conditions (residual replacement due; loop continues); 2 = batched loop:
+  // write them to F_NOTDUE / F_BLOOP (the loop's own kernels combine the
+  // problems' decisions)
   int cond = 0;
   cudaGraphConditionalHandle h_rep = 0, h_loop = 0;
   double* s = nullptr;
@@ -52,7 +56,7 @@ struct PostOp {
 int vec_grid(kp_ctx* ctx, long long n);
 kp_status dot2_dev(kp_ctx* ctx, const void* a, const void* b, const void* c, long long n, bool f64, double* out,
                    const int* flags, PostOp post = PostOp());
-kp_status norm_amax_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out2);
+kp_status norm_amax_dev(kp_ctx* ctx, const void* x, long long n, bool f64, double* out2, const int* flags = nullptr);
 kp_status update_xr_dev(kp_ctx* ctx, void* x, void* r, void* r_old, const void* p, const void* q, long long n,
                         bool f64, const double* alpha_dev, double* out2, const int* flags, PostOp post = PostOp());
 // The same update, also writing the preconditioner's input narrow(r * s)
@@ -337,8 +341,14 @@ __device__ inline void run_post(const PostOp& po, const double* vals) {
         }
       }
       if (++f[F_GUARD] > f[F_MAXIT] + 8) loop = 0u;
-      cudaGraphSetConditional(po.h_rep, repl);
-      cudaGraphSetConditional(po.h_loop, loop);
+      if (po.cond == 1) {
+        cudaGraphSetConditional(po.h_rep, repl);
+        cudaGraphSetConditional(po.h_loop, loop);
+      } else {
+        f[F_NOTDUE] = repl ? 0 : 1;
+        f[F_BLOOP] = loop;
+        if (!loop) f[F_PAUSE] = 1;  // a stopped problem's kernels skip from here on
+      }
     }
   } else if (po.kind == POST_BETA) {  // vals[0] = z^T r, vals[1] = z^T r_old
     const double zn = vals[0], zo = vals[1], zr = s[S_ZR];

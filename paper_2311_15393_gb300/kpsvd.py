@@ -29,7 +29,7 @@ N_FEAT = 256  # spectral features per problem (kp_lambda_features, the MLP's inp
 EXPORTS = ["kp_create", "kp_destroy", "kp_setup", "kp_forward", "tik_pcg", "choose_lambda", "kp_apply_A",
            "kp_apply_K", "kp_apply_Minv", "kp_get_spectrum", "kp_get_terms", "kp_get_kpsvd", "kp_get_rank",
            "kp_set_option", "kp_launch_count", "kp_time_parts", "kp_test_bounded_wait", "kp_status_str", "kp_last_error", "kp_apply_Minv_noalloc",
-           "kp_solve_batch", "kp_lambda_features", "kp_mlp_create", "kp_mlp_destroy", "kp_mlp_param_count",
+           "kp_solve_batch", "kp_batch_release", "kp_batch_grouped", "kp_lambda_features", "kp_mlp_create", "kp_mlp_destroy", "kp_mlp_param_count",
            "kp_mlp_set_params", "kp_mlp_get_params", "kp_mlp_forward", "kp_mlp_gradients", "kp_mlp_train_step"]
 
 
@@ -57,7 +57,8 @@ class BatchOpts(ctypes.Structure):
     """kp_batch_opts."""
     _fields_ = [("op_prec", ctypes.c_int), ("pc_prec", ctypes.c_int), ("vec_prec", ctypes.c_int),
                 ("sigma", ctypes.c_int), ("method", ctypes.c_int), ("tol", ctypes.c_double),
-                ("maxit", ctypes.c_int), ("flexible", ctypes.c_int), ("workers", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("flexible", ctypes.c_int), ("workers", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -88,6 +89,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "kp_last_error": ([], ctypes.c_char_p),
         "kp_apply_Minv_noalloc": ([vp, vp, vp, i, i, d, vp, vp, vp], i),
         "kp_solve_batch": ([i, ctypes.POINTER(Problem), i, ctypes.POINTER(BatchOpts), dp], i),
+        "kp_batch_release": ([i], None),
+        "kp_batch_grouped": ([i, ctypes.POINTER(i)], i),
         "kp_lambda_features": ([vp, vp, vp], i),
         "kp_mlp_create": ([ctypes.POINTER(vp), i, vp, i, i, i], i),
         "kp_mlp_destroy": ([vp], None),
@@ -313,11 +316,14 @@ class KpContext:
 
 def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_prec: str = "f32",
                    sigma: str = "projected", method: str = "gcv", tol: float = 1e-7, maxit: int = 500,
-                   flexible: bool = True, workers: int = 8, device: int = 0, check: bool = True):
+                   flexible: bool = True, workers: int = 0, device: int = 0, check: bool = True,
+                   autotune: bool = False):
     """Solve a batch of independent problems (kp_solve_batch).  ``problems``:
     dicts with psf, b, x (torch CUDA tensors), n_r, n_c, center, bc, op_rank and
-    optionally lam (> 0: fixed) and lambda_param.  Returns (status, ms_total,
-    [(lambda, Info), ...]) in the order given."""
+    optionally lam (> 0: fixed) and lambda_param.  ``workers`` 0: the grouped
+    form (one launch per iteration step over all problems); > 0: host
+    threads.  Returns (status, ms_total, [(lambda, Info), ...]) in the order
+    given."""
     arr = (Problem * len(problems))()
     vt = _VEC_DTYPE.get(vec_prec, "float32")
     for k, p in enumerate(problems):
@@ -332,7 +338,7 @@ def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_pr
         q.lambda_ = p.get("lam") or 0.0
         q.lambda_param = p.get("lambda_param", 0.0)
     o = BatchOpts(PREC[op_prec], PREC[pc_prec], PREC[vec_prec], SIGMA[sigma], LAMBDA[method], tol, maxit,
-                  1 if flexible else 0, workers)
+                  1 if flexible else 0, workers, 1 if autotune else 0)
     ms = ctypes.c_double(0.0)
     st = _lib.kp_solve_batch(device, arr, len(problems), ctypes.byref(o), ctypes.byref(ms))
     if check and st != KP_OK:
@@ -340,6 +346,13 @@ def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_pr
     out = [(q.lambda_, Info(q.info.iters, q.info.replacements, q.info.rel_res, q.info.status, q.info.ms_solve,
                             np.zeros(0))) for q in arr]
     return st, ms.value, out
+
+
+def kp_batch_grouped(device: int = 0):
+    """(problems the last grouped kp_solve_batch ran in its grouped loop, the loop's passes)."""
+    passes = ctypes.c_int(0)
+    n = _lib.kp_batch_grouped(device, ctypes.byref(passes))
+    return n, passes.value
 
 
 class Mlp:
