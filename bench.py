@@ -176,7 +176,8 @@ def peaks():
 
 # the sources of the K application's kernels (tensor-core GEMM, term sums,
 # bf16 split) and the headers they include
-KAPPLY_SOURCES = ("kp_gemm_tc.cu", "kp_internal.h", "kp_ops.cu", "kp_ops.h", "kp_vec.cu", "kp_vec.cuh")
+KAPPLY_SOURCES = ("kp_gemm_tc.cu", "kp_group.cuh", "kp_internal.h", "kp_ops.cu", "kp_ops.h", "kp_vec.cu",
+                  "kp_vec.cuh")
 
 
 def sources_digest():

@@ -272,6 +272,11 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     scaled from the exact max|r|
  *   "jacobi_tol"      one-sided Jacobi rotation threshold (default 1e-15)
  *   "jacobi_max_sweeps" (default 40)
+ *   "jacobi_block"    1 (default): the FP32 Jacobi sweeps (FP32-vector setup)
+ *                     in block form, each launch running a full sweep over
+ *                     two blocks of 4 columns held in registers (n / 4
+ *                     launches per sweep instead of n - 1) where m, n <= 1024;
+ *                     0: one launch per round of column pairs
  *   "splitk"          > 0: fixed split-K factor of the square tensor-core
  *                     GEMMs (default 0 = chosen per shape)
  *   "tc_bn"           64, 128 or 256: fixed tensor-core tile width (default 0 =

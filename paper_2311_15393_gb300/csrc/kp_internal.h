@@ -152,6 +152,7 @@ struct kp_ctx {
   bool cg_fuse = true;  // the x / r update also writes the preconditioner's narrow input (where possible)
   double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD
   int jacobi_max_sweeps = 40;
+  bool jacobi_block = true;   // FP32 sweeps in the register block form (k_jacobi_rblock) where it fits
   bool pdl = true;           // programmatic dependent launch in the iteration
   bool device_loop = true;   // (F)PCG loop as a device-side graph while loop (host loop: false)
   cudaStream_t aux_stream = nullptr;  // second capture stream (nested graph bodies)

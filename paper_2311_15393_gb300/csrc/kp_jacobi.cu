@@ -136,6 +136,139 @@ __global__ void __launch_bounds__(JT) k_jacobi_round(T* __restrict__ W, T* __res
   }
 }
 
+// Block form of the FP32 sweep with the columns in registers.  A round of
+// k_jacobi_round streams all of W and V through L2 for one rotation per
+// column; here the n columns form nb blocks of RB_JB, a launch pairs the
+// blocks in the same round-robin order (nb - 1 launches per sweep), and each
+// thread block runs one full cyclic sweep over its 2 RB_JB columns (2 RB_JB
+// - 1 rounds of RB_JB disjoint pairs) with every thread holding rows
+// t, t + RB_T, ... of all of them in registers: a round is RB_JB x 3 dot
+// products (reduced across the block through shared memory) and the
+// rotations in registers.  Rotation and threshold are k_jacobi_round's.
+constexpr int RB_T = 128;
+constexpr int RB_JB = 4;
+__host__ __device__ constexpr int rb_player(int t, int round) {  // players 0 .. 2 RB_JB - 1
+  return t == 0 ? 0 : 1 + ((t - 1 + round) % (2 * RB_JB - 1));
+}
+__host__ __device__ constexpr int rb_lo(int p, int round) {
+  return rb_player(p, round) < rb_player(2 * RB_JB - 1 - p, round) ? rb_player(p, round)
+                                                                   : rb_player(2 * RB_JB - 1 - p, round);
+}
+__host__ __device__ constexpr int rb_hi(int p, int round) {
+  return rb_player(p, round) < rb_player(2 * RB_JB - 1 - p, round) ? rb_player(2 * RB_JB - 1 - p, round)
+                                                                   : rb_player(p, round);
+}
+
+template <int R>  // rows per thread: m, n <= R RB_T
+__global__ void __launch_bounds__(RB_T) k_jacobi_rblock(float* __restrict__ W, float* __restrict__ V, int m, int n,
+                                                        int nb, int round, float tol, float floor,
+                                                        unsigned int* __restrict__ rot_count) {
+  constexpr int C = 2 * RB_JB;
+  constexpr int NW = RB_T / 32;
+  __shared__ float red[NW][RB_JB][3];
+  __shared__ float rot[RB_JB][2];
+  __shared__ unsigned int s_rot;
+  const int bi = rr_player(blockIdx.x, round, nb);
+  const int bj = rr_player(nb - 1 - blockIdx.x, round, nb);
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  auto gcol = [&](int c) -> int {
+    const int g = c < RB_JB ? bi * RB_JB + c : bj * RB_JB + c - RB_JB;
+    return g < n ? g : -1;
+  };
+  float w[C][R], v[C][R];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int g = gcol(c);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = t + k * RB_T;
+      w[c][k] = (g >= 0 && r < m) ? W[(long long)g * m + r] : 0.f;
+      v[c][k] = (g >= 0 && r < n) ? V[(long long)g * n + r] : 0.f;
+    }
+  }
+  if (t == 0) s_rot = 0u;
+#pragma unroll
+  for (int rd = 0; rd < C - 1; ++rd) {
+    float part[RB_JB][3];
+#pragma unroll
+    for (int p = 0; p < RB_JB; ++p) {
+      const int i = rb_lo(p, rd), j = rb_hi(p, rd);
+      float sa = 0.f, sb = 0.f, sg = 0.f;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        sa = fmaf(w[i][k], w[i][k], sa);
+        sb = fmaf(w[j][k], w[j][k], sb);
+        sg = fmaf(w[i][k], w[j][k], sg);
+      }
+      part[p][0] = sa;
+      part[p][1] = sb;
+      part[p][2] = sg;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int p = 0; p < RB_JB; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) part[p][q] += __shfl_xor_sync(0xffffffffu, part[p][q], o);
+    if (lane == 0)
+#pragma unroll
+      for (int p = 0; p < RB_JB; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) red[wid][p][q] = part[p][q];
+    __syncthreads();
+    if (t < RB_JB) {
+      const int p = t;
+      float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+      for (int x = 0; x < NW; ++x) {
+        al += red[x][p][0];
+        be += red[x][p][1];
+        ga += red[x][p][2];
+      }
+      float c = 1.f, s = 0.f;
+      const bool valid = gcol(rb_lo(p, rd)) >= 0 && gcol(rb_hi(p, rd)) >= 0;
+      if (valid && ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be) && fabsf(ga) > floor * sqrtf(fmaxf(al, be))) {
+        const float zeta = (be - al) / (2.f * ga);
+        const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        c = 1.f / sqrtf(1.f + tt * tt);
+        s = c * tt;
+        atomicAdd(&s_rot, 1u);
+      }
+      rot[p][0] = c;
+      rot[p][1] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < RB_JB; ++p) {
+      const float c = rot[p][0], s = rot[p][1];
+      if (s != 0.f) {
+        const int i = rb_lo(p, rd), j = rb_hi(p, rd);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const float x = w[i][k], y = w[j][k];
+          w[i][k] = c * x - s * y;
+          w[j][k] = s * x + c * y;
+          const float a = v[i][k], b = v[j][k];
+          v[i][k] = c * a - s * b;
+          v[j][k] = s * a + c * b;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int g = gcol(c);
+    if (g < 0) continue;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = t + k * RB_T;
+      if (r < m) W[(long long)g * m + r] = w[c][k];
+      if (r < n) V[(long long)g * n + r] = v[c][k];
+    }
+  }
+  if (t == 0 && s_rot) atomicAdd(rot_count, s_rot);
+}
+
 __global__ void k_set_identity(double* V, int n) {
   long long tot = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
@@ -693,15 +826,33 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     kp_status gst = KP_OK;
+    // FP32 sweeps in the register block form where the rows fit (m, n <= 8 RB_T)
+    const int mx = std::max(m, n);
+    const int rneed = (mx + RB_T - 1) / RB_T;
+    const int rsel = rneed <= 1 ? 1 : rneed <= 2 ? 2 : rneed <= 4 ? 4 : rneed <= 6 ? 6 : rneed <= 8 ? 8 : 0;
+    const bool blocked = fast && ctx->jacobi_block && rsel > 0;
+    const int nbl = (n + RB_JB - 1) / RB_JB;
+    const int nb = nbl + (nbl & 1);
+    const int rounds = blocked ? nb - 1 : npad - 1;
     for (sweeps = 0; !clean && sweeps < ctx->jacobi_max_sweeps; ++sweeps) {
-      if (!exec) {  // one sweep (n - 1 rounds) as a graph, built at the first sweep
+      if (!exec) {  // one sweep (n - 1 rounds, or nb - 1 block rounds) as a graph, built at the first sweep
         KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         k_zero_u32<<<1, 1, 0, st>>>(cnt);
-        for (int round = 0; round < npad - 1; ++round) {
-          if (fast)
+        for (int round = 0; round < rounds; ++round) {
+          if (blocked) {
+            const float ft = (float)tol, ff = (float)floor;
+            switch (rsel) {
+              case 1: k_jacobi_rblock<1><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
+              case 2: k_jacobi_rblock<2><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
+              case 4: k_jacobi_rblock<4><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
+              case 6: k_jacobi_rblock<6><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
+              default: k_jacobi_rblock<8><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
+            }
+          } else if (fast) {
             k_jacobi_round<float><<<npad / 2, JT, 0, st>>>(W32, V32, m, n, npad, round, tol, floor, cnt);
-          else
+          } else {
             k_jacobi_round<double><<<npad / 2, JT, 0, st>>>(W, Vw, m, n, npad, round, tol, floor, cnt);
+          }
         }
         cudaError_t ce = cudaStreamEndCapture(st, &graph);
         if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -719,7 +870,7 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
         gst = KP_ECUDA;
         break;
       }
-      ctx->launches += npad;
+      ctx->launches += rounds + 1;
       if (h_cnt == 0) {
         ++sweeps;
         break;

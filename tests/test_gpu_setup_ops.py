@@ -77,6 +77,54 @@ def test_setup_fp32_products_match_oracle(kpsvd, case):
         np.testing.assert_allclose(V.T @ V, np.eye(V.shape[0]), rtol=0, atol=1e-4)
 
 
+@pytest.mark.parametrize("shape", [(200, 140), (12, 7)])
+def test_block_jacobi_matches_oracle_and_round_form(kpsvd, shape):
+    """The FP32 factor SVDs of eq. AKronSVD with the Jacobi sweeps in the
+    register block form (default: blocks of 4 columns, a full sweep over two
+    blocks per launch) and in the one-pair-per-thread-block form.  One-sided
+    Jacobi in FP32 stops when no pair's inner product is above the noise
+    floor m u ||A||_F (u = 2^-24 rounding, 2^-23 in the floor), so every
+    singular value is fixed to a few times that floor, whatever the rotation
+    order: both forms agree with the oracle, and with each other, to
+    4 m 2^-23 ||A||_F, and return orthonormal U, V.  Singular vectors are
+    unique (up to sign) only for isolated singular values: within a cluster
+    of near-equal ones only the subspace is, and U (from a second run, or V
+    with signs for a symmetric factor) may be rotated there against V.  So
+    G = U^T A V must equal diag(sigma) to the same level wherever
+    |sigma_i - sigma_j| exceeds 10 times it (i = j: sigma_i isolated).
+    140 columns are 35 blocks (one padding block), 200 are 50; a 7-column
+    factor is two blocks, one partly padding."""
+    pr = OracleProblem("deblur256_fp32", shape=shape, bc="zero", rank=3)
+    P = pr.P
+    out = {}
+    for blk in (1, 0):
+        ctx = kpsvd.KpContext(0)
+        ctx.kp_set_option("jacobi_block", blk)
+        ctx.kp_setup(kpsvd.to_device(P.psf), P.n_r, P.n_c, P.center, P.bc, P.op_rank, "f32", "f32", "f32")
+        out[blk] = (ctx.kp_get_kpsvd(), ctx.kp_get_spectrum())
+        ctx.close()
+    for side in ("r", "c"):
+        A1 = pr.op.Ar[0] if side == "r" else pr.op.Ac[0]
+        m = A1.shape[0]
+        bound = 4 * m * 2.0 ** -23 * np.linalg.norm(A1)
+        s_o = pr.kp.sr if side == "r" else pr.kp.sc
+        for blk in (1, 0):
+            svd = out[blk][0]
+            U, S, V = svd["U" + side], svd["s" + side], svd["V" + side]
+            print(f"{shape} side {side} block {blk}: max |sigma - oracle| {np.abs(S - s_o).max():.2e} "
+                  f"(bound {bound:.2e})")
+            np.testing.assert_allclose(S, s_o, rtol=0, atol=bound)
+            G = U.T @ A1 @ V - np.diag(S)
+            gap = np.abs(S[:, None] - S[None, :])
+            np.fill_diagonal(gap, np.inf)
+            apart = gap > 10 * bound
+            apart[np.diag_indices(m)] = gap.min(axis=1) > 10 * bound
+            assert np.abs(G[apart]).max() <= bound, np.abs(G[apart]).max()
+            np.testing.assert_allclose(U.T @ U, np.eye(m), rtol=0, atol=1e-4)
+            np.testing.assert_allclose(V.T @ V, np.eye(m), rtol=0, atol=1e-4)
+        np.testing.assert_allclose(out[1][0]["s" + side], out[0][0]["s" + side], rtol=0, atol=bound)
+
+
 @pytest.mark.parametrize("vec", ["f64", "f32"])
 @pytest.mark.parametrize("case", CASES[1:3], ids=lambda c: f"{c[2]}-{c[3]}")
 def test_apply_A_and_K(kpsvd, case, vec):
