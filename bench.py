@@ -738,6 +738,8 @@ def run_batched(args, ws, rank, local, dist):
               "converged": sum(info.status == kpsvd.KP_OK for _, info in res),
               "stagnated_above_tol": sum(info.status == kpsvd.KP_ENOCONV for _, info in res),
               "max_rel_res": max(info.rel_res for _, info in res),
+              "grouped": (dict(zip(("problems", "passes", "ms"), kpsvd.kp_batch_grouped(dev)))
+                          if args.workers <= 0 else None),
               "per_size": sizes}
     if rank == 0:
         print(json.dumps(result), flush=True)

@@ -277,6 +277,10 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     two blocks of 4 columns held in registers (n / 4
  *                     launches per sweep instead of n - 1) where m, n <= 1024;
  *                     0: one launch per round of column pairs
+ *   "jacobi_warm_u"   1 (default): for a factor that is not symmetric, the
+ *                     second Jacobi run (U, from F^T) starts from the first
+ *                     run's V instead of the DCT / DST transform; 0: from the
+ *                     transform
  *   "splitk"          > 0: fixed split-K factor of the square tensor-core
  *                     GEMMs (default 0 = chosen per shape)
  *   "tc_bn"           64, 128 or 256: fixed tensor-core tile width (default 0 =
@@ -379,8 +383,11 @@ kp_status kp_solve_batch(int device, kp_problem* probs, int nprob, const kp_batc
 void kp_batch_release(int device);
 
 /* How many problems the last grouped kp_solve_batch call on `device` ran in
- * its grouped loop (0 when none did), and that loop's passes (nullable). */
-int kp_batch_grouped(int device, int* passes);
+ * its grouped loop (0 when none did); passes (nullable): that loop's passes;
+ * ms (nullable, 3 doubles): host wall time of the steps before the loop
+ * (setups, lambdas, starts), of recording and building the loop, and of
+ * running it. */
+int kp_batch_grouped(int device, int* passes, double* ms);
 
 /* ---- Learned lambda (not in the paper; Section 5 asks for a systematic
  * parameter choice) ----------------------------------------------------------

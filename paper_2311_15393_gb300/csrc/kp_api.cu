@@ -322,6 +322,12 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
       return KP_EINVAL;
     }
     ctx->jacobi_block = value != 0;
+  } else if (!strcmp(name, "jacobi_warm_u")) {
+    if (value != 0 && value != 1) {
+      kp_set_error("jacobi_warm_u must be 0 or 1");
+      return KP_EINVAL;
+    }
+    ctx->jacobi_warm_u = value != 0;
   } else if (!strcmp(name, "splitk")) {
     ctx->splitk_override = (int)value;
   } else if (!strcmp(name, "pdl")) {

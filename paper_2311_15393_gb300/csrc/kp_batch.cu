@@ -188,6 +188,7 @@ struct GroupPool {
   size_t dev_bytes = 0;
   int last_grouped = 0;  // problems the last call's grouped loop ran
   int last_passes = 0;   // passes of that loop
+  double last_ms[3] = {0.0, 0.0, 0.0};  // host wall time: before the loop, building it, running it
 };
 std::mutex g_pools_mu;
 std::map<int, GroupPool*> g_pools;
@@ -240,10 +241,12 @@ kp_status launch_groups(kp_ctx* dctx, const std::vector<Group>& gs, const unsign
 
 }  // namespace
 
-extern "C" int kp_batch_grouped(int device, int* passes) {
+extern "C" int kp_batch_grouped(int device, int* passes, double* ms) {
   GroupPool* p = group_pool(device);
   std::lock_guard<std::mutex> lock(p->mu);
   if (passes) *passes = p->last_passes;
+  if (ms)
+    for (int i = 0; i < 3; ++i) ms[i] = p->last_ms[i];
   return p->last_grouped;
 }
 
@@ -261,12 +264,154 @@ extern "C" void kp_batch_release(int device) {
   if (prev >= 0) cudaSetDevice(prev);
 }
 
+// One epoch of the grouped loop over the problems `act` (all armed, their
+// iterations of equal shape): record one iteration of each, build the graph
+// while (any runs and fewer than max_passes) { first halves; if (any
+// replacement due) { replacements }; second halves }, run it; *done = passes.
+static kp_status run_epoch(GroupPool* pool, const std::vector<int>& act, const std::vector<BatchRun*>& runs,
+                           int max_passes, int* done) {
+  using clk = std::chrono::steady_clock;
+  const clk::time_point t0 = clk::now();
+  *done = 0;
+  const int n = (int)act.size();
+  std::vector<KpRecorder> ra(n), rr(n), rb(n);
+  for (int j = 0; j < n; ++j) KP_TRY(batch_record(pool->ctxs[act[j]], runs[act[j]], &ra[j], &rr[j], &rb[j]));
+  std::vector<KpRecorder*> sa, sr, sb;
+  for (int j = 0; j < n; ++j) {
+    sa.push_back(&ra[j]);
+    sr.push_back(&rr[j]);
+    sb.push_back(&rb[j]);
+  }
+  std::vector<Group> ga, gr, gb;
+  size_t bytes = 0;
+  plan_segment(sa, &ga, &bytes);
+  plan_segment(sr, &gr, &bytes);
+  plan_segment(sb, &gb, &bytes);
+  const size_t off_flags = bytes;
+  bytes += sizeof(int*) * n + sizeof(int) * 64;
+  const size_t off_passes = off_flags + sizeof(int*) * n;
+  if (bytes > pool->dev_bytes) {
+    if (pool->dev) cudaFree(pool->dev);
+    pool->dev = nullptr;
+    pool->dev_bytes = 0;
+    KP_CUDA(cudaMalloc((void**)&pool->dev, bytes));
+    pool->dev_bytes = bytes;
+  }
+  std::vector<unsigned char> host(bytes, 0);
+  for (auto* gs : {&ga, &gr, &gb})
+    for (const Group& g : *gs) g.recs[0]->table(g.recs.data(), (int)g.recs.size(), host.data() + g.off);
+  for (int j = 0; j < n; ++j) {
+    int* fp = pool->ctxs[act[j]]->dflags;
+    std::memcpy(host.data() + off_flags + sizeof(int*) * j, &fp, sizeof(fp));
+  }
+  KP_CUDA(cudaMemcpy(pool->dev, host.data(), bytes, cudaMemcpyHostToDevice));
+  int* const* dflags = reinterpret_cast<int* const*>(pool->dev + off_flags);
+  int* passes = reinterpret_cast<int*>(pool->dev + off_passes);
+  kp_ctx* dctx = pool->ctxs[act[0]];
+  cudaStream_t s0 = dctx->stream;
+  if (!dctx->aux_stream) KP_CUDA(cudaStreamCreateWithFlags(&dctx->aux_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  KP_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h_loop, h_rep;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = h_loop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
+  cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_rep, body, 0, 0);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(s0, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    kp_set_error("kp_solve_batch: loop graph: %s", cudaGetErrorString(e));
+    return KP_ECUDA;
+  }
+  kp_status cs = launch_groups(dctx, ga, pool->dev);
+  if (cs == KP_OK) {
+    k_batch_any<<<1, 256, 0, s0>>>(dflags, n, F_NOTDUE, 1, nullptr, 0, h_rep);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_rep;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    e = cudaStreamGetCaptureInfo(s0, &cst, nullptr, &cg, &deps, &ed, &nd);
+    if (e == cudaSuccess) e = cudaGraphAddNode(&inode, cg, deps, ed, nd, &ip);
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(s0, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(dctx->aux_stream, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      kp_set_error("kp_solve_batch: loop graph (replacement): %s", cudaGetErrorString(e));
+      cs = KP_ECUDA;
+    } else {
+      dctx->stream = dctx->aux_stream;
+      cs = launch_groups(dctx, gr, pool->dev);
+      dctx->stream = s0;
+      cudaGraph_t tmp = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(dctx->aux_stream, &tmp);
+      if (cs == KP_OK && e2 != cudaSuccess) {
+        kp_set_error("kp_solve_batch: loop graph (replacement): %s", cudaGetErrorString(e2));
+        cs = KP_ECUDA;
+      }
+    }
+  }
+  if (cs == KP_OK) cs = launch_groups(dctx, gb, pool->dev);
+  if (cs == KP_OK) k_batch_any<<<1, 256, 0, s0>>>(dflags, n, F_BLOOP, 0, passes, max_passes, h_loop);
+  {
+    cudaGraph_t tmp = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s0, &tmp);
+    if (cs == KP_OK && ee != cudaSuccess) {
+      kp_set_error("kp_solve_batch: loop graph capture: %s", cudaGetErrorString(ee));
+      cs = KP_ECUDA;
+    }
+  }
+  if (cs == KP_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+    kp_set_error("kp_solve_batch: loop graph instantiation failed");
+    cs = KP_ECUDA;
+  }
+  const clk::time_point t1 = clk::now();
+  if (cs == KP_OK) {
+    int hp = 0;
+    cudaError_t le = cudaMemsetAsync(passes, 0, sizeof(int), s0);
+    if (le == cudaSuccess) le = cudaGraphLaunch(ge, s0);
+    if (le == cudaSuccess) le = cudaMemcpyAsync(&hp, passes, sizeof(int), cudaMemcpyDeviceToHost, s0);
+    if (le == cudaSuccess) le = cudaStreamSynchronize(s0);
+    if (le != cudaSuccess) {
+      kp_set_error("kp_solve_batch: grouped loop: %s", cudaGetErrorString(le));
+      cs = KP_ECUDA;
+    }
+    *done = hp;
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  pool->last_ms[1] += std::chrono::duration<double, std::milli>(t1 - t0).count();
+  pool->last_ms[2] += std::chrono::duration<double, std::milli>(clk::now() - t1).count();
+  return cs;
+}
+
 static kp_status solve_grouped(int device, kp_problem* probs, int nprob, const kp_batch_opts* o) {
   GroupPool* pool = group_pool(device);
   std::lock_guard<std::mutex> lock(pool->mu);
   pool->last_grouped = 0;
   pool->last_passes = 0;
+  for (double& v : pool->last_ms) v = 0.0;
   KP_CUDA(cudaSetDevice(device));
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+  const clk::time_point t_begin = clk::now();
+  clk::time_point t_mark = t_begin;
   const bool bf16 = o->op_prec == KP_BF16;
   const double auto_cond = 1e4;  // ill-conditioned problems of a BF16 batch: BF16X3 inner operator
   while ((int)pool->ctxs.size() < nprob) {
@@ -314,6 +459,8 @@ static kp_status solve_grouped(int device, kp_problem* probs, int nprob, const k
     if (s == KP_OK) s = batch_begin(ctx, p.b, lam, o->tol, o->maxit, o->flexible, p.x, &runs[i]);
     if (s != KP_OK) fail(i, s);
   }
+  pool->last_ms[0] = ms_since(t_begin);
+  t_mark = clk::now();
   // record one iteration of every problem whose loop can run grouped
   std::vector<int> grp;
   std::string record_msg;
@@ -341,127 +488,36 @@ static kp_status solve_grouped(int device, kp_problem* probs, int nprob, const k
   std::vector<char> in_grp(nprob, 0);
   for (int i : grp) in_grp[i] = 1;
   kp_status gst = KP_OK;
+  pool->last_ms[1] = ms_since(t_mark);
   if (!grp.empty()) {
-    std::vector<KpRecorder*> sa, sr, sb;
-    for (int i : grp) {
-      sa.push_back(&ra[i]);
-      sr.push_back(&rr[i]);
-      sb.push_back(&rb[i]);
-    }
-    std::vector<Group> ga, gr, gb;
-    size_t bytes = 0;
-    plan_segment(sa, &ga, &bytes);
-    plan_segment(sr, &gr, &bytes);
-    plan_segment(sb, &gb, &bytes);
-    const size_t off_flags = bytes;
-    bytes += sizeof(int*) * grp.size() + sizeof(int) * 64;
-    const size_t off_passes = off_flags + sizeof(int*) * grp.size();
-    if (bytes > pool->dev_bytes) {
-      if (pool->dev) cudaFree(pool->dev);
-      pool->dev = nullptr;
-      pool->dev_bytes = 0;
-      KP_CUDA(cudaMalloc((void**)&pool->dev, bytes));
-      pool->dev_bytes = bytes;
-    }
-    std::vector<unsigned char> host(bytes, 0);
-    for (auto* gs : {&ga, &gr, &gb})
-      for (const Group& g : *gs) g.recs[0]->table(g.recs.data(), (int)g.recs.size(), host.data() + g.off);
-    for (size_t j = 0; j < grp.size(); ++j) {
-      int* fp = pool->ctxs[grp[j]]->dflags;
-      std::memcpy(host.data() + off_flags + sizeof(int*) * j, &fp, sizeof(fp));
-    }
-    KP_CUDA(cudaMemcpy(pool->dev, host.data(), bytes, cudaMemcpyHostToDevice));
-    int* const* dflags = reinterpret_cast<int* const*>(pool->dev + off_flags);
-    int* passes = reinterpret_cast<int*>(pool->dev + off_passes);
-    // the graph: while (any problem runs) { first halves; if (any replacement
-    // due) { replacements }; second halves }
-    kp_ctx* dctx = pool->ctxs[grp[0]];
-    cudaStream_t s0 = dctx->stream;
-    if (!dctx->aux_stream) KP_CUDA(cudaStreamCreateWithFlags(&dctx->aux_stream, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    KP_CUDA(cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle h_loop, h_rep;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault);
-    cudaGraphNodeParams wp = {};
-    wp.type = cudaGraphNodeTypeConditional;
-    wp.conditional.handle = h_loop;
-    wp.conditional.type = cudaGraphCondTypeWhile;
-    wp.conditional.size = 1;
-    cudaGraphNode_t wnode;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
-    cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_rep, body, 0, 0);
-    if (e == cudaSuccess)
-      e = cudaStreamBeginCaptureToGraph(s0, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(g);
-      kp_set_error("kp_solve_batch: loop graph: %s", cudaGetErrorString(e));
-      return KP_ECUDA;
-    }
-    const int n = (int)grp.size();
-    kp_status cs = launch_groups(dctx, ga, pool->dev);
-    if (cs == KP_OK) {
-      k_batch_any<<<1, 256, 0, s0>>>(dflags, n, F_NOTDUE, 1, nullptr, 0, h_rep);
-      cudaStreamCaptureStatus cst;
-      cudaGraph_t cg = nullptr;
-      const cudaGraphNode_t* deps = nullptr;
-      const cudaGraphEdgeData* ed = nullptr;
-      size_t nd = 0;
-      cudaGraphNodeParams ip = {};
-      ip.type = cudaGraphNodeTypeConditional;
-      ip.conditional.handle = h_rep;
-      ip.conditional.type = cudaGraphCondTypeIf;
-      ip.conditional.size = 1;
-      cudaGraphNode_t inode;
-      e = cudaStreamGetCaptureInfo(s0, &cst, nullptr, &cg, &deps, &ed, &nd);
-      if (e == cudaSuccess) e = cudaGraphAddNode(&inode, cg, deps, ed, nd, &ip);
-      if (e == cudaSuccess)
-        e = cudaStreamUpdateCaptureDependencies(s0, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
-      if (e == cudaSuccess)
-        e = cudaStreamBeginCaptureToGraph(dctx->aux_stream, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) {
-        kp_set_error("kp_solve_batch: loop graph (replacement): %s", cudaGetErrorString(e));
-        cs = KP_ECUDA;
-      } else {
-        dctx->stream = dctx->aux_stream;
-        cs = launch_groups(dctx, gr, pool->dev);
-        dctx->stream = s0;
-        cudaGraph_t tmp = nullptr;
-        const cudaError_t e2 = cudaStreamEndCapture(dctx->aux_stream, &tmp);
-        if (cs == KP_OK && e2 != cudaSuccess) {
-          kp_set_error("kp_solve_batch: loop graph (replacement): %s", cudaGetErrorString(e2));
-          cs = KP_ECUDA;
-        }
-      }
-    }
-    if (cs == KP_OK) cs = launch_groups(dctx, gb, pool->dev);
-    if (cs == KP_OK) k_batch_any<<<1, 256, 0, s0>>>(dflags, n, F_BLOOP, 0, passes, o->maxit + 16, h_loop);
-    {
-      cudaGraph_t tmp = nullptr;
-      const cudaError_t ee = cudaStreamEndCapture(s0, &tmp);
-      if (cs == KP_OK && ee != cudaSuccess) {
-        kp_set_error("kp_solve_batch: loop graph capture: %s", cudaGetErrorString(ee));
-        cs = KP_ECUDA;
-      }
-    }
-    if (cs == KP_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
-      kp_set_error("kp_solve_batch: loop graph instantiation failed");
-      cs = KP_ECUDA;
-    }
+    // Epochs of 16, 32, 64, ... passes; after each, the graph is rebuilt for
+    // the problems still running, so that the long tail of a few slow
+    // problems does not pay for the launches of the ones that stopped.
     for (int i : grp)
-      if (cs == KP_OK) cs = batch_arm(pool->ctxs[i], runs[i]);
-    if (cs == KP_OK) {
-      KP_CUDA(cudaMemsetAsync(passes, 0, sizeof(int), s0));
-      KP_CUDA(cudaGraphLaunch(ge, s0));
-      KP_CUDA(cudaMemcpyAsync(&pool->last_passes, passes, sizeof(int), cudaMemcpyDeviceToHost, s0));
+      if (gst == KP_OK) gst = batch_arm(pool->ctxs[i], runs[i]);
+    std::vector<int> act = grp;
+    int total = 0, epoch = 16;
+    while (gst == KP_OK && !act.empty()) {
+      const int left = o->maxit + 16 - total;
+      if (left <= 0) break;
+      int done = 0;
+      gst = run_epoch(pool, act, runs, std::min(epoch, left), &done);
+      total += done;
+      epoch *= 2;
+      if (gst != KP_OK) break;
+      std::vector<int> still;
+      std::vector<int> go(act.size(), 0);
+      cudaStream_t s0 = pool->ctxs[act[0]]->stream;
+      for (size_t j = 0; j < act.size(); ++j)
+        KP_CUDA(cudaMemcpyAsync(&go[j], pool->ctxs[act[j]]->dflags + F_BLOOP, sizeof(int), cudaMemcpyDeviceToHost,
+                                s0));
       KP_CUDA(cudaStreamSynchronize(s0));
-      pool->last_grouped = n;
+      for (size_t j = 0; j < act.size(); ++j)
+        if (go[j]) still.push_back(act[j]);
+      act.swap(still);
     }
-    if (ge) cudaGraphExecDestroy(ge);
-    cudaGraphDestroy(g);
-    gst = cs;
+    pool->last_passes = total;
+    if (gst == KP_OK) pool->last_grouped = (int)grp.size();
   }
   // results; problems outside the grouped loop run it alone; a BF16 inner
   // operator that stalled or broke down is retried with BF16X3 (as alone)

@@ -153,6 +153,7 @@ struct kp_ctx {
   double jacobi_tol = 1e-15;  // raised to m * eps inside the SVD
   int jacobi_max_sweeps = 40;
   bool jacobi_block = true;   // FP32 sweeps in the register block form (k_jacobi_rblock) where it fits
+  bool jacobi_warm_u = true;  // second factor-SVD run (U from F^T) starts from the first run's V
   bool pdl = true;           // programmatic dependent launch in the iteration
   bool device_loop = true;   // (F)PCG loop as a device-side graph while loop (host loop: false)
   cudaStream_t aux_stream = nullptr;  // second capture stream (nested graph bodies)

@@ -964,8 +964,11 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
   const int g = std::max(1, std::min((int)((nn + 255) / 256), ctx->sm_count * 16));
   KP_TRY(make_transform(ctx, n, transform, C));
   if (fast) KP_TRY(convert_f64_to_f32(ctx, C, C32, nn));
-  // W (col-major) = X C for X given row-major, computed as the row-major
-  // product D[k][i] = sum_j C[j,k] X[i,j]; FP32 products are widened to FP64
+  // W (col-major) = X R for X given row-major and R col-major (R = C, or V
+  // of the first run), computed as the row-major product D[k][i] = sum_j
+  // R[j,k] X[i,j]; FP32 products are widened to FP64
+  const double* R = C;
+  const float* R32 = C32;
   auto mul = [&](const double* X_rm, double* out) -> kp_status {
     GemmDesc gd;
     gd.M = n;
@@ -976,18 +979,18 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
     gd.epi.mode = EPI_T;
     gd.epi.ldd = n;
     if (ctx->setup_tc) {  // tensor cores: FP32-level (3 slices) or half precision (1)
-      KP_TRY(tc_product(ctx, C, true, n, X_rm, true, n, n, W32, ctx->setup_half ? 1 : 3));
+      KP_TRY(tc_product(ctx, R, true, n, X_rm, true, n, n, W32, ctx->setup_half ? 1 : 3));
       return convert_f32_to_f64(ctx, W32, out, nn);
     }
     if (fast) {
       KP_TRY(convert_f64_to_f32(ctx, X_rm, F32, nn));
-      gd.A.ptr = C32;
+      gd.A.ptr = R32;
       gd.B.ptr = F32;
       gd.epi.out = W32;
       KP_TRY(simt_gemm<float>(ctx, gd));
       return convert_f32_to_f64(ctx, W32, out, nn);
     }
-    gd.A.ptr = C;
+    gd.A.ptr = R;
     gd.B.ptr = X_rm;
     gd.epi.out = out;
     return simt_gemm<double>(ctx, gd);
@@ -1011,11 +1014,23 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
   if (asym == 0) {
     KP_CUDA(cudaMemcpyAsync(U, V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
   } else {
-    // run 2: F^T = V' S U^T  (F^T row-major = F column-major = transpose of F_rm)
+    // run 2: F^T = V' S U^T  (F^T row-major = F column-major = transpose of F_rm),
+    // started from the first run's V instead of the transform: exactly
+    // orthogonal, and for the nearly symmetric (or antisymmetric) factors of
+    // a PSF symmetric about its centre F^T V = V S U^T V is nearly orthogonal
+    // already (U ~ +-V), so the sweeps only finish what the boundary rows of
+    // the factor make asymmetric
     k_transpose_cm<double><<<g, 256, 0, st>>>(F_rm, n, n, FT_rm);
     KP_LAUNCHED(ctx);
+    if (ctx->jacobi_warm_u) {
+      R = V;
+      if (fast && !ctx->setup_tc) {
+        KP_TRY(convert_f64_to_f32(ctx, V, C32, nn));
+        R32 = C32;
+      }
+    }
     KP_TRY(mul(FT_rm, W));
-    KP_CUDA(cudaMemcpyAsync(Vw, C, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+    KP_CUDA(cudaMemcpyAsync(Vw, R, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
     KP_TRY(jacobi_run(ctx, W, n, n, Vw, FT_rm /* scratch */, s2, U, &sw2, fast));
   }
   k_align_signs<<<n, JT, 0, st>>>(U, U1, n);

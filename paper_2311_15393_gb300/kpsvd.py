@@ -90,7 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "kp_apply_Minv_noalloc": ([vp, vp, vp, i, i, d, vp, vp, vp], i),
         "kp_solve_batch": ([i, ctypes.POINTER(Problem), i, ctypes.POINTER(BatchOpts), dp], i),
         "kp_batch_release": ([i], None),
-        "kp_batch_grouped": ([i, ctypes.POINTER(i)], i),
+        "kp_batch_grouped": ([i, ctypes.POINTER(i), dp], i),
         "kp_lambda_features": ([vp, vp, vp], i),
         "kp_mlp_create": ([ctypes.POINTER(vp), i, vp, i, i, i], i),
         "kp_mlp_destroy": ([vp], None),
@@ -349,10 +349,12 @@ def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_pr
 
 
 def kp_batch_grouped(device: int = 0):
-    """(problems the last grouped kp_solve_batch ran in its grouped loop, the loop's passes)."""
+    """(problems the last grouped kp_solve_batch ran in its grouped loop, the
+    loop's passes, [ms before the loop, ms building it, ms running it])."""
     passes = ctypes.c_int(0)
-    n = _lib.kp_batch_grouped(device, ctypes.byref(passes))
-    return n, passes.value
+    ms = (ctypes.c_double * 3)()
+    n = _lib.kp_batch_grouped(device, ctypes.byref(passes), ms)
+    return n, passes.value, list(ms)
 
 
 class Mlp:

@@ -81,7 +81,9 @@ def test_setup_fp32_products_match_oracle(kpsvd, case):
 def test_block_jacobi_matches_oracle_and_round_form(kpsvd, shape):
     """The FP32 factor SVDs of eq. AKronSVD with the Jacobi sweeps in the
     register block form (default: blocks of 4 columns, a full sweep over two
-    blocks per launch) and in the one-pair-per-thread-block form.  One-sided
+    blocks per launch) with the second run (U from F^T) started from the
+    first run's V (default), and in the one-pair-per-thread-block form
+    started from the transform.  One-sided
     Jacobi in FP32 stops when no pair's inner product is above the noise
     floor m u ||A||_F (u = 2^-24 rounding, 2^-23 in the floor), so every
     singular value is fixed to a few times that floor, whatever the rotation
@@ -97,9 +99,10 @@ def test_block_jacobi_matches_oracle_and_round_form(kpsvd, shape):
     pr = OracleProblem("deblur256_fp32", shape=shape, bc="zero", rank=3)
     P = pr.P
     out = {}
-    for blk in (1, 0):
+    for blk in (1, 0):  # block form with the warm second run (defaults), and the former form
         ctx = kpsvd.KpContext(0)
         ctx.kp_set_option("jacobi_block", blk)
+        ctx.kp_set_option("jacobi_warm_u", blk)
         ctx.kp_setup(kpsvd.to_device(P.psf), P.n_r, P.n_c, P.center, P.bc, P.op_rank, "f32", "f32", "f32")
         out[blk] = (ctx.kp_get_kpsvd(), ctx.kp_get_spectrum())
         ctx.close()
