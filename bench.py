@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--fp64-form", action="store_true", help="also time the all-FP64 GPU form per iteration")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the whole-step all-FP64 GPU form")
     ap.add_argument("--n", type=int, default=None, help="override the image size (smaller test runs)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run the (F)PCG iterations as host-launched graph blocks instead of the device-side "
+                         "loop (the same kernels; profilers list the kernels of these blocks, not those inside "
+                         "the device loop's conditional nodes)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no phase breakdown, e2e, kernel timing or CPU baseline): for launch lists")
     ap.add_argument("--workload", default="deblur1024_mixed",
@@ -59,8 +63,9 @@ def parse():
     ap.add_argument("--workers", type=int, default=0,
                     help="batched64: 0 = grouped form (one launch per iteration step over all problems, one host "
                          "thread); > 0 = that many host threads, one context each")
-    ap.add_argument("--autotune", action="store_true",
-                    help="batched64 (grouped): tile shapes of the grouped GEMMs chosen by timing")
+    ap.add_argument("--batch-tiles", default="uniform", choices=["uniform", "timed", "per-shape"],
+                    help="batched64 (grouped): one tile shape for all problems (each step one launch), shapes "
+                         "chosen by timing (autotuner), or the size rule of single solves")
     ap.add_argument("--kernel-only", choices=["kapply", "minv"], default=None,
                     help="set up once, then run only the operator application (or preconditioner solve) "
                          "--steps times: for kernel profiles")
@@ -361,6 +366,8 @@ def run_ours(args, ws, rank, local, dist):
         bs = [torch.empty(N, dtype=f32, device=dev) for _ in gs]
         xs = [torch.zeros(N, dtype=f32, device=dev) for _ in gs]
         ctx = kpsvd.KpContext(dev, stream=stream.cuda_stream)
+        if args.host_loop:
+            ctx.kp_set_option("device_loop", 0)
         # observed data with this context's own operator (untimed input preparation)
         ctx.kp_setup(psf, n_r, n_c, P.center, P.bc, P.op_rank, args.op, args.pc, "f32", "projected")
         for g, b, nl in zip(gs, bs, P.noise_levels):
@@ -665,7 +672,7 @@ def run_batched(args, ws, rank, local, dist):
             d["x"].zero_()
         st, ms_, res_ = kpsvd.kp_solve_batch(dp, op_prec=args.op, pc_prec=args.pc, tol=1e-7, maxit=500,
                                              workers=args.workers, device=dev, check=False,
-                                             autotune=args.autotune)
+                                             autotune={"uniform": 0, "timed": 1, "per-shape": 2}[args.batch_tiles])
         bad = [i.status for _, i in res_ if i.status not in (kpsvd.KP_OK, kpsvd.KP_ENOCONV)]
         if bad:  # anything but convergence or stagnation at FP32 accuracy is a failure
             raise RuntimeError(f"kp_solve_batch failed: statuses {bad}: {kpsvd._lib.kp_last_error().decode()}")
@@ -728,7 +735,7 @@ def run_batched(args, ws, rank, local, dist):
                          "workers": args.workers,
                          "form": ("grouped: one launch per iteration step over all problems, one CUDA graph with "
                                   "a device-side loop" if args.workers <= 0 else f"{args.workers} host threads"),
-                         "autotune": bool(args.autotune), "parallelism": f"replicas x{ws}",
+                         "tiles": args.batch_tiles, "parallelism": f"replicas x{ws}",
                          "l2": "256 MiB buffer written before every step",
                          "step": "kp_solve_batch over 64 problems"},
               "e2e": {"value": sum_over_ranks(dist, float(n_ok)) / (e2e_ms / 1e3), "unit": "solves/s",
@@ -738,7 +745,7 @@ def run_batched(args, ws, rank, local, dist):
               "converged": sum(info.status == kpsvd.KP_OK for _, info in res),
               "stagnated_above_tol": sum(info.status == kpsvd.KP_ENOCONV for _, info in res),
               "max_rel_res": max(info.rel_res for _, info in res),
-              "grouped": (dict(zip(("problems", "passes", "ms"), kpsvd.kp_batch_grouped(dev)))
+              "grouped": (dict(zip(("problems", "passes", "ms", "launches"), kpsvd.kp_batch_grouped(dev)))
                           if args.workers <= 0 else None),
               "per_size": sizes}
     if rank == 0:

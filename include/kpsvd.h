@@ -369,8 +369,10 @@ typedef struct {
   int maxit;
   int flexible;
   int workers;  /* <= 0: grouped form (one host thread); > 0: that many host threads */
-  int autotune; /* grouped form: nonzero = tile shapes of the grouped GEMMs chosen by timing
-                   (the tc_autotune option; cache file KPSVD_TUNE_CACHE) */
+  int autotune; /* grouped form, tile shapes of the grouped GEMMs: 0 = one shape for every
+                   problem (128 wide; each step is then one launch), 1 = each GEMM shape's
+                   chosen by timing (the tc_autotune option; cache file KPSVD_TUNE_CACHE),
+                   2 = each GEMM shape's by the size rule of single solves */
 } kp_batch_opts;
 
 /* Solve probs[0..nprob) (device `device`).  Returns KP_OK when every problem
@@ -386,8 +388,10 @@ void kp_batch_release(int device);
  * its grouped loop (0 when none did); passes (nullable): that loop's passes;
  * ms (nullable, 3 doubles): host wall time of the steps before the loop
  * (setups, lambdas, starts), of recording and building the loop, and of
- * running it. */
-int kp_batch_grouped(int device, int* passes, double* ms);
+ * running it; shape (nullable, 4 ints): for the first epoch, the launches of
+ * one problem's iteration outside the residual replacement and the grouped
+ * launches they became, then the same inside the replacement. */
+int kp_batch_grouped(int device, int* passes, double* ms, int* shape);
 
 /* ---- Learned lambda (not in the paper; Section 5 asks for a systematic
  * parameter choice) ----------------------------------------------------------

@@ -189,6 +189,8 @@ struct GroupPool {
   int last_grouped = 0;  // problems the last call's grouped loop ran
   int last_passes = 0;   // passes of that loop
   double last_ms[3] = {0.0, 0.0, 0.0};  // host wall time: before the loop, building it, running it
+  int last_shape[4] = {0, 0, 0, 0};     // first epoch: launch positions and grouped launches per pass
+                                        // (outside the replacement), and the same inside it
 };
 std::mutex g_pools_mu;
 std::map<int, GroupPool*> g_pools;
@@ -241,12 +243,14 @@ kp_status launch_groups(kp_ctx* dctx, const std::vector<Group>& gs, const unsign
 
 }  // namespace
 
-extern "C" int kp_batch_grouped(int device, int* passes, double* ms) {
+extern "C" int kp_batch_grouped(int device, int* passes, double* ms, int* shape) {
   GroupPool* p = group_pool(device);
   std::lock_guard<std::mutex> lock(p->mu);
   if (passes) *passes = p->last_passes;
   if (ms)
     for (int i = 0; i < 3; ++i) ms[i] = p->last_ms[i];
+  if (shape)
+    for (int i = 0; i < 4; ++i) shape[i] = p->last_shape[i];
   return p->last_grouped;
 }
 
@@ -287,6 +291,12 @@ static kp_status run_epoch(GroupPool* pool, const std::vector<int>& act, const s
   plan_segment(sa, &ga, &bytes);
   plan_segment(sr, &gr, &bytes);
   plan_segment(sb, &gb, &bytes);
+  if (pool->last_shape[0] == 0) {
+    pool->last_shape[0] = (int)(ra[0].recs.size() + rb[0].recs.size());
+    pool->last_shape[1] = (int)(ga.size() + gb.size());
+    pool->last_shape[2] = (int)rr[0].recs.size();
+    pool->last_shape[3] = (int)gr.size();
+  }
   const size_t off_flags = bytes;
   bytes += sizeof(int*) * n + sizeof(int) * 64;
   const size_t off_passes = off_flags + sizeof(int*) * n;
@@ -407,6 +417,7 @@ static kp_status solve_grouped(int device, kp_problem* probs, int nprob, const k
   pool->last_grouped = 0;
   pool->last_passes = 0;
   for (double& v : pool->last_ms) v = 0.0;
+  for (int& v : pool->last_shape) v = 0;
   KP_CUDA(cudaSetDevice(device));
   using clk = std::chrono::steady_clock;
   auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
@@ -434,7 +445,8 @@ static kp_status solve_grouped(int device, kp_problem* probs, int nprob, const k
     kp_ctx* ctx = pool->ctxs[i];
     kp_status s = kp_set_option(ctx, "op_auto_cond", bf16 ? auto_cond : 0.0);
     ctx->tc_group = true;  // grouped GEMMs: one-CTA tiles, no K split
-    if (s == KP_OK) s = kp_set_option(ctx, "tc_autotune", o->autotune ? 1 : 0);
+    ctx->tc_group_uniform = o->autotune == 0;
+    if (s == KP_OK) s = kp_set_option(ctx, "tc_autotune", o->autotune == 1 ? 1 : 0);
     entered[i] = 0;
     if (s == KP_OK)
       s = kp_setup(ctx, p.psf, p.n_r, p.n_c, p.center_r, p.center_c, p.bc, p.op_rank, 1, o->op_prec, o->pc_prec,

@@ -1273,9 +1273,13 @@ static kp_status tc_plan_create_one(kp_ctx* ctx, const GemmDesc& g, int kind, in
     bn = 128;
   if (ctx->tc_bn_override == 64 || ctx->tc_bn_override == 128 || ctx->tc_bn_override == 256)
     bn = ctx->tc_bn_override;
+  // grouped launches of a batched solve with one tile shape for all problems
+  // (so that one launch covers every problem's GEMM at that step)
+  const bool uniform = ctx->tc_grouping && ctx->tc_group_uniform;
+  if (uniform) bn = g.N >= 128 ? 128 : 64;
   const int tiles_bn = tiles_of(bn);
-  int cps = (bn == 128 && tiles_bn > sms) ? 2 : 1;
-  if (bn == 128 && (ctx->tc_cps_override == 1 || ctx->tc_cps_override == 2)) cps = ctx->tc_cps_override;
+  int cps = (bn == 128 && tiles_bn > sms && !uniform) ? 2 : 1;
+  if (bn == 128 && !uniform && (ctx->tc_cps_override == 1 || ctx->tc_cps_override == 2)) cps = ctx->tc_cps_override;
   if (splits < 1) {  // K split only when even 64-wide tiles leave most SMs idle
     splits = 1;
     if (2 * tiles_bn < sms && !ctx->tc_grouping)

@@ -260,6 +260,7 @@ struct kp_ctx {
   struct KpRecorder* rec = nullptr;
   bool tc_group = false;     // batched solve: the operator's and preconditioner's plans run in grouped launches
   bool tc_grouping = false;  // set while those plans are made: no K split, no CTA pairs
+  bool tc_group_uniform = true;  // ... and one tile shape (128 wide, one CTA per SM) for all problems
 };
 
 // ---------------------------------------------------------------- recorded launches

@@ -90,7 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "kp_apply_Minv_noalloc": ([vp, vp, vp, i, i, d, vp, vp, vp], i),
         "kp_solve_batch": ([i, ctypes.POINTER(Problem), i, ctypes.POINTER(BatchOpts), dp], i),
         "kp_batch_release": ([i], None),
-        "kp_batch_grouped": ([i, ctypes.POINTER(i), dp], i),
+        "kp_batch_grouped": ([i, ctypes.POINTER(i), dp, ctypes.POINTER(i)], i),
         "kp_lambda_features": ([vp, vp, vp], i),
         "kp_mlp_create": ([ctypes.POINTER(vp), i, vp, i, i, i], i),
         "kp_mlp_destroy": ([vp], None),
@@ -317,13 +317,14 @@ class KpContext:
 def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_prec: str = "f32",
                    sigma: str = "projected", method: str = "gcv", tol: float = 1e-7, maxit: int = 500,
                    flexible: bool = True, workers: int = 0, device: int = 0, check: bool = True,
-                   autotune: bool = False):
+                   autotune: int = 0):
     """Solve a batch of independent problems (kp_solve_batch).  ``problems``:
     dicts with psf, b, x (torch CUDA tensors), n_r, n_c, center, bc, op_rank and
     optionally lam (> 0: fixed) and lambda_param.  ``workers`` 0: the grouped
     form (one launch per iteration step over all problems); > 0: host
     threads.  Returns (status, ms_total, [(lambda, Info), ...]) in the order
-    given."""
+    given.  ``autotune`` (grouped form): 0 one tile shape for all problems,
+    1 shapes chosen by timing, 2 the size rule of single solves."""
     arr = (Problem * len(problems))()
     vt = _VEC_DTYPE.get(vec_prec, "float32")
     for k, p in enumerate(problems):
@@ -338,7 +339,7 @@ def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_pr
         q.lambda_ = p.get("lam") or 0.0
         q.lambda_param = p.get("lambda_param", 0.0)
     o = BatchOpts(PREC[op_prec], PREC[pc_prec], PREC[vec_prec], SIGMA[sigma], LAMBDA[method], tol, maxit,
-                  1 if flexible else 0, workers, 1 if autotune else 0)
+                  1 if flexible else 0, workers, int(autotune))
     ms = ctypes.c_double(0.0)
     st = _lib.kp_solve_batch(device, arr, len(problems), ctypes.byref(o), ctypes.byref(ms))
     if check and st != KP_OK:
@@ -350,11 +351,14 @@ def kp_solve_batch(problems, op_prec: str = "bf16", pc_prec: str = "f16", vec_pr
 
 def kp_batch_grouped(device: int = 0):
     """(problems the last grouped kp_solve_batch ran in its grouped loop, the
-    loop's passes, [ms before the loop, ms building it, ms running it])."""
+    loop's passes, [ms before the loop, ms building it, ms running it],
+    [launches per problem iteration, grouped launches per pass, the same
+    for the residual replacement])."""
     passes = ctypes.c_int(0)
     ms = (ctypes.c_double * 3)()
-    n = _lib.kp_batch_grouped(device, ctypes.byref(passes), ms)
-    return n, passes.value, list(ms)
+    shape = (ctypes.c_int * 4)()
+    n = _lib.kp_batch_grouped(device, ctypes.byref(passes), ms, shape)
+    return n, passes.value, list(ms), list(shape)
 
 
 class Mlp:

@@ -61,7 +61,8 @@ def test_batch_matches_oracle(kpsvd, problems, workers):
     st, ms, res = kpsvd.kp_solve_batch(dev, tol=TOL, workers=workers, check=False)
     assert st in (kpsvd.KP_OK, kpsvd.KP_ENOCONV), kpsvd._lib.kp_last_error().decode()
     if workers == 0:  # every problem that iterated did so in the grouped loop
-        n_grouped, passes, _ = kpsvd.kp_batch_grouped(0)
+        n_grouped, passes, _, shape = kpsvd.kp_batch_grouped(0)
+        print(f"launches per iteration / grouped launches per pass: {shape}")
         print(f"grouped loop: {n_grouped} problems, {passes} passes")
         assert n_grouped == sum(info.iters > 0 for _, info in res), kpsvd._lib.kp_last_error().decode()
         assert passes >= 1
