@@ -139,3 +139,36 @@ def test_batch_fixed_lambda_and_failing_problem(kpsvd, problems, workers):
     assert res[1][1].status == kpsvd.KP_OK
     x_star = opcg.tik_exact(problems[0]["op"], problems[0]["kp"], problems[0]["B"], 0.05, tol=1e-10)
     assert rel(kpsvd.from_device(dev[0]["x"], P.n_r, P.n_c), x_star) < 1e-4
+
+
+def test_grouped_batch_edge_cases(kpsvd, problems):
+    """Grouped form: a problem whose b is zero stops before the loop (x = 0,
+    no iterations) while the others iterate in the grouped loop; a batch whose
+    operator has no fused iteration (FP32 SIMT operator) cannot be grouped, so
+    every problem runs alone, and each is still solved to the oracle's x_lambda."""
+    dev = device_problems(kpsvd, problems[:3])
+    dev[1]["b"].zero_()
+    dev[1]["x"].fill_(1.0)
+    dev[1]["lam"] = 0.05  # (no lambda criterion has a minimum for b = 0)
+    st, _, res = kpsvd.kp_solve_batch(dev, tol=TOL, workers=0, check=False)
+    assert res[1][1].status == kpsvd.KP_OK and res[1][1].iters == 0
+    assert torch.count_nonzero(dev[1]["x"]).item() == 0
+    n_grouped, passes, _, _ = kpsvd.kp_batch_grouped(0)
+    assert n_grouped == sum(info.iters > 0 for _, info in res) == 2
+    for k in (0, 2):
+        pr, d, (lam, info) = problems[k], dev[k], res[k]
+        P = pr["P"]
+        x_star = opcg.tik_exact(pr["op"], pr["kp"], pr["B"], lam, tol=1e-10)
+        cond = (np.max(np.abs(pr["kp"].Sigma)) ** 2 + lam ** 2) / lam ** 2
+        assert rel(kpsvd.from_device(d["x"], P.n_r, P.n_c), x_star) < (1e-4 if cond <= 1e4 else cond * TOL)
+
+    dev = device_problems(kpsvd, problems[:2])
+    st, _, res = kpsvd.kp_solve_batch(dev, op_prec="f32", pc_prec="f32", tol=TOL, workers=0, check=False)
+    assert st == kpsvd.KP_OK, kpsvd._lib.kp_last_error().decode()
+    assert kpsvd.kp_batch_grouped(0)[0] == 0
+    for pr, d, (lam, info) in zip(problems[:2], dev, res):
+        P = pr["P"]
+        x_star = opcg.tik_exact(pr["op"], pr["kp"], pr["B"], lam, tol=1e-10)
+        cond = (np.max(np.abs(pr["kp"].Sigma)) ** 2 + lam ** 2) / lam ** 2
+        assert info.status == kpsvd.KP_OK
+        assert rel(kpsvd.from_device(d["x"], P.n_r, P.n_c), x_star) < (1e-4 if cond <= 1e4 else cond * TOL)
