@@ -329,8 +329,9 @@ kp_status kp_set_option(kp_ctx* ctx, const char* name, double value);
  * configuration of the project's workloads.  Each problem computes what
  * kp_setup, choose_lambda and tik_pcg compute for it alone.
  * Grouped form (workers <= 0, the default): one host thread; setup and
- * lambda problem by problem, then the (F)PCG iterations of all problems
- * together: every launch of the iteration (a tensor-core GEMM, a vector
+ * lambda of each problem in a cooperative fiber on the calling thread (a
+ * fiber that waits for the GPU yields to the others, so the setups overlap on
+ * the GPU), then the (F)PCG iterations of all problems together: every launch of the iteration (a tensor-core GEMM, a vector
  * update, a reduction) is ONE launch over all problems (GEMMs: a persistent
  * kernel over the (problem, tile) units of all problems, each problem's
  * tensor maps in a device table; vector kernels: one grid row per problem),
@@ -388,9 +389,10 @@ void kp_batch_release(int device);
  * its grouped loop (0 when none did); passes (nullable): that loop's passes;
  * ms (nullable, 3 doubles): host wall time of the steps before the loop
  * (setups, lambdas, starts), of recording and building the loop, and of
- * running it; shape (nullable, 4 ints): for the first epoch, the launches of
+ * running it; shape (nullable, 6 ints): for the first epoch, the launches of
  * one problem's iteration outside the residual replacement and the grouped
- * launches they became, then the same inside the replacement. */
+ * launches they became, then the same inside the replacement; then 1 if the
+ * setups ran as fibers, and how many times their waits yielded. */
 int kp_batch_grouped(int device, int* passes, double* ms, int* shape);
 
 /* ---- Learned lambda (not in the paper; Section 5 asks for a systematic

@@ -181,10 +181,22 @@ extern "C" kp_status kp_test_bounded_wait(kp_ctx* ctx, double limit_ms) {
   return st != KP_OK ? st : l;
 }
 
+cudaError_t kp_wait(kp_ctx* ctx, cudaStream_t st) {
+  if (!ctx->yield) return cudaStreamSynchronize(st);
+  if (!ctx->ev_wait) {
+    const cudaError_t e = cudaEventCreateWithFlags(&ctx->ev_wait, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaEventRecord(ctx->ev_wait, st);
+  if (e != cudaSuccess) return e;
+  while ((e = cudaEventQuery(ctx->ev_wait)) == cudaErrorNotReady) ctx->yield(ctx->yield_arg);
+  return e;
+}
+
 kp_status read_status(kp_ctx* ctx) {
   int h = 0;
   KP_CUDA(cudaMemcpyAsync(&h, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  KP_CUDA(kp_wait(ctx, ctx->stream));
   if (h & DEV_ERR_TIMEOUT) {
     kp_set_error("a bounded device-side wait gave up (status word 0x%x)", h);
     return KP_ETIMEOUT;
@@ -261,6 +273,7 @@ extern "C" void kp_destroy(kp_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   for (auto& e : ctx->ev_blk)
     if (e) cudaEventDestroy(e);
+  if (ctx->ev_wait) cudaEventDestroy(ctx->ev_wait);
   if (ctx->ctx_block) cudaFree(ctx->ctx_block);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);

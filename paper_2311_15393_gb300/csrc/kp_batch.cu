@@ -25,12 +25,17 @@
 #include <atomic>
 #include <chrono>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
 #include <vector>
+
+#include <sys/mman.h>
+#include <ucontext.h>
+#include <unistd.h>
 
 #include "kp_internal.h"
 #include "kp_vec.cuh"
@@ -189,9 +194,11 @@ struct GroupPool {
   int last_grouped = 0;  // problems the last call's grouped loop ran
   int last_passes = 0;   // passes of that loop
   double last_ms[3] = {0.0, 0.0, 0.0};  // host wall time: before the loop, building it, running it
-  int last_shape[4] = {0, 0, 0, 0};     // first epoch: launch positions and grouped launches per pass
-                                        // (outside the replacement), and the same inside it
+  int last_shape[6] = {0, 0, 0, 0, 0, 0};  // first epoch: launch positions and grouped launches per
+                                           // pass (outside the replacement), the same inside it;
+                                           // then the setups' fibers (1: ran as fibers) and yields
 };
+long long g_yields = 0;
 std::mutex g_pools_mu;
 std::map<int, GroupPool*> g_pools;
 
@@ -250,7 +257,7 @@ extern "C" int kp_batch_grouped(int device, int* passes, double* ms, int* shape)
   if (ms)
     for (int i = 0; i < 3; ++i) ms[i] = p->last_ms[i];
   if (shape)
-    for (int i = 0; i < 4; ++i) shape[i] = p->last_shape[i];
+    for (int i = 0; i < 6; ++i) shape[i] = p->last_shape[i];
   return p->last_grouped;
 }
 
@@ -266,6 +273,80 @@ extern "C" void kp_batch_release(int device) {
   p->dev = nullptr;
   p->dev_bytes = 0;
   if (prev >= 0) cudaSetDevice(prev);
+}
+
+// ---- cooperative fibers (one host thread): run work[k] on ctxs[k] as fibers
+// that yield at their GPU waits (kp_wait); the scheduler resumes them in turn
+// until all have finished.  Each fiber has its own stack with a guard page.
+struct Fiber {
+  ucontext_t uc;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  std::function<void()>* fn = nullptr;
+  bool done = false;
+  ucontext_t* main = nullptr;
+};
+static void fiber_entry(unsigned lo, unsigned hi) {
+  Fiber* f = reinterpret_cast<Fiber*>((uintptr_t)lo | ((uintptr_t)hi << 32));
+  (*f->fn)();
+  f->done = true;
+  swapcontext(&f->uc, f->main);
+}
+static void fiber_yield(void* arg) {
+  Fiber* f = static_cast<Fiber*>(arg);
+  ++g_yields;
+  swapcontext(&f->uc, f->main);
+}
+static kp_status run_fibers(std::vector<std::function<void()>>& work, const std::vector<kp_ctx*>& ctxs) {
+  constexpr size_t STACK = 2u << 20;
+  const size_t page = (size_t)sysconf(_SC_PAGESIZE);
+  const int n = (int)work.size();
+  std::vector<Fiber> fs(n);
+  ucontext_t main_uc;
+  kp_status st = KP_OK;
+  for (int k = 0; k < n && st == KP_OK; ++k) {
+    Fiber& f = fs[k];
+    f.bytes = STACK + page;
+    f.mem = mmap(nullptr, f.bytes, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (f.mem == MAP_FAILED) {
+      f.mem = nullptr;
+      st = KP_ENOMEM;
+      break;
+    }
+    mprotect(f.mem, page, PROT_NONE);  // guard page below the stack
+    if (getcontext(&f.uc) != 0) {
+      st = KP_EINVAL;
+      break;
+    }
+    f.uc.uc_stack.ss_sp = static_cast<char*>(f.mem) + page;
+    f.uc.uc_stack.ss_size = STACK;
+    f.uc.uc_link = nullptr;
+    f.fn = &work[k];
+    f.main = &main_uc;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(&f);
+    makecontext(&f.uc, reinterpret_cast<void (*)()>(fiber_entry), 2, (unsigned)(a & 0xffffffffu), (unsigned)(a >> 32));
+  }
+  if (st == KP_OK) {
+    for (int k = 0; k < n; ++k) {
+      ctxs[k]->yield = fiber_yield;
+      ctxs[k]->yield_arg = &fs[k];
+    }
+    for (int left = n; left > 0;) {
+      left = 0;
+      for (int k = 0; k < n; ++k) {
+        if (fs[k].done) continue;
+        swapcontext(&main_uc, &fs[k].uc);
+        if (!fs[k].done) ++left;
+      }
+    }
+    for (int k = 0; k < n; ++k) {
+      ctxs[k]->yield = nullptr;
+      ctxs[k]->yield_arg = nullptr;
+    }
+  }
+  for (Fiber& f : fs)
+    if (f.mem) munmap(f.mem, f.bytes);
+  return st;
 }
 
 // One epoch of the grouped loop over the problems `act` (all armed, their
@@ -439,8 +520,12 @@ static kp_status solve_grouped(int device, kp_problem* probs, int nprob, const k
     msg[i] = kp_last_error();
     probs[i].info.status = s;
   };
-  // setup, lambda and the steps before the iterations, problem by problem
-  for (int i = 0; i < nprob; ++i) {
+  // setup, lambda and the steps before the iterations of every problem, each
+  // problem in a fiber of its own on this thread: where its host code waits
+  // for the GPU (a convergence test read back, a scalar), it yields, and the
+  // other problems' work is queued meanwhile, so the GPU runs many setups at
+  // once (largest problems first)
+  auto phase1 = [&](int i) {
     kp_problem& p = probs[i];
     kp_ctx* ctx = pool->ctxs[i];
     kp_status s = kp_set_option(ctx, "op_auto_cond", bf16 ? auto_cond : 0.0);
@@ -470,6 +555,24 @@ static kp_status solve_grouped(int device, kp_problem* probs, int nprob, const k
     }
     if (s == KP_OK) s = batch_begin(ctx, p.b, lam, o->tol, o->maxit, o->flexible, p.x, &runs[i]);
     if (s != KP_OK) fail(i, s);
+  };
+  {
+    std::vector<int> order(nprob);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return (long long)probs[a].n_r * probs[a].n_c > (long long)probs[b].n_r * probs[b].n_c;
+    });
+    std::vector<std::function<void()>> work;
+    for (int i : order) work.push_back([&, i]() { phase1(i); });
+    std::vector<kp_ctx*> cs;
+    for (int i : order) cs.push_back(pool->ctxs[i]);
+    g_yields = 0;
+    const kp_status fs = run_fibers(work, cs);
+    if (fs != KP_OK) {  // no fibers: the same work, one problem after another
+      for (int i : order) phase1(i);
+    }
+    pool->last_shape[4] = fs == KP_OK ? 1 : 0;
+    pool->last_shape[5] = (int)std::min<long long>(g_yields, 2000000000LL);
   }
   pool->last_ms[0] = ms_since(t_begin);
   t_mark = clk::now();

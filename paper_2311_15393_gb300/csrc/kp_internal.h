@@ -258,6 +258,12 @@ struct kp_ctx {
 
   // batched solves: while set, launches are recorded here instead of run
   struct KpRecorder* rec = nullptr;
+  // batched solves: the setups of several problems run as cooperative fibers
+  // on one host thread; while `yield` is set, kp_wait hands the thread to the
+  // other problems instead of blocking
+  void (*yield)(void*) = nullptr;
+  void* yield_arg = nullptr;
+  cudaEvent_t ev_wait = nullptr;
   bool tc_group = false;     // batched solve: the operator's and preconditioner's plans run in grouped launches
   bool tc_grouping = false;  // set while those plans are made: no K split, no CTA pairs
   bool tc_group_uniform = true;  // ... and one tile shape (128 wide, one CTA per SM) for all problems
@@ -359,6 +365,9 @@ kp_status split_bf16(kp_ctx* ctx, const void* x, bool f64, long long n, void* ou
                      long long slice_stride, const int* flags = nullptr);
 kp_status copy_vec(kp_ctx* ctx, const void* x, void* y, long long n, bool f64);
 kp_status read_status(kp_ctx* ctx);
+// wait until the work queued on st so far is done (cudaStreamSynchronize, or,
+// inside a batched solve's fiber, yield to the other fibers until it is)
+cudaError_t kp_wait(kp_ctx* ctx, cudaStream_t st);
 kp_status kp_check_ready(kp_ctx* ctx);
 kp_status kp_enter(kp_ctx* ctx);   // order the work stream after the caller's stream
 kp_status kp_leave(kp_ctx* ctx);   // order the caller's stream after the work stream

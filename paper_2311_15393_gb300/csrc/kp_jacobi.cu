@@ -761,7 +761,7 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
   KP_TRY(dot_dev(ctx, W, W, (long long)m * n, true, nrm));
   double fro2 = 0.0;
   KP_CUDA(cudaMemcpyAsync(&fro2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
-  KP_CUDA(cudaStreamSynchronize(st));
+  KP_CUDA(kp_wait(ctx, st));
   const double eps = fast ? 1.1920928955078125e-07 : 2.220446049250313e-16;
   const double floor = (double)m * eps * sqrt(fro2);
   // pairs count as orthogonal at |gamma| <= tol sqrt(alpha beta); below m eps
@@ -815,7 +815,7 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
       KP_LAUNCHED(ctx);
       unsigned int h = 0;
       KP_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-      KP_CUDA(cudaStreamSynchronize(st));
+      KP_CUDA(kp_wait(ctx, st));
       *clean = h == 0;
       return KP_OK;
     };
@@ -864,7 +864,7 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
       }
       cudaError_t ce = cudaGraphLaunch(exec, st);
       if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_cnt, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
-      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+      if (ce == cudaSuccess) ce = kp_wait(ctx, st);
       if (ce != cudaSuccess) {
         kp_set_error("jacobi_svd: sweep failed: %s", cudaGetErrorString(ce));
         gst = KP_ECUDA;
@@ -1010,7 +1010,7 @@ kp_status factor_svd(kp_ctx* ctx, const double* F_rm, int n, int transform, doub
   KP_LAUNCHED(ctx);
   unsigned int asym = 1;
   KP_CUDA(cudaMemcpyAsync(&asym, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-  KP_CUDA(cudaStreamSynchronize(st));
+  KP_CUDA(kp_wait(ctx, st));
   if (asym == 0) {
     KP_CUDA(cudaMemcpyAsync(U, V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
   } else {
@@ -1110,7 +1110,7 @@ static kp_status topr_run(kp_ctx* ctx, const T* W, const T* WT, int m, int n, in
     k_small_right<T><<<gz, 256, 0, st>>>(Z, n, p, UR, p, Uz);
     ctx->launches += 3;
     KP_CUDA(cudaMemcpyAsync(cur.data(), sz, sizeof(T) * r, cudaMemcpyDeviceToHost, st));
-    KP_CUDA(cudaStreamSynchronize(st));
+    KP_CUDA(kp_wait(ctx, st));
     double d = 0.0;
     for (int k = 0; k < r; ++k)
       d = std::max(d, std::fabs((double)cur[k] - (double)prev[k]) / std::max((double)cur[0], 1e-300));
@@ -1126,7 +1126,7 @@ static kp_status topr_run(kp_ctx* ctx, const T* W, const T* WT, int m, int n, in
   }
   int h = 0;
   KP_CUDA(cudaMemcpyAsync(&h, jstat, sizeof(int), cudaMemcpyDeviceToHost, st));
-  KP_CUDA(cudaStreamSynchronize(st));
+  KP_CUDA(kp_wait(ctx, st));
   if (h) {
     kp_set_error("topr_svd: Ritz-step Jacobi did not converge in %d sweeps", ctx->jacobi_max_sweeps);
     return KP_ENOCONV;

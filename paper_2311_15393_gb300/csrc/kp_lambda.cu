@@ -357,7 +357,7 @@ static kp_status eval64(LamCtx& L, const double* lams, int k, double* s1, double
   KP_LAUNCHED(ctx);
   double h[32];
   KP_CUDA(cudaMemcpyAsync(h, L.sums, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, ctx->stream));
-  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  KP_CUDA(kp_wait(ctx, ctx->stream));
   for (int i = 0; i < k; ++i) {
     s1[i] = h[2 * i];
     s2[i] = h[2 * i + 1];
@@ -373,7 +373,7 @@ static kp_status deriv64(LamCtx& L, double lam, double* s6) {
   k_sum6_finish<<<1, 256, 0, ctx->stream>>>(L.part, L.chunks, L.sums);
   KP_LAUNCHED(ctx);
   KP_CUDA(cudaMemcpyAsync(s6, L.sums, sizeof(double) * 6, cudaMemcpyDeviceToHost, ctx->stream));
-  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  KP_CUDA(kp_wait(ctx, ctx->stream));
   return KP_OK;
 }
 
@@ -552,7 +552,7 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
   k_prep_coeffs<<<gr, 256, 0, st>>>(bh, xh, N, bhf, xhf);
   KP_LAUNCHED(ctx);
   if (!ctx->lam_sigma_ready) {
-    KP_CUDA(cudaStreamSynchronize(st));
+    KP_CUDA(kp_wait(ctx, st));
     ctx->lam_sigma_ready = true;
   }
   if (coeffs_only) {
@@ -697,7 +697,7 @@ static kp_status choose_lambda_impl(kp_ctx* ctx, const void* b, kp_lambda_method
   }
   std::vector<double> hsum(2 * NGRID);
   KP_CUDA(cudaMemcpyAsync(hsum.data(), sums, sizeof(double) * 2 * NGRID, cudaMemcpyDeviceToHost, st));
-  KP_CUDA(cudaStreamSynchronize(st));
+  KP_CUDA(kp_wait(ctx, st));
   // every grid sum is bounded for finite data (phi in [0, 1], d >= lam^2 > 0):
   // a NaN or Inf comes from b (or x_true) and would leave no minimum to find
   for (int g = 0; g < 2 * NGRID; ++g) {

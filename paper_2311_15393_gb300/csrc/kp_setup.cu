@@ -353,7 +353,7 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
     double h[2];
     KP_TRY(norm_amax_dev(ctx, W, N, true, ctx->dscal + S_RR));
     KP_CUDA(cudaMemcpyAsync(h, ctx->dscal + S_RR, sizeof(h), cudaMemcpyDeviceToHost, st));
-    KP_CUDA(cudaStreamSynchronize(st));
+    KP_CUDA(kp_wait(ctx, st));
     if (!std::isfinite(h[0]) || !std::isfinite(h[1])) {
       kp_set_error("kp_setup: the PSF holds a NaN or Inf");
       return KP_ENUMERIC;
@@ -525,7 +525,7 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
       ctx->launches += 2;
       double h[2];
       KP_CUDA(cudaMemcpyAsync(h, am, sizeof(h), cudaMemcpyDeviceToHost, st));
-      KP_CUDA(cudaStreamSynchronize(st));
+      KP_CUDA(kp_wait(ctx, st));
       int e;
       std::frexp(448.0 / h[0], &e);
       sc_c = std::ldexp(1.0, e - 1);
@@ -559,7 +559,7 @@ extern "C" kp_status kp_setup(kp_ctx* ctx, const double* psf, int n_r, int n_c, 
   // ---- workspaces and GEMM plans
   KP_TRY(ops_prepare(ctx));
   KP_CUDA(cudaEventRecord(ctx->ev_setup[1], st));
-  KP_CUDA(cudaStreamSynchronize(st));
+  KP_CUDA(kp_wait(ctx, st));
   KP_TRY(read_status(ctx));
   {
     float ms = 0.f;

@@ -228,13 +228,13 @@ struct HostFlags {
 static kp_status read_flags(kp_ctx* ctx, HostFlags* h, double* hs) {
   KP_CUDA(cudaMemcpyAsync(h, ctx->dflags, sizeof(HostFlags), cudaMemcpyDeviceToHost, ctx->stream));
   if (hs) KP_CUDA(cudaMemcpyAsync(hs, ctx->dscal, 12 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  KP_CUDA(kp_wait(ctx, ctx->stream));
   return KP_OK;
 }
 
 static kp_status set_scalar(kp_ctx* ctx, int slot, double v) {
   KP_CUDA(cudaMemcpyAsync(ctx->dscal + slot, &v, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  KP_CUDA(cudaStreamSynchronize(ctx->stream));  // v is a host stack value
+  KP_CUDA(kp_wait(ctx, ctx->stream));  // v is a host stack value
   return KP_OK;
 }
 
@@ -371,7 +371,7 @@ static kp_status choose_inner(kp_ctx* ctx, double lam2) {
     double h[2];
     KP_TRY(norm_amax_dev(ctx, ctx->Sigma64, (long long)ctx->n_r * ctx->n_c, true, ctx->dscal + S_RR));
     KP_CUDA(cudaMemcpyAsync(h, ctx->dscal + S_RR, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
-    KP_CUDA(cudaStreamSynchronize(ctx->stream));
+    KP_CUDA(kp_wait(ctx, ctx->stream));
     ctx->sigma_max = h[1];
   }
   const double cond = (ctx->sigma_max * ctx->sigma_max + lam2) / lam2;
@@ -430,7 +430,7 @@ static kp_status solve_begin(kp_ctx* ctx, const void* b, double lambda, double t
   {
     int hf[5] = {0, 0, 0, maxit, flexible ? 1 : 0};
     KP_CUDA(cudaMemcpyAsync(ctx->dflags, hf, sizeof(hf), cudaMemcpyHostToDevice, st));
-    KP_CUDA(cudaStreamSynchronize(st));
+    KP_CUDA(kp_wait(ctx, st));
   }
   // rhs = A^T b (accurate operator) and its norm
   KP_TRY(op_apply(ctx, b, B.rhs, 1, OP_ACCURATE));
@@ -470,7 +470,7 @@ static kp_status solve_begin(kp_ctx* ctx, const void* b, double lambda, double t
   KP_TRY(dot2_dev(ctx, B.z, B.r, nullptr, N, f64, ctx->dscal + S_ZR, nullptr));
   const int sl = op_inner_slices(ctx);
   KP_TRY(p_update_dev(ctx, B.p, B.z, N, f64, nullptr, sl ? (__nv_bfloat16*)ctx->w_img2 : nullptr, sl, N, nullptr));
-  KP_CUDA(cudaStreamSynchronize(st));  // h0 is a host stack value
+  KP_CUDA(kp_wait(ctx, st));  // h0 is a host stack value
   R->need_loop = true;
   return KP_OK;
 }

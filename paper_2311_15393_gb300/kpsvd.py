@@ -353,10 +353,10 @@ def kp_batch_grouped(device: int = 0):
     """(problems the last grouped kp_solve_batch ran in its grouped loop, the
     loop's passes, [ms before the loop, ms building it, ms running it],
     [launches per problem iteration, grouped launches per pass, the same
-    for the residual replacement])."""
+    for the residual replacement, setups ran as fibers, fiber yields])."""
     passes = ctypes.c_int(0)
     ms = (ctypes.c_double * 3)()
-    shape = (ctypes.c_int * 4)()
+    shape = (ctypes.c_int * 6)()
     n = _lib.kp_batch_grouped(device, ctypes.byref(passes), ms, shape)
     return n, passes.value, list(ms), list(shape)
 
