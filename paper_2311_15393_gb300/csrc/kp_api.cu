@@ -274,6 +274,7 @@ extern "C" void kp_destroy(kp_ctx* ctx) {
   for (auto& e : ctx->ev_blk)
     if (e) cudaEventDestroy(e);
   if (ctx->ev_wait) cudaEventDestroy(ctx->ev_wait);
+  jacobi_cache_free(ctx);
   if (ctx->ctx_block) cudaFree(ctx->ctx_block);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);

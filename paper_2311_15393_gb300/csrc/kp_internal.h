@@ -261,6 +261,7 @@ struct kp_ctx {
   // batched solves: the setups of several problems run as cooperative fibers
   // on one host thread; while `yield` is set, kp_wait hands the thread to the
   // other problems instead of blocking
+  void* jac_cache = nullptr;  // instantiated Jacobi sweep graphs (kp_jacobi.cu)
   void (*yield)(void*) = nullptr;
   void* yield_arg = nullptr;
   cudaEvent_t ev_wait = nullptr;
@@ -368,6 +369,7 @@ kp_status read_status(kp_ctx* ctx);
 // wait until the work queued on st so far is done (cudaStreamSynchronize, or,
 // inside a batched solve's fiber, yield to the other fibers until it is)
 cudaError_t kp_wait(kp_ctx* ctx, cudaStream_t st);
+void jacobi_cache_free(kp_ctx* ctx);
 kp_status kp_check_ready(kp_ctx* ctx);
 kp_status kp_enter(kp_ctx* ctx);   // order the work stream after the caller's stream
 kp_status kp_leave(kp_ctx* ctx);   // order the caller's stream after the work stream

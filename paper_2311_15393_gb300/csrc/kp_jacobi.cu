@@ -66,8 +66,9 @@ __device__ __forceinline__ int rr_player(int t, int round, int npad) {
 // the FP32-vector setup, whose tolerance is FP32-level anyway)
 template <typename T>
 __global__ void __launch_bounds__(JT) k_jacobi_round(T* __restrict__ W, T* __restrict__ V, int m, int n, int npad,
-                                                     int round, double tol, double floor,
+                                                     int round, const double* __restrict__ thr,
                                                      unsigned int* __restrict__ rot_count) {
+  const double tol = thr[0], floor = thr[1];  // (in device memory: a captured sweep serves any matrix)
   const int pidx = blockIdx.x;
   int i = rr_player(pidx, round, npad);
   int j = rr_player(npad - 1 - pidx, round, npad);
@@ -161,8 +162,9 @@ __host__ __device__ constexpr int rb_hi(int p, int round) {
 
 template <int R>  // rows per thread: m, n <= R RB_T
 __global__ void __launch_bounds__(RB_T) k_jacobi_rblock(float* __restrict__ W, float* __restrict__ V, int m, int n,
-                                                        int nb, int round, float tol, float floor,
+                                                        int nb, int round, const double* __restrict__ thr,
                                                         unsigned int* __restrict__ rot_count) {
+  const float tol = (float)thr[0], floor = (float)thr[1];
   constexpr int C = 2 * RB_JB;
   constexpr int NW = RB_T / 32;
   __shared__ float red[NW][RB_JB][3];
@@ -744,6 +746,36 @@ __global__ void __launch_bounds__(SJ_T) k_jacobi_small(const T* __restrict__ A, 
 
 }  // namespace
 
+// instantiated sweep graphs of a context (at most 16; the oldest is dropped)
+struct JacobiCache {
+  struct Entry {
+    const void* w;
+    const void* v;
+    const void* cnt;
+    int m, n, kind;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Entry> entries;
+};
+static JacobiCache* jacobi_cache(kp_ctx* ctx) {
+  if (!ctx->jac_cache) ctx->jac_cache = new JacobiCache();
+  return static_cast<JacobiCache*>(ctx->jac_cache);
+}
+static void jacobi_cache_put(JacobiCache* jc, const JacobiCache::Entry& e) {
+  if (jc->entries.size() >= 16) {
+    cudaGraphExecDestroy(jc->entries.front().exec);
+    jc->entries.erase(jc->entries.begin());
+  }
+  jc->entries.push_back(e);
+}
+void jacobi_cache_free(kp_ctx* ctx) {
+  if (!ctx->jac_cache) return;
+  auto* jc = static_cast<JacobiCache*>(ctx->jac_cache);
+  for (auto& e : jc->entries) cudaGraphExecDestroy(e.exec);
+  delete jc;
+  ctx->jac_cache = nullptr;
+}
+
 // Sweeps on W (m x n col-major, in place) accumulating into V (n x n,
 // holding its initial value); then sigma, sorting, U = W / sigma.
 static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, double* U, double* s, double* V,
@@ -834,33 +866,52 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
     const int nbl = (n + RB_JB - 1) / RB_JB;
     const int nb = nbl + (nbl & 1);
     const int rounds = blocked ? nb - 1 : npad - 1;
+    // the thresholds live in device memory, so a captured sweep depends only on
+    // the buffers and sizes: the sweep graphs are kept per context and reused
+    // whenever the same buffers come back (repeated setups of equal sizes)
+    double* thr = ctx->dscal + S_JACOBI;
+    {
+      const double th[2] = {tol, floor};
+      KP_CUDA(cudaMemcpyAsync(thr, th, sizeof(th), cudaMemcpyHostToDevice, st));
+      KP_CUDA(kp_wait(ctx, st));  // th is a host stack value
+    }
+    JacobiCache* jc = jacobi_cache(ctx);
+    const void* kw = fast ? (const void*)W32 : (const void*)W;
+    const void* kv = fast ? (const void*)V32 : (const void*)Vw;
+    const int kind = blocked ? rsel : (fast ? -1 : -2);
+    for (const auto& e : jc->entries)
+      if (e.w == kw && e.v == kv && e.cnt == cnt && e.m == m && e.n == n && e.kind == kind) exec = e.exec;
     for (sweeps = 0; !clean && sweeps < ctx->jacobi_max_sweeps; ++sweeps) {
       if (!exec) {  // one sweep (n - 1 rounds, or nb - 1 block rounds) as a graph, built at the first sweep
         KP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         k_zero_u32<<<1, 1, 0, st>>>(cnt);
         for (int round = 0; round < rounds; ++round) {
           if (blocked) {
-            const float ft = (float)tol, ff = (float)floor;
             switch (rsel) {
-              case 1: k_jacobi_rblock<1><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
-              case 2: k_jacobi_rblock<2><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
-              case 4: k_jacobi_rblock<4><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
-              case 6: k_jacobi_rblock<6><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
-              default: k_jacobi_rblock<8><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, ft, ff, cnt); break;
+              case 1: k_jacobi_rblock<1><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, thr, cnt); break;
+              case 2: k_jacobi_rblock<2><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, thr, cnt); break;
+              case 4: k_jacobi_rblock<4><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, thr, cnt); break;
+              case 6: k_jacobi_rblock<6><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, thr, cnt); break;
+              default: k_jacobi_rblock<8><<<nb / 2, RB_T, 0, st>>>(W32, V32, m, n, nb, round, thr, cnt); break;
             }
           } else if (fast) {
-            k_jacobi_round<float><<<npad / 2, JT, 0, st>>>(W32, V32, m, n, npad, round, tol, floor, cnt);
+            k_jacobi_round<float><<<npad / 2, JT, 0, st>>>(W32, V32, m, n, npad, round, thr, cnt);
           } else {
-            k_jacobi_round<double><<<npad / 2, JT, 0, st>>>(W, Vw, m, n, npad, round, tol, floor, cnt);
+            k_jacobi_round<double><<<npad / 2, JT, 0, st>>>(W, Vw, m, n, npad, round, thr, cnt);
           }
         }
         cudaError_t ce = cudaStreamEndCapture(st, &graph);
         if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) {
+          cudaGraphDestroy(graph);
+          graph = nullptr;
+        }
         if (ce != cudaSuccess) {
           kp_set_error("jacobi_svd: sweep graph capture failed: %s", cudaGetErrorString(ce));
           gst = KP_ECUDA;
           break;
         }
+        jacobi_cache_put(jc, JacobiCache::Entry{kw, kv, cnt, m, n, kind, exec});
       }
       cudaError_t ce = cudaGraphLaunch(exec, st);
       if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_cnt, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
@@ -886,7 +937,6 @@ static kp_status jacobi_run(kp_ctx* ctx, double* W, int m, int n, double* Vw, do
         }
       }
     }
-    if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     KP_TRY(gst);
     if (fast && sweeps > 0) {

@@ -29,6 +29,7 @@ constexpr int F_GUARD = 15;  // device loop: passes of the loop body
 // the multi-term preconditioner's inner PCG keeps its scalars and flags in
 // blocks of their own, at these offsets into ctx->dscal / ctx->dflags
 constexpr int S_INNER = 64, F_INNER = 16;
+constexpr int S_JACOBI = 320;  // setup: the Jacobi thresholds (tol, floor) the sweep kernels read
 // a reliable update is also due after this many iterations without one (so a
 // recurred residual that stops falling is checked against the true one)
 constexpr int REPLACE_EVERY = 50;
