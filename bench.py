@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--batch-tiles", default="uniform", choices=["uniform", "timed", "per-shape"],
                     help="batched64 (grouped): one tile shape for all problems (each step one launch), shapes "
                          "chosen by timing (autotuner), or the size rule of single solves")
+    ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
+                    help="context option (kp_set_option) set before kp_setup, e.g. tc_kcat=1; repeatable "
+                         "(1024^2 workload and --kernel-only)")
     ap.add_argument("--kernel-only", choices=["kapply", "minv"], default=None,
                     help="set up once, then run only the operator application (or preconditioner solve) "
                          "--steps times: for kernel profiles")
@@ -368,6 +371,9 @@ def run_ours(args, ws, rank, local, dist):
         ctx = kpsvd.KpContext(dev, stream=stream.cuda_stream)
         if args.host_loop:
             ctx.kp_set_option("device_loop", 0)
+        for o in args.opt:
+            name, _, value = o.partition("=")
+            ctx.kp_set_option(name, float(value))
         # observed data with this context's own operator (untimed input preparation)
         ctx.kp_setup(psf, n_r, n_c, P.center, P.bc, P.op_rank, args.op, args.pc, "f32", "projected")
         for g, b, nl in zip(gs, bs, P.noise_levels):
@@ -599,7 +605,8 @@ def run_ours(args, ws, rank, local, dist):
                    "setup": "FP32 products, rotations and subspace iteration (FP64 norms, sort, Sigma); "
                             "setup_ms.fp64 times the FP64 form",
                    "l2": "256 MiB buffer written before every step",
-                   "step": "kp_setup + 2 x (choose_lambda GCV + tik_pcg FPCG)"},
+                   "step": "kp_setup + 2 x (choose_lambda GCV + tik_pcg FPCG)",
+                   **({"options": args.opt} if args.opt else {})},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"kernel": "K application q = (A^T A + lambda^2 I) p as the iteration runs it "

@@ -300,6 +300,18 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     SM pairs run on CTA pairs (tcgen05 cta_group::2, one
  *                     256 x 256 tile per pair of SMs); 1: never; 2: wherever
  *                     the shape allows (N >= 256, per-term blocks of 256 rows)
+ *   "tc_kcat"         0 (default): the second and fourth GEMM of the inner
+ *                     operator as per-term products and a separate term sum
+ *                     (measured faster at 1024^2); 1: where 128 x 64 tiles of
+ *                     the sum over terms fill most SMs, as ONE product over
+ *                     all terms (the terms summed in the tensor-memory
+ *                     accumulator: no per-term outputs, no term sum), the
+ *                     fourth GEMM's epilogue also reducing p^T q and max |q|;
+ *                     2: the same wherever the shape allows (any size; n_r a
+ *                     multiple of 256 with clusters of four)
+ *   "tc_kcat_cluster" 1 (default) or 4: CTAs per cluster of those products;
+ *                     4: neighbouring tiles share their A tiles by TMA
+ *                     multicast
  *                     The tile options take effect at the next kp_setup.
  *   "device_loop"     1 (default): tik_pcg runs its whole iteration as one CUDA
  *                     graph with a device-side while loop (the residual

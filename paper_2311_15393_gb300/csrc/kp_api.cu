@@ -364,6 +364,18 @@ extern "C" kp_status kp_set_option(kp_ctx* ctx, const char* name, double value) 
     ctx->tc_autotune = value != 0.0;
   } else if (!strcmp(name, "tc_pair")) {
     ctx->tc_pair_override = (int)value;
+  } else if (!strcmp(name, "tc_kcat")) {
+    if (value != 0.0 && value != 1.0 && value != 2.0) {
+      kp_set_error("tc_kcat must be 0, 1 or 2");
+      return KP_EINVAL;
+    }
+    ctx->tc_kcat = (int)value;
+  } else if (!strcmp(name, "tc_kcat_cluster")) {
+    if (value != 1.0 && value != 4.0) {
+      kp_set_error("tc_kcat_cluster must be 1 or 4");
+      return KP_EINVAL;
+    }
+    ctx->tc_kcat_cluster = (int)value;
   } else if (!strcmp(name, "setup_fp64")) {
     ctx->force_setup_fp64 = value != 0.0;
   } else if (!strcmp(name, "setup_half")) {

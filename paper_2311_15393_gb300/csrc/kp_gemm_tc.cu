@@ -84,6 +84,14 @@ struct TcParams {
   const float* alpha_dev;   // optional device scale multiplied into the output
   const int* flags;
   int* status;
+  // multicast-cluster kernel only: sum(out * aux) as a double-float pair and
+  // max |out| over the whole output into dot_out[0..1] (null: none), the
+  // last CTA to finish running dot_po on them
+  double* dot_out;
+  double* dot_part;
+  unsigned int* dot_count;
+  PostOp dot_po;
+  int dot_qmax;
 };
 
 // ------------------------------------------------------------- PTX helpers
@@ -647,7 +655,7 @@ __global__ void __launch_bounds__(TC_THREADS, CPS)
 // pause flag is set (its problem has stopped) contributes no work: every
 // role reads the same flag, written before this launch, and skips its units.
 // No split-K; the ring and accumulator phases run on across plans.
-struct alignas(64) TcGroupEntry {
+struct alignas(128) TcGroupEntry {  // the alignment of CUtensorMap
   CUtensorMap mapA, mapB;
   TcParams p;
 };
@@ -1161,6 +1169,383 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// ------------------------------------------------------------- K-concatenated products
+// A product summed over many k-blocks (the operator's sum over Kronecker
+// terms as ONE GEMM over the concatenated K of all terms, the terms summed in
+// the TMEM accumulator) on narrow 128 x 64 tiles, so that a 1024 x 1024
+// output still gives one tile per SM, and without per-term outputs.  The
+// epilogue can also reduce sum(out * aux) (double-float) and max |out| over
+// the whole output, finished by the last CTA to arrive (for the operator's
+// last GEMM: p^T q, max |q| and the alpha step).
+// With CL = 4 the CTAs form clusters of four along N: they compute
+// neighbouring tiles of the same 128 output rows, so they read the same A
+// tile at every k-block, and each loads one quarter of its rows (32) and
+// multicasts it to the whole cluster (12 KiB instead of 24 KiB from L2 per
+// CTA and k-block).  A ring slot is then refilled only after the MMAs of
+// every CTA of the cluster have read it: each CTA's MMA thread commits its
+// reads to that slot's empty barrier in all of them (count CL).  A CTA's
+// full barrier counts the bytes landing in its own shared memory (its B tile
+// and the slices of A), armed by its own producer; slices from the other
+// CTAs may land before it is armed (the barrier's pending arrival keeps the
+// phase open until then).
+//   warp 0      TMA producer (lanes 2q / 2q + 1: A (slice) / B tile of k-block q)
+//   warp 1      TMEM allocation + MMA issuer (one thread)
+//   warps 2..5  epilogue; optionally the dot reduction of the output
+// Every wait is bounded; the producer waits, before the CTA leaves, until the
+// cluster has read every slot it filled, and all CTAs end at a cluster
+// barrier, so no CTA leaves while another may still write its shared memory.
+constexpr int KC_BN = 64;
+
+template <int KPS, int CL>
+struct KcCfg {
+  static constexpr int A_BYTES = TBM * 128;     // the whole A tile of a k-block (CL slices)
+  static constexpr int A_SLICE = A_BYTES / CL;  // the rows one CTA of the cluster loads
+  static constexpr int B_BYTES = KC_BN * 128;
+  static constexpr int KB_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGE = KPS * KB_BYTES;
+  static constexpr int STAGES = 196608 / STAGE;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
+  static constexpr int TMEM_COLS = 2 * KC_BN;
+  static_assert(STAGES >= 2, "ring too shallow");
+  static_assert(A_SLICE % 1024 == 0, "A slices must keep the 1024-byte swizzle atoms");
+};
+
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                               uint32_t bar, uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+      "%3, %4}], [%5], %6;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "h"(cta_mask)
+      : "memory");
+}
+// arrive (once) on the barrier at this offset in every CTA of the mask when
+// the MMAs issued so far have completed
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(cta_mask)
+      : "memory");
+}
+
+struct KcUnit {
+  int m0, n0;
+};
+// unit u = one cluster's CL neighbouring tiles of a 128-row block
+template <int CL>
+__device__ __forceinline__ KcUnit decode_kc(const TcParams& p, int u, int rank) {
+  const int groups_n = p.tiles_n / CL;
+  KcUnit r;
+  r.m0 = (u / groups_n) * TBM;
+  r.n0 = ((u % groups_n) * CL + rank) * KC_BN;
+  return r;
+}
+
+// sum(out * aux) and max |out| of one stored 32-column row segment (out: the
+// values epi_store32 wrote, in v)
+__device__ __forceinline__ void kc_dot_segment(const EpiParams& e, int gm, int gn0, int N, const float (&v)[32],
+                                               float& dh, float& dl, float& mx) {
+  const int cnt = min(32, N - gn0);
+  const float* aux = (const float*)e.aux + (long long)gm * e.ld_aux + gn0;
+  if (cnt == 32 && ((reinterpret_cast<uintptr_t>(aux) & 15) == 0)) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 t = *reinterpret_cast<const float4*>(aux + 4 * q);
+      kpv::df_add_prod(dh, dl, v[4 * q + 0], t.x);
+      kpv::df_add_prod(dh, dl, v[4 * q + 1], t.y);
+      kpv::df_add_prod(dh, dl, v[4 * q + 2], t.z);
+      kpv::df_add_prod(dh, dl, v[4 * q + 3], t.w);
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) mx = fmaxf(mx, fabsf(v[c]));
+  } else {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      if (c < cnt) {
+        kpv::df_add_prod(dh, dl, v[c], aux[c]);
+        mx = fmaxf(mx, fabsf(v[c]));
+      }
+    }
+  }
+}
+
+// the epilogue warps' (128 threads, named barrier 1) double-float sum and max:
+// within the warp, then over the four warps in a fixed order
+__device__ __forceinline__ void kc_epi_reduce(float& h, float& l, float& mx, float2 (*red)[2], int quarter,
+                                              int lane) {
+  kpv::df_warp_sum(h, l);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    red[quarter][0] = make_float2(h, l);
+    red[quarter][1] = make_float2(mx, 0.f);
+  }
+  epi_bar();
+  h = 0.f;
+  l = 0.f;
+  mx = 0.f;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    l += red[w][0].y;
+    kpv::df_add(h, l, red[w][0].x);
+    mx = fmaxf(mx, red[w][1].x);
+  }
+  epi_bar();  // red is read by every thread before it is written again
+}
+
+template <int KIND, int KPS, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kcat_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+  using C = KcCfg<KPS, CL>;
+  if (threadIdx.x == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + C::STAGES;
+  uint64_t* tfull = bars + 2 * C::STAGES;  // [2]
+  uint64_t* tempty = tfull + 2;            // [2]
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  __shared__ int s_abort;
+  __shared__ int s_last;
+  __shared__ float2 s_red[4][2];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = (int)cluster_rank();
+  const int cl = blockIdx.x / CL, ncl = gridDim.x / CL;
+  const uint16_t all = (uint16_t)((1u << CL) - 1u);
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), CL);  // the MMA threads of the whole cluster
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // every CTA's barriers initialised before any multicast reaches them
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ksh = KIND == TC_E4M3 ? 0 : 1;
+  const int nk = p.nkron;
+  const int nstages = (p.steps_total + KPS - 1) / KPS;
+  bool skip = false;
+  if (warp == 0 && lane < 2 * KPS) {
+    // ---------------- TMA producer
+    const bool isB = lane & 1;
+    const int q = lane >> 1;
+    const CUtensorMap* map = isB ? &tmB : &tmA;
+    const unsigned mask = (1u << (2 * KPS)) - 1u;
+    auto load = [&](const KcUnit& w, int j, int s, bool a_side) {
+      const int nkb = min(KPS, p.steps_total - j * KPS);
+      if (q >= nkb || isB == a_side) return;
+      const int stp = j * KPS + q;
+      const int kb = stp % p.kblocks;
+      const int rest = stp / p.kblocks;
+      const int k = rest % nk, pr = rest / nk;
+      const int term = (isB ? p.sb[pr] * p.b_terms : p.sa[pr] * p.a_terms) + k;
+      const uint32_t kbase = smem_u32(smem + s * C::STAGE + q * C::KB_BYTES);
+      if (isB)
+        tma_load_3d(kbase + (uint32_t)C::A_BYTES, map, (kb * 128) >> ksh, w.n0, term, smem_u32(&full[s]));
+      else if constexpr (CL == 1)
+        tma_load_3d(kbase, map, (kb * 128) >> ksh, w.m0, term, smem_u32(&full[s]));
+      else
+        tma_load_3d_mc(kbase + (uint32_t)(rank * C::A_SLICE), map, (kb * 128) >> ksh, w.m0 + (TBM / CL) * rank, term,
+                       smem_u32(&full[s]), all);
+    };
+    auto arm = [&](int j, int s) {
+      const int nkb = min(KPS, p.steps_total - j * KPS);
+      mbar_expect_tx(smem_u32(&full[s]), (uint32_t)(nkb * C::KB_BYTES));
+    };
+    // prefetch: the A slices (a constant factor) of the first ring stages
+    // before waiting for the previous kernel
+    int npre = 0;
+    KcUnit w0;
+    if (cl < p.units) {
+      w0 = decode_kc<CL>(p, cl, rank);
+      npre = min(C::STAGES, nstages);
+      for (int j = 0; j < npre; ++j) {
+        if (lane == 0) arm(j, j);
+        __syncwarp(mask);
+        load(w0, j, j, true);
+      }
+    }
+    KP_PDL_WAIT();
+    KP_PDL_TRIGGER();
+    skip = p.flags && *(volatile const int*)p.flags;
+    for (int j = 0; j < npre; ++j) load(w0, j, j, false);
+    if (skip) {
+      if (lane == 0)  // every prefetched stage (all CTAs' slices) lands before the CTA leaves
+        for (int j = 0; j < npre; ++j) mbar_wait_t(smem_u32(&full[j]), 0, p.status);
+    } else {
+      int it = npre;
+      bool run = true;
+      for (int u = cl; run && u < p.units && !*(volatile int*)&s_abort; u += ncl) {
+        const KcUnit w = decode_kc<CL>(p, u, rank);
+        for (int j = u == cl ? npre : 0; j < nstages; ++j, ++it) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (it / C::STAGES) & 1;
+          int okw = 1;
+          if (lane == 0) {
+            okw = mbar_wait_t(smem_u32(&empty[s]), ph ^ 1, p.status) ? 1 : 0;
+            if (okw) arm(j, s);
+          }
+          okw = __shfl_sync(mask, okw, 0);
+          if (!okw) {
+            if (lane == 0) s_abort = 1;
+            run = false;
+            break;
+          }
+          load(w, j, s, true);
+          load(w, j, s, false);
+        }
+      }
+      // tail: the whole cluster has read every slot this CTA filled (their
+      // commits to this CTA's empty barriers have landed)
+      if (run && lane == 0) {
+        for (int t = it; t < it + C::STAGES; ++t)
+          if (!mbar_wait_t(smem_u32(&empty[t % C::STAGES]), ((t / C::STAGES) & 1) ^ 1, p.status)) break;
+      }
+    }
+  } else {
+    KP_PDL_WAIT();
+    KP_PDL_TRIGGER();
+    skip = p.flags && *(volatile const int*)p.flags;
+  }
+
+  if (skip || warp == 0) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int it = 0, i = 0;
+      for (int u = cl; u < p.units; u += ncl, ++i) {
+        const int buf = i & 1;
+        if (*(volatile int*)&s_abort || !mbar_wait_t(smem_u32(&tempty[buf]), ((i >> 1) & 1) ^ 1, p.status)) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * KC_BN);
+        bool ok = true;
+        for (int j = 0; j < nstages; ++j, ++it) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (it / C::STAGES) & 1;
+          if (*(volatile int*)&s_abort || !mbar_wait_t(smem_u32(&full[s]), ph, p.status)) {
+            s_abort = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int nkb = min(KPS, p.steps_total - j * KPS);
+#pragma unroll
+          for (int q = 0; q < KPS; ++q) {
+            if (q < nkb) {
+              const uint32_t a0 = smem_u32(smem + s * C::STAGE + q * C::KB_BYTES);
+              const uint32_t b0 = a0 + C::A_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                mma_issue<KIND>(d, make_sdesc(a0 + kk * 32), make_sdesc(b0 + kk * 32), p.idesc,
+                                (j > 0 || q > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          if constexpr (CL == 1)
+            mma_commit(smem_u32(&empty[s]));
+          else
+            mma_commit_mc(smem_u32(&empty[s]), all);
+        }
+        mma_commit(smem_u32(&tfull[buf]));
+        if (!ok) break;
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 2..5 -> TMEM lanes 32 * (warp % 4)
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const int etid = threadIdx.x - 64;
+    const float sdev = p.alpha_dev ? *p.alpha_dev : 1.f;
+    const bool dot = p.dot_out != nullptr;
+    float dh = 0.f, dl = 0.f, dmx = 0.f;
+    int i = 0;
+    for (int u = cl; u < p.units; u += ncl, ++i) {
+      const KcUnit w = decode_kc<CL>(p, u, rank);
+      const int buf = i & 1;
+      if (!mbar_wait_t(smem_u32(&tfull[buf]), (i >> 1) & 1, p.status)) break;
+      tc_fence_after();
+      const int gm = w.m0 + row;
+      const bool row_ok = gm < p.M;
+      float tmax = 0.f;
+#pragma unroll 1
+      for (int chunk = 0; chunk < KC_BN / 32; ++chunk) {
+        float acc[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * KC_BN + chunk * 32), acc);
+        const int gn0 = w.n0 + chunk * 32;
+        if (row_ok && gn0 < p.N) {
+          epi_store32(p.epi, sdev, gm, gn0, p.N, acc, tmax);
+          if (dot) kc_dot_segment(p.epi, gm, gn0, p.N, acc, dh, dl, dmx);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&tempty[buf]));
+      if (p.epi.amax_bits) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        if (lane == 0 && tmax > 0.f) atomicMax(p.epi.amax_bits, __float_as_uint(tmax));
+      }
+    }
+    if (dot) {
+      // this CTA's sums, then the last CTA to arrive adds all CTAs' in order
+      kc_epi_reduce(dh, dl, dmx, s_red, quarter, lane);
+      float2* pp = reinterpret_cast<float2*>(p.dot_part);
+      if (etid == 0) {
+        pp[2 * blockIdx.x] = make_float2(dh, dl);
+        pp[2 * blockIdx.x + 1] = make_float2(dmx, 0.f);
+        __threadfence();
+        s_last = atomicAdd(p.dot_count, 1u) == gridDim.x - 1 ? 1 : 0;
+      }
+      epi_bar();
+      if (s_last) {
+        __threadfence();
+        dh = dl = dmx = 0.f;
+        for (int b = etid; b < (int)gridDim.x; b += 128) {
+          const float2 t = __ldcg(pp + 2 * b);
+          dl += t.y;
+          kpv::df_add(dh, dl, t.x);
+          dmx = fmaxf(dmx, __ldcg(pp + 2 * b + 1).x);
+        }
+        kc_epi_reduce(dh, dl, dmx, s_red, quarter, lane);
+        if (etid == 0) {
+          double fin[2] = {(double)dh + (double)dl, (double)dmx};
+          p.dot_out[0] = fin[0];
+          if (p.dot_qmax) p.dot_out[1] = fin[1];
+          *p.dot_count = 0u;
+          if (p.dot_po.kind != POST_NONE) kpv::run_post(p.dot_po, fin);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // no CTA leaves while another may still signal or fill it
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- host side
@@ -1172,6 +1557,7 @@ struct TcGemmPlan {
   int cps;
   int kps;
   bool pair;  // 256 x 256 tiles on CTA pairs (tc_gemm_pair_kernel)
+  int kcat;   // > 0: K-concatenated product on tc_gemm_kcat_kernel, clusters of this many CTAs
   dim3 grid;
 };
 
@@ -1243,6 +1629,34 @@ bool tc_device_supported(kp_ctx* ctx) {
   return major == 10 && minor == 3;
 }
 
+// clusters of the K-concatenated kernel that fit on the GPU at once (0: none
+// or unknown, then the plan does not use the kernel)
+template <int KPS, int CL>
+static int kcat_max_clusters(kp_ctx* ctx) {
+  static std::atomic<int> cached{-1};
+  int v = cached.load();
+  if (v >= 0) return v;
+  using C = KcCfg<KPS, CL>;
+  v = 0;
+  if (cudaFuncSetAttribute(tc_gemm_kcat_kernel<TC_BF16, KPS, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           C::SMEM) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL * std::max(1, ctx->sm_count / CL), 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = ctx->stream;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kcat_kernel<TC_BF16, KPS, CL>, &cfg) == cudaSuccess) v = n;
+  }
+  cudaGetLastError();
+  cached = v;
+  return v;
+}
+static int kcat_clusters(kp_ctx* ctx, int kps, int cl) {
+  if (cl == 4) return kps == 4 ? kcat_max_clusters<4, 4>(ctx) : (kps == 2 ? kcat_max_clusters<2, 4>(ctx) : kcat_max_clusters<1, 4>(ctx));
+  return kps == 4 ? kcat_max_clusters<4, 1>(ctx) : (kps == 2 ? kcat_max_clusters<2, 1>(ctx) : kcat_max_clusters<1, 1>(ctx));
+}
+
 static kp_status tc_plan_create_one(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, TcGemmPlan** out) {
   if (g.npairs < 1 || g.npairs > KP_MAX_PAIRS || g.nkron < 1) {
     kp_set_error("tc_plan_create: bad term description");
@@ -1294,14 +1708,32 @@ static kp_status tc_plan_create_one(kp_ctx* ctx, const GemmDesc& g, int kind, in
   // (plans of a batched solve run in grouped launches: one-CTA tiles, no K split)
   const bool pair = pair_ok && !ctx->tc_grouping && ctx->tc_pair_override != 1 &&
                     (ctx->tc_pair_override == 2 || (ctx->tc_bn_override == 0 && 4 * pair_tiles >= 3 * (sms / 2)));
+  // a K-concatenated product on 128 x 64 tiles (clusters of g.kcat CTAs along
+  // N) where those tiles fill most SMs (option tc_kcat 2: wherever the shape
+  // allows)
+  const int kc_kps = (ctx->tc_kps_override == 1 || ctx->tc_kps_override == 2) ? ctx->tc_kps_override : 4;
+  const int kc_cl = g.kcat == 4 ? 4 : 1;
+  int kc_maxc = 0;
+  bool kcat = false;
+  if (g.kcat && kind == TC_BF16 && splits <= 1 && g.batch_rows == 0 && !ctx->tc_grouping &&
+      (kc_cl == 1 || g.N % (KC_BN * kc_cl) == 0)) {
+    const int kc_tiles = tm * ((g.N + KC_BN - 1) / KC_BN);
+    kc_maxc = kcat_clusters(ctx, kc_kps, kc_cl);
+    kcat = kc_maxc > 0 && (ctx->tc_kcat == 2 || 4 * kc_tiles >= 3 * sms);
+  }
   TcGemmPlan* pl = new TcGemmPlan();
-  pl->pair = pair;
-  if (pair) {
+  pl->pair = pair && !kcat;
+  pl->kcat = kcat ? kc_cl : 0;
+  if (kcat) {
+    splits = 1;
+    bn = KC_BN;
+    cps = 1;
+  } else if (pair) {
     splits = 1;
     bn = PAIR_N;
   }
-  kp_status st = make_map(&pl->mapA, g.A, kind, TBM);
-  if (st == KP_OK) st = make_map(&pl->mapB, g.B, kind, pair ? PAIR_N / 2 : bn);
+  kp_status st = make_map(&pl->mapA, g.A, kind, kcat ? TBM / kc_cl : TBM);
+  if (st == KP_OK) st = make_map(&pl->mapB, g.B, kind, pl->pair ? PAIR_N / 2 : bn);
   if (st != KP_OK) {
     delete pl;
     return st;
@@ -1322,13 +1754,18 @@ static kp_status tc_plan_create_one(kp_ctx* ctx, const GemmDesc& g, int kind, in
   p.kblocks = (g.K + bk - 1) / bk;
   p.batch_rows = g.batch_rows;
   p.steps_total = g.npairs * (g.batch_rows > 0 ? 1 : g.nkron) * p.kblocks;
-  p.tiles_m = pair ? (g.M + PAIR_M - 1) / PAIR_M : (g.M + TBM - 1) / TBM;
+  p.tiles_m = pl->pair ? (g.M + PAIR_M - 1) / PAIR_M : (g.M + TBM - 1) / TBM;
   p.tiles_n = (g.N + bn - 1) / bn;
   const int tiles = p.tiles_m * p.tiles_n;
   splits = std::min(splits, p.steps_total);
   p.splits = splits;
-  p.units = tiles * splits;
-  p.idesc = make_idesc(kind, bn, pair ? PAIR_M : TBM);
+  p.units = kcat ? tiles / kc_cl : tiles * splits;  // K-concatenated: one unit per cluster's tiles
+  p.idesc = make_idesc(kind, bn, pl->pair ? PAIR_M : TBM);
+  p.dot_out = nullptr;
+  p.dot_part = nullptr;
+  p.dot_count = nullptr;
+  p.dot_po = PostOp();
+  p.dot_qmax = 0;
   p.epi = g.epi;
   if (p.epi.ld_aux == 0) p.epi.ld_aux = p.epi.ldd;
   p.ws = ctx->w_split;
@@ -1360,9 +1797,13 @@ static kp_status tc_plan_create_one(kp_ctx* ctx, const GemmDesc& g, int kind, in
       (ctx->tc_kps_override == 4 && bn == 64))
     pl->kps = ctx->tc_kps_override;
   pl->grid = dim3(std::min(p.units, ctx->sm_count * cps), 1, 1);
-  if (pair) {
+  if (pl->pair) {
     pl->kps = (ctx->tc_kps_override == 1) ? 1 : 2;
     pl->grid = dim3(2 * std::min(p.units, ctx->sm_count / 2), 1, 1);
+  }
+  if (kcat) {
+    pl->kps = kc_kps;
+    pl->grid = dim3(kc_cl * std::min(p.units, kc_maxc), 1, 1);
   }
   ctx->tc_plans.push_back(pl);
   *out = pl;
@@ -1526,7 +1967,7 @@ void plan_discard(kp_ctx* ctx, TcGemmPlan* pl) {
 }  // namespace
 
 kp_status tc_plan_create(kp_ctx* ctx, const GemmDesc& g, int kind, int splits, TcGemmPlan** out) {
-  if (!ctx->tc_autotune) return tc_plan_create_one(ctx, g, kind, splits, out);
+  if (!ctx->tc_autotune || g.kcat) return tc_plan_create_one(ctx, g, kind, splits, out);
   const std::string key = tune_key(g, kind, splits, ctx->sm_count);
   TuneCfg best{0, 0, 0, 0};
   bool have = false;
@@ -1641,6 +2082,21 @@ static kp_status launch_pair(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
   return KP_OK;
 }
 
+template <int KIND, int KPS, int CL>
+static kp_status launch_kcat(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
+  using C = KcCfg<KPS, CL>;
+  static std::atomic<bool> attr_set{false};
+  if (!attr_set.load()) {
+    KP_CUDA(cudaFuncSetAttribute(tc_gemm_kcat_kernel<KIND, KPS, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 C::SMEM));
+    attr_set = true;
+  }
+  KP_CUDA(kp_launch(ctx, tc_gemm_kcat_kernel<KIND, KPS, CL>, pl->grid, dim3(TC_THREADS), C::SMEM, pl->mapA, pl->mapB,
+                    p));
+  KP_LAUNCHED(ctx);
+  return KP_OK;
+}
+
 // recorded launches of a batched solve (see KpRec): the records of one
 // kernel configuration at one position become one tc_gemm_group_kernel launch
 template <int KIND, int BN, int CPS, int KPS>
@@ -1704,8 +2160,8 @@ struct GemmGroup {
 
 template <int KIND>
 static kp_status record_cfg(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
-  if (pl->pair || p.splits != 1) {
-    kp_set_error("batched solve: a CTA-pair or split-K GEMM plan cannot be grouped");
+  if (pl->pair || pl->kcat || p.splits != 1) {
+    kp_set_error("batched solve: a CTA-pair, K-concatenated or split-K GEMM plan cannot be grouped");
     return KP_ENOTSUP;
   }
   if (pl->bn == 256) {
@@ -1728,6 +2184,19 @@ static kp_status record_cfg(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
 template <int KIND>
 static kp_status launch_cfg(kp_ctx* ctx, TcGemmPlan* pl, const TcParams& p) {
   if (ctx->rec) return record_cfg<KIND>(ctx, pl, p);
+  if (pl->kcat) {
+    if constexpr (KIND == TC_BF16) {
+      if (pl->kcat == 4) {
+        if (pl->kps == 4) return launch_kcat<KIND, 4, 4>(ctx, pl, p);
+        return pl->kps == 2 ? launch_kcat<KIND, 2, 4>(ctx, pl, p) : launch_kcat<KIND, 1, 4>(ctx, pl, p);
+      }
+      if (pl->kps == 4) return launch_kcat<KIND, 4, 1>(ctx, pl, p);
+      return pl->kps == 2 ? launch_kcat<KIND, 2, 1>(ctx, pl, p) : launch_kcat<KIND, 1, 1>(ctx, pl, p);
+    } else {
+      kp_set_error("tensor-core GEMM: K-concatenated products are built for BF16 only");
+      return KP_ENOTSUP;
+    }
+  }
   if (pl->pair) {
     if constexpr (KIND == TC_BF16) {
       return pl->kps == 1 ? launch_pair<KIND, 1>(ctx, pl, p) : launch_pair<KIND, 2>(ctx, pl, p);
@@ -1759,6 +2228,31 @@ kp_status tc_plan_run(kp_ctx* ctx, TcGemmPlan* pl, const EpiParams* epi_override
   else
     st = launch_cfg<TC_E4M3>(ctx, pl, p);
   KP_TRY(st);
+  KP_CUDA(cudaGetLastError());
+  return KP_OK;
+}
+
+bool tc_plan_is_kcat(const TcGemmPlan* plan) { return plan && plan->kcat > 0; }
+
+void tc_plan_release(kp_ctx* ctx, TcGemmPlan* plan) {
+  if (plan) plan_discard(ctx, plan);
+}
+
+kp_status tc_plan_run_dot(kp_ctx* ctx, TcGemmPlan* pl, const EpiParams& epi, double* out2, double* partials,
+                          unsigned int* counter, const PostOp& post, int qmax) {
+  if (!pl->kcat || epi.mode != EPI_F32 || !epi.aux || !out2 || !partials || !counter) {
+    kp_set_error("tc_plan_run_dot: needs a K-concatenated plan, an FP32 output with aux and the reduction buffers");
+    return KP_EINVAL;
+  }
+  TcParams p = pl->params;
+  p.epi = epi;
+  if (p.epi.ld_aux == 0) p.epi.ld_aux = p.epi.ldd;
+  p.dot_out = out2;
+  p.dot_part = partials;
+  p.dot_count = counter;
+  p.dot_po = post;
+  p.dot_qmax = qmax;
+  KP_TRY(launch_cfg<TC_BF16>(ctx, pl, p));
   KP_CUDA(cudaGetLastError());
   return KP_OK;
 }

@@ -117,6 +117,12 @@ struct GemmDesc {
   // (k + 1) * batch_rows) are the product with term k alone (M = nkron *
   // batch_rows); the caller sums the per-term outputs
   int batch_rows = 0;
+  // > 0: one product summed over all k-blocks on 128 x 64 tiles
+  // (tc_gemm_kcat_kernel), in clusters of this many CTAs (1 or 4; 4: the A
+  // tile shared by multicast), where the shape allows it (BF16, no K split,
+  // not batched, whole clusters of tiles along N); otherwise the plan falls
+  // back to the usual choice
+  int kcat = 0;
 };
 
 // ---------------------------------------------------------------- context
@@ -166,6 +172,8 @@ struct kp_ctx {
   int tc_cps_override = 0;  // 1 / 2: fixed CTAs per SM for 128-wide tiles
   int tc_kps_override = 0;  // 1 / 2: fixed k-blocks per ring stage
   int tc_pair_override = 0;  // 1: no CTA-pair tiles; 2: CTA-pair tiles wherever the shape allows
+  int tc_kcat = 0;  // G2 / G4 of the inner operator as one K-concatenated GEMM: 0 never, 1 where its tiles fill most SMs, 2 wherever the shape allows
+  int tc_kcat_cluster = 1;  // CTAs per cluster of those GEMMs: 1, or 4 (A tiles shared by multicast)
   bool tc_autotune = false;  // pick each GEMM shape's tile configuration by timing (cached)
 
   // device allocations: ctx_block lives with the context, allocs with the
@@ -374,3 +382,8 @@ kp_status kp_check_ready(kp_ctx* ctx);
 kp_status kp_enter(kp_ctx* ctx);   // order the work stream after the caller's stream
 kp_status kp_leave(kp_ctx* ctx);   // order the caller's stream after the work stream
 void tc_plan_set_runtime(TcGemmPlan* plan, const float* alpha_dev, const int* flags);
+// whether the plan is a K-concatenated product (tc_gemm_kcat_kernel, which
+// can fuse the output's dot reduction into its epilogue: tc_plan_run_dot in
+// kp_vec.cuh)
+bool tc_plan_is_kcat(const TcGemmPlan* plan);
+void tc_plan_release(kp_ctx* ctx, TcGemmPlan* plan);  // free a plan before the context does

@@ -303,6 +303,19 @@ static kp_status op_plan(kp_ctx* ctx, OpsState* os, int mode, int w, TcGemmPlan*
   const void* bptr = w == 0 ? (mode == OP_INNER ? ctx->w_img2 : ctx->w_img3) : (w == 2 ? ctx->w_img : nullptr);
   const int t = terms > 0 ? terms : ctx->rank;
   GemmDesc g = op_desc(ctx, w, mode, bptr, t);
+  if ((w == 1 || w == 3) && mode == OP_INNER && ctx->tc_kcat && ctx->splitk_override == 0) {
+    // the sum over terms as one product (terms summed in the accumulator, no
+    // per-term outputs, no term sum), where its tiles fit
+    GemmDesc gk = g;
+    gk.kcat = ctx->tc_kcat_cluster;
+    TcGemmPlan* pl = nullptr;
+    KP_TRY(tc_plan_create(ctx, gk, TC_BF16, 1, &pl));
+    if (tc_plan_is_kcat(pl)) {
+      *out = pl;
+      return KP_OK;
+    }
+    tc_plan_release(ctx, pl);
+  }
   int splits = (w == 1 || w == 3) ? square_splits(ctx) : 1;
   if ((w == 1 || w == 3) && os->batched) {
     g.batch_rows = ctx->n_c;
@@ -428,6 +441,13 @@ static kp_status run_op(kp_ctx* ctx, int which, int mode, const void* bptr, cons
       return KP_ESTATE;
     }
     tc_plan_set_runtime(pl, nullptr, flags);
+    if (tc_plan_is_kcat(pl)) {  // the terms summed in the accumulator; the dot in the epilogue
+      if (td && e.mode == EPI_F32 && e.aux) {
+        if (dot_done) *dot_done = true;
+        return tc_plan_run_dot(ctx, pl, e, td->out, td->partials, td->counter, td->po, td->qmax);
+      }
+      return tc_plan_run(ctx, pl, &e);
+    }
     if (!(os->batched && (which == 1 || which == 3))) return tc_plan_run(ctx, pl, &e);
     // per-term FP32 outputs into the split workspace, then the term sum
     EpiParams ez;

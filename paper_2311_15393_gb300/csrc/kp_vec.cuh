@@ -54,6 +54,13 @@ struct PostOp {
   int hist_cap = 0;
 };
 
+// a K-concatenated GEMM plan (tc_plan_is_kcat) whose epilogue also reduces
+// sum(out * aux) as a double-float pair into out2[0] (and max |out| into
+// out2[1] when qmax), finished by the last CTA, which runs `post` on them;
+// epi must be EPI_F32 with aux
+kp_status tc_plan_run_dot(kp_ctx* ctx, TcGemmPlan* plan, const EpiParams& epi, double* out2, double* partials,
+                          unsigned int* counter, const PostOp& post, int qmax);
+
 int vec_grid(kp_ctx* ctx, long long n);
 kp_status dot2_dev(kp_ctx* ctx, const void* a, const void* b, const void* c, long long n, bool f64, double* out,
                    const int* flags, PostOp post = PostOp());
