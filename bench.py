@@ -281,6 +281,18 @@ def oracle_sample(P, iters_per_solve, k=3):
     return {"step_s": step, "sample_s": t4 - t0, "t_setup": t_setup, "t_lambda": t_lam, "t_iter": t_it}
 
 
+def oracle_sample_1thread(n, iters_per_solve, k):
+    """oracle_sample with the BLAS pinned to one thread: run in a child
+    process, since the thread count of numpy's BLAS is fixed when it loads."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench.oracle_sample(bench.make_inputs({n!r}, 0), {iters_per_solve}, {k})))")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def blas_threads():
     for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(k):
@@ -638,6 +650,14 @@ def run_ours(args, ws, rank, local, dist):
                                   "sample": f"FP64 oracle setup + GCV lambda (one noise level) + {k_cpu} FPCG "
                                             f"iterations ({smp['sample_s']:.1f} s measured), extrapolated to setup "
                                             f"+ 2 x lambda + the step's {iters} iterations"}
+        k_one = 5
+        one = oracle_sample_1thread(args.n, max(iters), k_one)
+        if one is not None:
+            step1 = one["t_setup"] + sum(one["t_lambda"] + (it + 1) * one["t_iter"] for it in iters)
+            result["cpu_baseline"]["one_thread"] = {
+                "value": 2.0 / step1, "unit": "solves/s", "cores": 1,
+                "sample": f"the same with the BLAS on one thread: setup + GCV lambda + {k_one} FPCG iterations "
+                          f"({one['sample_s']:.1f} s measured), extrapolated the same way"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0
