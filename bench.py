@@ -167,6 +167,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ problem
+def synth_problem(name):
+    from paper_2311_15393_gb300 import synth
+    return synth.make_problem(name)
+
+
 def make_inputs(n, seed_offset):
     from paper_2311_15393_gb300 import synth
     P = synth.make_problem(WORKLOAD, n=n, seed=synth.SEED_BASE + synth.WORKLOAD_INDEX[WORKLOAD] + seed_offset)
@@ -574,6 +579,31 @@ def run_ours(args, ws, rank, local, dist):
                                  "preconditioner, FP64 vectors), one whole step measured with CUDA events"}
             ctx64.close()
 
+        # latency of the small full-rank FP64 problem (64 x 64, 64 Kronecker
+        # terms, zero BC, lambda 0.01): device time per FPCG iteration
+        lat = None
+        if not args.no_fp64_form:
+            P64 = synth_problem("deblur64_fp64")
+            c64 = kpsvd.KpContext(dev, stream=stream.cuda_stream)
+            c64.kp_setup(kpsvd.to_device(P64.psf, torch.float64, f"cuda:{dev}"), P64.n_r, P64.n_c, P64.center,
+                         P64.bc, P64.op_rank, "f64", "f64", "f64", "projected")
+            xt64 = kpsvd.to_device(P64.x_true, torch.float64, f"cuda:{dev}")
+            bb = torch.empty_like(xt64)
+            c64.kp_forward(xt64, kpsvd.to_device(P64.noise_dirs[0], torch.float64, f"cuda:{dev}"),
+                           P64.noise_levels[0], bb)
+            its, ms_sol = 0, 0.0
+            for rep in range(4):
+                xx = torch.zeros_like(bb)
+                inf = c64.tik_pcg(bb, P64.lam, 0.0, 50, True, xx, check=False)
+                if rep > 0:   # the first solve builds and captures the iteration graph
+                    its += inf.iters
+                    ms_sol += inf.ms_solve
+            lat = {"workload": "deblur64_fp64", "n": P64.n_r, "op_rank": P64.op_rank, "prec": "f64",
+                   "us_per_iteration": 1e3 * ms_sol / max(its, 1), "iterations_timed": its,
+                   "note": "FPCG at lambda 0.01 for 50 iterations, device time (CUDA events) per iteration, "
+                           "including the solve's start and end"}
+            c64.close()
+
         if args.fp64_form:
             ctx64 = kpsvd.KpContext(dev, stream=stream.cuda_stream)
             psf64 = psf
@@ -639,6 +669,8 @@ def run_ours(args, ws, rank, local, dist):
     }
     if fp64_form:
         result["fp64_form"] = fp64_form
+    if lat:
+        result["latency_small_fp64"] = lat
     ctx.close()
     if rank == 0 and not args.no_cpu_baseline:
         iters = [inf.iters for _, inf in last]
