@@ -128,6 +128,8 @@ void kp_free_all(kp_ctx* ctx) {
   ctx->lam_img16 = ctx->lam_t16 = nullptr;
   ctx->lam_t32 = ctx->lam_o32 = nullptr;
   ctx->lam_ws = nullptr;
+  ctx->simt_ws = nullptr;
+  ctx->simt_ws_bytes = 0;
   ctx->lam_sigma_ready = false;
   ctx->Uc32 = ctx->Ur32 = ctx->Vc32 = ctx->Vr32 = nullptr;
   ctx->ready = false;

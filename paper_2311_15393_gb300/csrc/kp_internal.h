@@ -251,6 +251,10 @@ struct kp_ctx {
   int hist_cap = 0;
   float* w_split = nullptr;  // split-K partials
   long long w_split_elems = 0;
+  // SIMT GEMMs with fewer output tiles than SMs split their (pair, term,
+  // k-tile) steps over blocks; partial tiles go here (null: no split)
+  void* simt_ws = nullptr;
+  size_t simt_ws_bytes = 0;
   void* pc_in = nullptr;     // quantised residual R
   void* pc_t1 = nullptr;     // P1 out
   void* pc_t2 = nullptr;     // P2 out

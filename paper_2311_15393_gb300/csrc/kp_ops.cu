@@ -392,6 +392,12 @@ kp_status ops_prepare(kp_ctx* ctx) {
   const long long nmax = std::max(n_r, n_c);
   ctx->w_split_elems = 8 * nmax * nmax;
   KP_TRY(kp_alloc(ctx, (void**)&ctx->w_split, sizeof(float) * ctx->w_split_elems));
+  // partial tiles of SIMT GEMMs split over blocks (small problems on the FP64
+  // / FP32 operator or preconditioner): up to 4 x the stacked intermediate
+  if ((!op_is_tc(ctx) || !pc_is_tc(ctx)) && (long long)((n_c + 63) / 64) * ((n_r + 63) / 64) < ctx->sm_count) {
+    ctx->simt_ws_bytes = vs * 4 * (size_t)std::max(r, 1) * (size_t)N;
+    KP_TRY(kp_alloc(ctx, &ctx->simt_ws, ctx->simt_ws_bytes));
+  }
 
   if (op_is_tc(ctx)) {
     // G2 / G4 as one GEMM over the stacked per-term products (4x the tiles
