@@ -331,6 +331,16 @@ kp_status kp_get_rank(kp_ctx* ctx, int* op_rank);
  *                     vec_prec is KP_F32 (Gram convergence test at FP32
  *                     tolerance), which moves the chosen lambda by ~2.5e-7
  *                     relative at 1024^2; FP64 vectors always use FP64.
+ *                     Takes effect at the next kp_setup.
+ *   "setup_half"      nonzero: with the FP32 setup on the tensor cores (FP32
+ *                     vectors, n_r and n_c multiples of 16, "setup_fp64"
+ *                     off), the products that form V_r, V_c and Sigma (the
+ *                     DCT / DST transform of each factor before its Jacobi
+ *                     SVD, the projected spectrum) take bf16 inputs with FP32
+ *                     accumulation instead of the FP32-level three-slice
+ *                     split (Section 3, after eq. PreconSolve: the
+ *                     preconditioner computed, not only stored, in half
+ *                     precision); the Jacobi rotations stay FP32.  Default 0.
  *                     Takes effect at the next kp_setup. */
 kp_status kp_set_option(kp_ctx* ctx, const char* name, double value);
 
